@@ -1,0 +1,229 @@
+"""FP64 CPU oracle for the OSOG forward model (arxiv 2606.21381).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product package
+never imports this module, and this module imports nothing from the product.
+
+The arithmetic lives in ``osog_oracle.c`` (plain C, double precision, one
+definition per step, see that file's header for the equations it follows).
+This module compiles it with gcc, loads it with ctypes and exposes numpy-level
+wrappers.  Optics are passed as plain dicts with the keys of ``OPTICS_KEYS``.
+
+Parity pins (closed forms, brute force, library special cases) live in
+``tests/test_oracle_pins.py``.  Every oracle function is pinned there except
+the bevel constant of the prism chamfers, whose value the paper does not give
+(parity unpinned: the chamfer slope is a definition of this project, shared
+by both sides only as a written formula).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "osog_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MODE_BF, MODE_OBLIQUE, MODE_DIC = 1, 2, 4
+
+OPTICS_KEYS = ("H", "W", "dx", "lambda_um", "NA", "n_medium", "defocus",
+               "modes", "oblique_frac", "oblique_angle", "shear_px",
+               "shear_angle", "bias_phase", "bevel_slope")
+
+DEFAULT_OPTICS = dict(dx=0.5, lambda_um=0.55, NA=0.4, n_medium=1.0, defocus=0.0,
+                      modes=MODE_BF, oblique_frac=0.3, oblique_angle=0.0,
+                      shear_px=1.0, shear_angle=np.pi / 4, bias_phase=np.pi / 4,
+                      bevel_slope=1.0)
+
+
+class _Optics(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("NA", ctypes.c_double), ("n_medium", ctypes.c_double),
+                ("defocus", ctypes.c_double), ("modes", ctypes.c_uint32),
+                ("oblique_frac", ctypes.c_double), ("oblique_angle", ctypes.c_double),
+                ("shear_px", ctypes.c_double), ("shear_angle", ctypes.c_double),
+                ("bias_phase", ctypes.c_double), ("bevel_slope", ctypes.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so next to its source (gcc, -O2, OpenMP)."""
+    with _lock:
+        if (not force and os.path.exists(_LIB)
+                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            return _LIB
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared",
+                               "-std=c11", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        d, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        lib.orc_halfspace_chord.restype = ctypes.c_double
+        lib.orc_halfspace_chord.argtypes = [d, d, i32, ctypes.c_double, ctypes.c_double]
+        lib.orc_prism_halfspaces.argtypes = [ctypes.c_double] * 4 + [d, d]
+        lib.orc_opd_att.argtypes = [d, i64, i32, i32, i32, ctypes.c_double,
+                                    ctypes.c_double, i32, d, d]
+        lib.orc_opd_at.argtypes = [d, i64, i32, ctypes.c_double, ctypes.c_double,
+                                   d, i64, i32, d, d]
+        lib.orc_field.argtypes = [d, d, i64, ctypes.c_double, d, d]
+        lib.orc_fft2.argtypes = [d, d, i32, i32, i32]
+        lib.orc_dft2_brute.argtypes = [d, d, i32, i32, i32, d, d]
+        lib.orc_transfer.argtypes = [ctypes.POINTER(_Optics), i32, d, d]
+        lib.orc_images.argtypes = [ctypes.POINTER(_Optics), d, d, d]
+        lib.orc_render.argtypes = [d, i64, i32, ctypes.POINTER(_Optics), d, d, d, d, d]
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_optics(H: int, W: int, **kw) -> dict:
+    o = dict(DEFAULT_OPTICS)
+    o.update(kw)
+    o["H"], o["W"] = int(H), int(W)
+    unknown = set(o) - set(OPTICS_KEYS)
+    if unknown:
+        raise KeyError(f"unknown optics keys {sorted(unknown)}")
+    return o
+
+
+def _optics_struct(o: dict) -> _Optics:
+    s = _Optics()
+    s.H, s.W = int(o["H"]), int(o["W"])
+    s.dx, s.lambda_, s.NA = o["dx"], o["lambda_um"], o["NA"]
+    s.n_medium, s.defocus, s.modes = o["n_medium"], o["defocus"], int(o["modes"])
+    s.oblique_frac, s.oblique_angle = o["oblique_frac"], o["oblique_angle"]
+    s.shear_px, s.shear_angle = o["shear_px"], o["shear_angle"]
+    s.bias_phase, s.bevel_slope = o["bias_phase"], o["bevel_slope"]
+    return s
+
+
+def n_modes(o: dict) -> int:
+    return bin(int(o["modes"]) & 7).count("1")
+
+
+def _soa(soa: np.ndarray):
+    soa = np.ascontiguousarray(soa, dtype=np.float32)
+    if soa.ndim != 2 or soa.shape[0] != 9:
+        raise ValueError("soa must be a (9, ld) float32 array")
+    return soa, soa.shape[1]
+
+
+# ---------------------------------------------------------------- geometry
+def prism_halfspaces(hx_um: float, hy_um: float, T: float, slope: float):
+    """(A, b) of the bevelled prism's 14 half-spaces (Eq. 1)."""
+    A = np.zeros((14, 3))
+    b = np.zeros(14)
+    _load().orc_prism_halfspaces(hx_um, hy_um, T, slope, _p(A), _p(b))
+    return A, b
+
+
+def halfspace_chord(A: np.ndarray, b: np.ndarray, u: float, v: float) -> float:
+    """Vertical chord through (u, v) of the polyhedron {x: A x <= b}."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    return _load().orc_halfspace_chord(_p(A), _p(b), len(b), float(u), float(v))
+
+
+def opd_att(soa: np.ndarray, n: int, H: int, W: int, dx: float = 0.5,
+            bevel_slope: float = 1.0, full_canvas: bool = False):
+    """OPD (um) and absorption-thickness maps, each (H, W) float64."""
+    soa, ld = _soa(soa)
+    opd = np.zeros((H, W))
+    att = np.zeros((H, W))
+    _load().orc_opd_att(_p(soa), ld, int(n), H, W, dx, bevel_slope,
+                        int(full_canvas), _p(opd), _p(att))
+    return opd, att
+
+
+def opd_at(soa: np.ndarray, n: int, W: int, pixels: np.ndarray, dx: float = 0.5,
+           bevel_slope: float = 1.0):
+    """OPD and ATT at flat pixel indices, by brute force over all particles."""
+    soa, ld = _soa(soa)
+    pix = np.ascontiguousarray(pixels, dtype=np.int64)
+    opd = np.zeros(len(pix))
+    att = np.zeros(len(pix))
+    _load().orc_opd_at(_p(soa), ld, int(n), dx, bevel_slope, _p(pix), len(pix),
+                       W, _p(opd), _p(att))
+    return opd, att
+
+
+def field(opd: np.ndarray, att: np.ndarray, lambda_um: float) -> np.ndarray:
+    """Exit wave exp(-att) exp(i 2 pi opd / lambda) as complex128."""
+    opd = np.ascontiguousarray(opd, dtype=np.float64)
+    att = np.ascontiguousarray(att, dtype=np.float64)
+    re = np.empty_like(opd)
+    im = np.empty_like(opd)
+    _load().orc_field(_p(opd), _p(att), opd.size, lambda_um, _p(re), _p(im))
+    return re + 1j * im
+
+
+# ---------------------------------------------------------------- Fourier
+def fft2(x: np.ndarray, sign: int = -1) -> np.ndarray:
+    """The oracle's own radix-2 2-D FFT (unnormalised)."""
+    re = np.ascontiguousarray(x.real, dtype=np.float64).copy()
+    im = np.ascontiguousarray(x.imag, dtype=np.float64).copy()
+    H, W = re.shape
+    _load().orc_fft2(_p(re), _p(im), H, W, int(sign))
+    return re + 1j * im
+
+
+def dft2_brute(x: np.ndarray, sign: int = -1) -> np.ndarray:
+    """O((HW)^2) DFT straight from the definition."""
+    re = np.ascontiguousarray(x.real, dtype=np.float64)
+    im = np.ascontiguousarray(x.imag, dtype=np.float64)
+    H, W = re.shape
+    ore = np.empty_like(re)
+    oim = np.empty_like(re)
+    _load().orc_dft2_brute(_p(re), _p(im), H, W, int(sign), _p(ore), _p(oim))
+    return ore + 1j * oim
+
+
+# ---------------------------------------------------------------- optics
+def transfer(o: dict, mode: int) -> np.ndarray:
+    """H_m(k) on the (H, W) DFT grid as complex128."""
+    s = _optics_struct(o)
+    hr = np.empty((o["H"], o["W"]))
+    hi = np.empty_like(hr)
+    _load().orc_transfer(ctypes.byref(s), int(mode), _p(hr), _p(hi))
+    return hr + 1j * hi
+
+
+def images_from_field(o: dict, E: np.ndarray) -> np.ndarray:
+    """(K, H, W) intensities of every selected modality for exit wave E."""
+    s = _optics_struct(o)
+    re = np.ascontiguousarray(E.real, dtype=np.float64)
+    im = np.ascontiguousarray(E.imag, dtype=np.float64)
+    out = np.empty((n_modes(o), o["H"], o["W"]))
+    _load().orc_images(ctypes.byref(s), _p(re), _p(im), _p(out))
+    return out
+
+
+def render(soa: np.ndarray, n: int, o: dict) -> dict:
+    """Whole forward model: returns dict(opd, att, field, images)."""
+    soa, ld = _soa(soa)
+    s = _optics_struct(o)
+    H, W = o["H"], o["W"]
+    opd = np.empty((H, W))
+    att = np.empty_like(opd)
+    er = np.empty_like(opd)
+    ei = np.empty_like(opd)
+    img = np.empty((n_modes(o), H, W))
+    _load().orc_render(_p(soa), ld, int(n), ctypes.byref(s), _p(opd), _p(att),
+                       _p(er), _p(ei), _p(img))
+    return dict(opd=opd, att=att, field=er + 1j * ei, images=img)

@@ -1,0 +1,394 @@
+/*
+ * FP64 CPU oracle for the OSOG optical forward model (arxiv 2606.21381).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links or calls
+ * this file; only the tests, __graft_entry__.smoke() and bench.py's CPU
+ * baseline leg use it.  It shares no code, header, table or constant with
+ * the CUDA path: every quantity here is computed from its plain definition
+ * in double precision, slowly and in the paper's order.
+ *
+ * What it computes (paper sections / equations):
+ *   - particle geometry: ellipsoids (quadric chord) and bevelled rectangular
+ *     prisms as an intersection of M = 14 half-spaces, P = {x : A x <= b}
+ *     (Sec. III.A, Eq. 1);
+ *   - OPD and absorption maps: sum over particles of dn_p * t_p and
+ *     mu_p * t_p, overlaps add (Eq. 2's integral over z; Eq. 7's
+ *     accumulate=True composition, Sec. III.C);
+ *   - exit wave E = exp(-ATT) * exp(i 2 pi OPD / lambda) (Eq. 2, Beer-Lambert
+ *     amplitude of Eq. 4);
+ *   - pupil P(k) = circ(|k|/k_NA) exp(i dz (sqrt(k0^2 - |k|^2) - k0)) (Eq. 3)
+ *     and the coherent image I = |E * h_obj|^2 (Sec. III.B, brightfield);
+ *     oblique illumination as the pupil shifted by k_ill (Fig. 2 discussion:
+ *     "asymmetric Fourier pupil"); DIC as the sheared-field difference of
+ *     Eq. 5 taken coherently through the pupil;
+ *   - an own radix-2 FFT and a brute-force DFT (used to pin the FFT).
+ *
+ * Conventions (readings of points the paper leaves open):
+ *   - pixel (i, j) is sampled at its centre (x, y) = (j + 0.5, i + 0.5) px;
+ *   - local frame u = c (x - cx) + s (y - cy), v = -s (x - cx) + c (y - cy);
+ *   - ellipsoid: in-plane semi-axes a, b (px), full central thickness T (um);
+ *   - prism: half-lengths hx, hy (px), thickness T (um), chamfer planes of
+ *     slope s_b on all top and bottom edges meeting at zero wall height;
+ *   - forward DFT kernel exp(-2 pi i jk/N); inverse unnormalised, the
+ *     image carries 1/(H W);
+ *   - k grid 2 pi * fftfreq(N, dx); k0 = 2 pi n_m / lambda.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* Field order of the structure-of-arrays particle tensor, row by row. */
+enum { F_CX = 0, F_CY, F_TH, F_A, F_B, F_T, F_DN, F_MU, F_KIND, F_COUNT };
+
+typedef struct {
+    int32_t H, W;
+    double dx;            /* pixel pitch, um */
+    double lambda;        /* wavelength, um */
+    double NA;
+    double n_medium;
+    double defocus;       /* dz, um */
+    uint32_t modes;       /* bit 0 brightfield, bit 1 oblique, bit 2 DIC */
+    double oblique_frac;  /* |k_ill| = frac * k_NA */
+    double oblique_angle; /* direction of k_ill, rad */
+    double shear_px;      /* 2 |ds| in px */
+    double shear_angle;   /* direction of ds, rad */
+    double bias_phase;    /* theta of Eq. 5 */
+    double bevel_slope;   /* s_b of the prism chamfers */
+} orc_optics;
+
+/* ------------------------------------------------------------------ */
+/* Geometry                                                            */
+/* ------------------------------------------------------------------ */
+
+/* Chord length (um) of the vertical line through local point (u, v) (um)
+ * inside the convex polyhedron {x : A x <= b}: the z-interval bounded by
+ * every half-space, Eq. 1.  A is m x 3 row-major. */
+double orc_halfspace_chord(const double *A, const double *b, int m,
+                           double u, double v)
+{
+    double zlo = -INFINITY, zhi = INFINITY;
+    for (int i = 0; i < m; ++i) {
+        double ax = A[3 * i], ay = A[3 * i + 1], az = A[3 * i + 2];
+        double rhs = b[i] - ax * u - ay * v;
+        if (az > 0.0) {
+            double z = rhs / az;
+            if (z < zhi) zhi = z;
+        } else if (az < 0.0) {
+            double z = rhs / az;
+            if (z > zlo) zlo = z;
+        } else if (rhs < 0.0) {
+            return 0.0;
+        }
+    }
+    return zhi > zlo ? zhi - zlo : 0.0;
+}
+
+/* The 14 half-spaces of a bevelled rectangular prism in its local frame
+ * (um): top and bottom faces, four side walls, and eight chamfers of slope
+ * s on the top and bottom edges.  Writes A (14 x 3) and b (14). */
+void orc_prism_halfspaces(double hx_um, double hy_um, double T, double s,
+                          double *A, double *b)
+{
+    const double h = 0.5 * T;
+    double rows[14][4] = {
+        { 0, 0, 1, h},  { 0, 0, -1, h},
+        { 1, 0, 0, hx_um}, {-1, 0, 0, hx_um},
+        { 0, 1, 0, hy_um}, { 0, -1, 0, hy_um},
+        { s, 0, 1, s * hx_um}, {-s, 0, 1, s * hx_um},
+        { 0, s, 1, s * hy_um}, { 0, -s, 1, s * hy_um},
+        { s, 0, -1, s * hx_um}, {-s, 0, -1, s * hx_um},
+        { 0, s, -1, s * hy_um}, { 0, -s, -1, s * hy_um},
+    };
+    for (int i = 0; i < 14; ++i) {
+        A[3 * i] = rows[i][0];
+        A[3 * i + 1] = rows[i][1];
+        A[3 * i + 2] = rows[i][2];
+        b[i] = rows[i][3];
+    }
+}
+
+/* Thickness t (um) of particle p (fields widened from fp32) at the canvas
+ * point (x, y) px. */
+static double particle_thickness(const double *q, double dx, double bevel,
+                                 double x, double y)
+{
+    double c = cos(q[F_TH]), s = sin(q[F_TH]);
+    double ex = x - q[F_CX], ey = y - q[F_CY];
+    double u = c * ex + s * ey;
+    double v = -s * ex + c * ey;
+    if (q[F_KIND] > 0.5) {
+        double A[42], b[14];
+        orc_prism_halfspaces(q[F_A] * dx, q[F_B] * dx, q[F_T], bevel, A, b);
+        return orc_halfspace_chord(A, b, 14, u * dx, v * dx);
+    }
+    double ua = u / q[F_A], vb = v / q[F_B];
+    double r = 1.0 - ua * ua - vb * vb;
+    return r > 0.0 ? q[F_T] * sqrt(r) : 0.0;
+}
+
+static void load_particle(const float *soa, int64_t ld, int p, double *q)
+{
+    for (int f = 0; f < F_COUNT; ++f) q[f] = (double)soa[(int64_t)f * ld + p];
+}
+
+/* OPD and absorption-thickness maps (H x W, row-major), Eq. 2 / Eq. 7:
+ * opd(x, y) = sum_p dn_p t_p(x, y), att(x, y) = sum_p mu_p t_p(x, y), with
+ * particles added in ascending index.  Each particle is evaluated on the
+ * pixels of its circumscribed square plus one pixel (t is zero outside it)
+ * unless full_canvas is set, in which case every pixel is evaluated. */
+void orc_opd_att(const float *soa, int64_t ld, int n, int H, int W,
+                 double dx, double bevel, int full_canvas,
+                 double *opd, double *att)
+{
+    memset(opd, 0, sizeof(double) * (size_t)H * W);
+    memset(att, 0, sizeof(double) * (size_t)H * W);
+    for (int p = 0; p < n; ++p) {
+        double q[F_COUNT];
+        load_particle(soa, ld, p, q);
+        int j0 = 0, j1 = W - 1, i0 = 0, i1 = H - 1;
+        if (!full_canvas) {
+            double R = q[F_KIND] > 0.5 ? sqrt(q[F_A] * q[F_A] + q[F_B] * q[F_B])
+                                       : fmax(q[F_A], q[F_B]);
+            double jl = floor(q[F_CX] - R - 1.5), jh = ceil(q[F_CX] + R + 0.5);
+            double il = floor(q[F_CY] - R - 1.5), ih = ceil(q[F_CY] + R + 0.5);
+            if (jh < 0 || ih < 0 || jl > W - 1 || il > H - 1) continue;
+            j0 = jl < 0 ? 0 : (int)jl;
+            j1 = jh > W - 1 ? W - 1 : (int)jh;
+            i0 = il < 0 ? 0 : (int)il;
+            i1 = ih > H - 1 ? H - 1 : (int)ih;
+        }
+        for (int i = i0; i <= i1; ++i)
+            for (int j = j0; j <= j1; ++j) {
+                double t = particle_thickness(q, dx, bevel, j + 0.5, i + 0.5);
+                if (t != 0.0) {
+                    opd[(size_t)i * W + j] += q[F_DN] * t;
+                    att[(size_t)i * W + j] += q[F_MU] * t;
+                }
+            }
+    }
+}
+
+/* OPD at a list of pixels by brute force over every particle (no window):
+ * an independent route to single samples of a large canvas. */
+void orc_opd_at(const float *soa, int64_t ld, int n, double dx, double bevel,
+                const int64_t *pix, int64_t npix, int W, double *opd,
+                double *att)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t k = 0; k < npix; ++k) {
+        int i = (int)(pix[k] / W), j = (int)(pix[k] % W);
+        double so = 0.0, sa = 0.0;
+        for (int p = 0; p < n; ++p) {
+            double q[F_COUNT];
+            load_particle(soa, ld, p, q);
+            double t = particle_thickness(q, dx, bevel, j + 0.5, i + 0.5);
+            so += q[F_DN] * t;
+            sa += q[F_MU] * t;
+        }
+        opd[k] = so;
+        att[k] = sa;
+    }
+}
+
+/* Exit wave, Eq. 2 with the Beer-Lambert amplitude of Eq. 4:
+ * E = exp(-att) * (cos, sin)(2 pi opd / lambda). */
+void orc_field(const double *opd, const double *att, int64_t count,
+               double lambda, double *re, double *im)
+{
+    for (int64_t k = 0; k < count; ++k) {
+        double a = exp(-att[k]);
+        double ph = 2.0 * M_PI * opd[k] / lambda;
+        re[k] = a * cos(ph);
+        im[k] = a * sin(ph);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Fourier transforms                                                  */
+/* ------------------------------------------------------------------ */
+
+/* In-place radix-2 decimation-in-time FFT of one line of n points (n a
+ * power of two) with stride 1: bit-reversal permutation, then log2(n)
+ * butterfly stages with twiddles exp(sign 2 pi i k / len).  Unnormalised. */
+static void fft_line(double *re, double *im, int n, int sign)
+{
+    for (int i = 1, j = 0; i < n; ++i) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            double t = re[i]; re[i] = re[j]; re[j] = t;
+            t = im[i]; im[i] = im[j]; im[j] = t;
+        }
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+        int half = len >> 1;
+        for (int k = 0; k < half; ++k) {
+            double ang = sign * 2.0 * M_PI * (double)k / (double)len;
+            double wr = cos(ang), wi = sin(ang);
+            for (int s = 0; s < n; s += len) {
+                int a = s + k, b = s + k + half;
+                double tr = re[b] * wr - im[b] * wi;
+                double ti = re[b] * wi + im[b] * wr;
+                re[b] = re[a] - tr; im[b] = im[a] - ti;
+                re[a] += tr;        im[a] += ti;
+            }
+        }
+    }
+}
+
+/* 2-D FFT of an H x W row-major array: every row, then every column.
+ * sign = -1 forward, +1 inverse; unnormalised. */
+void orc_fft2(double *re, double *im, int H, int W, int sign)
+{
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < H; ++i) fft_line(re + (size_t)i * W, im + (size_t)i * W, W, sign);
+#pragma omp parallel
+    {
+        double *cr = (double *)malloc(sizeof(double) * H);
+        double *ci = (double *)malloc(sizeof(double) * H);
+#pragma omp for schedule(static)
+        for (int j = 0; j < W; ++j) {
+            for (int i = 0; i < H; ++i) { cr[i] = re[(size_t)i * W + j]; ci[i] = im[(size_t)i * W + j]; }
+            fft_line(cr, ci, H, sign);
+            for (int i = 0; i < H; ++i) { re[(size_t)i * W + j] = cr[i]; im[(size_t)i * W + j] = ci[i]; }
+        }
+        free(cr);
+        free(ci);
+    }
+}
+
+/* Brute-force 2-D DFT straight from its definition, O((HW)^2):
+ * X[k, l] = sum_{i, j} x[i, j] exp(sign 2 pi i (k i / H + l j / W)). */
+void orc_dft2_brute(const double *re, const double *im, int H, int W, int sign,
+                    double *ore, double *oim)
+{
+    for (int k = 0; k < H; ++k)
+        for (int l = 0; l < W; ++l) {
+            double sr = 0.0, si = 0.0;
+            for (int i = 0; i < H; ++i)
+                for (int j = 0; j < W; ++j) {
+                    double ang = sign * 2.0 * M_PI *
+                                 ((double)((int64_t)k * i % H) / H + (double)((int64_t)l * j % W) / W);
+                    double c = cos(ang), s = sin(ang);
+                    double xr = re[(size_t)i * W + j], xi = im[(size_t)i * W + j];
+                    sr += xr * c - xi * s;
+                    si += xr * s + xi * c;
+                }
+            ore[(size_t)k * W + l] = sr;
+            oim[(size_t)k * W + l] = si;
+        }
+}
+
+/* ------------------------------------------------------------------ */
+/* Optical head                                                        */
+/* ------------------------------------------------------------------ */
+
+/* Angular spatial frequency of DFT index idx on an n-point grid of pitch
+ * dx: 2 pi * fftfreq(n, dx)[idx]. */
+static double kfreq(int idx, int n, double dx)
+{
+    int f = idx < n / 2 ? idx : idx - n;
+    return 2.0 * M_PI * (double)f / ((double)n * dx);
+}
+
+/* Pupil of Eq. 3 at angular frequency q: circ(|q| / k_NA) times the
+ * defocus phase exp(i dz (sqrt(k0^2 - |q|^2) - k0)); the constant -k0 only
+ * removes a global phase.  The circle is closed (|q| = k_NA is inside). */
+static void pupil(const orc_optics *o, double qx, double qy, double *pr, double *pi)
+{
+    double kna = 2.0 * M_PI * o->NA / o->lambda;
+    double k0 = 2.0 * M_PI * o->n_medium / o->lambda;
+    double q2 = qx * qx + qy * qy;
+    if (q2 > kna * kna) { *pr = 0.0; *pi = 0.0; return; }
+    double chi = o->defocus * (sqrt(k0 * k0 - q2) - k0);
+    *pr = cos(chi);
+    *pi = sin(chi);
+}
+
+/* Transfer function H_m(k) on the H x W DFT grid for one modality:
+ *   mode 1 brightfield:  P(k)
+ *   mode 2 oblique:      P(k + k_ill), k_ill = frac k_NA (cos phi, sin phi)
+ *   mode 4 DIC:          P(k) * 2i sin(k . ds + theta), ds = shear_px dx / 2
+ *                        along shear_angle (Fourier transform of
+ *                        U(r + ds) e^{i theta} - U(r - ds) e^{-i theta}). */
+void orc_transfer(const orc_optics *o, int mode, double *hre, double *him)
+{
+    int H = o->H, W = o->W;
+    double kna = 2.0 * M_PI * o->NA / o->lambda;
+    double offx = 0.0, offy = 0.0;
+    if (mode == 2) {
+        offx = o->oblique_frac * kna * cos(o->oblique_angle);
+        offy = o->oblique_frac * kna * sin(o->oblique_angle);
+    }
+    double dsx = 0.5 * o->shear_px * o->dx * cos(o->shear_angle);
+    double dsy = 0.5 * o->shear_px * o->dx * sin(o->shear_angle);
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j) {
+            double kx = kfreq(j, W, o->dx), ky = kfreq(i, H, o->dx);
+            double pr, pi;
+            pupil(o, kx + offx, ky + offy, &pr, &pi);
+            if (mode == 4) {
+                double g = 2.0 * sin(kx * dsx + ky * dsy + o->bias_phase);
+                /* (pr + i pi) * (i g) */
+                double r = -pi * g, m = pr * g;
+                pr = r;
+                pi = m;
+            }
+            hre[(size_t)i * W + j] = pr;
+            him[(size_t)i * W + j] = pi;
+        }
+}
+
+/* Images for every modality in o->modes (bit order: brightfield, oblique,
+ * DIC) from an exit wave:  I_m = | IDFT2( DFT2(E) * H_m ) / (H W) |^2.
+ * images is K x H x W.  The field arrays are left unchanged. */
+void orc_images(const orc_optics *o, const double *ere, const double *eim,
+                double *images)
+{
+    int H = o->H, W = o->W;
+    size_t hw = (size_t)H * W;
+    double *fr = (double *)malloc(sizeof(double) * hw);
+    double *fi = (double *)malloc(sizeof(double) * hw);
+    double *hr = (double *)malloc(sizeof(double) * hw);
+    double *hi = (double *)malloc(sizeof(double) * hw);
+    double *zr = (double *)malloc(sizeof(double) * hw);
+    double *zi = (double *)malloc(sizeof(double) * hw);
+    memcpy(fr, ere, sizeof(double) * hw);
+    memcpy(fi, eim, sizeof(double) * hw);
+    orc_fft2(fr, fi, H, W, -1);
+    int k = 0;
+    for (int bit = 0; bit < 3; ++bit) {
+        int mode = 1 << bit;
+        if (!(o->modes & (uint32_t)mode)) continue;
+        orc_transfer(o, mode, hr, hi);
+        for (size_t t = 0; t < hw; ++t) {
+            zr[t] = fr[t] * hr[t] - fi[t] * hi[t];
+            zi[t] = fr[t] * hi[t] + fi[t] * hr[t];
+        }
+        orc_fft2(zr, zi, H, W, +1);
+        double inv = 1.0 / (double)hw;
+        double *img = images + (size_t)k * hw;
+        for (size_t t = 0; t < hw; ++t) {
+            double a = zr[t] * inv, b = zi[t] * inv;
+            img[t] = a * a + b * b;
+        }
+        ++k;
+    }
+    free(fr); free(fi); free(hr); free(hi); free(zr); free(zi);
+}
+
+/* Whole forward model f(Theta) = I: OPD/ATT maps, exit wave, images. */
+void orc_render(const float *soa, int64_t ld, int n, const orc_optics *o,
+                double *opd, double *att, double *ere, double *eim,
+                double *images)
+{
+    orc_opd_att(soa, ld, n, o->H, o->W, o->dx, o->bevel_slope, 0, opd, att);
+    orc_field(opd, att, (int64_t)o->H * o->W, o->lambda, ere, eim);
+    orc_images(o, ere, eim, images);
+}
