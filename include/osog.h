@@ -1,0 +1,217 @@
+/*
+ * osog.h - C ABI of libosog, a GB300 (sm_103a) renderer for the OSOG
+ * optical forward model (arxiv 2606.21381).
+ *
+ * The library computes, for a structure-of-arrays tensor of transparent
+ * particles, the multi-modal micrograph f(Theta) = I of Sec. III:
+ *
+ *   1. per-pixel thickness footprints of ellipsoids and bevelled prisms
+ *      (Sec. III.A; the prism is the half-space intersection of Eq. 1);
+ *   2. composition of the optical path difference OPD = sum_p dn_p t_p and
+ *      of the absorption exponent ATT = sum_p mu_p t_p, overlaps adding
+ *      (Eq. 2's integral over z, Eq. 7's accumulate=True splat);
+ *   3. the exit wave E = exp(-ATT) exp(i 2 pi OPD / lambda) (Eq. 2, with the
+ *      Beer-Lambert amplitude of Eq. 4);
+ *   4. the optical head: forward 2-D DFT, multiplication by the transfer
+ *      function of each selected modality (pupil of Eq. 3 with NA cutoff and
+ *      defocus; oblique illumination as the pupil shifted by k_ill; DIC as
+ *      the coherent shear difference of Eq. 5), inverse 2-D DFT;
+ *   5. intensity I = |E_out|^2 (Sec. III.B, "I_BF = |U_exit * h_obj|^2").
+ *
+ * Conventions shared by every entry point:
+ *   - Particle tensor: float32, planar [9][ld] on the device, rows
+ *       0 cx (px)  1 cy (px)  2 theta (rad, from +x toward +y)
+ *       3 a | hx (px)  4 b | hy (px)  5 T (um)  6 dn  7 mu (1/um)
+ *       8 kind (0 = ellipsoid with semi-axes a, b and full thickness T;
+ *               1 = rectangular prism with half-lengths hx, hy, thickness T
+ *               and chamfers of slope bevel_slope on all top/bottom edges).
+ *   - Pixel (i, j) is sampled at its centre (x, y) = (j + 0.5, i + 0.5) px;
+ *     rows are y.  Images are float32 [K][H][W], K = number of bits set in
+ *     optics->modes, in bit order brightfield, oblique, DIC.
+ *   - H and W are powers of two in [32, 2048] (OSOG_ERR_UNSUPPORTED_SIZE).
+ *   - All device buffers belong to the caller.  The library allocates device
+ *     memory only in osog_plan_create; every other call runs asynchronously
+ *     on the given stream and allocates nothing.
+ *   - Errors found on the host are returned at once (and described by
+ *     osog_last_error).  Errors found on the device (non-finite or invalid
+ *     particle fields, bin overflow, timeouts) are latched in the plan's
+ *     device status word; osog_sync_status synchronises the stream, returns
+ *     the first latched code and clears it.  Nothing aborts, traps or prints.
+ *   - A plan may be used by one host thread at a time.
+ */
+#ifndef OSOG_H
+#define OSOG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define OSOG_OK 0
+#define OSOG_ERR_INVALID_ARG 1        /* bad pointer, size or option */
+#define OSOG_ERR_UNSUPPORTED_SIZE 2   /* H or W not a power of two in [32, 2048] */
+#define OSOG_ERR_WORKSPACE 3          /* workspace too small or misaligned */
+#define OSOG_ERR_BIN_OVERFLOW 4       /* more particle-band pairs than reserved */
+#define OSOG_ERR_NONFINITE_INPUT 5    /* NaN or Inf in a particle field */
+#define OSOG_ERR_TIMEOUT 6            /* a bounded device wait gave up */
+#define OSOG_ERR_CUDA 7               /* a CUDA runtime call failed */
+#define OSOG_ERR_INVALID_PARTICLE 8   /* a <= 0, b <= 0, T < 0 or unknown kind */
+
+/* Modality bits of osog_optics_t.modes. */
+#define OSOG_MODE_BRIGHTFIELD 1u
+#define OSOG_MODE_OBLIQUE 2u
+#define OSOG_MODE_DIC 4u
+
+/* Kernel classes reported by osog_profile_end. */
+#define OSOG_KERNEL_BIN_COUNT 0
+#define OSOG_KERNEL_BIN_SCAN 1
+#define OSOG_KERNEL_BIN_FILL 2
+#define OSOG_KERNEL_STRIP_FORWARD 3
+#define OSOG_KERNEL_COLUMN 4
+#define OSOG_KERNEL_STRIP_INVERSE 5
+#define OSOG_KERNEL_CLASS_COUNT 6
+
+typedef struct osog_plan osog_plan_t;
+/* Binary-compatible with cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *osog_stream_t;
+
+/*
+ * Optics of one scene (host struct, passed by pointer; Sec. III.B).
+ *   dx_um       pixel pitch in the sample plane (um)
+ *   lambda_um   wavelength (um)
+ *   NA          numerical aperture; k_NA = 2 pi NA / lambda (Eq. 3)
+ *   n_medium    medium index n_m; k0 = 2 pi n_m / lambda (Eq. 2, Eq. 3)
+ *   defocus_um  dz of Eq. 3; the pupil phase is dz (sqrt(k0^2-|k|^2) - k0)
+ *   modes       OSOG_MODE_* bits; K = number of bits set (1..3)
+ *   oblique_frac, oblique_angle
+ *               oblique modality: transfer P(k + k_ill) with
+ *               k_ill = oblique_frac k_NA (cos, sin)(oblique_angle)
+ *   shear_px, shear_angle, bias_phase
+ *               DIC (Eq. 5): shear distance 2|ds| = shear_px pixels along
+ *               shear_angle, bias theta; transfer P(k) 2i sin(k.ds + theta)
+ *   bevel_slope prism chamfer slope s_b; chord = clamp(2 s_b d, 0, T) with d
+ *               the in-plane distance to the nearest side wall (um)
+ */
+typedef struct {
+    int32_t H, W;
+    double dx_um, lambda_um, NA, n_medium, defocus_um;
+    uint32_t modes;
+    double oblique_frac, oblique_angle;
+    double shear_px, shear_angle, bias_phase;
+    double bevel_slope;
+} osog_optics_t;
+
+/*
+ * Tuning of the batched path (osog_batch_submit).  Zero fields take the
+ * autotuned or default value.
+ *   pairs_per_particle  particle-band pairs reserved per particle (default 8)
+ *   use_graph           1: replay the launch sequence as a CUDA graph that the
+ *                       plan caches per batch shape; 0: launch directly
+ */
+typedef struct {
+    int32_t pairs_per_particle;
+    int32_t use_graph;
+    int32_t reserved[6];
+} osog_tuning_t;
+
+/*
+ * Create a plan for H x W canvases: uploads FP64-built twiddle tables
+ * exp(-2 pi i k / N) rounded to float32 and allocates the device status
+ * word.  Returns OSOG_ERR_UNSUPPORTED_SIZE for a bad size, OSOG_ERR_CUDA if
+ * the device allocation fails.  *plan is NULL on failure.
+ */
+int osog_plan_create(osog_plan_t **plan, int32_t H, int32_t W);
+
+/* Release a plan and its device memory (NULL is ignored).  The caller must
+ * make sure no work using the plan is still running. */
+void osog_plan_destroy(osog_plan_t *plan);
+
+/*
+ * Workspace bytes needed by a render of `batch` scenes holding `n_max`
+ * particles in total with K modalities (osog_render: batch = 1).  The
+ * workspace is a caller-owned device buffer aligned to 256 bytes.  Returns
+ * 0 for invalid arguments.
+ */
+size_t osog_workspace_size(const osog_plan_t *plan, int32_t n_max, int32_t K,
+                           int32_t batch);
+
+/*
+ * Forward render of one scene (the whole path, Sec. III.A-C).
+ *   soa      device float32 [9][ld], n particles in columns 0..n-1
+ *   n        particle count, 0 <= n <= ld (0 renders an empty field)
+ *   optics   host struct; optics->H, ->W must equal the plan's size
+ *   image    device float32 [K][H][W], written completely
+ *   ws       device workspace of ws_bytes >= osog_workspace_size(plan, n, K, 1)
+ * Returns OSOG_OK or a host-side error; device-side errors are latched.
+ */
+int osog_render(osog_plan_t *plan, const float *soa, int64_t ld, int32_t n,
+                const osog_optics_t *optics, float *image, void *ws,
+                size_t ws_bytes, osog_stream_t stream);
+
+/*
+ * Stage entry: rasterise only.  Writes the OPD and ATT maps of Eq. 2 as a
+ * device float32 [H][W][2] array (opd, att per pixel), in the same order of
+ * summation as osog_render.  Workspace as for osog_render with K = 1.
+ */
+int osog_render_opd(osog_plan_t *plan, const float *soa, int64_t ld, int32_t n,
+                    const osog_optics_t *optics, float *opd_att, void *ws,
+                    size_t ws_bytes, osog_stream_t stream);
+
+/*
+ * Stage entry: optics only.  Takes a device float32 [H][W][2] OPD/ATT map,
+ * forms the exit wave (Eq. 2, Eq. 4) and images every selected modality
+ * into device float32 [K][H][W].  Workspace: osog_workspace_size(plan, 0, K, 1).
+ */
+int osog_optics_from_opd(osog_plan_t *plan, const float *opd_att,
+                         const osog_optics_t *optics, float *image, void *ws,
+                         size_t ws_bytes, osog_stream_t stream);
+
+/*
+ * Batched forward render of S scenes that share the plan's H x W and the
+ * same modality bits (per-scene optics may otherwise differ).
+ *   soa_all  device float32 [9][ld]; scene s owns columns
+ *            offsets[s] .. offsets[s+1]-1
+ *   offsets  HOST int32 [S+1], non-decreasing, offsets[S] <= ld
+ *   optics   HOST array of S structs
+ *   images   device float32 [S][K][H][W]
+ *   tuning   NULL for defaults
+ *   ws       >= osog_workspace_size(plan, offsets[S]-offsets[0], K, S)
+ */
+int osog_batch_submit(osog_plan_t *plan, const float *soa_all, int64_t ld,
+                      const int32_t *offsets, int32_t S,
+                      const osog_optics_t *optics, float *images,
+                      const osog_tuning_t *tuning, void *ws, size_t ws_bytes,
+                      osog_stream_t stream);
+
+/* Synchronise `stream`, return the first device-latched status since the
+ * last call (OSOG_OK if none) and clear it. */
+int osog_sync_status(osog_plan_t *plan, osog_stream_t stream);
+
+/* Text of the last host-side error of the calling thread ("" if none). */
+const char *osog_last_error(void);
+
+/* Number of kernels this plan has launched since it was created (graph
+ * replays count each kernel node once per replay). */
+int64_t osog_plan_launch_count(const osog_plan_t *plan);
+
+/*
+ * Per-kernel timing.  Between osog_profile_begin and osog_profile_end every
+ * kernel the plan launches is bracketed by CUDA events on its stream (graph
+ * replay is disabled meanwhile).  osog_profile_end synchronises `stream`
+ * and writes, per kernel class (OSOG_KERNEL_*), the summed device time in
+ * milliseconds and the launch count.  Arrays have OSOG_KERNEL_CLASS_COUNT
+ * entries.  At most 8192 launches are timed per session; later ones are
+ * counted but not timed.
+ */
+int osog_profile_begin(osog_plan_t *plan);
+int osog_profile_end(osog_plan_t *plan, osog_stream_t stream, float *ms,
+                     int32_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OSOG_H */

@@ -1,0 +1,499 @@
+// C ABI of libosog: plans, argument checks, workspace layout, launch
+// sequencing, CUDA-graph cache of the batched path, per-kernel timing.
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "osog_kernels.h"
+
+using namespace osog;
+
+struct osog_plan {
+    int H = 0, W = 0;
+    Geometry geo{};
+    float2 *tw_w = nullptr;   // W-point twiddles exp(-2 pi i k / W)
+    float2 *tw_h = nullptr;   // H-point twiddles (aliases tw_w when H == W)
+    int32_t *status = nullptr;
+    int32_t *status_host = nullptr;  // pinned
+    int64_t launches = 0;
+    // per-kernel timing
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;  // pairs (start, stop)
+    std::vector<int> ev_cls;
+    int ev_used = 0;
+    int32_t prof_launches[OSOG_KERNEL_CLASS_COUNT] = {};
+    // cached graph of the last batched launch sequence
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<unsigned char> gkey;
+    int64_t graph_kernels = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+    return fail(OSOG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool pow2_in_range(int v) { return v >= 32 && v <= 2048 && (v & (v - 1)) == 0; }
+
+int popcount3(uint32_t m) { return (int)(m & 1u) + (int)((m >> 1) & 1u) + (int)((m >> 2) & 1u); }
+
+constexpr int kDefaultPairs = 8;
+constexpr int kMaxTimed = 8192;
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t rec, rect, cnt, band_off, pairs, G, Q, total;
+};
+
+// Workspace regions for a launch group of up to S scenes, n records,
+// nchunks binning chunks and pair_total band slots.
+Layout make_layout(const Geometry &geo, int64_t n, int64_t nchunks, int S, int K,
+                   int64_t pair_total) {
+    Layout l;
+    size_t o = 0;
+    l.rec = o;
+    o = align256(o + (size_t)n * sizeof(PRec));
+    l.rect = o;
+    o = align256(o + (size_t)n * sizeof(Rect));
+    l.cnt = o;
+    o = align256(o + (size_t)nchunks * geo.nbands * sizeof(int32_t));
+    l.band_off = o;
+    o = align256(o + (size_t)S * (geo.nbands + 1) * sizeof(int32_t));
+    l.pairs = o;
+    o = align256(o + (size_t)pair_total * sizeof(int32_t));
+    l.G = o;
+    o = align256(o + (size_t)S * geo.H * geo.W * sizeof(float2));
+    l.Q = o;
+    o = align256(o + (size_t)S * K * geo.H * geo.W * sizeof(float2));
+    l.total = o;
+    return l;
+}
+
+Work carve(void *ws, const Layout &l, int32_t *status) {
+    char *b = static_cast<char *>(ws);
+    Work w;
+    w.rec = reinterpret_cast<PRec *>(b + l.rec);
+    w.rect = reinterpret_cast<Rect *>(b + l.rect);
+    w.cnt = reinterpret_cast<int32_t *>(b + l.cnt);
+    w.band_off = reinterpret_cast<int32_t *>(b + l.band_off);
+    w.pairs = reinterpret_cast<int32_t *>(b + l.pairs);
+    w.G = reinterpret_cast<float2 *>(b + l.G);
+    w.Q = reinterpret_cast<float2 *>(b + l.Q);
+    w.status = status;
+    return w;
+}
+
+bool finite_all(std::initializer_list<double> v) {
+    for (double x : v)
+        if (!isfinite(x)) return false;
+    return true;
+}
+
+int check_optics(const osog_plan *p, const osog_optics_t *o) {
+    if (!o) return fail(OSOG_ERR_INVALID_ARG, "optics is NULL");
+    if (o->H != p->H || o->W != p->W)
+        return fail(OSOG_ERR_INVALID_ARG, "optics H, W differ from the plan's");
+    if (!finite_all({o->dx_um, o->lambda_um, o->NA, o->n_medium, o->defocus_um, o->oblique_frac,
+                     o->oblique_angle, o->shear_px, o->shear_angle, o->bias_phase, o->bevel_slope}))
+        return fail(OSOG_ERR_INVALID_ARG, "optics has a non-finite field");
+    if (!(o->dx_um > 0) || !(o->lambda_um > 0) || !(o->NA > 0) || !(o->n_medium >= o->NA))
+        return fail(OSOG_ERR_INVALID_ARG, "optics needs dx > 0, lambda > 0, 0 < NA <= n_medium");
+    if (!(o->bevel_slope > 0)) return fail(OSOG_ERR_INVALID_ARG, "bevel_slope must be > 0");
+    if (o->modes == 0 || (o->modes & ~7u)) return fail(OSOG_ERR_INVALID_ARG, "modes must be in 1..7");
+    return OSOG_OK;
+}
+
+SceneDev scene_dev(const osog_optics_t &o) {
+    SceneDev s{};
+    s.two_over_lambda = (float)(2.0 / o.lambda_um);
+    s.prism_g = (float)(2.0 * o.bevel_slope * o.dx_um);
+    return s;
+}
+
+ModeDev mode_dev(const osog_optics_t &o, uint32_t mode) {
+    const double two_pi = 6.283185307179586476925286766559;
+    ModeDev m{};
+    const double r = o.NA / o.lambda_um;
+    m.r2 = r * r;
+    m.ox = m.oy = 0.0;
+    if (mode == OSOG_MODE_OBLIQUE) {
+        m.ox = o.oblique_frac * r * cos(o.oblique_angle);
+        m.oy = o.oblique_frac * r * sin(o.oblique_angle);
+    }
+    m.fx_scale = 1.0 / ((double)o.W * o.dx_um);
+    m.fy_span = (double)o.H * o.dx_um;
+    m.kstep_x = (float)(two_pi / ((double)o.W * o.dx_um));
+    m.kstep_y = (float)(two_pi / ((double)o.H * o.dx_um));
+    m.qoff_x = (float)(two_pi * m.ox);
+    m.qoff_y = (float)(two_pi * m.oy);
+    m.k0 = (float)(two_pi * o.n_medium / o.lambda_um);
+    m.dz = (float)o.defocus_um;
+    m.dsx = (float)(0.5 * o.shear_px * o.dx_um * cos(o.shear_angle));
+    m.dsy = (float)(0.5 * o.shear_px * o.dx_um * sin(o.shear_angle));
+    m.bias = (float)o.bias_phase;
+    m.scale = (float)(1.0 / ((double)o.H * o.W));
+    m.dic = mode == OSOG_MODE_DIC ? 1 : 0;
+    return m;
+}
+
+// Launch helper: optional event bracketing and the launch counter.
+template <typename F>
+int run_kernel(osog_plan *p, int cls, cudaStream_t st, F &&launch) {
+    bool timed = false;
+    if (p->prof) {
+        p->prof_launches[cls]++;
+        if (p->ev_used < kMaxTimed) {
+            if ((size_t)(2 * p->ev_used + 2) > p->ev.size()) {
+                cudaEvent_t a, b;
+                if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+                    return fail(OSOG_ERR_CUDA, "cudaEventCreate failed");
+                p->ev.push_back(a);
+                p->ev.push_back(b);
+                p->ev_cls.push_back(0);
+            }
+            cudaEventRecord(p->ev[2 * p->ev_used], st);
+            timed = true;
+        }
+    }
+    cudaError_t e = launch();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if (timed) {
+        cudaEventRecord(p->ev[2 * p->ev_used + 1], st);
+        p->ev_cls[p->ev_used] = cls;
+        p->ev_used++;
+    }
+    p->launches++;
+    return OSOG_OK;
+}
+
+enum Stage { kFull, kOpdOnly, kFromMap };
+
+// One launch group: up to kMaxScenes scenes whose records start at soa.
+int enqueue_group(osog_plan *p, const float *soa, int64_t ld, const int32_t *counts, int S,
+                  const osog_optics_t *optics, int K, int pairs_per_particle, void *ws,
+                  size_t ws_bytes, float *images, const float *opd_att, float *opd_out,
+                  Stage stage, cudaStream_t st) {
+    const Geometry &geo = p->geo;
+    GroupDev gd{};
+    gd.S = S;
+    gd.K = K;
+    int64_t n = 0, chunks = 0, pairs = 0;
+    for (int s = 0; s < S; ++s) {
+        SceneDev sc = scene_dev(optics[s]);
+        sc.p0 = (int32_t)n;
+        sc.n = counts[s];
+        sc.chunk0 = (int32_t)chunks;
+        sc.pair0 = (int32_t)pairs;
+        sc.pair_cap = (int32_t)((int64_t)counts[s] * pairs_per_particle);
+        gd.sc[s] = sc;
+        n += counts[s];
+        chunks += (counts[s] + kChunk - 1) / kChunk;
+        pairs += (int64_t)counts[s] * pairs_per_particle;
+        int k = 0;
+        for (int bit = 0; bit < 3; ++bit)
+            if (optics[s].modes & (1u << bit)) gd.md[s][k++] = mode_dev(optics[s], 1u << bit);
+    }
+    if (pairs > INT32_MAX || n > INT32_MAX) return fail(OSOG_ERR_INVALID_ARG, "too many particles");
+    gd.nchunks = (int32_t)chunks;
+    const Layout l = make_layout(geo, n, chunks, S, stage == kFull || stage == kFromMap ? K : 0, pairs);
+    if (l.total > ws_bytes) return fail(OSOG_ERR_WORKSPACE, "workspace too small");
+    const Work w = carve(ws, l, p->status);
+    int rc;
+    if (stage != kFromMap) {
+        rc = run_kernel(p, OSOG_KERNEL_BIN_COUNT, st, [&] { return launch_bin_count(soa, ld, gd, geo, w, st); });
+        if (rc) return rc;
+        rc = run_kernel(p, OSOG_KERNEL_BIN_SCAN, st, [&] { return launch_bin_scan(gd, geo, w, st); });
+        if (rc) return rc;
+        rc = run_kernel(p, OSOG_KERNEL_BIN_FILL, st, [&] { return launch_bin_fill(gd, geo, w, st); });
+        if (rc) return rc;
+    }
+    StripArgs sa{};
+    sa.geo = geo;
+    sa.w = w;
+    sa.tw = p->tw_w;
+    sa.opd_att = reinterpret_cast<const float2 *>(opd_att);
+    sa.opd_out = reinterpret_cast<float2 *>(opd_out);
+    sa.S = S;
+    for (int s = 0; s < S; ++s) sa.sc[s] = gd.sc[s];
+    const StripMode sm = stage == kOpdOnly ? kStripOpdOnly : stage == kFromMap ? kStripFromMap : kStripRender;
+    rc = run_kernel(p, OSOG_KERNEL_STRIP_FORWARD, st, [&] { return launch_strip_forward(sa, sm, st); });
+    if (rc || stage == kOpdOnly) return rc;
+    ColumnArgs ca{};
+    ca.geo = geo;
+    ca.w = w;
+    ca.tw = p->tw_h;
+    ca.S = S;
+    ca.K = K;
+    for (int s = 0; s < S; ++s)
+        for (int k = 0; k < K; ++k) ca.md[s][k] = gd.md[s][k];
+    rc = run_kernel(p, OSOG_KERNEL_COLUMN, st, [&] { return launch_column(ca, st); });
+    if (rc) return rc;
+    InverseArgs ia{};
+    ia.geo = geo;
+    ia.w = w;
+    ia.tw = p->tw_w;
+    ia.images = images;
+    ia.S = S;
+    ia.K = K;
+    return run_kernel(p, OSOG_KERNEL_STRIP_INVERSE, st, [&] { return launch_strip_inverse(ia, st); });
+}
+
+int check_ws(void *ws, size_t need, size_t have) {
+    if (!ws && need) return fail(OSOG_ERR_WORKSPACE, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(OSOG_ERR_WORKSPACE, "workspace not 256-byte aligned");
+    if (have < need) return fail(OSOG_ERR_WORKSPACE, "workspace too small");
+    return OSOG_OK;
+}
+
+size_t ws_need(const osog_plan *p, int64_t n_total, int K, int S, int pairs_pp) {
+    const int Sg = S < kMaxScenes ? S : kMaxScenes;
+    const int64_t chunks = (n_total + kChunk - 1) / kChunk + S;
+    return make_layout(p->geo, n_total, chunks, Sg, K, n_total * pairs_pp).total;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *osog_last_error(void) { return g_err.c_str(); }
+
+int osog_plan_create(osog_plan_t **out, int32_t H, int32_t W) {
+    if (!out) return fail(OSOG_ERR_INVALID_ARG, "plan pointer is NULL");
+    *out = nullptr;
+    if (!pow2_in_range(H) || !pow2_in_range(W))
+        return fail(OSOG_ERR_UNSUPPORTED_SIZE, "H and W must be powers of two in [32, 2048]");
+    osog_plan *p = new osog_plan();
+    p->H = H;
+    p->W = W;
+    p->geo = make_geometry(H, W);
+    cudaError_t e = cudaMalloc(&p->tw_w, sizeof(float2) * (W + H));
+    if (e == cudaSuccess) e = cudaMalloc(&p->status, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&p->status_host, sizeof(int32_t));
+    if (e == cudaSuccess) {
+        std::vector<float2> tw(W + H);
+        const double two_pi = 6.283185307179586476925286766559;
+        for (int k = 0; k < W; ++k)
+            tw[k] = make_float2((float)cos(two_pi * k / W), (float)-sin(two_pi * k / W));
+        for (int k = 0; k < H; ++k)
+            tw[W + k] = make_float2((float)cos(two_pi * k / H), (float)-sin(two_pi * k / H));
+        p->tw_h = p->tw_w + W;
+        e = cudaMemcpy(p->tw_w, tw.data(), sizeof(float2) * (W + H), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(int32_t));
+    if (e == cudaSuccess) e = prepare_kernels(H, W);
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e, "osog_plan_create");
+        osog_plan_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return OSOG_OK;
+}
+
+void osog_plan_destroy(osog_plan_t *p) {
+    if (!p) return;
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    cudaFree(p->tw_w);
+    cudaFree(p->status);
+    cudaFreeHost(p->status_host);
+    delete p;
+}
+
+size_t osog_workspace_size(const osog_plan_t *p, int32_t n_max, int32_t K, int32_t batch) {
+    if (!p || n_max < 0 || K < 0 || K > 3 || batch < 1) return 0;
+    return ws_need(p, n_max, K, batch, kDefaultPairs);
+}
+
+static int render_stage(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
+                        const osog_optics_t *optics, float *image, const float *opd_att,
+                        float *opd_out, void *ws, size_t ws_bytes, osog_stream_t stream,
+                        Stage stage) {
+    if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    int rc = check_optics(p, optics);
+    if (rc) return rc;
+    if (n < 0 || (int64_t)n > ld) return fail(OSOG_ERR_INVALID_ARG, "need 0 <= n <= ld");
+    if (stage != kFromMap && n > 0 && !soa) return fail(OSOG_ERR_INVALID_ARG, "soa is NULL");
+    if (stage == kFromMap && !opd_att) return fail(OSOG_ERR_INVALID_ARG, "opd_att is NULL");
+    if (stage == kOpdOnly && !opd_out) return fail(OSOG_ERR_INVALID_ARG, "opd_att output is NULL");
+    if (stage != kOpdOnly && !image) return fail(OSOG_ERR_INVALID_ARG, "image is NULL");
+    const int K = popcount3(optics->modes);
+    const int nn = stage == kFromMap ? 0 : n;
+    rc = check_ws(ws, ws_need(p, nn, stage == kOpdOnly ? 0 : K, 1, kDefaultPairs), ws_bytes);
+    if (rc) return rc;
+    return enqueue_group(p, soa, ld, &nn, 1, optics, K, kDefaultPairs, ws, ws_bytes, image,
+                         opd_att, opd_out, stage, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int osog_render(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
+                const osog_optics_t *optics, float *image, void *ws, size_t ws_bytes,
+                osog_stream_t stream) {
+    return render_stage(p, soa, ld, n, optics, image, nullptr, nullptr, ws, ws_bytes, stream, kFull);
+}
+
+int osog_render_opd(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
+                    const osog_optics_t *optics, float *opd_att, void *ws, size_t ws_bytes,
+                    osog_stream_t stream) {
+    return render_stage(p, soa, ld, n, optics, nullptr, nullptr, opd_att, ws, ws_bytes, stream,
+                        kOpdOnly);
+}
+
+int osog_optics_from_opd(osog_plan_t *p, const float *opd_att, const osog_optics_t *optics,
+                         float *image, void *ws, size_t ws_bytes, osog_stream_t stream) {
+    return render_stage(p, nullptr, 0, 0, optics, image, opd_att, nullptr, ws, ws_bytes, stream,
+                        kFromMap);
+}
+
+static int batch_enqueue(osog_plan_t *p, const float *soa_all, int64_t ld, const int32_t *offsets,
+                         int32_t S, const osog_optics_t *optics, float *images, int K, int ppp,
+                         void *ws, size_t ws_bytes, cudaStream_t st) {
+    const size_t img_scene = (size_t)K * p->H * p->W;
+    for (int g0 = 0; g0 < S; g0 += kMaxScenes) {
+        const int Sg = S - g0 < kMaxScenes ? S - g0 : kMaxScenes;
+        int32_t counts[kMaxScenes];
+        for (int s = 0; s < Sg; ++s) counts[s] = offsets[g0 + s + 1] - offsets[g0 + s];
+        const float *soa_g = soa_all ? soa_all + offsets[g0] : nullptr;
+        int rc = enqueue_group(p, soa_g, ld, counts, Sg, optics + g0, K, ppp, ws, ws_bytes,
+                               images + (size_t)g0 * img_scene, nullptr, nullptr, kFull, st);
+        if (rc) return rc;
+    }
+    return OSOG_OK;
+}
+
+int osog_batch_submit(osog_plan_t *p, const float *soa_all, int64_t ld, const int32_t *offsets,
+                      int32_t S, const osog_optics_t *optics, float *images,
+                      const osog_tuning_t *tuning, void *ws, size_t ws_bytes,
+                      osog_stream_t stream) {
+    if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    if (S < 1 || !offsets || !optics || !images)
+        return fail(OSOG_ERR_INVALID_ARG, "need S >= 1 and non-NULL offsets, optics, images");
+    for (int s = 0; s < S; ++s) {
+        if (offsets[s + 1] < offsets[s] || offsets[s] < 0)
+            return fail(OSOG_ERR_INVALID_ARG, "offsets must be non-decreasing and >= 0");
+        int rc = check_optics(p, optics + s);
+        if (rc) return rc;
+        if (optics[s].modes != optics[0].modes)
+            return fail(OSOG_ERR_INVALID_ARG, "all scenes must select the same modes");
+    }
+    if ((int64_t)offsets[S] > ld) return fail(OSOG_ERR_INVALID_ARG, "offsets[S] > ld");
+    const int64_t n_total = (int64_t)offsets[S] - offsets[0];
+    if (n_total > 0 && !soa_all) return fail(OSOG_ERR_INVALID_ARG, "soa_all is NULL");
+    const int K = popcount3(optics[0].modes);
+    const int ppp = tuning && tuning->pairs_per_particle > 0 ? tuning->pairs_per_particle : kDefaultPairs;
+    const bool use_graph = !tuning || tuning->use_graph != 0;
+    int rc = check_ws(ws, ws_need(p, n_total, K, S, ppp), ws_bytes);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (st) cudaStreamIsCapturing(st, &cs);
+    if (!use_graph || p->prof || !st || cs != cudaStreamCaptureStatusNone)
+        return batch_enqueue(p, soa_all, ld, offsets, S, optics, images, K, ppp, ws, ws_bytes, st);
+
+    // Key of the launch sequence: every argument that ends up in a kernel.
+    std::vector<unsigned char> key;
+    auto put = [&key](const void *d, size_t b) {
+        const unsigned char *c = static_cast<const unsigned char *>(d);
+        key.insert(key.end(), c, c + b);
+    };
+    put(&soa_all, sizeof soa_all);
+    put(&ld, sizeof ld);
+    put(&S, sizeof S);
+    put(offsets, sizeof(int32_t) * (S + 1));
+    put(optics, sizeof(osog_optics_t) * S);
+    put(&images, sizeof images);
+    put(&ws, sizeof ws);
+    put(&ws_bytes, sizeof ws_bytes);
+    put(&ppp, sizeof ppp);
+    if (!(p->gexec && key == p->gkey)) {
+        const int64_t before = p->launches;
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        rc = batch_enqueue(p, soa_all, ld, offsets, S, optics, images, K, ppp, ws, ws_bytes, st);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(st, &g);
+        p->graph_kernels = p->launches - before;
+        p->launches = before;
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        if (p->gexec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(p->gexec, g, &info) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(p->gexec);
+                p->gexec = nullptr;
+            }
+        }
+        if (!p->gexec) {
+            e = cudaGraphInstantiate(&p->gexec, g, 0);
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(g);
+                p->gexec = nullptr;
+                return cuda_fail(e, "cudaGraphInstantiate");
+            }
+        }
+        cudaGraphDestroy(g);
+        p->gkey.swap(key);
+    }
+    cudaError_t e = cudaGraphLaunch(p->gexec, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    p->launches += p->graph_kernels;
+    return OSOG_OK;
+}
+
+int osog_sync_status(osog_plan_t *p, osog_stream_t stream) {
+    if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(p->status_host, p->status, sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "osog_sync_status");
+    return *p->status_host;
+}
+
+int64_t osog_plan_launch_count(const osog_plan_t *p) { return p ? p->launches : 0; }
+
+int osog_profile_begin(osog_plan_t *p) {
+    if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    p->prof = true;
+    p->ev_used = 0;
+    memset(p->prof_launches, 0, sizeof p->prof_launches);
+    return OSOG_OK;
+}
+
+int osog_profile_end(osog_plan_t *p, osog_stream_t stream, float *ms, int32_t *launches) {
+    if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "osog_profile_end");
+    float acc[OSOG_KERNEL_CLASS_COUNT] = {};
+    for (int i = 0; i < p->ev_used; ++i) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, p->ev[2 * i], p->ev[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        acc[p->ev_cls[i]] += t;
+    }
+    for (int c = 0; c < OSOG_KERNEL_CLASS_COUNT; ++c) {
+        if (ms) ms[c] = acc[c];
+        if (launches) launches[c] = p->prof_launches[c];
+    }
+    p->prof = false;
+    p->ev_used = 0;
+    return OSOG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+// Particle setup and deterministic particle-to-band binning.
+//
+// The composition step of the paper (Sec. III.C, Eq. 7) scatters every
+// particle's patch into the canvas with an atomic accumulate.  Here the
+// canvas is instead gathered per pixel in a fixed particle order, so the
+// sum is deterministic and needs no floating-point atomics.  To find the
+// particles that can touch a strip of rows, particles are binned to bands
+// of BH rows:
+//
+//   count  (one CTA per chunk of 256 particles): per-particle setup (record,
+//          bounding rectangle, band range), then per band a warp ballot of
+//          the particles that overlap it; per-warp counts are summed into
+//          cnt[chunk][band].
+//   scan   (one CTA per scene): exclusive prefix of cnt over the scene's
+//          chunks for every band, then over bands, giving each band's list
+//          start in the scene's pair region.
+//   fill   (one CTA per chunk): the ballots again; a particle's slot is the
+//          band start + chunk prefix + earlier warps of the chunk + the
+//          popcount of lower lanes.  Each band list is therefore in
+//          ascending particle order.
+#include <math.h>
+
+#include "osog_kernels.h"
+
+namespace osog {
+
+namespace {
+
+__device__ __forceinline__ int scene_of_chunk(const GroupDev &gd, int chunk) {
+    int s = 0;
+    for (int t = 1; t < gd.S; ++t)
+        if (gd.sc[t].chunk0 <= chunk) s = t;
+    return s;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Band range [b0, b1] of a particle from its rectangle (b0 > b1: none).
+__device__ __forceinline__ void band_range(const Rect &r, int BH, int &b0, int &b1) {
+    if (r.x0 > r.x1 || r.y0 > r.y1) {
+        b0 = 1;
+        b1 = 0;
+    } else {
+        b0 = r.y0 / BH;
+        b1 = r.y1 / BH;
+    }
+}
+
+// Setup of one particle: validation, FP64-rounded record, bounding rect.
+__device__ Rect setup_particle(const float *soa, int64_t ld, int p, const SceneDev &sc,
+                               const Geometry &geo, PRec *rec, int32_t *status) {
+    float f[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) f[k] = __ldg(soa + (int64_t)k * ld + p);
+    const Rect empty = {1, 0, 1, 0};
+    bool finite = true;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) finite = finite && isfinite(f[k]);
+    if (!finite) {
+        latch(status, OSOG_ERR_NONFINITE_INPUT);
+        return empty;
+    }
+    const float cx = f[0], cy = f[1], th = f[2], a = f[3], b = f[4], T = f[5];
+    const float kind = f[8];
+    if (!(a > 0.f) || !(b > 0.f) || !(T >= 0.f) || !(kind == 0.f || kind == 1.f)) {
+        latch(status, OSOG_ERR_INVALID_PARTICLE);
+        return empty;
+    }
+    double sd, cd;
+    sincos((double)th, &sd, &cd);
+    PRec r;
+    r.cx = cx;
+    r.cy = cy;
+    r.ch = (float)cd;
+    r.cl = (float)(cd - (double)r.ch);
+    r.sh = (float)sd;
+    r.sl = (float)(sd - (double)r.sh);
+    r.T = T;
+    r.dn = f[6];
+    r.mu = f[7];
+    float ex, ey;
+    const float c = fabsf(r.ch), s = fabsf(r.sh);
+    if (kind == 1.f) {
+        r.p0h = a;
+        r.p0l = 0.f;
+        r.p1h = b;
+        r.p1l = 0.f;
+        r.g = sc.prism_g;
+        ex = a * c + b * s;
+        ey = a * s + b * c;
+    } else {
+        const double ia = 1.0 / (double)a, ib = 1.0 / (double)b;
+        r.p0h = (float)ia;
+        r.p0l = (float)(ia - (double)r.p0h);
+        r.p1h = (float)ib;
+        r.p1l = (float)(ib - (double)r.p1h);
+        r.g = 0.f;
+        ex = sqrtf(a * a * c * c + b * b * s * s);
+        ey = sqrtf(a * a * s * s + b * b * c * c);
+    }
+    rec[p] = r;
+    // Pixel centres j + 0.5 inside [cx - ex, cx + ex], widened by one pixel
+    // on each side; the thickness is exactly zero on the extra pixels.
+    const float xl = floorf(cx - ex - 1.5f), xh = ceilf(cx + ex + 0.5f);
+    const float yl = floorf(cy - ey - 1.5f), yh = ceilf(cy + ey + 0.5f);
+    if (xh < 0.f || yh < 0.f || xl > (float)(geo.W - 1) || yl > (float)(geo.H - 1))
+        return empty;
+    Rect q;
+    q.x0 = (int16_t)fmaxf(xl, 0.f);
+    q.x1 = (int16_t)fminf(xh, (float)(geo.W - 1));
+    q.y0 = (int16_t)fmaxf(yl, 0.f);
+    q.y1 = (int16_t)fminf(yh, (float)(geo.H - 1));
+    return q;
+}
+
+__global__ void __launch_bounds__(kChunk)
+k_bin_count(const float *__restrict__ soa, int64_t ld, const __grid_constant__ GroupDev gd,
+            Geometry geo, Work w) {
+    __shared__ int wcnt[kChunk / 32][kMaxBands];
+    const int chunk = blockIdx.x;
+    const int s = scene_of_chunk(gd, chunk);
+    const SceneDev &sc = gd.sc[s];
+    const int local = (chunk - sc.chunk0) * kChunk + threadIdx.x;
+    const bool mine = local < sc.n;
+    const int p = sc.p0 + local;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < (kChunk / 32) * kMaxBands; i += kChunk) (&wcnt[0][0])[i] = 0;
+    int b0 = 1, b1 = 0;
+    if (mine) {
+        Rect r = setup_particle(soa, ld, p, sc, geo, w.rec, w.status);
+        w.rect[p] = r;
+        band_range(r, geo.BH, b0, b1);
+    }
+    __syncthreads();
+    const bool any = b0 <= b1;
+    const int lo = __reduce_min_sync(0xffffffffu, any ? b0 : kMaxBands);
+    const int hi = __reduce_max_sync(0xffffffffu, any ? b1 : -1);
+    for (int b = lo; b <= hi; ++b) {
+        const unsigned m = __ballot_sync(0xffffffffu, any && b0 <= b && b <= b1);
+        if (lane == 0) wcnt[warp][b] = __popc(m);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < geo.nbands; b += kChunk) {
+        int t = 0;
+#pragma unroll
+        for (int k = 0; k < kChunk / 32; ++k) t += wcnt[k][b];
+        w.cnt[(int64_t)chunk * geo.nbands + b] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+k_bin_scan(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
+    __shared__ int total[kMaxBands];
+    const int s = blockIdx.x;
+    const SceneDev &sc = gd.sc[s];
+    const int nch = (s + 1 < gd.S ? gd.sc[s + 1].chunk0 : gd.nchunks) - sc.chunk0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int b = warp; b < geo.nbands; b += 32) {
+        int run = 0;
+        for (int c0 = 0; c0 < nch; c0 += 32) {
+            const int c = c0 + lane;
+            int32_t *cell = w.cnt + (int64_t)(sc.chunk0 + c) * geo.nbands + b;
+            const int v = c < nch ? *cell : 0;
+            int inc = v;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, inc, d);
+                if (lane >= d) inc += t;
+            }
+            if (c < nch) *cell = run + inc - v;
+            run += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (lane == 0) total[b] = run;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t *off = w.band_off + (int64_t)s * (geo.nbands + 1);
+        int acc = 0;
+        for (int b = 0; b < geo.nbands; ++b) {
+            off[b] = acc;
+            acc += total[b];
+        }
+        off[geo.nbands] = acc;
+        if (acc > sc.pair_cap) latch(w.status, OSOG_ERR_BIN_OVERFLOW);
+    }
+}
+
+__global__ void __launch_bounds__(kChunk)
+k_bin_fill(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
+    __shared__ int wpre[kChunk / 32][kMaxBands];
+    const int chunk = blockIdx.x;
+    const int s = scene_of_chunk(gd, chunk);
+    const SceneDev &sc = gd.sc[s];
+    const int local = (chunk - sc.chunk0) * kChunk + threadIdx.x;
+    const bool mine = local < sc.n;
+    const int p = sc.p0 + local;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < (kChunk / 32) * kMaxBands; i += kChunk) (&wpre[0][0])[i] = 0;
+    int b0 = 1, b1 = 0;
+    if (mine) band_range(w.rect[p], geo.BH, b0, b1);
+    __syncthreads();
+    const bool any = b0 <= b1;
+    const int lo = __reduce_min_sync(0xffffffffu, any ? b0 : kMaxBands);
+    const int hi = __reduce_max_sync(0xffffffffu, any ? b1 : -1);
+    for (int b = lo; b <= hi; ++b) {
+        const unsigned m = __ballot_sync(0xffffffffu, any && b0 <= b && b <= b1);
+        if (lane == 0) wpre[warp][b] = __popc(m);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < geo.nbands; b += kChunk) {  // exclusive over warps
+        int acc = 0;
+#pragma unroll
+        for (int k = 0; k < kChunk / 32; ++k) {
+            const int t = wpre[k][b];
+            wpre[k][b] = acc;
+            acc += t;
+        }
+    }
+    __syncthreads();
+    const int32_t *off = w.band_off + (int64_t)s * (geo.nbands + 1);
+    const int32_t *pre = w.cnt + (int64_t)chunk * geo.nbands;
+    const unsigned lt = lanemask_lt();
+    for (int b = lo; b <= hi; ++b) {
+        const bool in = any && b0 <= b && b <= b1;
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (in) {
+            const int slot = off[b] + pre[b] + wpre[warp][b] + __popc(m & lt);
+            if (slot < sc.pair_cap) w.pairs[sc.pair0 + slot] = p;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_bin_count(const float *soa, int64_t ld, const GroupDev &gd,
+                             const Geometry &geo, const Work &w, cudaStream_t st) {
+    if (gd.nchunks == 0) return cudaSuccess;
+    k_bin_count<<<gd.nchunks, kChunk, 0, st>>>(soa, ld, gd, geo, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_scan(const GroupDev &gd, const Geometry &geo, const Work &w,
+                            cudaStream_t st) {
+    k_bin_scan<<<gd.S, 1024, 0, st>>>(gd, geo, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_fill(const GroupDev &gd, const Geometry &geo, const Work &w,
+                            cudaStream_t st) {
+    if (gd.nchunks == 0) return cudaSuccess;
+    k_bin_fill<<<gd.nchunks, kChunk, 0, st>>>(gd, geo, w);
+    return cudaGetLastError();
+}
+
+}  // namespace osog

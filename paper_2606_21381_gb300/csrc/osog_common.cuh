@@ -1,0 +1,198 @@
+// Internal definitions shared by the libosog translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "osog.h"
+
+namespace osog {
+
+// ---------------------------------------------------------------- layout
+// Every FFT-bearing kernel works on a set of 8192 complex samples held in
+// shared memory: a strip of R = 8192 / W full rows, or a block of
+// B = 8192 / H full columns (fewer when the canvas is smaller).
+constexpr int kSetElems = 8192;
+constexpr int kThreads = 256;          // threads of every FFT-bearing CTA
+constexpr int kChunk = 256;            // particles per binning CTA
+constexpr int kMaxBands = 64;          // bands (binning rows) per canvas
+constexpr int kMaxScenes = 32;         // scenes per launch group
+constexpr int kMaxModes = 3;
+constexpr int kListCap = 1024;         // strip-list entries staged per pass
+
+// Shared-memory index of element i of an FFT line: one float2 of padding
+// after every 16 keeps the strided Stockham accesses free of bank conflicts.
+__host__ __device__ constexpr int pad16(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int line_stride(int n) { return n + (n >> 4) + 4; }
+
+struct Geometry {
+    int H, W;
+    int R;        // rows per strip
+    int nstrips;  // H / R
+    int B;        // columns per column block
+    int nblocks;  // W / B
+    int BH;       // rows per binning band (multiple of R)
+    int nbands;   // H / BH
+};
+
+__host__ inline Geometry make_geometry(int H, int W) {
+    Geometry g;
+    g.H = H;
+    g.W = W;
+    g.R = kSetElems / W < H ? kSetElems / W : H;
+    g.nstrips = H / g.R;
+    g.B = kSetElems / H < W ? kSetElems / H : W;
+    g.nblocks = W / g.B;
+    int bh = H / kMaxBands;
+    g.BH = bh > g.R ? bh : g.R;
+    g.nbands = H / g.BH;
+    return g;
+}
+
+// Per-particle record written by the setup pass (64 bytes).  Angles and
+// inverse semi-axes are stored as float-float pairs (hi + lo) rounded from
+// double precision so that the ellipsoid rim can be evaluated with ~2^-44
+// relative error (see thickness()).
+struct __align__(16) PRec {
+    float cx, cy;
+    float ch, cl, sh, sl;     // cos(theta), sin(theta) hi/lo
+    float p0h, p0l, p1h, p1l; // ellipsoid: 1/a, 1/b hi/lo; prism: hx, hy, -, -
+    float T, dn, mu;
+    float g;                  // 0 for an ellipsoid, 2 s_b dx for a prism
+};
+static_assert(sizeof(PRec) == 64, "PRec is 64 bytes");
+
+// Bounding rectangle of the pixels a particle may touch (inclusive), or an
+// empty rectangle (x0 > x1) for a skipped particle.
+struct __align__(8) Rect {
+    int16_t x0, x1, y0, y1;
+};
+
+// Per-scene constants of a launch group (kernel parameters, by value).
+struct SceneDev {
+    int32_t p0;        // first record of the scene (soa column - group base)
+    int32_t n;         // particles
+    int32_t chunk0;    // first binning chunk
+    int32_t pair0;     // first slot of the scene's pair region
+    int32_t pair_cap;  // slots reserved for the scene
+    float two_over_lambda;
+    float prism_g;     // 2 s_b dx
+    float pad_;
+};
+
+// Transfer-function constants of one (scene, modality).
+struct ModeDev {
+    double r2;            // (NA / lambda)^2, cycles^2 / um^2
+    double ox, oy;        // pupil centre shift (cycles / um)
+    double fx_scale;      // 1 / (W dx)
+    double fy_span;       // H dx (um): signed row index per cycle/um
+    float kstep_x, kstep_y;  // 2 pi / (W dx), 2 pi / (H dx)
+    float qoff_x, qoff_y;    // 2 pi (ox, oy)
+    float k0, dz;
+    float dsx, dsy, bias;
+    float scale;          // 1 / (H W)
+    int32_t dic;          // 1 for the DIC factor
+    int32_t pad_;
+};
+
+struct GroupDev {
+    int32_t S;
+    int32_t K;
+    int32_t nchunks;               // total binning chunks
+    int32_t pad_;
+    SceneDev sc[kMaxScenes];
+    ModeDev md[kMaxScenes][kMaxModes];
+};
+
+// Pointers into the workspace for one launch group.
+struct Work {
+    PRec *rec;
+    Rect *rect;
+    int32_t *cnt;       // [nchunks][nbands]: counts, then exclusive prefix
+    int32_t *band_off;  // [S][nbands + 1]
+    int32_t *pairs;     // record indices, per band, ascending
+    float2 *G;          // [S][W/B][H][B] row spectra
+    float2 *Q;          // [S][K][W/B][H][B] filtered columns
+    int32_t *status;    // plan status word
+};
+
+// ---------------------------------------------------------------- status
+__device__ __forceinline__ void latch(int32_t *status, int code) {
+    atomicCAS(status, 0, code);
+}
+
+// ---------------------------------------------------------------- complex
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+// ---------------------------------------------------------------- float-float
+// Error-free transformations (Knuth TwoSum, FMA-based TwoProd; Dekker 1971,
+// Ogita-Rump-Oishi 2005).  The _rn intrinsics keep the compiler from
+// contracting or reordering the compensated steps.
+struct ff {
+    float h, l;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = two_sum(a.h, b.h);
+    float e = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
+    return fast_two_sum(s.h, e);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.h, -a.l}; }
+
+// ---------------------------------------------------------------- geometry
+// Thickness (um) of particle r at pixel centre (x, y) (px).  Ellipsoid:
+// t = T sqrt(1 - (u/a)^2 - (v/b)^2); prism: t = clamp(g min(hx-|u|, hy-|v|),
+// 0, T) with g = 2 s_b dx.  The ellipsoid is first evaluated in float32;
+// where 1 - rho^2 is small (|delta| < 4e-3) the value is recomputed in
+// float-float, because the float32 rounding of rho^2 (~2e-7) would
+// otherwise put an error of order T sqrt(2e-7) on the rim pixels.
+__device__ __forceinline__ float thickness(const PRec &r, float x, float y) {
+    float ex = x - r.cx, ey = y - r.cy;
+    float u = fmaf(r.ch, ex, r.sh * ey);
+    float v = fmaf(r.ch, ey, -r.sh * ex);
+    if (r.g > 0.f) {
+        float d = fminf(r.p0h - fabsf(u), r.p1h - fabsf(v));
+        return fminf(fmaxf(r.g * d, 0.f), r.T);
+    }
+    float ua = u * r.p0h, vb = v * r.p1h;
+    float delta = 1.f - fmaf(ua, ua, vb * vb);
+    if (delta >= 4e-3f) return r.T * sqrtf(delta);
+    if (delta <= -4e-3f) return 0.f;
+    ff exf = two_sum(x, -r.cx);
+    ff eyf = two_sum(y, -r.cy);
+    ff c = {r.ch, r.cl}, s = {r.sh, r.sl};
+    ff uf = ff_add(ff_mul(c, exf), ff_mul(s, eyf));
+    ff vf = ff_add(ff_mul(c, eyf), ff_neg(ff_mul(s, exf)));
+    ff uaf = ff_mul(uf, ff{r.p0h, r.p0l});
+    ff vbf = ff_mul(vf, ff{r.p1h, r.p1l});
+    ff rho2 = ff_add(ff_mul(uaf, uaf), ff_mul(vbf, vbf));
+    ff d = ff_add(ff{1.f, 0.f}, ff_neg(rho2));
+    float dd = d.h + d.l;
+    return dd > 0.f ? r.T * sqrtf(dd) : 0.f;
+}
+
+}  // namespace osog

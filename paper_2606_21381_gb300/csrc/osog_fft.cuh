@@ -1,0 +1,172 @@
+// Shared-memory Stockham FFT for sets of lines held by one CTA.
+//
+// A CTA owns L lines of N complex samples (N a power of two, 32..2048) in
+// shared memory, line l at buf + l * line_stride(N), sample i at pad16(i).
+// The transform runs as a few radix-P passes (P in {4, 8, 16}).  In each
+// pass every thread loads whole butterflies into registers, the CTA
+// synchronises, and the results are written back in Stockham (self-sorting)
+// order, so no bit reversal is needed and a single buffer suffices.
+//
+// Stockham radix-P pass with sub-transform length Ns (product of the radices
+// of the earlier passes), for butterfly j in [0, N/P), k = j mod Ns:
+//     v_r = x[j + r N/P] * w^{r k},   w = exp(-+ 2 pi i / (Ns P))
+//     V   = DFT_P(v)
+//     x'[(j - k) P + k + r Ns] = V_r
+// (the self-sorting formulation of Stockham's autosort FFT, e.g.
+// Govindaraju et al., "High performance discrete Fourier transforms on
+// graphics processors", SC 2008).  The twiddles w^{rk} = W_N^{r k N/(Ns P)}
+// come from a table of W_N^m = exp(-2 pi i m / N) that the host builds in
+// double precision and rounds to float once.  Inverse transforms use the
+// conjugate twiddles and are unnormalised.
+#pragma once
+
+#include "osog_common.cuh"
+
+namespace osog {
+
+// cos and sin of 2 pi m / 16, m = 0..15 (cos(pi/8) = sqrt(2 + sqrt 2) / 2,
+// sin(pi/8) = sqrt(2 - sqrt 2) / 2, cos(pi/4) = sqrt(1/2)).
+__host__ __device__ constexpr float quarter_cos16(int m) {  // m in 0..4
+    return m == 0 ? 1.0f
+         : m == 1 ? 0.92387953251128674f
+         : m == 2 ? 0.70710678118654752f
+         : m == 3 ? 0.38268343236508977f
+         : 0.0f;
+}
+__host__ __device__ constexpr float cos16(int m) {
+    m &= 15;
+    return m <= 4 ? quarter_cos16(m)
+         : m <= 8 ? -quarter_cos16(8 - m)
+         : m <= 12 ? -quarter_cos16(m - 8)
+         : quarter_cos16(16 - m);
+}
+__host__ __device__ constexpr float sin16(int m) { return cos16(m - 4); }
+
+// x * exp(-+ 2 pi i K / P) with K, P compile-time (P divides 16).
+template <int P, int K, bool INV>
+__device__ __forceinline__ float2 twc(float2 x) {
+    constexpr int m = (K * 16 / P) & 15;
+    if constexpr (m == 0) {
+        return x;
+    } else if constexpr (m == 4) {
+        return INV ? make_float2(-x.y, x.x) : make_float2(x.y, -x.x);
+    } else if constexpr (m == 8) {
+        return make_float2(-x.x, -x.y);
+    } else if constexpr (m == 12) {
+        return INV ? make_float2(x.y, -x.x) : make_float2(-x.y, x.x);
+    } else {
+        constexpr float c = cos16(m);
+        constexpr float s = INV ? sin16(m) : -sin16(m);
+        return make_float2(x.x * c - x.y * s, x.x * s + x.y * c);
+    }
+}
+
+template <int P, bool INV, int K = 0>
+__device__ __forceinline__ void twiddle_odds(float2 *o) {
+    if constexpr (K < P / 2) {
+        o[K] = twc<P, K, INV>(o[K]);
+        twiddle_odds<P, INV, K + 1>(o);
+    }
+}
+
+// In-register DFT of P points (radix-2 decimation in time, unrolled).
+template <int P, bool INV>
+__device__ __forceinline__ void dft(float2 *v) {
+    if constexpr (P == 2) {
+        float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else {
+        float2 e[P / 2], o[P / 2];
+#pragma unroll
+        for (int k = 0; k < P / 2; ++k) {
+            e[k] = v[2 * k];
+            o[k] = v[2 * k + 1];
+        }
+        dft<P / 2, INV>(e);
+        dft<P / 2, INV>(o);
+        twiddle_odds<P, INV>(o);
+#pragma unroll
+        for (int k = 0; k < P / 2; ++k) {
+            v[k] = cadd(e[k], o[k]);
+            v[k + P / 2] = csub(e[k], o[k]);
+        }
+    }
+}
+
+// One Stockham pass over L lines of N points.
+template <int N, int L, int P, int NS, bool INV>
+__device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restrict__ tw) {
+    constexpr int NB = N / P;
+    constexpr int TOT = L * NB;
+    constexpr int PER = (TOT + kThreads - 1) / kThreads;
+    constexpr int LS = line_stride(N);
+    float2 v[PER][P];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int b = threadIdx.x + q * kThreads;
+        if (TOT % kThreads == 0 || b < TOT) {
+            const int l = b / NB, j = b % NB;
+            const float2 *src = buf + l * LS;
+#pragma unroll
+            for (int r = 0; r < P; ++r) v[q][r] = src[pad16(j + r * NB)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int b = threadIdx.x + q * kThreads;
+        if (TOT % kThreads == 0 || b < TOT) {
+            const int l = b / NB, j = b % NB;
+            const int k = j & (NS - 1);
+            if constexpr (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < P; ++r) {
+                    const float2 w = __ldg(tw + r * k * (N / (NS * P)));
+                    v[q][r] = INV ? cmulc(v[q][r], w) : cmul(v[q][r], w);
+                }
+            }
+            dft<P, INV>(v[q]);
+            float2 *dst = buf + l * LS;
+            const int base = (j - k) * P + k;
+#pragma unroll
+            for (int r = 0; r < P; ++r) dst[pad16(base + r * NS)] = v[q][r];
+        }
+    }
+    __syncthreads();
+}
+
+// Full FFT of the L lines (forward: exp(-2 pi i jk/N); inverse: conjugate,
+// unnormalised).  Radix plans: 32 = 8.4, 64 = 8.8, 128 = 16.8, 256 = 16.16,
+// 512 = 8.8.8, 1024 = 16.8.8, 2048 = 16.16.8.
+template <int N, int L, bool INV>
+__device__ __forceinline__ void fft_lines(float2 *buf, const float2 *__restrict__ tw) {
+    if constexpr (N == 32) {
+        stockham_pass<N, L, 8, 1, INV>(buf, tw);
+        stockham_pass<N, L, 4, 8, INV>(buf, tw);
+    } else if constexpr (N == 64) {
+        stockham_pass<N, L, 8, 1, INV>(buf, tw);
+        stockham_pass<N, L, 8, 8, INV>(buf, tw);
+    } else if constexpr (N == 128) {
+        stockham_pass<N, L, 16, 1, INV>(buf, tw);
+        stockham_pass<N, L, 8, 16, INV>(buf, tw);
+    } else if constexpr (N == 256) {
+        stockham_pass<N, L, 16, 1, INV>(buf, tw);
+        stockham_pass<N, L, 16, 16, INV>(buf, tw);
+    } else if constexpr (N == 512) {
+        stockham_pass<N, L, 8, 1, INV>(buf, tw);
+        stockham_pass<N, L, 8, 8, INV>(buf, tw);
+        stockham_pass<N, L, 8, 64, INV>(buf, tw);
+    } else if constexpr (N == 1024) {
+        stockham_pass<N, L, 16, 1, INV>(buf, tw);
+        stockham_pass<N, L, 8, 16, INV>(buf, tw);
+        stockham_pass<N, L, 8, 128, INV>(buf, tw);
+    } else {
+        static_assert(N == 2048, "FFT sizes are powers of two in [32, 2048]");
+        stockham_pass<N, L, 16, 1, INV>(buf, tw);
+        stockham_pass<N, L, 16, 16, INV>(buf, tw);
+        stockham_pass<N, L, 8, 256, INV>(buf, tw);
+    }
+}
+
+}  // namespace osog

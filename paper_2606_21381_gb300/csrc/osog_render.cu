@@ -1,0 +1,403 @@
+// Render kernels: raster + exit wave + row FFT, column pass with the
+// optical head, inverse row FFT + intensity.
+//
+// Data flow for one H x W scene (complex64 intermediates in HBM):
+//   strip forward  (CTA per strip of R = 8192/W rows): gathers the OPD and
+//                  ATT of every particle overlapping the strip in ascending
+//                  particle order (Eq. 2, Eq. 7), forms the exit wave
+//                  exp(-ATT) exp(i 2 pi OPD / lambda) (Eq. 2, Eq. 4), runs
+//                  the forward row DFTs and writes G in a column-blocked
+//                  layout [W/B][H][B] so that the column pass reads one
+//                  contiguous block.
+//   column         (CTA per block of B = 8192/H columns): forward column
+//                  DFTs, then for every modality the transfer function of
+//                  Eq. 3 / Eq. 5 / oblique shift times 1/(HW), inverse column
+//                  DFTs, written as Q[m] in the same blocked layout.
+//   strip inverse  (CTA per strip and modality): inverse row DFTs and
+//                  I = |E|^2 (Sec. III.B), float32 image rows.
+#include <math.h>
+
+#include "osog_fft.cuh"
+#include "osog_kernels.h"
+
+namespace osog {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
+
+// Accumulate one particle's OPD / ATT over the pixels [xa, xb] x [ya, yb]
+// of the strip buffer.  Lanes tile the rectangle in a power-of-two grid.
+__device__ __forceinline__ void raster_particle(float2 *buf, int LS, int y0, const PRec &r,
+                                                int xa, int xb, int ya, int yb, int lane) {
+    const int bw = xb - xa + 1;
+    const int lxn = bw >= 32 ? 32 : (bw <= 1 ? 1 : 1 << (32 - __clz(bw - 1)));
+    const int sh = ilog2(lxn);
+    const int lyn = 32 >> sh;
+    const int lx = lane & (lxn - 1), ly = lane >> sh;
+    for (int yy = ya + ly; yy <= yb; yy += lyn) {
+        const float yc = (float)yy + 0.5f;
+        float2 *row = buf + (yy - y0) * LS;
+        for (int xx = xa + lx; xx <= xb; xx += lxn) {
+            const float t = thickness(r, (float)xx + 0.5f, yc);
+            float2 v = row[pad16(xx)];
+            v.x = fmaf(r.dn, t, v.x);
+            v.y = fmaf(r.mu, t, v.y);
+            row[pad16(xx)] = v;
+        }
+    }
+}
+
+// OPD/ATT of the strip [y0, y0 + R) into buf, particles in list order.
+template <int N>
+__device__ void raster_strip(const StripArgs &a, int s, int y0, float2 *buf, int *list,
+                             int *wsum) {
+    constexpr int LS = line_stride(N);
+    constexpr int NW = kThreads / 32;
+    const Geometry &geo = a.geo;
+    const SceneDev &sc = a.sc[s];
+    const int band = y0 / geo.BH;
+    const int32_t *off = a.w.band_off + (size_t)s * (geo.nbands + 1);
+    int hi = min(off[band + 1], sc.pair_cap);
+    int lo = min(off[band], hi);
+    const int32_t *ids = a.w.pairs + sc.pair0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cw = N / NW;
+    const int c0 = warp * cw, c1 = c0 + cw - 1;
+    const int ylast = y0 + geo.R - 1;
+    const unsigned lt = lanemask_lt();
+    for (int base = lo; base < hi; base += kListCap) {
+        const int cnt = min(kListCap, hi - base);
+        int nl = 0;
+        for (int r0 = 0; r0 < cnt; r0 += kThreads) {
+            const int i = r0 + threadIdx.x;
+            int id = -1;
+            bool keep = false;
+            if (i < cnt) {
+                id = ids[base + i];
+                const Rect q = a.w.rect[id];
+                keep = q.y0 <= ylast && q.y1 >= y0;
+            }
+            const unsigned m = __ballot_sync(kFull, keep);
+            if (lane == 0) wsum[warp] = __popc(m);
+            __syncthreads();
+            int before = nl, tot = 0;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const int c = wsum[k];
+                before += k < warp ? c : 0;
+                tot += c;
+            }
+            if (keep) list[before + __popc(m & lt)] = id;
+            __syncthreads();
+            nl += tot;
+        }
+        for (int i0 = 0; i0 < nl; i0 += 32) {
+            const int i = i0 + lane;
+            int id = 0;
+            Rect q = {1, 0, 1, 0};
+            if (i < nl) {
+                id = list[i];
+                q = a.w.rect[id];
+            }
+            const bool ov = i < nl && q.x0 <= c1 && q.x1 >= c0;
+            unsigned m = __ballot_sync(kFull, ov);
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1;
+                const int p = __shfl_sync(kFull, id, src);
+                const int qx0 = __shfl_sync(kFull, (int)q.x0, src);
+                const int qx1 = __shfl_sync(kFull, (int)q.x1, src);
+                const int qy0 = __shfl_sync(kFull, (int)q.y0, src);
+                const int qy1 = __shfl_sync(kFull, (int)q.y1, src);
+                const PRec r = a.w.rec[p];
+                raster_particle(buf, LS, y0, r, max(qx0, c0), min(qx1, c1), max(qy0, y0),
+                                min(qy1, ylast), lane);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(kThreads) k_strip_forward(const __grid_constant__ StripArgs a) {
+    constexpr int L = kSetElems / N;
+    constexpr int LS = line_stride(N);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
+    int *list = reinterpret_cast<int *>(buf + L * LS);
+    int *wsum = list + kListCap;
+    const Geometry &geo = a.geo;
+    const int s = blockIdx.y;
+    const int y0 = blockIdx.x * geo.R;
+    const int R = geo.R;
+    for (int i = threadIdx.x; i < L * LS; i += kThreads) buf[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    if constexpr (MODE == kStripFromMap) {
+        const float2 *src = a.opd_att + (size_t)y0 * N;
+        for (int e = threadIdx.x; e < R * N; e += kThreads)
+            buf[(e / N) * LS + pad16(e % N)] = src[e];
+    } else {
+        raster_strip<N>(a, s, y0, buf, list, wsum);
+    }
+    __syncthreads();
+    if constexpr (MODE == kStripOpdOnly) {
+        float2 *dst = a.opd_out + (size_t)y0 * N;
+        for (int e = threadIdx.x; e < R * N; e += kThreads) dst[e] = buf[(e / N) * LS + pad16(e % N)];
+        return;
+    } else {
+        const float tol = a.sc[s].two_over_lambda;
+        for (int e = threadIdx.x; e < R * N; e += kThreads) {
+            float2 *v = buf + (e / N) * LS + pad16(e % N);
+            float sn, cs;
+            sincospif(v->x * tol, &sn, &cs);
+            const float amp = expf(-v->y);
+            *v = make_float2(amp * cs, amp * sn);
+        }
+        __syncthreads();
+        fft_lines<N, L, false>(buf, a.tw);
+        const int B = geo.B, lb = ilog2(B), lr = ilog2(R);
+        float2 *G = a.w.G + (size_t)s * geo.H * N;
+        for (int e = threadIdx.x; e < R * N; e += kThreads) {
+            const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
+            G[((size_t)bk * geo.H + y0 + r) * B + c] = buf[r * LS + pad16(bk * B + c)];
+        }
+    }
+}
+
+// ------------------------------------------------------------ optical head
+// Interval [lo, hi] of signed row frequencies fy inside the (shifted) pupil
+// circle for column frequency fx, decided in double precision:
+// (fx / (W dx) + ox)^2 + (fy / (H dx) + oy)^2 <= (NA / lambda)^2.
+__device__ __forceinline__ int2 pupil_chord(const ModeDev &md, int fx) {
+    const double ax = (double)fx * md.fx_scale + md.ox;
+    const double rem = md.r2 - ax * ax;
+    if (rem < 0.0) return make_int2(1, 0);
+    const double root = sqrt(rem);
+    const double lo = (-root - md.oy) * md.fy_span;
+    const double hi = (root - md.oy) * md.fy_span;
+    return make_int2((int)ceil(lo), (int)floor(hi));
+}
+
+// Transfer function at signed frequency (fx, fy), including 1/(HW):
+// pupil circ * exp(i dz (sqrt(k0^2 - |q|^2) - k0)) at q = k + k_ill (Eq. 3,
+// oblique shift), times 2i sin(k . ds + theta) for DIC (Eq. 5).  The defocus
+// phase is evaluated as -dz |q|^2 / (sqrt(k0^2 - |q|^2) + k0), which has no
+// cancellation for small |q|.
+__device__ __forceinline__ float2 transfer(const ModeDev &md, int fx, int fy, int2 ch) {
+    if (fy < ch.x || fy > ch.y) return make_float2(0.f, 0.f);
+    const float kx = (float)fx * md.kstep_x, ky = (float)fy * md.kstep_y;
+    const float qx = kx + md.qoff_x, qy = ky + md.qoff_y;
+    const float q2 = fmaf(qx, qx, qy * qy);
+    const float chi = -md.dz * q2 / (sqrtf(fmaxf(fmaf(md.k0, md.k0, -q2), 0.f)) + md.k0);
+    float sn, cs;
+    sincosf(chi, &sn, &cs);
+    float2 h = make_float2(cs, sn);
+    if (md.dic) {
+        const float g = 2.f * sinf(fmaf(kx, md.dsx, fmaf(ky, md.dsy, md.bias)));
+        h = make_float2(-sn * g, cs * g);
+    }
+    return make_float2(h.x * md.scale, h.y * md.scale);
+}
+
+template <int N, bool MULTI>
+__global__ void __launch_bounds__(kThreads) k_column(const __grid_constant__ ColumnArgs a) {
+    constexpr int L = kSetElems / N;
+    constexpr int LS = line_stride(N);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *buf0 = reinterpret_cast<float2 *>(smem_raw);
+    float2 *buf1 = MULTI ? buf0 + L * LS : buf0;
+    int2 *chords = reinterpret_cast<int2 *>(buf1 + L * LS);
+    const Geometry &geo = a.geo;
+    const int s = blockIdx.y, bk = blockIdx.x;
+    const int B = geo.B, lb = ilog2(B), K = a.K;
+    const float2 *G = a.w.G + ((size_t)s * geo.nblocks + bk) * N * B;
+    for (int e = threadIdx.x; e < N * B; e += kThreads)
+        buf0[(e & (B - 1)) * LS + pad16(e >> lb)] = G[e];
+    for (int i = B * LS + threadIdx.x; i < L * LS; i += kThreads) buf0[i] = make_float2(0.f, 0.f);
+    for (int j = threadIdx.x; j < K * B; j += kThreads) {
+        const int m = j >> lb, c = j & (B - 1);
+        const int kx = bk * B + c;
+        const int fx = kx < geo.W / 2 ? kx : kx - geo.W;
+        chords[m * L + c] = pupil_chord(a.md[s][m], fx);
+    }
+    __syncthreads();
+    fft_lines<N, L, false>(buf0, a.tw);
+    for (int m = 0; m < K; ++m) {
+        const ModeDev &md = a.md[s][m];
+        for (int e = threadIdx.x; e < L * N; e += kThreads) {
+            const int c = e / N, y = e % N;
+            float2 v = make_float2(0.f, 0.f);
+            if (c < B) {
+                const int kx = bk * B + c;
+                const int fx = kx < geo.W / 2 ? kx : kx - geo.W;
+                const int fy = y < N / 2 ? y : y - N;
+                v = cmul(buf0[c * LS + pad16(y)], transfer(md, fx, fy, chords[m * L + c]));
+            }
+            buf1[c * LS + pad16(y)] = v;
+        }
+        __syncthreads();
+        fft_lines<N, L, true>(buf1, a.tw);
+        float2 *Qm = a.w.Q + (((size_t)s * K + m) * geo.nblocks + bk) * N * B;
+        for (int e = threadIdx.x; e < N * B; e += kThreads)
+            Qm[e] = buf1[(e & (B - 1)) * LS + pad16(e >> lb)];
+        __syncthreads();
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_strip_inverse(const __grid_constant__ InverseArgs a) {
+    constexpr int L = kSetElems / N;
+    constexpr int LS = line_stride(N);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
+    const Geometry &geo = a.geo;
+    const int K = a.K;
+    const int sm = blockIdx.y;
+    const int y0 = blockIdx.x * geo.R;
+    const int R = geo.R, B = geo.B, lb = ilog2(B), lr = ilog2(R);
+    const float2 *Qm = a.w.Q + (size_t)sm * geo.nblocks * geo.H * B;
+    for (int e = threadIdx.x; e < R * N; e += kThreads) {
+        const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
+        buf[r * LS + pad16(bk * B + c)] = Qm[((size_t)bk * geo.H + y0 + r) * B + c];
+    }
+    for (int i = R * LS + threadIdx.x; i < L * LS; i += kThreads) buf[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    fft_lines<N, L, true>(buf, a.tw);
+    float *img = a.images + ((size_t)sm * geo.H + y0) * N;
+    for (int e = threadIdx.x; e < R * N; e += kThreads) {
+        const float2 v = buf[(e / N) * LS + pad16(e % N)];
+        img[e] = fmaf(v.x, v.x, v.y * v.y);
+    }
+    (void)K;
+}
+
+template <template <int> class F, typename... Args>
+cudaError_t dispatch_n(int n, Args &&...args) {
+    switch (n) {
+        case 32: return F<32>::run(args...);
+        case 64: return F<64>::run(args...);
+        case 128: return F<128>::run(args...);
+        case 256: return F<256>::run(args...);
+        case 512: return F<512>::run(args...);
+        case 1024: return F<1024>::run(args...);
+        case 2048: return F<2048>::run(args...);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int N>
+struct StripFwdLaunch {
+    static cudaError_t run(const StripArgs &a, StripMode mode, cudaStream_t st, size_t smem) {
+        dim3 grid(a.geo.nstrips, a.S);
+        if (mode == kStripRender)
+            k_strip_forward<N, kStripRender><<<grid, kThreads, smem, st>>>(a);
+        else if (mode == kStripOpdOnly)
+            k_strip_forward<N, kStripOpdOnly><<<grid, kThreads, smem, st>>>(a);
+        else
+            k_strip_forward<N, kStripFromMap><<<grid, kThreads, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    static cudaError_t prepare(size_t smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_strip_forward<N, kStripRender>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_strip_forward<N, kStripOpdOnly>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_strip_forward<N, kStripFromMap>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return e;
+    }
+};
+
+template <int N>
+struct ColumnLaunch {
+    static cudaError_t run(const ColumnArgs &a, cudaStream_t st, size_t smem) {
+        dim3 grid(a.geo.nblocks, a.S);
+        if (a.K > 1)
+            k_column<N, true><<<grid, kThreads, smem, st>>>(a);
+        else
+            k_column<N, false><<<grid, kThreads, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    static cudaError_t prepare(size_t smem1, size_t smem2) {
+        cudaError_t e = cudaFuncSetAttribute(k_column<N, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_column<N, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        return e;
+    }
+};
+
+template <int N>
+struct InverseLaunch {
+    static cudaError_t run(const InverseArgs &a, cudaStream_t st, size_t smem) {
+        dim3 grid(a.geo.nstrips, a.S * a.K);
+        k_strip_inverse<N><<<grid, kThreads, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    static cudaError_t prepare(size_t smem) {
+        return cudaFuncSetAttribute(k_strip_inverse<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    }
+};
+
+template <int N>
+struct Prepare {
+    static cudaError_t run(int which, int other) {
+        (void)other;
+        if (which == 0) return StripFwdLaunch<N>::prepare(strip_forward_smem(N));
+        if (which == 1) return ColumnLaunch<N>::prepare(column_smem(N, 1), column_smem(N, 3));
+        return InverseLaunch<N>::prepare(strip_inverse_smem(N));
+    }
+};
+
+}  // namespace
+
+size_t strip_forward_smem(int W) {
+    const int L = kSetElems / W;
+    return (size_t)L * line_stride(W) * sizeof(float2) + kListCap * sizeof(int) + 64;
+}
+
+size_t column_smem(int H, int K) {
+    const int L = kSetElems / H;
+    return (size_t)(K > 1 ? 2 : 1) * L * line_stride(H) * sizeof(float2) +
+           (size_t)kMaxModes * L * sizeof(int2);
+}
+
+size_t strip_inverse_smem(int W) {
+    const int L = kSetElems / W;
+    return (size_t)L * line_stride(W) * sizeof(float2);
+}
+
+cudaError_t prepare_kernels(int H, int W) {
+    cudaError_t e = dispatch_n<Prepare>(W, 0, 0);
+    if (e == cudaSuccess) e = dispatch_n<Prepare>(H, 1, 0);
+    if (e == cudaSuccess) e = dispatch_n<Prepare>(W, 2, 0);
+    return e;
+}
+
+cudaError_t launch_strip_forward(const StripArgs &a, StripMode mode, cudaStream_t st) {
+    return dispatch_n<StripFwdLaunch>(a.geo.W, a, mode, st, strip_forward_smem(a.geo.W));
+}
+
+cudaError_t launch_column(const ColumnArgs &a, cudaStream_t st) {
+    return dispatch_n<ColumnLaunch>(a.geo.H, a, st, column_smem(a.geo.H, a.K));
+}
+
+cudaError_t launch_strip_inverse(const InverseArgs &a, cudaStream_t st) {
+    return dispatch_n<InverseLaunch>(a.geo.W, a, st, strip_inverse_smem(a.geo.W));
+}
+
+}  // namespace osog

@@ -1,0 +1,170 @@
+"""Torch-facing wrapper of libosog: plans, workspaces, device tensors.
+
+PyTorch provides device memory and the current CUDA stream; every step of
+the render runs in libosog's kernels, reached through the C ABI in
+``_lib``.  There is no CPU path: constructing a :class:`Renderer` without a
+CUDA device raises.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import OsogError, Optics, Tuning, check, optics_struct
+
+
+def n_modes(optics: dict) -> int:
+    return bin(int(optics["modes"]) & 7).count("1")
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Renderer:
+    """A plan for H x W canvases plus a growable device workspace."""
+
+    def __init__(self, H: int, W: int, device: torch.device | str | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libosog renders on a CUDA device; none is available")
+        self.device = torch.device(device or "cuda")
+        self.H, self.W = int(H), int(W)
+        self._L = _lib.lib()
+        self.plan = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self._L.osog_plan_create(ctypes.byref(self.plan), self.H, self.W),
+                  "osog_plan_create")
+        self._ws = None
+
+    def close(self) -> None:
+        if self.plan:
+            torch.cuda.synchronize(self.device)
+            self._L.osog_plan_destroy(self.plan)
+            self.plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ workspace
+    def workspace_size(self, n: int, K: int, batch: int = 1) -> int:
+        b = self._L.osog_workspace_size(self.plan, int(n), int(K), int(batch))
+        if b == 0:
+            raise OsogError(1, "osog_workspace_size")
+        return int(b)
+
+    def workspace(self, nbytes: int) -> torch.Tensor:
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def _check_soa(self, soa: torch.Tensor) -> None:
+        if soa.device.type != "cuda" or soa.dtype != torch.float32 or soa.dim() != 2 \
+                or soa.shape[0] != 9 or not soa.is_contiguous():
+            raise ValueError("soa must be a contiguous cuda float32 tensor of shape (9, ld)")
+
+    # ------------------------------------------------------------ entry points
+    def render(self, soa: torch.Tensor, n: int | None, optics: dict, out=None, stream=None):
+        """osog_render: (K, H, W) float32 image of one scene."""
+        self._check_soa(soa)
+        n = soa.shape[1] if n is None else int(n)
+        K = n_modes(optics)
+        if out is None:
+            out = torch.empty((K, self.H, self.W), dtype=torch.float32, device=self.device)
+        ws = self.workspace(self.workspace_size(n, K, 1))
+        o = optics_struct(optics)
+        check(self._L.osog_render(self.plan, _ptr(soa), soa.shape[1], n, ctypes.byref(o),
+                                  _ptr(out), _ptr(ws), ws.numel(), _stream(stream)),
+              "osog_render")
+        return out
+
+    def render_opd(self, soa: torch.Tensor, n: int | None, optics: dict, out=None, stream=None):
+        """osog_render_opd: (H, W, 2) float32 OPD / ATT map."""
+        self._check_soa(soa)
+        n = soa.shape[1] if n is None else int(n)
+        if out is None:
+            out = torch.empty((self.H, self.W, 2), dtype=torch.float32, device=self.device)
+        ws = self.workspace(self.workspace_size(n, 1, 1))
+        o = optics_struct(optics)
+        check(self._L.osog_render_opd(self.plan, _ptr(soa), soa.shape[1], n, ctypes.byref(o),
+                                      _ptr(out), _ptr(ws), ws.numel(), _stream(stream)),
+              "osog_render_opd")
+        return out
+
+    def optics_from_opd(self, opd_att: torch.Tensor, optics: dict, out=None, stream=None):
+        """osog_optics_from_opd: (K, H, W) images from an (H, W, 2) OPD/ATT map."""
+        if opd_att.shape != (self.H, self.W, 2) or opd_att.dtype != torch.float32 \
+                or not opd_att.is_contiguous() or opd_att.device.type != "cuda":
+            raise ValueError("opd_att must be a contiguous cuda float32 (H, W, 2) tensor")
+        K = n_modes(optics)
+        if out is None:
+            out = torch.empty((K, self.H, self.W), dtype=torch.float32, device=self.device)
+        ws = self.workspace(self.workspace_size(0, K, 1))
+        o = optics_struct(optics)
+        check(self._L.osog_optics_from_opd(self.plan, _ptr(opd_att), ctypes.byref(o), _ptr(out),
+                                           _ptr(ws), ws.numel(), _stream(stream)),
+              "osog_optics_from_opd")
+        return out
+
+    def batch(self, soa_all: torch.Tensor, offsets, optics_list: list[dict], out=None,
+              tuning: dict | None = None, stream=None):
+        """osog_batch_submit: (S, K, H, W) images of S scenes."""
+        self._check_soa(soa_all)
+        offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+        S = len(optics_list)
+        if offs.shape != (S + 1,):
+            raise ValueError("offsets must have S + 1 entries")
+        K = n_modes(optics_list[0])
+        if out is None:
+            out = torch.empty((S, K, self.H, self.W), dtype=torch.float32, device=self.device)
+        n_total = int(offs[-1] - offs[0])
+        t = Tuning()
+        t.use_graph = 1
+        if tuning:
+            t.pairs_per_particle = int(tuning.get("pairs_per_particle", 0))
+            t.use_graph = int(tuning.get("use_graph", 1))
+        need = self.workspace_size(n_total, K, S)
+        if t.pairs_per_particle > 8:
+            need = int(need * t.pairs_per_particle / 8) + (1 << 20)
+        ws = self.workspace(need)
+        arr = (Optics * S)(*[optics_struct(o) for o in optics_list])
+        check(self._L.osog_batch_submit(
+            self.plan, _ptr(soa_all), soa_all.shape[1],
+            offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), S, arr, _ptr(out),
+            ctypes.byref(t), _ptr(ws), ws.numel(), _stream(stream)), "osog_batch_submit")
+        return out
+
+    def render_host(self, soa_host: torch.Tensor, n: int, optics: dict,
+                    image_host: torch.Tensor, stream=None):
+        """End-to-end call from host buffers: copy the particle tensor in,
+        render, copy the image out (pinned host tensors, stream ordered)."""
+        dev = soa_host.to(self.device, non_blocking=True)
+        img = self.render(dev, n, optics, stream=stream)
+        image_host.copy_(img, non_blocking=True)
+        return image_host
+
+    # ------------------------------------------------------------ status / timing
+    def sync_status(self, stream=None) -> int:
+        return int(self._L.osog_sync_status(self.plan, _stream(stream)))
+
+    def launch_count(self) -> int:
+        return int(self._L.osog_plan_launch_count(self.plan))
+
+    def profile_begin(self) -> None:
+        check(self._L.osog_profile_begin(self.plan), "osog_profile_begin")
+
+    def profile_end(self, stream=None) -> dict:
+        ms = (ctypes.c_float * 6)()
+        cnt = (ctypes.c_int32 * 6)()
+        check(self._L.osog_profile_end(self.plan, _stream(stream), ms, cnt), "osog_profile_end")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(_lib.KERNEL_CLASSES)}
