@@ -1,0 +1,433 @@
+"""Throughput of the OSOG render path on GB300.
+
+One step = one batched render (osog_batch_submit, replayed as a CUDA graph)
+of 32 scenes of 2048 x 2048 pixels whose particle counts are log-uniform in
+[1,000, 40,000] (one scene holds exactly 40,000), oblique illumination
+(NA 0.4, pupil offset 0.3 NA), inputs resident in HBM.  The value is
+frames/s over all ranks; particles/s, the per-scene-launch comparison, the
+single 40,000-particle scene, per-kernel times and the roofline of the
+dominant kernel are reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank renders its own batch (different seeds), no data
+collective; rank 0 prints one JSON line.  --impl reference times the FP64
+CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2606_21381_gb300 import scenes  # noqa: E402
+
+METRIC = ("frames/s & particles/s at 2048²/40k particles; fwd+bwd ms; "
+          "% HBM roofline")
+SIZE = 2048
+SCENES = 32  # overridden by --scenes (small cases for profiling)
+PAPER_CONTEXT = ("paper: 40,000 particles at 1024x1024 in < 50 ms (> 20 frames/s) "
+                 "on one A100 (Sec. IV.C, Fig. 5)")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------ workload
+def workload(seed_offset: int = 0):
+    counts = scenes.batch_2048_counts(seed=100 + seed_offset, scenes=SCENES)
+    soas, optics = [], []
+    for s, c in enumerate(counts):
+        soa, o = scenes.batch_2048_scene(s + seed_offset, c, SIZE)
+        soas.append(soa)
+        optics.append(o)
+    return counts, soas, optics
+
+
+def workload_config(counts):
+    return {"workload": f"batched render, {SCENES} scenes of {SIZE}x{SIZE}, particles "
+                        f"log-uniform in [1000, 40000] (one scene 40000), oblique NA 0.4",
+            "scenes": SCENES, "H": SIZE, "W": SIZE, "modalities": 1,
+            "particles_per_batch": int(sum(counts)), "max_particles": int(max(counts)),
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap,utilization.gpu")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def __enter__(self):
+        def run():
+            while not self._stop.is_set():
+                try:
+                    out = subprocess.run(
+                        ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                         "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                        timeout=5).stdout.strip()
+                    if out:
+                        self.rows.append([x.strip() for x in out.split(",")])
+                except Exception:
+                    pass
+                self._stop.wait(0.1)
+        self._t = threading.Thread(target=run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        sm, mx, reasons = [], [], set()
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for k, v in zip(names, r[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(k)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    it was taken on the current kernel sources (matching source digest)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    digest = source_digest()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel \
+                and parts[1] == digest:
+            return float(parts[2])
+    return None
+
+
+def source_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2606_21381_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def algorithmic_bytes(kernel: str, counts, H: int, W: int, K: int, pairs: int):
+    """Minimum HBM bytes of one launch of each kernel over the batch."""
+    px = len(counts) * H * W
+    n = int(sum(counts))
+    return {
+        "bin_count": n * (36 + 64 + 8),
+        "bin_scan": 0,
+        "bin_fill": n * 8 + pairs * 4,
+        "strip_forward": px * 8 + n * (64 + 8) + pairs * 4,
+        "column": px * (8 + 8 * K),
+        "strip_inverse": px * (8 * K + 4 * K),
+    }[kernel]
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2606_21381_gb300.render import Renderer
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    counts, soas, optics = workload(seed_offset=1000 * rank)
+    soa_all, offs = scenes.concat(soas)
+    K = 1
+    r = Renderer(SIZE, SIZE, dev)
+    soa_dev = torch.from_numpy(soa_all).to(dev)
+    out = torch.empty((SCENES, K, SIZE, SIZE), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def step(tuning=None):
+        r.batch(soa_dev, offs, optics, out=out, tuning=tuning, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            flush.fill_(1)
+            step()
+        stream.synchronize()
+        if r.sync_status(stream) != 0:
+            raise RuntimeError("device status set during warm-up")
+
+        # ---- timed region: graph replays, per-step events on the launch stream
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        launches0 = r.launch_count()
+        barrier()
+        torch.cuda.synchronize(dev)
+        with ClockSampler(local_rank) as clocks:
+            t0 = time.perf_counter()
+            for i in range(args.steps):
+                flush.fill_(i & 0xff)
+                starts[i].record(stream)
+                step()
+                ends[i].record(stream)
+            torch.cuda.synchronize(dev)
+            wall = time.perf_counter() - t0
+        barrier()
+        launches = r.launch_count() - launches0
+        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        timed_ms = float(sum(step_ms))
+
+        # ---- per-kernel times (same batch, direct launches, events per kernel)
+        r.profile_begin()
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)
+            step()
+        prof = r.profile_end(stream)
+
+        # ---- per-scene launches of the same batch (osog_render per scene)
+        per_scene_ms, single40k, e2e_ms = [float("nan")], [float("nan")], [float("nan")]
+        if args.quick:
+            status = r.sync_status(stream)
+            if status != 0:
+                raise RuntimeError(f"device status {status} after the timed runs")
+            return finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms,
+                          single40k, e2e_ms, launches, clocks, wall, K)
+        per_scene_ms = []
+        singles = [torch.from_numpy(s).to(dev) for s in soas]
+        for i in range(max(2, args.steps // 4)):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+            a.record(stream)
+            for s in range(SCENES):
+                r.render(singles[s], None, optics[s], out=out[s], stream=stream)
+            b.record(stream)
+            stream.synchronize()
+            per_scene_ms.append(a.elapsed_time(b))
+        big = int(np.argmax(counts))
+        single40k = []
+        for i in range(max(5, args.steps)):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+            a.record(stream)
+            r.render(singles[big], None, optics[big], out=out[big], stream=stream)
+            b.record(stream)
+            stream.synchronize()
+            single40k.append(a.elapsed_time(b))
+
+        # ---- end to end from pinned host buffers through the public API
+        soa_host = torch.from_numpy(soa_all).pin_memory()
+        img_host = torch.empty((SCENES, K, SIZE, SIZE), dtype=torch.float32).pin_memory()
+        e2e_ms = []
+        for i in range(max(3, min(args.steps // 2, 20))):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+            a.record(stream)
+            d = soa_host.to(dev, non_blocking=True)
+            r.batch(d, offs, optics, out=out, stream=stream)
+            img_host.copy_(out, non_blocking=True)
+            b.record(stream)
+            stream.synchronize()
+            e2e_ms.append(a.elapsed_time(b))
+        status = r.sync_status(stream)
+        if status != 0:
+            raise RuntimeError(f"device status {status} after the timed runs")
+    return finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms,
+                  single40k, e2e_ms, launches, clocks, wall, K, soas=soas, optics=optics)
+
+
+def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms, single40k,
+           e2e_ms, launches, clocks, wall, K, soas=None, optics=None):
+    import torch
+    import torch.distributed as dist
+
+    # max over ranks of the timed region
+    t = torch.tensor([timed_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    timed_max = float(t.item())
+    frames = SCENES * args.steps * world
+    value = frames / (timed_max / 1e3)
+    if rank != 0:
+        return None
+
+    # dominant kernel and its roofline
+    kernels = {k: {"ms_total": v[0], "launches": v[1],
+                   "ms_per_launch": v[0] / v[1] if v[1] else None}
+               for k, v in prof.items()}
+    tot = sum(v["ms_total"] for v in kernels.values()) or 1.0
+    for v in kernels.values():
+        v["share"] = v["ms_total"] / tot
+    dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
+    pairs_est = int(sum(counts) * 2)
+    peak, peak_src = measured_peaks()
+    bytes_dom = algorithmic_bytes(dom, counts, SIZE, SIZE, K, pairs_est)
+    dur_s = kernels[dom]["ms_per_launch"] / 1e3
+    achieved = bytes_dom / dur_s / 1e9
+    traffic = ncu_traffic(dom)
+    step_bytes = sum(algorithmic_bytes(k, counts, SIZE, SIZE, K, pairs_est) for k in kernels)
+    ms_step = timed_max / args.steps
+    return {
+        "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded scenes shaped like the paper's workloads)",
+        "config": dict(workload_config(counts), parallelism=f"replicas x{world}"),
+        "particles_per_s": round(sum(counts) * args.steps * world / (timed_max / 1e3), 1),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": bytes_dom},
+        "step_roofline": {"algorithmic_bytes": step_bytes,
+                          "achieved_gbs": round(step_bytes / (ms_step / 1e3) / 1e9, 1),
+                          "frac": round(step_bytes / (ms_step / 1e3) / 1e9 / peak, 4)},
+        "kernels": kernels,
+        "per_scene_launches": None if args.quick else {
+                               "ms_per_batch": round(statistics.median(per_scene_ms), 4),
+                               "frames_per_s": round(SCENES / (statistics.median(per_scene_ms) / 1e3), 2),
+                               "batched_speedup": round(statistics.median(per_scene_ms) / ms_step, 3)},
+        "single_scene_40k": None if args.quick else {
+                             "ms": round(statistics.median(single40k), 4),
+                             "frames_per_s": round(1e3 / statistics.median(single40k), 2),
+                             "context": PAPER_CONTEXT},
+        "e2e": None if args.quick else {
+                "value": round(SCENES / (statistics.median(e2e_ms) / 1e3), 2), "unit": "frames/s",
+                "h2d_bytes_per_step": int(soa_all.nbytes),
+                "d2h_bytes_per_step": int(SCENES * K * SIZE * SIZE * 4)},
+        "gpu_launches": int(launches),
+        "clocks": clocks.summary(),
+        "wall_s_timed": round(wall, 4),
+        "cpu_baseline": cpu_baseline(soas, optics, counts)
+        if (world == 1 and soas is not None) else None,
+    }
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_frames(soas, optics, budget_s: float, max_scenes: int, start: int = 0):
+    import oracle
+    done, t0, parts = 0, time.perf_counter(), 0
+    i = start
+    while done < max_scenes:
+        soa = soas[i % len(soas)]
+        oracle.render(soa, soa.shape[1], oracle.make_optics(**optics[i % len(soas)]))
+        done += 1
+        parts += soa.shape[1]
+        i += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    return done, parts, time.perf_counter() - t0
+
+
+def cpu_baseline(soas, optics, counts):
+    import oracle
+    oracle.build()
+    n, parts, dt = oracle_frames(soas, optics, budget_s=15.0, max_scenes=SCENES)
+    return {"value": round(n / dt, 4), "unit": "frames/s", "cores": os.cpu_count(),
+            "kind": "oracle", "particles_per_s": round(parts / dt, 1),
+            "sample": f"{n} of the {SCENES} scenes ({parts} particles), FP64 C oracle, "
+                      f"OpenMP over FFT lines, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    counts, soas, optics = workload()
+    for i in range(args.warmup):
+        oracle_frames(soas, optics, 0.0, 1, start=i)
+    t0 = time.perf_counter()
+    parts = 0
+    for i in range(args.steps):
+        _, p, _ = oracle_frames(soas, optics, 0.0, 1, start=args.warmup + i)
+        parts += p
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "frames/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded scenes shaped like the paper's workloads)",
+            "config": workload_config(counts),
+            "cpu_baseline": {"value": round(value, 4), "unit": "frames/s",
+                             "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"one {SIZE}x{SIZE} scene of the batch per step "
+                                       f"({parts} particles over {args.steps} steps)"},
+            "e2e": {"value": round(value, 4), "unit": "frames/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="osog", choices=["osog", "reference"])
+    ap.add_argument("--scenes", type=int, default=32,
+                    help="scenes per batch (32 is the benchmarked workload)")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed region and per-kernel pass only (profiling runs)")
+    args = ap.parse_args()
+    global SCENES
+    SCENES = args.scenes
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        if args.warmup < 3:
+            args.warmup = 3
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
+        res = run_gpu(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()
