@@ -210,6 +210,32 @@ int osog_profile_begin(osog_plan_t *plan);
 int osog_profile_end(osog_plan_t *plan, osog_stream_t stream, float *ms,
                      int32_t *launches);
 
+/*
+ * Forward render that allocates nothing (no counterpart in the paper).
+ * For callers that cannot call cudaMalloc, or cannot create a plan, because
+ * their host application owns all device memory (a plugin inside another
+ * framework, a real-time loop that may not block on an allocator).  Same
+ * arguments and result as osog_render minus the plan and the workspace: the
+ * twiddle tables, the status word and every intermediate buffer live in
+ * static device arrays of the library (8 MiB of scratch plus 33 KB of
+ * tables) that each GPU loading the library keeps until the process exits.
+ *   Limit: the render's scratch must fit in 8 MiB, e.g. a 256 x 256 canvas
+ *   with 3 modalities and up to ~55,000 particles, or 512 x 512 with one
+ *   modality and up to ~35,000; larger renders return OSOG_ERR_WORKSPACE
+ *   before any device work.  Other host-side errors: OSOG_ERR_INVALID_ARG,
+ *   OSOG_ERR_UNSUPPORTED_SIZE, OSOG_ERR_CUDA; osog_last_error is not set.
+ *   The first call on a device sets that device up (resolves the static
+ *   arrays' addresses, uploads the tables, sets kernel attributes); make it
+ *   before any stream capture.
+ *   All calls share the static scratch: calls that overlap on the GPU (on
+ *   different streams, or from different threads) race and must be ordered
+ *   by the caller.  Invalid particles are skipped as in osog_render, but no
+ *   device status is reported by this entry point.
+ */
+int osog_render_noalloc(const float *soa, int64_t ld, int32_t n,
+                        const osog_optics_t *optics, float *image,
+                        osog_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

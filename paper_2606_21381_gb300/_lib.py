@@ -22,7 +22,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_SIZE", 3: "WORKSPACE",
 EXPORTS = ("osog_plan_create", "osog_plan_destroy", "osog_workspace_size", "osog_render",
            "osog_render_opd", "osog_optics_from_opd", "osog_batch_submit",
            "osog_sync_status", "osog_last_error", "osog_plan_launch_count",
-           "osog_profile_begin", "osog_profile_end")
+           "osog_profile_begin", "osog_profile_end", "osog_render_noalloc")
 
 
 class OsogError(RuntimeError):
@@ -104,6 +104,8 @@ def lib(build_if_missing: bool = True):
     L.osog_profile_begin.restype = ctypes.c_int
     L.osog_profile_end.argtypes = [vp, vp, P(ctypes.c_float), P(i32)]
     L.osog_profile_end.restype = ctypes.c_int
+    L.osog_render_noalloc.argtypes = [vp, i64, i32, P(Optics), vp, vp]
+    L.osog_render_noalloc.restype = ctypes.c_int
     _lib = L
     return L
 
