@@ -53,7 +53,7 @@ constexpr int kMaxTimed = 8192;
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t rec, rect, cnt, band_off, pairs, G, Q, total;
+    size_t rec, rect, cnt, band_off, pairs, G, Q, chord, colrange, total;
 };
 
 // Workspace regions for a launch group of up to S scenes, n records,
@@ -76,6 +76,10 @@ Layout make_layout(const Geometry &geo, int64_t n, int64_t nchunks, int S, int K
     o = align256(o + (size_t)S * geo.H * geo.W * sizeof(float2));
     l.Q = o;
     o = align256(o + (size_t)S * K * geo.H * geo.W * sizeof(float2));
+    l.chord = o;
+    o = align256(o + (size_t)S * kMaxModes * geo.W * sizeof(int2));
+    l.colrange = o;
+    o = align256(o + (size_t)S * sizeof(int2));
     l.total = o;
     return l;
 }
@@ -90,6 +94,8 @@ Work carve(void *ws, const Layout &l, int32_t *status) {
     w.pairs = reinterpret_cast<int32_t *>(b + l.pairs);
     w.G = reinterpret_cast<float2 *>(b + l.G);
     w.Q = reinterpret_cast<float2 *>(b + l.Q);
+    w.chord = reinterpret_cast<int2 *>(b + l.chord);
+    w.colrange = reinterpret_cast<int2 *>(b + l.colrange);
     w.status = status;
     return w;
 }
@@ -213,8 +219,11 @@ int enqueue_group(osog_plan *p, const float *soa, int64_t ld, const int32_t *cou
     if (stage != kFromMap) {
         rc = run_kernel(p, OSOG_KERNEL_BIN_COUNT, st, [&] { return launch_bin_count(soa, ld, gd, geo, w, st); });
         if (rc) return rc;
-        rc = run_kernel(p, OSOG_KERNEL_BIN_SCAN, st, [&] { return launch_bin_scan(gd, geo, w, st); });
-        if (rc) return rc;
+    }
+    // The scan also tabulates the pupil chords used by the render kernels.
+    rc = run_kernel(p, OSOG_KERNEL_BIN_SCAN, st, [&] { return launch_bin_scan(gd, geo, w, st); });
+    if (rc) return rc;
+    if (stage != kFromMap) {
         rc = run_kernel(p, OSOG_KERNEL_BIN_FILL, st, [&] { return launch_bin_fill(gd, geo, w, st); });
         if (rc) return rc;
     }

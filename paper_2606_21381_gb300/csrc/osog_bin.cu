@@ -14,6 +14,8 @@
 //   scan   (one CTA per scene): exclusive prefix of cnt over the scene's
 //          chunks for every band, then over bands, giving each band's list
 //          start in the scene's pair region.
+//          The same kernel tabulates, per scene, the pupil chord of every
+//          column (double precision) and which columns any pupil passes.
 //   fill   (one CTA per chunk): the ballots again; a particle's slot is the
 //          band start + chunk prefix + earlier warps of the chunk + the
 //          popcount of lower lanes.  Each band list is therefore in
@@ -155,7 +157,12 @@ k_bin_count(const float *__restrict__ soa, int64_t ld, const __grid_constant__ G
 __global__ void __launch_bounds__(1024)
 k_bin_scan(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
     __shared__ int total[kMaxBands];
+    __shared__ int frange[2];
     const int s = blockIdx.x;
+    if (threadIdx.x == 0) {
+        frange[0] = INT32_MAX;
+        frange[1] = INT32_MIN;
+    }
     const SceneDev &sc = gd.sc[s];
     const int nch = (s + 1 < gd.S ? gd.sc[s + 1].chunk0 : gd.nchunks) - sc.chunk0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -187,6 +194,24 @@ k_bin_scan(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
         off[geo.nbands] = acc;
         if (acc > sc.pair_cap) latch(w.status, OSOG_ERR_BIN_OVERFLOW);
     }
+    // Pupil chords of every column and modality (double precision), and the
+    // hull [lo, hi] of the signed column frequencies that any modality passes
+    // (each pupil's columns form an interval, so the hull covers them all).
+    for (int kx = threadIdx.x; kx < geo.W; kx += blockDim.x) {
+        const int fx = kx < geo.W / 2 ? kx : kx - geo.W;
+        bool act = false;
+        for (int m = 0; m < gd.K; ++m) {
+            const int2 ch = pupil_chord(gd.md[s][m], fx);
+            w.chord[((size_t)s * gd.K + m) * geo.W + kx] = ch;
+            act = act || ch.x <= ch.y;
+        }
+        if (act) {
+            atomicMin(&frange[0], fx);
+            atomicMax(&frange[1], fx);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) w.colrange[s] = make_int2(frange[0], frange[1]);
 }
 
 __global__ void __launch_bounds__(kChunk)

@@ -18,7 +18,6 @@ constexpr int kChunk = 256;            // particles per binning CTA
 constexpr int kMaxBands = 64;          // bands (binning rows) per canvas
 constexpr int kMaxScenes = 32;         // scenes per launch group
 constexpr int kMaxModes = 3;
-constexpr int kListCap = 1024;         // strip-list entries staged per pass
 
 // Shared-memory index of element i of an FFT line: one float2 of padding
 // after every 16 keeps the strided Stockham accesses free of bank conflicts.
@@ -52,7 +51,7 @@ __host__ inline Geometry make_geometry(int H, int W) {
 // Per-particle record written by the setup pass (64 bytes).  Angles and
 // inverse semi-axes are stored as float-float pairs (hi + lo) rounded from
 // double precision so that the ellipsoid rim can be evaluated with ~2^-44
-// relative error (see thickness()).
+// relative error (see ellipse_delta_ff()).
 struct __align__(16) PRec {
     float cx, cy;
     float ch, cl, sh, sl;     // cos(theta), sin(theta) hi/lo
@@ -113,8 +112,25 @@ struct Work {
     int32_t *pairs;     // record indices, per band, ascending
     float2 *G;          // [S][W/B][H][B] row spectra
     float2 *Q;          // [S][K][W/B][H][B] filtered columns
+    int2 *chord;        // [S][K][W] rows [lo, hi] inside the pupil per column
+    int2 *colrange;     // [S] signed column frequencies [lo, hi] any pupil passes
     int32_t *status;    // plan status word
 };
+
+// ---------------------------------------------------------------- pupil
+// Interval [lo, hi] of signed row frequencies fy inside the (shifted) pupil
+// circle for column frequency fx, decided in double precision:
+// (fx / (W dx) + ox)^2 + (fy / (H dx) + oy)^2 <= (NA / lambda)^2.
+// An empty column returns lo > hi.
+__device__ __forceinline__ int2 pupil_chord(const ModeDev &md, int fx) {
+    const double ax = (double)fx * md.fx_scale + md.ox;
+    const double rem = md.r2 - ax * ax;
+    if (rem < 0.0) return make_int2(1, 0);
+    const double root = sqrt(rem);
+    const double lo = (-root - md.oy) * md.fy_span;
+    const double hi = (root - md.oy) * md.fy_span;
+    return make_int2((int)ceil(lo), (int)floor(hi));
+}
 
 // ---------------------------------------------------------------- status
 __device__ __forceinline__ void latch(int32_t *status, int code) {
@@ -164,24 +180,12 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
 __device__ __forceinline__ ff ff_neg(ff a) { return {-a.h, -a.l}; }
 
 // ---------------------------------------------------------------- geometry
-// Thickness (um) of particle r at pixel centre (x, y) (px).  Ellipsoid:
-// t = T sqrt(1 - (u/a)^2 - (v/b)^2); prism: t = clamp(g min(hx-|u|, hy-|v|),
-// 0, T) with g = 2 s_b dx.  The ellipsoid is first evaluated in float32;
-// where 1 - rho^2 is small (|delta| < 4e-3) the value is recomputed in
-// float-float, because the float32 rounding of rho^2 (~2e-7) would
-// otherwise put an error of order T sqrt(2e-7) on the rim pixels.
-__device__ __forceinline__ float thickness(const PRec &r, float x, float y) {
-    float ex = x - r.cx, ey = y - r.cy;
-    float u = fmaf(r.ch, ex, r.sh * ey);
-    float v = fmaf(r.ch, ey, -r.sh * ex);
-    if (r.g > 0.f) {
-        float d = fminf(r.p0h - fabsf(u), r.p1h - fabsf(v));
-        return fminf(fmaxf(r.g * d, 0.f), r.T);
-    }
-    float ua = u * r.p0h, vb = v * r.p1h;
-    float delta = 1.f - fmaf(ua, ua, vb * vb);
-    if (delta >= 4e-3f) return r.T * sqrtf(delta);
-    if (delta <= -4e-3f) return 0.f;
+// 1 - rho^2 of an ellipsoid at pixel centre (x, y) in float-float, from the
+// FP64-rounded record: u = c ex + s ey, v = -s ex + c ey, rho^2 = (u/a)^2 +
+// (v/b)^2 with ex = x - cx taken exactly (TwoSum).  Used where the float32
+// value of 1 - rho^2 is small: there the float32 rounding of rho^2 (~2e-7)
+// would put an error of order T sqrt(2e-7) on the thickness T sqrt(1 - rho^2).
+__device__ __forceinline__ float ellipse_delta_ff(const PRec &r, float x, float y) {
     ff exf = two_sum(x, -r.cx);
     ff eyf = two_sum(y, -r.cy);
     ff c = {r.ch, r.cl}, s = {r.sh, r.sl};
@@ -191,8 +195,12 @@ __device__ __forceinline__ float thickness(const PRec &r, float x, float y) {
     ff vbf = ff_mul(vf, ff{r.p1h, r.p1l});
     ff rho2 = ff_add(ff_mul(uaf, uaf), ff_mul(vbf, vbf));
     ff d = ff_add(ff{1.f, 0.f}, ff_neg(rho2));
-    float dd = d.h + d.l;
-    return dd > 0.f ? r.T * sqrtf(dd) : 0.f;
+    return d.h + d.l;
 }
+
+// Band of 1 - rho^2 (float32) inside which the ellipsoid is re-evaluated in
+// float-float.  Outside it the float32 error of the thickness is below
+// T * 5e-7 / (2 sqrt(4e-3)) ~ 4e-6 T.
+constexpr float kRimBand = 4e-3f;
 
 }  // namespace osog

@@ -94,22 +94,40 @@ __device__ __forceinline__ void dft(float2 *v) {
     }
 }
 
+// pad16(base + r * stride) - pad16(base) for the bases the Stockham passes
+// write from: with stride >= 16 (a power of two) the carry into the padding
+// term is r * stride / 16; with stride 8 the base's low part k < 8 never
+// carries, leaving r / 2; with stride 1 the base is a multiple of the radix
+// P <= 16 and base % 16 + r < 16.  Every offset folds to a constant once the
+// r loop is unrolled.
+__device__ __forceinline__ constexpr int stride_off(int stride, int r) {
+    return stride >= 16 ? r * (stride + stride / 16) : stride == 8 ? 8 * r + (r >> 1) : r;
+}
+
 // One Stockham pass over L lines of N points.
 template <int N, int L, int P, int NS, bool INV>
 __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restrict__ tw) {
+    static_assert(NS == 1 || NS == 8 || NS % 16 == 0, "unsupported Stockham stride");
     constexpr int NB = N / P;
     constexpr int TOT = L * NB;
     constexpr int PER = (TOT + kThreads - 1) / kThreads;
     constexpr int LS = line_stride(N);
+    constexpr int TWS = N / (NS * P);
     float2 v[PER][P];
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
         const int b = threadIdx.x + q * kThreads;
         if (TOT % kThreads == 0 || b < TOT) {
             const int l = b / NB, j = b % NB;
-            const float2 *src = buf + l * LS;
+            if constexpr (NB % 16 == 0) {
+                const float2 *src = buf + l * LS + pad16(j);
 #pragma unroll
-            for (int r = 0; r < P; ++r) v[q][r] = src[pad16(j + r * NB)];
+                for (int r = 0; r < P; ++r) v[q][r] = src[r * (NB + NB / 16)];
+            } else {
+                const float2 *src = buf + l * LS;
+#pragma unroll
+                for (int r = 0; r < P; ++r) v[q][r] = src[pad16(j + r * NB)];
+            }
         }
     }
     __syncthreads();
@@ -120,17 +138,17 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restr
             const int l = b / NB, j = b % NB;
             const int k = j & (NS - 1);
             if constexpr (NS > 1) {
+                const int kk = k * TWS;
 #pragma unroll
                 for (int r = 1; r < P; ++r) {
-                    const float2 w = __ldg(tw + r * k * (N / (NS * P)));
+                    const float2 w = __ldg(tw + r * kk);
                     v[q][r] = INV ? cmulc(v[q][r], w) : cmul(v[q][r], w);
                 }
             }
             dft<P, INV>(v[q]);
-            float2 *dst = buf + l * LS;
-            const int base = (j - k) * P + k;
+            float2 *dst = buf + l * LS + pad16((j - k) * P + k);
 #pragma unroll
-            for (int r = 0; r < P; ++r) dst[pad16(base + r * NS)] = v[q][r];
+            for (int r = 0; r < P; ++r) dst[stride_off(NS, r)] = v[q][r];
         }
     }
     __syncthreads();

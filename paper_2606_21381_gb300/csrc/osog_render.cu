@@ -35,92 +35,127 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 __device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
 
 // Accumulate one particle's OPD / ATT over the pixels [xa, xb] x [ya, yb]
-// of the strip buffer.  Lanes tile the rectangle in a power-of-two grid.
+// of the strip buffer.  The warp's lanes cover the particle's rows (the
+// next power of two of their count, at most 32) times 32 / that many
+// consecutive columns, stepping across the columns.
+//   ellipsoid: t = T sqrt(1 - rho^2), rho^2 = u'^2 + v'^2 with
+//              u' = (c ex + s ey) / a, v' = (-s ex + c ey) / b, evaluated
+//              in float32 and redone in float-float inside the rim band;
+//   prism:     t = clamp(g min(hx - |u|, hy - |v|), 0, T), g = 2 s_b dx.
 __device__ __forceinline__ void raster_particle(float2 *buf, int LS, int y0, const PRec &r,
                                                 int xa, int xb, int ya, int yb, int lane) {
-    const int bw = xb - xa + 1;
-    const int lxn = bw >= 32 ? 32 : (bw <= 1 ? 1 : 1 << (32 - __clz(bw - 1)));
-    const int sh = ilog2(lxn);
-    const int lyn = 32 >> sh;
-    const int lx = lane & (lxn - 1), ly = lane >> sh;
-    for (int yy = ya + ly; yy <= yb; yy += lyn) {
-        const float yc = (float)yy + 0.5f;
-        float2 *row = buf + (yy - y0) * LS;
-        for (int xx = xa + lx; xx <= xb; xx += lxn) {
-            const float t = thickness(r, (float)xx + 0.5f, yc);
-            float2 v = row[pad16(xx)];
-            v.x = fmaf(r.dn, t, v.x);
-            v.y = fmaf(r.mu, t, v.y);
-            row[pad16(xx)] = v;
+    const int bh = yb - ya + 1;
+    const int lyn = bh >= 32 ? 32 : (bh <= 1 ? 1 : 1 << (32 - __clz(bh - 1)));
+    const int lxn = 32 / lyn;
+    const int shx = ilog2(lxn);
+    const int lx = lane & (lxn - 1), ly = lane >> shx;
+    if (r.g > 0.f) {
+        for (int yy = ya + ly; yy <= yb; yy += lyn) {
+            const float ey = ((float)yy + 0.5f) - r.cy;
+            const float s_ey = r.sh * ey, c_ey = r.ch * ey;
+            float2 *row = buf + (yy - y0) * LS;
+            for (int xx = xa + lx; xx <= xb; xx += lxn) {
+                const float ex = ((float)xx + 0.5f) - r.cx;
+                const float u = fmaf(r.ch, ex, s_ey);
+                const float v = fmaf(-r.sh, ex, c_ey);
+                const float d = fminf(r.p0h - fabsf(u), r.p1h - fabsf(v));
+                const float t = fminf(fmaxf(r.g * d, 0.f), r.T);
+                float2 acc = row[pad16(xx)];
+                acc.x = fmaf(r.dn, t, acc.x);
+                acc.y = fmaf(r.mu, t, acc.y);
+                row[pad16(xx)] = acc;
+            }
+        }
+    } else {
+        const float cia = r.ch * r.p0h, sia = r.sh * r.p0h;
+        const float cib = r.ch * r.p1h, sib = r.sh * r.p1h;
+        for (int yy = ya + ly; yy <= yb; yy += lyn) {
+            const float yc = (float)yy + 0.5f;
+            const float ey = yc - r.cy;
+            const float u0 = sia * ey, v0 = cib * ey;
+            float2 *row = buf + (yy - y0) * LS;
+            for (int xx = xa + lx; xx <= xb; xx += lxn) {
+                const float xc = (float)xx + 0.5f;
+                const float ex = xc - r.cx;
+                const float ua = fmaf(cia, ex, u0);
+                const float vb = fmaf(-sib, ex, v0);
+                float delta = 1.f - fmaf(ua, ua, vb * vb);
+                if (delta < kRimBand) {
+                    if (delta <= -kRimBand) continue;
+                    delta = ellipse_delta_ff(r, xc, yc);
+                    if (!(delta > 0.f)) continue;
+                }
+                const float t = r.T * delta * rsqrtf(delta);
+                float2 acc = row[pad16(xx)];
+                acc.x = fmaf(r.dn, t, acc.x);
+                acc.y = fmaf(r.mu, t, acc.y);
+                row[pad16(xx)] = acc;
+            }
         }
     }
 }
 
 // OPD/ATT of the strip [y0, y0 + R) into buf, particles in list order.
+// The band list is consumed kThreads entries at a time: every thread tests
+// one entry against the strip's rows and the kept entries are compacted, in
+// order, into shared memory together with their records (one parallel
+// global load per round instead of one dependent load per particle).  Each
+// warp then rasterises, in order, the staged particles that overlap its own
+// N/8 columns.
 template <int N>
-__device__ void raster_strip(const StripArgs &a, int s, int y0, float2 *buf, int *list,
-                             int *wsum) {
+__device__ void raster_strip(const StripArgs &a, int s, int y0, float2 *buf, PRec *srec,
+                             Rect *srect, int *wsum) {
     constexpr int LS = line_stride(N);
     constexpr int NW = kThreads / 32;
     const Geometry &geo = a.geo;
     const SceneDev &sc = a.sc[s];
     const int band = y0 / geo.BH;
     const int32_t *off = a.w.band_off + (size_t)s * (geo.nbands + 1);
-    int hi = min(off[band + 1], sc.pair_cap);
-    int lo = min(off[band], hi);
+    const int hi = min(off[band + 1], sc.pair_cap);
+    const int lo = min(off[band], hi);
     const int32_t *ids = a.w.pairs + sc.pair0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cw = N / NW;
     const int c0 = warp * cw, c1 = c0 + cw - 1;
     const int ylast = y0 + geo.R - 1;
     const unsigned lt = lanemask_lt();
-    for (int base = lo; base < hi; base += kListCap) {
-        const int cnt = min(kListCap, hi - base);
-        int nl = 0;
-        for (int r0 = 0; r0 < cnt; r0 += kThreads) {
-            const int i = r0 + threadIdx.x;
-            int id = -1;
-            bool keep = false;
-            if (i < cnt) {
-                id = ids[base + i];
-                const Rect q = a.w.rect[id];
-                keep = q.y0 <= ylast && q.y1 >= y0;
-            }
-            const unsigned m = __ballot_sync(kFull, keep);
-            if (lane == 0) wsum[warp] = __popc(m);
-            __syncthreads();
-            int before = nl, tot = 0;
-#pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                const int c = wsum[k];
-                before += k < warp ? c : 0;
-                tot += c;
-            }
-            if (keep) list[before + __popc(m & lt)] = id;
-            __syncthreads();
-            nl += tot;
+    for (int base = lo; base < hi; base += kThreads) {
+        const int i = base + threadIdx.x;
+        int id = 0;
+        Rect q = {1, 0, 1, 0};
+        if (i < hi) {
+            id = ids[i];
+            q = a.w.rect[id];
         }
+        const bool keep = i < hi && q.y0 <= ylast && q.y1 >= y0;
+        const unsigned m = __ballot_sync(kFull, keep);
+        if (lane == 0) wsum[warp] = __popc(m);
+        __syncthreads();
+        int before = 0, nl = 0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            const int c = wsum[k];
+            before += k < warp ? c : 0;
+            nl += c;
+        }
+        if (keep) {
+            const int slot = before + __popc(m & lt);
+            srect[slot] = q;
+            srec[slot] = a.w.rec[id];
+        }
+        __syncthreads();
         for (int i0 = 0; i0 < nl; i0 += 32) {
-            const int i = i0 + lane;
-            int id = 0;
-            Rect q = {1, 0, 1, 0};
-            if (i < nl) {
-                id = list[i];
-                q = a.w.rect[id];
-            }
-            const bool ov = i < nl && q.x0 <= c1 && q.x1 >= c0;
-            unsigned m = __ballot_sync(kFull, ov);
-            while (m) {
-                const int src = __ffs(m) - 1;
-                m &= m - 1;
-                const int p = __shfl_sync(kFull, id, src);
-                const int qx0 = __shfl_sync(kFull, (int)q.x0, src);
-                const int qx1 = __shfl_sync(kFull, (int)q.x1, src);
-                const int qy0 = __shfl_sync(kFull, (int)q.y0, src);
-                const int qy1 = __shfl_sync(kFull, (int)q.y1, src);
-                const PRec r = a.w.rec[p];
-                raster_particle(buf, LS, y0, r, max(qx0, c0), min(qx1, c1), max(qy0, y0),
-                                min(qy1, ylast), lane);
+            const int k = i0 + lane;
+            Rect r = {1, 0, 1, 0};
+            if (k < nl) r = srect[k];
+            unsigned mm = __ballot_sync(kFull, k < nl && r.x0 <= c1 && r.x1 >= c0);
+            while (mm) {
+                const int src = __ffs(mm) - 1;
+                mm &= mm - 1;
+                const Rect rq = srect[i0 + src];
+                const PRec rec = srec[i0 + src];
+                raster_particle(buf, LS, y0, rec, max((int)rq.x0, c0), min((int)rq.x1, c1),
+                                max((int)rq.y0, y0), min((int)rq.y1, ylast), lane);
                 __syncwarp();
             }
         }
@@ -129,13 +164,14 @@ __device__ void raster_strip(const StripArgs &a, int s, int y0, float2 *buf, int
 }
 
 template <int N, int MODE>
-__global__ void __launch_bounds__(kThreads) k_strip_forward(const __grid_constant__ StripArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_strip_forward(const __grid_constant__ StripArgs a) {
     constexpr int L = kSetElems / N;
     constexpr int LS = line_stride(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
-    int *list = reinterpret_cast<int *>(buf + L * LS);
-    int *wsum = list + kListCap;
+    PRec *srec = reinterpret_cast<PRec *>(buf + L * LS);
+    Rect *srect = reinterpret_cast<Rect *>(srec + kThreads);
+    int *wsum = reinterpret_cast<int *>(srect + kThreads);
     const Geometry &geo = a.geo;
     const int s = blockIdx.y;
     const int y0 = blockIdx.x * geo.R;
@@ -147,7 +183,7 @@ __global__ void __launch_bounds__(kThreads) k_strip_forward(const __grid_constan
         for (int e = threadIdx.x; e < R * N; e += kThreads)
             buf[(e / N) * LS + pad16(e % N)] = src[e];
     } else {
-        raster_strip<N>(a, s, y0, buf, list, wsum);
+        raster_strip<N>(a, s, y0, buf, srec, srect, wsum);
     }
     __syncthreads();
     if constexpr (MODE == kStripOpdOnly) {
@@ -167,34 +203,24 @@ __global__ void __launch_bounds__(kThreads) k_strip_forward(const __grid_constan
         fft_lines<N, L, false>(buf, a.tw);
         const int B = geo.B, lb = ilog2(B), lr = ilog2(R);
         float2 *G = a.w.G + (size_t)s * geo.H * N;
+        const int2 cr = a.w.colrange[s];
         for (int e = threadIdx.x; e < R * N; e += kThreads) {
             const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
-            G[((size_t)bk * geo.H + y0 + r) * B + c] = buf[r * LS + pad16(bk * B + c)];
+            const int kx = bk * B + c, fx = kx < N / 2 ? kx : kx - N;
+            if (fx >= cr.x && fx <= cr.y)  // columns outside every pupil are never read
+                G[((size_t)bk * geo.H + y0 + r) * B + c] = buf[r * LS + pad16(kx)];
         }
     }
 }
 
 // ------------------------------------------------------------ optical head
-// Interval [lo, hi] of signed row frequencies fy inside the (shifted) pupil
-// circle for column frequency fx, decided in double precision:
-// (fx / (W dx) + ox)^2 + (fy / (H dx) + oy)^2 <= (NA / lambda)^2.
-__device__ __forceinline__ int2 pupil_chord(const ModeDev &md, int fx) {
-    const double ax = (double)fx * md.fx_scale + md.ox;
-    const double rem = md.r2 - ax * ax;
-    if (rem < 0.0) return make_int2(1, 0);
-    const double root = sqrt(rem);
-    const double lo = (-root - md.oy) * md.fy_span;
-    const double hi = (root - md.oy) * md.fy_span;
-    return make_int2((int)ceil(lo), (int)floor(hi));
-}
-
-// Transfer function at signed frequency (fx, fy), including 1/(HW):
+// Transfer function at signed frequency (fx, fy) inside the pupil chord,
+// including 1/(HW):
 // pupil circ * exp(i dz (sqrt(k0^2 - |q|^2) - k0)) at q = k + k_ill (Eq. 3,
 // oblique shift), times 2i sin(k . ds + theta) for DIC (Eq. 5).  The defocus
 // phase is evaluated as -dz |q|^2 / (sqrt(k0^2 - |q|^2) + k0), which has no
 // cancellation for small |q|.
-__device__ __forceinline__ float2 transfer(const ModeDev &md, int fx, int fy, int2 ch) {
-    if (fy < ch.x || fy > ch.y) return make_float2(0.f, 0.f);
+__device__ __forceinline__ float2 transfer(const ModeDev &md, int fx, int fy) {
     const float kx = (float)fx * md.kstep_x, ky = (float)fy * md.kstep_y;
     const float qx = kx + md.qoff_x, qy = ky + md.qoff_y;
     const float q2 = fmaf(qx, qx, qy * qy);
@@ -210,7 +236,7 @@ __device__ __forceinline__ float2 transfer(const ModeDev &md, int fx, int fy, in
 }
 
 template <int N, bool MULTI>
-__global__ void __launch_bounds__(kThreads) k_column(const __grid_constant__ ColumnArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_column(const __grid_constant__ ColumnArgs a) {
     constexpr int L = kSetElems / N;
     constexpr int LS = line_stride(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -220,15 +246,25 @@ __global__ void __launch_bounds__(kThreads) k_column(const __grid_constant__ Col
     const Geometry &geo = a.geo;
     const int s = blockIdx.y, bk = blockIdx.x;
     const int B = geo.B, lb = ilog2(B), K = a.K;
+    const int2 cr = a.w.colrange[s];
+    // A block whose columns all lie outside every pupil has nothing to filter:
+    // its Q block is never read.  The block's unsigned columns [u0, u1] map to
+    // signed frequencies [u0, min(u1, W/2 - 1)] and [max(u0, W/2), u1] - W.
+    const int u0 = bk * B, u1 = u0 + B - 1, half = geo.W / 2;
+    const bool lo_part = u0 < half && u0 <= cr.y && min(u1, half - 1) >= cr.x;
+    const bool hi_part = u1 >= half && max(u0, half) - geo.W <= cr.y && u1 - geo.W >= cr.x;
+    if (!lo_part && !hi_part) return;
     const float2 *G = a.w.G + ((size_t)s * geo.nblocks + bk) * N * B;
-    for (int e = threadIdx.x; e < N * B; e += kThreads)
-        buf0[(e & (B - 1)) * LS + pad16(e >> lb)] = G[e];
+    for (int e = threadIdx.x; e < N * B; e += kThreads) {
+        const int c = e & (B - 1);
+        const int kx = u0 + c, fx = kx < half ? kx : kx - geo.W;
+        const bool on = fx >= cr.x && fx <= cr.y;
+        buf0[c * LS + pad16(e >> lb)] = on ? G[e] : make_float2(0.f, 0.f);
+    }
     for (int i = B * LS + threadIdx.x; i < L * LS; i += kThreads) buf0[i] = make_float2(0.f, 0.f);
     for (int j = threadIdx.x; j < K * B; j += kThreads) {
         const int m = j >> lb, c = j & (B - 1);
-        const int kx = bk * B + c;
-        const int fx = kx < geo.W / 2 ? kx : kx - geo.W;
-        chords[m * L + c] = pupil_chord(a.md[s][m], fx);
+        chords[m * L + c] = a.w.chord[((size_t)s * K + m) * geo.W + bk * B + c];
     }
     __syncthreads();
     fft_lines<N, L, false>(buf0, a.tw);
@@ -241,7 +277,9 @@ __global__ void __launch_bounds__(kThreads) k_column(const __grid_constant__ Col
                 const int kx = bk * B + c;
                 const int fx = kx < geo.W / 2 ? kx : kx - geo.W;
                 const int fy = y < N / 2 ? y : y - N;
-                v = cmul(buf0[c * LS + pad16(y)], transfer(md, fx, fy, chords[m * L + c]));
+                const int2 ch = chords[m * L + c];
+                if (fy >= ch.x && fy <= ch.y)
+                    v = cmul(buf0[c * LS + pad16(y)], transfer(md, fx, fy));
             }
             buf1[c * LS + pad16(y)] = v;
         }
@@ -255,7 +293,7 @@ __global__ void __launch_bounds__(kThreads) k_column(const __grid_constant__ Col
 }
 
 template <int N>
-__global__ void __launch_bounds__(kThreads) k_strip_inverse(const __grid_constant__ InverseArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_strip_inverse(const __grid_constant__ InverseArgs a) {
     constexpr int L = kSetElems / N;
     constexpr int LS = line_stride(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -266,9 +304,13 @@ __global__ void __launch_bounds__(kThreads) k_strip_inverse(const __grid_constan
     const int y0 = blockIdx.x * geo.R;
     const int R = geo.R, B = geo.B, lb = ilog2(B), lr = ilog2(R);
     const float2 *Qm = a.w.Q + (size_t)sm * geo.nblocks * geo.H * B;
+    const int2 cr = a.w.colrange[sm / K];
     for (int e = threadIdx.x; e < R * N; e += kThreads) {
         const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
-        buf[r * LS + pad16(bk * B + c)] = Qm[((size_t)bk * geo.H + y0 + r) * B + c];
+        const int kx = bk * B + c, fx = kx < N / 2 ? kx : kx - N;
+        buf[r * LS + pad16(kx)] = fx >= cr.x && fx <= cr.y
+                                      ? Qm[((size_t)bk * geo.H + y0 + r) * B + c]
+                                      : make_float2(0.f, 0.f);
     }
     for (int i = R * LS + threadIdx.x; i < L * LS; i += kThreads) buf[i] = make_float2(0.f, 0.f);
     __syncthreads();
@@ -278,7 +320,6 @@ __global__ void __launch_bounds__(kThreads) k_strip_inverse(const __grid_constan
         const float2 v = buf[(e / N) * LS + pad16(e % N)];
         img[e] = fmaf(v.x, v.x, v.y * v.y);
     }
-    (void)K;
 }
 
 template <template <int> class F, typename... Args>
@@ -367,7 +408,8 @@ struct Prepare {
 
 size_t strip_forward_smem(int W) {
     const int L = kSetElems / W;
-    return (size_t)L * line_stride(W) * sizeof(float2) + kListCap * sizeof(int) + 64;
+    return (size_t)L * line_stride(W) * sizeof(float2) + kThreads * (sizeof(PRec) + sizeof(Rect)) +
+           64;
 }
 
 size_t column_smem(int H, int K) {
