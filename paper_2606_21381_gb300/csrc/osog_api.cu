@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include "osog_fft.cuh"
 #include "osog_kernels.h"
 
 using namespace osog;
@@ -13,8 +14,8 @@ using namespace osog;
 struct osog_plan {
     int H = 0, W = 0;
     Geometry geo{};
-    float2 *tw_w = nullptr;   // W-point twiddles exp(-2 pi i k / W)
-    float2 *tw_h = nullptr;   // H-point twiddles (aliases tw_w when H == W)
+    float2 *tw_w = nullptr;   // twiddle tables of the W-point transform (W entries)
+    float2 *tw_h = nullptr;   // twiddle tables of the H-point transform (H entries)
     int32_t *status = nullptr;
     int32_t *status_host = nullptr;  // pinned
     int64_t launches = 0;
@@ -291,11 +292,8 @@ int osog_plan_create(osog_plan_t **out, int32_t H, int32_t W) {
     if (e == cudaSuccess) e = cudaMallocHost(&p->status_host, sizeof(int32_t));
     if (e == cudaSuccess) {
         std::vector<float2> tw(W + H);
-        const double two_pi = 6.283185307179586476925286766559;
-        for (int k = 0; k < W; ++k)
-            tw[k] = make_float2((float)cos(two_pi * k / W), (float)-sin(two_pi * k / W));
-        for (int k = 0; k < H; ++k)
-            tw[W + k] = make_float2((float)cos(two_pi * k / H), (float)-sin(two_pi * k / H));
+        fill_twiddles(W, tw.data());
+        fill_twiddles(H, tw.data() + W);
         p->tw_h = p->tw_w + W;
         e = cudaMemcpy(p->tw_w, tw.data(), sizeof(float2) * (W + H), cudaMemcpyHostToDevice);
     }

@@ -13,7 +13,7 @@ namespace osog {
 // shared memory: a strip of R = 8192 / W full rows, or a block of
 // B = 8192 / H full columns (fewer when the canvas is smaller).
 constexpr int kSetElems = 8192;
-constexpr int kThreads = 256;          // threads of every FFT-bearing CTA
+constexpr int kThreads = 512;          // threads of every FFT-bearing CTA
 constexpr int kChunk = 256;            // particles per binning CTA
 constexpr int kMaxBands = 64;          // bands (binning rows) per canvas
 constexpr int kMaxScenes = 32;         // scenes per launch group

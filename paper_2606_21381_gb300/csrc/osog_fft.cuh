@@ -14,11 +14,15 @@
 //     x'[(j - k) P + k + r Ns] = V_r
 // (the self-sorting formulation of Stockham's autosort FFT, e.g.
 // Govindaraju et al., "High performance discrete Fourier transforms on
-// graphics processors", SC 2008).  The twiddles w^{rk} = W_N^{r k N/(Ns P)}
-// come from a table of W_N^m = exp(-2 pi i m / N) that the host builds in
-// double precision and rounds to float once.  Inverse transforms use the
-// conjugate twiddles and are unnormalised.
+// graphics processors", SC 2008).  The twiddles w^{rk} come from per-pass
+// tables laid out [r - 1][k] (so the lanes of a warp, which hold
+// consecutive k, read consecutive entries) that the host builds in double
+// precision and rounds to float once; the tables of all passes of an
+// N-point transform fit in N entries.  Inverse transforms use the conjugate
+// twiddles and are unnormalised.
 #pragma once
+
+#include <math.h>
 
 #include "osog_common.cuh"
 
@@ -94,6 +98,27 @@ __device__ __forceinline__ void dft(float2 *v) {
     }
 }
 
+// Radix plans: 32 = 8.4, 64 = 8.8, 128 = 16.8, 256 = 16.16, 512 = 8.8.8,
+// 1024 = 16.8.8, 2048 = 16.16.8.
+__host__ __device__ constexpr int fft_passes(int n) { return n >= 512 ? 3 : 2; }
+__host__ __device__ constexpr int fft_radix(int n, int p) {
+    return n == 32 ? (p == 0 ? 8 : 4)
+         : n == 64 ? 8
+         : n == 128 ? (p == 0 ? 16 : 8)
+         : n == 256 ? 16
+         : n == 512 ? 8
+         : n == 1024 ? (p == 0 ? 16 : 8)
+         : (p < 2 ? 16 : 8);
+}
+__host__ __device__ constexpr int fft_ns(int n, int p) {  // sub-transform length before pass p
+    return p == 0 ? 1 : fft_ns(n, p - 1) * fft_radix(n, p - 1);
+}
+__host__ __device__ constexpr int fft_twoff(int n, int p) {  // start of pass p's table
+    return p == 0 ? 0
+                  : fft_twoff(n, p - 1) +
+                        (fft_ns(n, p - 1) > 1 ? (fft_radix(n, p - 1) - 1) * fft_ns(n, p - 1) : 0);
+}
+
 // pad16(base + r * stride) - pad16(base) for the bases the Stockham passes
 // write from: with stride >= 16 (a power of two) the carry into the padding
 // term is r * stride / 16; with stride 8 the base's low part k < 8 never
@@ -112,7 +137,6 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restr
     constexpr int TOT = L * NB;
     constexpr int PER = (TOT + kThreads - 1) / kThreads;
     constexpr int LS = line_stride(N);
-    constexpr int TWS = N / (NS * P);
     float2 v[PER][P];
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
@@ -138,10 +162,10 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restr
             const int l = b / NB, j = b % NB;
             const int k = j & (NS - 1);
             if constexpr (NS > 1) {
-                const int kk = k * TWS;
+                const float2 *t = tw + k;  // this pass's table, entry [r - 1][k]
 #pragma unroll
                 for (int r = 1; r < P; ++r) {
-                    const float2 w = __ldg(tw + r * kk);
+                    const float2 w = __ldg(t + (r - 1) * NS);
                     v[q][r] = INV ? cmulc(v[q][r], w) : cmul(v[q][r], w);
                 }
             }
@@ -155,35 +179,33 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restr
 }
 
 // Full FFT of the L lines (forward: exp(-2 pi i jk/N); inverse: conjugate,
-// unnormalised).  Radix plans: 32 = 8.4, 64 = 8.8, 128 = 16.8, 256 = 16.16,
-// 512 = 8.8.8, 1024 = 16.8.8, 2048 = 16.16.8.
-template <int N, int L, bool INV>
+// unnormalised), following the radix plan above.  tw is the N-point
+// transform's table block.
+template <int N, int L, bool INV, int PASS = 0>
 __device__ __forceinline__ void fft_lines(float2 *buf, const float2 *__restrict__ tw) {
-    if constexpr (N == 32) {
-        stockham_pass<N, L, 8, 1, INV>(buf, tw);
-        stockham_pass<N, L, 4, 8, INV>(buf, tw);
-    } else if constexpr (N == 64) {
-        stockham_pass<N, L, 8, 1, INV>(buf, tw);
-        stockham_pass<N, L, 8, 8, INV>(buf, tw);
-    } else if constexpr (N == 128) {
-        stockham_pass<N, L, 16, 1, INV>(buf, tw);
-        stockham_pass<N, L, 8, 16, INV>(buf, tw);
-    } else if constexpr (N == 256) {
-        stockham_pass<N, L, 16, 1, INV>(buf, tw);
-        stockham_pass<N, L, 16, 16, INV>(buf, tw);
-    } else if constexpr (N == 512) {
-        stockham_pass<N, L, 8, 1, INV>(buf, tw);
-        stockham_pass<N, L, 8, 8, INV>(buf, tw);
-        stockham_pass<N, L, 8, 64, INV>(buf, tw);
-    } else if constexpr (N == 1024) {
-        stockham_pass<N, L, 16, 1, INV>(buf, tw);
-        stockham_pass<N, L, 8, 16, INV>(buf, tw);
-        stockham_pass<N, L, 8, 128, INV>(buf, tw);
-    } else {
-        static_assert(N == 2048, "FFT sizes are powers of two in [32, 2048]");
-        stockham_pass<N, L, 16, 1, INV>(buf, tw);
-        stockham_pass<N, L, 16, 16, INV>(buf, tw);
-        stockham_pass<N, L, 8, 256, INV>(buf, tw);
+    if constexpr (PASS < fft_passes(N)) {
+        stockham_pass<N, L, fft_radix(N, PASS), fft_ns(N, PASS), INV>(buf,
+                                                                      tw + fft_twoff(N, PASS));
+        fft_lines<N, L, INV, PASS + 1>(buf, tw);
+    }
+}
+
+// Host: the twiddle tables of an n-point transform, n entries, in double
+// precision rounded once to float: pass p's block holds
+// exp(-2 pi i r k / (Ns P)) at [(r - 1) Ns + k], r = 1..P-1, k = 0..Ns-1.
+__host__ inline void fill_twiddles(int n, float2 *out) {
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int i = 0; i < n; ++i) out[i] = make_float2(0.f, 0.f);
+    for (int p = 0; p < fft_passes(n); ++p) {
+        const int P = fft_radix(n, p), NS = fft_ns(n, p);
+        if (NS == 1) continue;
+        float2 *t = out + fft_twoff(n, p);
+        for (int r = 1; r < P; ++r)
+            for (int k = 0; k < NS; ++k) {
+                const long m = (long)r * k % (long)(NS * P);
+                const double ang = two_pi * (double)m / (double)(NS * P);
+                t[(r - 1) * NS + k] = make_float2((float)cos(ang), (float)-sin(ang));
+            }
     }
 }
 

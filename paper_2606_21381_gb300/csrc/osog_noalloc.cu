@@ -14,6 +14,7 @@
 #include <math.h>
 #include <mutex>
 
+#include "osog_fft.cuh"
 #include "osog_kernels.h"
 
 using namespace osog;
@@ -26,7 +27,7 @@ constexpr int kMaxDevices = 64;
 constexpr int kPairsPerParticle = 8;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
-static __device__ __align__(256) float2 g_twiddles[kTwiddleCount];  // sizes 32..2048 in turn
+static __device__ __align__(256) float2 g_twiddles[kTwiddleCount];  // tables of sizes 32..2048
 static __device__ __align__(256) int32_t g_status;
 
 struct DeviceState {
@@ -61,12 +62,7 @@ int setup_device(int dev, DeviceState **out) {
         if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return OSOG_ERR_CUDA;
         st.status = static_cast<int32_t *>(p);
         static float2 host_tw[kTwiddleCount];
-        const double two_pi = 6.283185307179586476925286766559;
-        for (int n = 32; n <= 2048; n <<= 1) {
-            float2 *t = host_tw + twiddle_offset(n);
-            for (int k = 0; k < n; ++k)
-                t[k] = make_float2((float)cos(two_pi * k / n), (float)-sin(two_pi * k / n));
-        }
+        for (int n = 32; n <= 2048; n <<= 1) fill_twiddles(n, host_tw + twiddle_offset(n));
         if (cudaMemcpyToSymbol(g_twiddles, host_tw, sizeof host_tw) != cudaSuccess)
             return OSOG_ERR_CUDA;
         for (int n = 32; n <= 2048; n <<= 1)

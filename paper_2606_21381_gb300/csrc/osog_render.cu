@@ -163,6 +163,11 @@ __device__ void raster_strip(const StripArgs &a, int s, int y0, float2 *buf, PRe
     }
 }
 
+// Elements of an 8192-sample set handled by each thread in the copy loops;
+// the loops are fully unrolled so that every thread has all of its global
+// loads in flight at once.
+constexpr int kEPT = kSetElems / kThreads;
+
 template <int N, int MODE>
 __global__ void __launch_bounds__(kThreads, 2) k_strip_forward(const __grid_constant__ StripArgs a) {
     constexpr int L = kSetElems / N;
@@ -176,38 +181,60 @@ __global__ void __launch_bounds__(kThreads, 2) k_strip_forward(const __grid_cons
     const int s = blockIdx.y;
     const int y0 = blockIdx.x * geo.R;
     const int R = geo.R;
-    for (int i = threadIdx.x; i < L * LS; i += kThreads) buf[i] = make_float2(0.f, 0.f);
-    __syncthreads();
+    const int RN = R * N;  // <= kSetElems; lines R..L-1 are never read back
     if constexpr (MODE == kStripFromMap) {
         const float2 *src = a.opd_att + (size_t)y0 * N;
-        for (int e = threadIdx.x; e < R * N; e += kThreads)
-            buf[(e / N) * LS + pad16(e % N)] = src[e];
+        float2 v[kEPT];
+#pragma unroll
+        for (int i = 0; i < kEPT; ++i) {
+            const int e = threadIdx.x + i * kThreads;
+            if (e < RN) v[i] = src[e];
+        }
+#pragma unroll
+        for (int i = 0; i < kEPT; ++i) {
+            const int e = threadIdx.x + i * kThreads;
+            if (e < RN) buf[(e / N) * LS + pad16(e % N)] = v[i];
+        }
     } else {
+        float4 *b4 = reinterpret_cast<float4 *>(buf);
+        for (int i = threadIdx.x; i < R * LS / 2; i += kThreads) b4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
         raster_strip<N>(a, s, y0, buf, srec, srect, wsum);
     }
     __syncthreads();
     if constexpr (MODE == kStripOpdOnly) {
         float2 *dst = a.opd_out + (size_t)y0 * N;
-        for (int e = threadIdx.x; e < R * N; e += kThreads) dst[e] = buf[(e / N) * LS + pad16(e % N)];
+#pragma unroll
+        for (int i = 0; i < kEPT; ++i) {
+            const int e = threadIdx.x + i * kThreads;
+            if (e < RN) dst[e] = buf[(e / N) * LS + pad16(e % N)];
+        }
         return;
     } else {
         const float tol = a.sc[s].two_over_lambda;
-        for (int e = threadIdx.x; e < R * N; e += kThreads) {
-            float2 *v = buf + (e / N) * LS + pad16(e % N);
-            float sn, cs;
-            sincospif(v->x * tol, &sn, &cs);
-            const float amp = expf(-v->y);
-            *v = make_float2(amp * cs, amp * sn);
+#pragma unroll
+        for (int i = 0; i < kEPT; ++i) {
+            const int e = threadIdx.x + i * kThreads;
+            if (e < RN) {
+                float2 *v = buf + (e / N) * LS + pad16(e % N);
+                const float2 oa = *v;
+                float sn, cs;
+                sincospif(oa.x * tol, &sn, &cs);
+                const float amp = expf(-oa.y);
+                *v = make_float2(amp * cs, amp * sn);
+            }
         }
         __syncthreads();
         fft_lines<N, L, false>(buf, a.tw);
         const int B = geo.B, lb = ilog2(B), lr = ilog2(R);
         float2 *G = a.w.G + (size_t)s * geo.H * N;
         const int2 cr = a.w.colrange[s];
-        for (int e = threadIdx.x; e < R * N; e += kThreads) {
+#pragma unroll
+        for (int i = 0; i < kEPT; ++i) {
+            const int e = threadIdx.x + i * kThreads;
             const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
             const int kx = bk * B + c, fx = kx < N / 2 ? kx : kx - N;
-            if (fx >= cr.x && fx <= cr.y)  // columns outside every pupil are never read
+            if (e < RN && fx >= cr.x && fx <= cr.y)  // columns outside every pupil are never read
                 G[((size_t)bk * geo.H + y0 + r) * B + c] = buf[r * LS + pad16(kx)];
         }
     }
@@ -255,13 +282,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_column(const __grid_constant__ 
     const bool hi_part = u1 >= half && max(u0, half) - geo.W <= cr.y && u1 - geo.W >= cr.x;
     if (!lo_part && !hi_part) return;
     const float2 *G = a.w.G + ((size_t)s * geo.nblocks + bk) * N * B;
-    for (int e = threadIdx.x; e < N * B; e += kThreads) {
-        const int c = e & (B - 1);
-        const int kx = u0 + c, fx = kx < half ? kx : kx - geo.W;
-        const bool on = fx >= cr.x && fx <= cr.y;
-        buf0[c * LS + pad16(e >> lb)] = on ? G[e] : make_float2(0.f, 0.f);
+    const int NB_ = N * B;  // <= kSetElems; lines B..L-1 are never read back
+    {
+        float2 v[kEPT];
+#pragma unroll
+        for (int i = 0; i < kEPT; ++i) {
+            const int e = threadIdx.x + i * kThreads;
+            const int kx = u0 + (e & (B - 1)), fx = kx < half ? kx : kx - geo.W;
+            v[i] = e < NB_ && fx >= cr.x && fx <= cr.y ? G[e] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < kEPT; ++i) {
+            const int e = threadIdx.x + i * kThreads;
+            if (e < NB_) buf0[(e & (B - 1)) * LS + pad16(e >> lb)] = v[i];
+        }
     }
-    for (int i = B * LS + threadIdx.x; i < L * LS; i += kThreads) buf0[i] = make_float2(0.f, 0.f);
     for (int j = threadIdx.x; j < K * B; j += kThreads) {
         const int m = j >> lb, c = j & (B - 1);
         chords[m * L + c] = a.w.chord[((size_t)s * K + m) * geo.W + bk * B + c];
@@ -270,24 +305,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_column(const __grid_constant__ 
     fft_lines<N, L, false>(buf0, a.tw);
     for (int m = 0; m < K; ++m) {
         const ModeDev &md = a.md[s][m];
-        for (int e = threadIdx.x; e < L * N; e += kThreads) {
+#pragma unroll 4
+        for (int i = 0; i < kEPT; ++i) {
+            const int e = threadIdx.x + i * kThreads;  // line-major: consecutive y
             const int c = e / N, y = e % N;
-            float2 v = make_float2(0.f, 0.f);
             if (c < B) {
                 const int kx = bk * B + c;
-                const int fx = kx < geo.W / 2 ? kx : kx - geo.W;
+                const int fx = kx < half ? kx : kx - geo.W;
                 const int fy = y < N / 2 ? y : y - N;
                 const int2 ch = chords[m * L + c];
+                float2 v = make_float2(0.f, 0.f);
                 if (fy >= ch.x && fy <= ch.y)
                     v = cmul(buf0[c * LS + pad16(y)], transfer(md, fx, fy));
+                buf1[c * LS + pad16(y)] = v;
             }
-            buf1[c * LS + pad16(y)] = v;
         }
         __syncthreads();
         fft_lines<N, L, true>(buf1, a.tw);
         float2 *Qm = a.w.Q + (((size_t)s * K + m) * geo.nblocks + bk) * N * B;
-        for (int e = threadIdx.x; e < N * B; e += kThreads)
-            Qm[e] = buf1[(e & (B - 1)) * LS + pad16(e >> lb)];
+#pragma unroll
+        for (int i = 0; i < kEPT; ++i) {
+            const int e = threadIdx.x + i * kThreads;
+            if (e < NB_) Qm[e] = buf1[(e & (B - 1)) * LS + pad16(e >> lb)];
+        }
         __syncthreads();
     }
 }
@@ -305,20 +345,34 @@ __global__ void __launch_bounds__(kThreads, 2) k_strip_inverse(const __grid_cons
     const int R = geo.R, B = geo.B, lb = ilog2(B), lr = ilog2(R);
     const float2 *Qm = a.w.Q + (size_t)sm * geo.nblocks * geo.H * B;
     const int2 cr = a.w.colrange[sm / K];
-    for (int e = threadIdx.x; e < R * N; e += kThreads) {
-        const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
-        const int kx = bk * B + c, fx = kx < N / 2 ? kx : kx - N;
-        buf[r * LS + pad16(kx)] = fx >= cr.x && fx <= cr.y
-                                      ? Qm[((size_t)bk * geo.H + y0 + r) * B + c]
-                                      : make_float2(0.f, 0.f);
+    const int RN = R * N;  // <= kSetElems; lines R..L-1 are never read back
+    {
+        float2 v[kEPT];
+#pragma unroll
+        for (int i = 0; i < kEPT; ++i) {
+            const int e = threadIdx.x + i * kThreads;
+            const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
+            const int kx = bk * B + c, fx = kx < N / 2 ? kx : kx - N;
+            v[i] = e < RN && fx >= cr.x && fx <= cr.y ? Qm[((size_t)bk * geo.H + y0 + r) * B + c]
+                                                      : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < kEPT; ++i) {
+            const int e = threadIdx.x + i * kThreads;
+            const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
+            if (e < RN) buf[r * LS + pad16(bk * B + c)] = v[i];
+        }
     }
-    for (int i = R * LS + threadIdx.x; i < L * LS; i += kThreads) buf[i] = make_float2(0.f, 0.f);
     __syncthreads();
     fft_lines<N, L, true>(buf, a.tw);
     float *img = a.images + ((size_t)sm * geo.H + y0) * N;
-    for (int e = threadIdx.x; e < R * N; e += kThreads) {
-        const float2 v = buf[(e / N) * LS + pad16(e % N)];
-        img[e] = fmaf(v.x, v.x, v.y * v.y);
+#pragma unroll
+    for (int i = 0; i < kEPT; ++i) {
+        const int e = threadIdx.x + i * kThreads;
+        if (e < RN) {
+            const float2 v = buf[(e / N) * LS + pad16(e % N)];
+            img[e] = fmaf(v.x, v.x, v.y * v.y);
+        }
     }
 }
 
