@@ -151,18 +151,36 @@ def source_digest() -> str:
     return h.hexdigest()[:12]
 
 
-def algorithmic_bytes(kernel: str, counts, H: int, W: int, K: int, pairs: int):
-    """Minimum HBM bytes of one launch of each kernel over the batch."""
+def active_fraction(optics: dict) -> float:
+    """Fraction of DFT columns that some selected pupil passes at all: the
+    render writes, filters and reads only these columns of the row spectra.
+    Computed here from the optics (measurement bookkeeping only)."""
+    W, dx, lam, NA = optics["W"], optics["dx"], optics["lambda_um"], optics["NA"]
+    r = NA / lam
+    f = np.fft.fftfreq(W, dx)
+    act = np.zeros(W, bool)
+    for bit in (1, 2, 4):
+        if optics["modes"] & bit:
+            ox = optics["oblique_frac"] * r * np.cos(optics["oblique_angle"]) if bit == 2 else 0.0
+            act |= (f + ox) ** 2 <= r * r
+    return float(act.mean())
+
+
+def algorithmic_bytes(kernel: str, counts, H: int, W: int, K: int, pairs: int,
+                      active: float = 1.0):
+    """Minimum HBM bytes of one launch of each kernel over the batch: row
+    spectra G and filtered columns Q only for the pupil-passed columns
+    (fraction `active`), the image in full."""
     px = len(counts) * H * W
     n = int(sum(counts))
-    return {
+    return int({
         "bin_count": n * (36 + 64 + 8),
         "bin_scan": 0,
         "bin_fill": n * 8 + pairs * 4,
-        "strip_forward": px * 8 + n * (64 + 8) + pairs * 4,
-        "column": px * (8 + 8 * K),
-        "strip_inverse": px * (8 * K + 4 * K),
-    }[kernel]
+        "strip_forward": px * 8 * active + n * (64 + 8) + pairs * 4,
+        "column": px * (8 + 8 * K) * active,
+        "strip_inverse": px * 8 * K * active + px * 4 * K,
+    }[kernel])
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -301,11 +319,12 @@ def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms
     dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
     pairs_est = int(sum(counts) * 2)
     peak, peak_src = measured_peaks()
-    bytes_dom = algorithmic_bytes(dom, counts, SIZE, SIZE, K, pairs_est)
+    act = active_fraction(scenes.batch_2048_scene(0, 1, SIZE)[1])
+    bytes_dom = algorithmic_bytes(dom, counts, SIZE, SIZE, K, pairs_est, act)
     dur_s = kernels[dom]["ms_per_launch"] / 1e3
     achieved = bytes_dom / dur_s / 1e9
     traffic = ncu_traffic(dom)
-    step_bytes = sum(algorithmic_bytes(k, counts, SIZE, SIZE, K, pairs_est) for k in kernels)
+    step_bytes = sum(algorithmic_bytes(k, counts, SIZE, SIZE, K, pairs_est, act) for k in kernels)
     ms_step = timed_max / args.steps
     return {
         "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": world,
@@ -317,7 +336,8 @@ def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "peak_source": peak_src,
-                     "algorithmic_bytes_per_launch": bytes_dom},
+                     "algorithmic_bytes_per_launch": bytes_dom,
+                     "pupil_active_columns": round(act, 4)},
         "step_roofline": {"algorithmic_bytes": step_bytes,
                           "achieved_gbs": round(step_bytes / (ms_step / 1e3) / 1e9, 1),
                           "frac": round(step_bytes / (ms_step / 1e3) / 1e9 / peak, 4)},
