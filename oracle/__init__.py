@@ -84,6 +84,7 @@ def _load():
         lib.orc_transfer.argtypes = [ctypes.POINTER(_Optics), i32, d, d]
         lib.orc_images.argtypes = [ctypes.POINTER(_Optics), d, d, d]
         lib.orc_render.argtypes = [d, i64, i32, ctypes.POINTER(_Optics), d, d, d, d, d]
+        lib.orc_render_grad.argtypes = [d, i64, i32, ctypes.POINTER(_Optics), d, d, d]
         _lib = lib
     return _lib
 
@@ -227,3 +228,18 @@ def render(soa: np.ndarray, n: int, o: dict) -> dict:
     _load().orc_render(_p(soa), ld, int(n), ctypes.byref(s), _p(opd), _p(att),
                        _p(er), _p(ei), _p(img))
     return dict(opd=opd, att=att, field=er + 1j * ei, images=img)
+
+
+def render_grad(soa: np.ndarray, n: int, o: dict, gI: np.ndarray):
+    """Gradient of L = sum(gI * images) with respect to the particle fields
+    ((9, n) float64, kind row zero) and the optics scalars (defocus,
+    shear_px, shear_angle, bias_phase), by the FP64 analytic adjoint."""
+    soa, ld = _soa(soa)
+    s = _optics_struct(o)
+    gI = np.ascontiguousarray(gI, dtype=np.float64)
+    if gI.shape != (n_modes(o), o["H"], o["W"]):
+        raise ValueError("gI must have shape (K, H, W)")
+    gsoa = np.zeros((9, max(int(n), 1)))
+    gopt = np.zeros(4)
+    _load().orc_render_grad(_p(soa), ld, int(n), ctypes.byref(s), _p(gI), _p(gsoa), _p(gopt))
+    return gsoa[:, :int(n)], gopt

@@ -21,7 +21,11 @@
  *     oblique illumination as the pupil shifted by k_ill (Fig. 2 discussion:
  *     "asymmetric Fourier pupil"); DIC as the sheared-field difference of
  *     Eq. 5 taken coherently through the pupil;
- *   - an own radix-2 FFT and a brute-force DFT (used to pin the FFT).
+ *   - an own radix-2 FFT and a brute-force DFT (used to pin the FFT);
+ *   - the gradient of a linear functional of the images with respect to
+ *     every particle field and to the optics scalars, by the analytic
+ *     adjoint of the chain above (orc_render_grad), pinned by central
+ *     finite differences of orc_render.
  *
  * Conventions (readings of points the paper leaves open):
  *   - pixel (i, j) is sampled at its centre (x, y) = (j + 0.5, i + 0.5) px;
@@ -391,4 +395,243 @@ void orc_render(const float *soa, int64_t ld, int n, const orc_optics *o,
     orc_opd_att(soa, ld, n, o->H, o->W, o->dx, o->bevel_slope, 0, opd, att);
     orc_field(opd, att, (int64_t)o->H * o->W, o->lambda, ere, eim);
     orc_images(o, ere, eim, images);
+}
+
+/* ------------------------------------------------------------------ */
+/* Gradient (analytic adjoint, FP64)                                   */
+/* ------------------------------------------------------------------ */
+
+/* Chord of the bevelled prism at local point (u, v) (um) and its partial
+ * derivatives, from the active half-spaces of Eq. 1: chord = z_top - z_bot
+ * with z_top the lowest upper bound (planes with a_z > 0) and z_bot the
+ * highest lower bound (a_z < 0), each z = (b - a_x u - a_y v) / a_z.  The
+ * derivative follows the two active planes; b depends on (hx, hy, T) with
+ * the partials of the 14 planes (top/bottom b = T/2, walls b = hx or hy,
+ * chamfers b = s hx or s hy).  d[0..4] = d chord / d(u, v, hx, hy, T), all
+ * in um.  Returns the chord (0 and zero partials outside). */
+static double prism_chord_grad(double hx, double hy, double T, double s,
+                               double u, double v, double d[5])
+{
+    double A[42], b[14];
+    /* db/d(hx, hy, T) of each plane, in the order of orc_prism_halfspaces:
+     * top, bottom (b = T/2); walls +-x (b = hx), +-y (b = hy); chamfers
+     * top +-x, top +-y, bottom +-x, bottom +-y (b = s hx or s hy). */
+    const double db[14][3] = {
+        {0, 0, 0.5}, {0, 0, 0.5}, {1, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 1, 0},
+        {s, 0, 0}, {s, 0, 0}, {0, s, 0}, {0, s, 0},
+        {s, 0, 0}, {s, 0, 0}, {0, s, 0}, {0, s, 0}};
+    orc_prism_halfspaces(hx, hy, T, s, A, b);
+    for (int k = 0; k < 5; ++k) d[k] = 0.0;
+    int top = -1, bot = -1;
+    double zhi = INFINITY, zlo = -INFINITY;
+    for (int i = 0; i < 14; ++i) {
+        double ax = A[3 * i], ay = A[3 * i + 1], az = A[3 * i + 2];
+        double rhs = b[i] - ax * u - ay * v;
+        if (az > 0.0) {
+            double z = rhs / az;
+            if (z < zhi) { zhi = z; top = i; }
+        } else if (az < 0.0) {
+            double z = rhs / az;
+            if (z > zlo) { zlo = z; bot = i; }
+        } else if (rhs < 0.0) {
+            return 0.0;
+        }
+    }
+    if (!(zhi > zlo)) return 0.0;
+    int act[2] = {top, bot};
+    double sign[2] = {1.0, -1.0};
+    for (int k = 0; k < 2; ++k) {
+        int i = act[k];
+        double ax = A[3 * i], ay = A[3 * i + 1], az = A[3 * i + 2];
+        d[0] += sign[k] * (-ax / az);
+        d[1] += sign[k] * (-ay / az);
+        d[2] += sign[k] * db[i][0] / az;
+        d[3] += sign[k] * db[i][1] / az;
+        d[4] += sign[k] * db[i][2] / az;
+    }
+    return zhi - zlo;
+}
+
+/* Thickness of particle q at (x, y) and its gradient with respect to the
+ * fields cx, cy, theta, a|hx, b|hy, T (g[0..5]; px, rad, um units of the
+ * particle tensor). */
+static double particle_thickness_grad(const double *q, double dx, double bevel,
+                                      double x, double y, double g[6])
+{
+    double c = cos(q[F_TH]), s = sin(q[F_TH]);
+    double ex = x - q[F_CX], ey = y - q[F_CY];
+    double u = c * ex + s * ey;
+    double v = -s * ex + c * ey;
+    /* du/d(cx, cy, theta) and dv/d(...) */
+    double du[3] = {-c, -s, v}, dv[3] = {s, -c, -u};
+    for (int k = 0; k < 6; ++k) g[k] = 0.0;
+    if (q[F_KIND] > 0.5) {
+        double d[5];
+        double t = prism_chord_grad(q[F_A] * dx, q[F_B] * dx, q[F_T], bevel, u * dx, v * dx, d);
+        if (t == 0.0) return 0.0;
+        for (int k = 0; k < 3; ++k) g[k] = dx * (d[0] * du[k] + d[1] * dv[k]);
+        g[3] = dx * d[2];
+        g[4] = dx * d[3];
+        g[5] = d[4];
+        return t;
+    }
+    double a = q[F_A], b = q[F_B];
+    double r = 1.0 - (u / a) * (u / a) - (v / b) * (v / b);
+    if (!(r > 0.0)) return 0.0;
+    double sr = sqrt(r), t = q[F_T] * sr;
+    double dtdr = q[F_T] / (2.0 * sr);
+    double drdu = -2.0 * u / (a * a), drdv = -2.0 * v / (b * b);
+    for (int k = 0; k < 3; ++k) g[k] = dtdr * (drdu * du[k] + drdv * dv[k]);
+    g[3] = dtdr * 2.0 * u * u / (a * a * a);
+    g[4] = dtdr * 2.0 * v * v / (b * b * b);
+    g[5] = sr;
+    return t;
+}
+
+/* d/d(defocus, shear_px, shear_angle, bias) of the transfer function of
+ * one modality at DFT sample (i, j); H itself is returned in (hr, hi). */
+static void transfer_grad(const orc_optics *o, int mode, int i, int j,
+                          double *hr, double *hi, double dh[4][2])
+{
+    double kna = 2.0 * M_PI * o->NA / o->lambda;
+    double k0 = 2.0 * M_PI * o->n_medium / o->lambda;
+    double kx = kfreq(j, o->W, o->dx), ky = kfreq(i, o->H, o->dx);
+    double qx = kx, qy = ky;
+    if (mode == 2) {
+        qx += o->oblique_frac * kna * cos(o->oblique_angle);
+        qy += o->oblique_frac * kna * sin(o->oblique_angle);
+    }
+    for (int k = 0; k < 4; ++k) dh[k][0] = dh[k][1] = 0.0;
+    double pr, pi;
+    pupil(o, qx, qy, &pr, &pi);
+    *hr = pr;
+    *hi = pi;
+    if (pr == 0.0 && pi == 0.0) return;
+    double kappa = sqrt(k0 * k0 - qx * qx - qy * qy) - k0;  /* d chi / d dz */
+    /* dP/ddz = i kappa P */
+    double dpr = -kappa * pi, dpi = kappa * pr;
+    if (mode != 4) {
+        dh[0][0] = dpr;
+        dh[0][1] = dpi;
+        return;
+    }
+    double ca = cos(o->shear_angle), sa = sin(o->shear_angle);
+    double dsx = 0.5 * o->shear_px * o->dx * ca, dsy = 0.5 * o->shear_px * o->dx * sa;
+    double arg = kx * dsx + ky * dsy + o->bias_phase;
+    double g = 2.0 * sin(arg), gp = 2.0 * cos(arg);
+    /* H = P * i g: (pr + i pi)(i g) = (-pi g, pr g) */
+    *hr = -pi * g;
+    *hi = pr * g;
+    dh[0][0] = -dpi * g;
+    dh[0][1] = dpr * g;
+    double darg[3] = {0.5 * o->dx * (kx * ca + ky * sa),
+                      0.5 * o->shear_px * o->dx * (-kx * sa + ky * ca), 1.0};
+    for (int k = 0; k < 3; ++k) {
+        dh[k + 1][0] = -pi * gp * darg[k];
+        dh[k + 1][1] = pr * gp * darg[k];
+    }
+}
+
+/* Gradient of L = sum_m sum_px gI[m][px] I_m[px] (gI = dL/dI given) with
+ * respect to every particle field (gsoa, [9][n] row-major, the kind row
+ * zero) and to the optics scalars gopt[4] = dL/d(defocus, shear_px,
+ * shear_angle, bias_phase).  Adjoint chain of orc_render:
+ *   E_m = IDFT2(DFT2(E) H_m) / (HW), I_m = |E_m|^2
+ *   dL/dE_m = 2 gI_m E_m; dL/dZ_m = DFT2(dL/dE_m) / (HW) with Z_m = E^ H_m;
+ *   dL/dE^ = sum_m conj(H_m) dL/dZ_m; dL/dE = IDFT2(dL/dE^);
+ *   dL/dOPD = (2 pi / lambda) Re(conj(dL/dE) i E), dL/dATT = -Re(conj(dL/dE) E);
+ *   dL/d(dn_p) = sum t_p dL/dOPD, dL/d(mu_p) = sum t_p dL/dATT,
+ *   dL/d(geometry_p) = sum (dn_p dL/dOPD + mu_p dL/dATT) dt_p/d(geometry_p);
+ *   dL/d(optics) = sum_m sum_k Re(conj(dL/dZ_m) E^ dH_m/d(optics)).
+ * Complex gradients are dL/dRe + i dL/dIm. */
+void orc_render_grad(const float *soa, int64_t ld, int n, const orc_optics *o,
+                     const double *gI, double *gsoa, double *gopt)
+{
+    int H = o->H, W = o->W;
+    size_t hw = (size_t)H * W;
+    double *opd = malloc(sizeof(double) * hw), *att = malloc(sizeof(double) * hw);
+    double *er = malloc(sizeof(double) * hw), *ei = malloc(sizeof(double) * hw);
+    double *fr = malloc(sizeof(double) * hw), *fi = malloc(sizeof(double) * hw);
+    double *zr = malloc(sizeof(double) * hw), *zi = malloc(sizeof(double) * hw);
+    double *gr = calloc(hw, sizeof(double)), *gi = calloc(hw, sizeof(double));
+    double *hr = malloc(sizeof(double) * hw), *hi = malloc(sizeof(double) * hw);
+    orc_opd_att(soa, ld, n, H, W, o->dx, o->bevel_slope, 0, opd, att);
+    orc_field(opd, att, (int64_t)hw, o->lambda, er, ei);
+    memcpy(fr, er, sizeof(double) * hw);
+    memcpy(fi, ei, sizeof(double) * hw);
+    orc_fft2(fr, fi, H, W, -1); /* E^ */
+    for (int k = 0; k < 4; ++k) gopt[k] = 0.0;
+    double inv = 1.0 / (double)hw;
+    int m = 0;
+    for (int bit = 0; bit < 3; ++bit) {
+        int mode = 1 << bit;
+        if (!(o->modes & (uint32_t)mode)) continue;
+        orc_transfer(o, mode, hr, hi);
+        for (size_t t = 0; t < hw; ++t) {
+            zr[t] = fr[t] * hr[t] - fi[t] * hi[t];
+            zi[t] = fr[t] * hi[t] + fi[t] * hr[t];
+        }
+        orc_fft2(zr, zi, H, W, +1); /* HW * E_m */
+        const double *g = gI + (size_t)m * hw;
+        for (size_t t = 0; t < hw; ++t) { /* dL/dE_m = 2 gI E_m */
+            double a = zr[t] * inv, b = zi[t] * inv;
+            zr[t] = 2.0 * g[t] * a;
+            zi[t] = 2.0 * g[t] * b;
+        }
+        orc_fft2(zr, zi, H, W, -1);
+        for (size_t t = 0; t < hw; ++t) { /* dL/dZ_m */
+            zr[t] *= inv;
+            zi[t] *= inv;
+        }
+        for (int i = 0; i < H; ++i)
+            for (int j = 0; j < W; ++j) {
+                size_t t = (size_t)i * W + j;
+                double h0, h1, dh[4][2];
+                transfer_grad(o, mode, i, j, &h0, &h1, dh);
+                /* dL/dE^ += conj(H) dL/dZ */
+                gr[t] += h0 * zr[t] + h1 * zi[t];
+                gi[t] += h0 * zi[t] - h1 * zr[t];
+                /* Re(conj(gZ) E^ dH) */
+                for (int k = 0; k < 4; ++k) {
+                    double wr = fr[t] * dh[k][0] - fi[t] * dh[k][1];
+                    double wi = fr[t] * dh[k][1] + fi[t] * dh[k][0];
+                    gopt[k] += zr[t] * wr + zi[t] * wi;
+                }
+            }
+        ++m;
+    }
+    orc_fft2(gr, gi, H, W, +1); /* dL/dE */
+    /* per-pixel dL/dOPD (into opd) and dL/dATT (into att), keeping E */
+    for (size_t t = 0; t < hw; ++t) {
+        double go = 2.0 * M_PI / o->lambda * (gr[t] * (-ei[t]) + gi[t] * er[t]);
+        double ga = -(gr[t] * er[t] + gi[t] * ei[t]);
+        opd[t] = go;
+        att[t] = ga;
+    }
+    memset(gsoa, 0, sizeof(double) * F_COUNT * (size_t)n);
+    for (int p = 0; p < n; ++p) {
+        double q[F_COUNT];
+        load_particle(soa, ld, p, q);
+        double R = q[F_KIND] > 0.5 ? sqrt(q[F_A] * q[F_A] + q[F_B] * q[F_B]) : fmax(q[F_A], q[F_B]);
+        double jl = floor(q[F_CX] - R - 1.5), jh = ceil(q[F_CX] + R + 0.5);
+        double il = floor(q[F_CY] - R - 1.5), ih = ceil(q[F_CY] + R + 0.5);
+        if (jh < 0 || ih < 0 || jl > W - 1 || il > H - 1) continue;
+        int j0 = jl < 0 ? 0 : (int)jl, j1 = jh > W - 1 ? W - 1 : (int)jh;
+        int i0 = il < 0 ? 0 : (int)il, i1 = ih > H - 1 ? H - 1 : (int)ih;
+        double acc[F_COUNT] = {0};
+        for (int i = i0; i <= i1; ++i)
+            for (int j = j0; j <= j1; ++j) {
+                double g6[6];
+                double t = particle_thickness_grad(q, o->dx, o->bevel_slope, j + 0.5, i + 0.5, g6);
+                if (t == 0.0) continue;
+                size_t s = (size_t)i * W + j;
+                double w = q[F_DN] * opd[s] + q[F_MU] * att[s];
+                for (int k = 0; k < 6; ++k) acc[k] += w * g6[k];
+                acc[F_DN] += t * opd[s];
+                acc[F_MU] += t * att[s];
+            }
+        for (int f = 0; f < F_COUNT; ++f) gsoa[(size_t)f * n + p] = acc[f];
+    }
+    free(opd); free(att); free(er); free(ei); free(fr); free(fi);
+    free(zr); free(zi); free(gr); free(gi); free(hr); free(hi);
 }
