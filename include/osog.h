@@ -72,7 +72,11 @@ extern "C" {
 #define OSOG_KERNEL_STRIP_FORWARD 3
 #define OSOG_KERNEL_COLUMN 4
 #define OSOG_KERNEL_STRIP_INVERSE 5
-#define OSOG_KERNEL_CLASS_COUNT 6
+#define OSOG_KERNEL_BWD_ROWS 6
+#define OSOG_KERNEL_BWD_COLUMN 7
+#define OSOG_KERNEL_BWD_STRIP 8
+#define OSOG_KERNEL_BWD_REDUCE 9
+#define OSOG_KERNEL_CLASS_COUNT 10
 
 typedef struct osog_plan osog_plan_t;
 /* Binary-compatible with cudaStream_t; NULL is the legacy default stream. */
@@ -168,6 +172,32 @@ int osog_render_opd(osog_plan_t *plan, const float *soa, int64_t ld, int32_t n,
 int osog_optics_from_opd(osog_plan_t *plan, const float *opd_att,
                          const osog_optics_t *optics, float *image, void *ws,
                          size_t ws_bytes, osog_stream_t stream);
+
+/*
+ * Workspace bytes needed by osog_render_backward for n_max particles and K
+ * modalities (0 for invalid arguments).
+ */
+size_t osog_backward_workspace_size(const osog_plan_t *plan, int32_t n_max, int32_t K);
+
+/*
+ * Gradient of a loss of the images of one scene (the adjoint of
+ * osog_render; the paper's end-to-end differentiability, Sec. III.C and
+ * Sec. IV.B).  Given grad_image = dL/dI (device float32 [K][H][W]) it writes
+ *   grad_soa     device float32 [9][ld]: dL/d(cx, cy, theta, a|hx, b|hy, T,
+ *                dn, mu) of particles 0..n-1 in the units of the particle
+ *                tensor; the kind row and particles skipped as invalid get 0
+ *   grad_optics  device float32 [4]: dL/d(defocus_um, shear_px, shear_angle,
+ *                bias_phase); the shear and bias entries are zero unless the
+ *                DIC modality is selected
+ * The forward intermediates are recomputed, not read from an earlier render;
+ * every sum runs in a fixed order (bitwise reproducible).  The pupil circle
+ * is a hard cut-off, so NA has no gradient.  Workspace:
+ * osog_backward_workspace_size(plan, n, K).  Errors as for osog_render.
+ */
+int osog_render_backward(osog_plan_t *plan, const float *soa, int64_t ld, int32_t n,
+                         const osog_optics_t *optics, const float *grad_image,
+                         float *grad_soa, float *grad_optics, void *ws, size_t ws_bytes,
+                         osog_stream_t stream);
 
 /*
  * Batched forward render of S scenes that share the plan's H x W and the

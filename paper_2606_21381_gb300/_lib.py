@@ -14,7 +14,7 @@ from . import build as _build
 
 MODE_BF, MODE_OBLIQUE, MODE_DIC = 1, 2, 4
 KERNEL_CLASSES = ("bin_count", "bin_scan", "bin_fill", "strip_forward", "column",
-                  "strip_inverse")
+                  "strip_inverse", "bwd_rows", "bwd_column", "bwd_strip", "bwd_reduce")
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_SIZE", 3: "WORKSPACE",
           4: "BIN_OVERFLOW", 5: "NONFINITE_INPUT", 6: "TIMEOUT", 7: "CUDA",
           8: "INVALID_PARTICLE"}
@@ -22,7 +22,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_SIZE", 3: "WORKSPACE",
 EXPORTS = ("osog_plan_create", "osog_plan_destroy", "osog_workspace_size", "osog_render",
            "osog_render_opd", "osog_optics_from_opd", "osog_batch_submit",
            "osog_sync_status", "osog_last_error", "osog_plan_launch_count",
-           "osog_profile_begin", "osog_profile_end", "osog_render_noalloc")
+           "osog_profile_begin", "osog_profile_end", "osog_render_noalloc",
+           "osog_backward_workspace_size", "osog_render_backward")
 
 
 class OsogError(RuntimeError):
@@ -104,6 +105,10 @@ def lib(build_if_missing: bool = True):
     L.osog_profile_begin.restype = ctypes.c_int
     L.osog_profile_end.argtypes = [vp, vp, P(ctypes.c_float), P(i32)]
     L.osog_profile_end.restype = ctypes.c_int
+    L.osog_backward_workspace_size.argtypes = [vp, i32, i32]
+    L.osog_backward_workspace_size.restype = sz
+    L.osog_render_backward.argtypes = [vp, vp, i64, i32, P(Optics), vp, vp, vp, vp, sz, vp]
+    L.osog_render_backward.restype = ctypes.c_int
     L.osog_render_noalloc.argtypes = [vp, i64, i32, P(Optics), vp, vp]
     L.osog_render_noalloc.restype = ctypes.c_int
     _lib = L

@@ -1,0 +1,55 @@
+"""Differentiable rendering: the forward render and its hand-written
+adjoint (osog_render / osog_render_backward) as a torch.autograd.Function.
+
+The paper's pipeline is differentiable end to end so that dI/dTheta drives
+inverse rendering (Sec. III.C, Sec. IV.B).  Here the particle tensor and the
+optics scalars (defocus, DIC shear length, shear angle and bias) are the
+differentiable inputs; gradients come from libosog's adjoint kernels, not
+from autograd tracing.
+"""
+from __future__ import annotations
+
+import torch
+
+from .render import Renderer
+
+OPTICS_PARAMS = ("defocus", "shear_px", "shear_angle", "bias_phase")
+
+
+def optics_with(optics: dict, params) -> dict:
+    """Copy of `optics` with the four differentiable scalars replaced."""
+    o = dict(optics)
+    vals = params.detach().double().cpu().tolist() if torch.is_tensor(params) else list(params)
+    for k, v in zip(OPTICS_PARAMS, vals):
+        o[k] = float(v)
+    return o
+
+
+class RenderFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, soa, optics_params, renderer: Renderer, optics: dict):
+        o = optics_with(optics, optics_params)
+        soa_c = soa.detach().contiguous()
+        img = renderer.render(soa_c, None, o)
+        ctx.save_for_backward(soa_c)
+        ctx.renderer, ctx.optics = renderer, o
+        ctx.params_meta = (optics_params.dtype, optics_params.device)
+        return img
+
+    @staticmethod
+    def backward(ctx, grad_image):
+        (soa,) = ctx.saved_tensors
+        gsoa, gopt = ctx.renderer.backward(soa, None, ctx.optics,
+                                           grad_image.contiguous().float())
+        dtype, device = ctx.params_meta
+        return gsoa, gopt.to(device=device, dtype=dtype), None, None
+
+
+def render(soa: torch.Tensor, optics: dict, renderer: Renderer,
+           optics_params: torch.Tensor | None = None) -> torch.Tensor:
+    """Differentiable (K, H, W) render of one scene.  `optics_params` holds
+    (defocus, shear_px, shear_angle, bias_phase); when None the values of
+    `optics` are used and receive no gradient."""
+    if optics_params is None:
+        optics_params = torch.tensor([float(optics[k]) for k in OPTICS_PARAMS])
+    return RenderFunction.apply(soa, optics_params, renderer, optics)

@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libosog.so")
-SOURCES = ("osog_api.cu", "osog_bin.cu", "osog_render.cu", "osog_noalloc.cu")
+SOURCES = ("osog_api.cu", "osog_bin.cu", "osog_render.cu", "osog_backward.cu",
+           "osog_noalloc.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
          "--expt-relaxed-constexpr"]

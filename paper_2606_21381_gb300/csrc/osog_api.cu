@@ -97,6 +97,8 @@ Work carve(void *ws, const Layout &l, int32_t *status) {
     w.Q = reinterpret_cast<float2 *>(b + l.Q);
     w.chord = reinterpret_cast<int2 *>(b + l.chord);
     w.colrange = reinterpret_cast<int2 *>(b + l.colrange);
+    w.slotmap = nullptr;
+    w.slotmap_ppp = 0;
     w.status = status;
     return w;
 }
@@ -151,6 +153,8 @@ ModeDev mode_dev(const osog_optics_t &o, uint32_t mode) {
     m.bias = (float)o.bias_phase;
     m.scale = (float)(1.0 / ((double)o.H * o.W));
     m.dic = mode == OSOG_MODE_DIC ? 1 : 0;
+    m.dsx1 = (float)(0.5 * o.dx_um * cos(o.shear_angle));
+    m.dsy1 = (float)(0.5 * o.dx_um * sin(o.shear_angle));
     return m;
 }
 
@@ -272,6 +276,29 @@ size_t ws_need(const osog_plan *p, int64_t n_total, int K, int S, int pairs_pp) 
     return make_layout(p->geo, n_total, chunks, Sg, K, n_total * pairs_pp).total;
 }
 
+// Workspace of the adjoint: the forward regions (one scene, K modalities)
+// followed by the slot map, the per-(band slot, strip) particle partials and
+// the per-block optics partials.
+struct BwdLayout {
+    Layout fwd;
+    size_t slotmap, part, opart, total;
+};
+
+BwdLayout make_bwd_layout(const Geometry &geo, int64_t n, int64_t chunks, int K, int ppp) {
+    BwdLayout b;
+    const int64_t pairs = n * ppp;
+    b.fwd = make_layout(geo, n, chunks, 1, K, pairs);
+    size_t o = b.fwd.total;
+    b.slotmap = o;
+    o = align256(o + (size_t)n * ppp * sizeof(int32_t));
+    b.part = o;
+    o = align256(o + (size_t)pairs * (geo.BH / geo.R) * 8 * sizeof(float));
+    b.opart = o;
+    o = align256(o + (size_t)geo.nblocks * 4 * sizeof(float));
+    b.total = o;
+    return b;
+}
+
 }  // namespace
 
 extern "C" {
@@ -299,6 +326,7 @@ int osog_plan_create(osog_plan_t **out, int32_t H, int32_t W) {
     }
     if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(int32_t));
     if (e == cudaSuccess) e = prepare_kernels(H, W);
+    if (e == cudaSuccess) e = prepare_backward(H, W);
     if (e != cudaSuccess) {
         int rc = cuda_fail(e, "osog_plan_create");
         osog_plan_destroy(p);
@@ -460,6 +488,115 @@ int osog_batch_submit(osog_plan_t *p, const float *soa_all, int64_t ld, const in
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     p->launches += p->graph_kernels;
     return OSOG_OK;
+}
+
+size_t osog_backward_workspace_size(const osog_plan_t *p, int32_t n_max, int32_t K) {
+    if (!p || n_max < 0 || K < 1 || K > 3) return 0;
+    return make_bwd_layout(p->geo, n_max, (n_max + kChunk - 1) / kChunk + 1, K, kDefaultPairs).total;
+}
+
+int osog_render_backward(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
+                         const osog_optics_t *optics, const float *grad_image, float *grad_soa,
+                         float *grad_optics, void *ws, size_t ws_bytes, osog_stream_t stream) {
+    if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    int rc = check_optics(p, optics);
+    if (rc) return rc;
+    if (n < 0 || (int64_t)n > ld) return fail(OSOG_ERR_INVALID_ARG, "need 0 <= n <= ld");
+    if (n > 0 && (!soa || !grad_soa)) return fail(OSOG_ERR_INVALID_ARG, "soa or grad_soa is NULL");
+    if (!grad_image || !grad_optics) return fail(OSOG_ERR_INVALID_ARG, "grad_image or grad_optics is NULL");
+    const int K = popcount3(optics->modes);
+    const Geometry &geo = p->geo;
+    const int64_t chunks = (n + kChunk - 1) / kChunk;
+    const int ppp = kDefaultPairs;
+    const BwdLayout bl = make_bwd_layout(geo, n, chunks, K, ppp);
+    rc = check_ws(ws, bl.total, ws_bytes);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    GroupDev gd{};
+    gd.S = 1;
+    gd.K = K;
+    gd.nchunks = (int32_t)chunks;
+    SceneDev sc = scene_dev(*optics);
+    sc.p0 = 0;
+    sc.n = n;
+    sc.chunk0 = 0;
+    sc.pair0 = 0;
+    sc.pair_cap = (int32_t)((int64_t)n * ppp);
+    gd.sc[0] = sc;
+    for (int bit = 0, k = 0; bit < 3; ++bit)
+        if (optics->modes & (1u << bit)) gd.md[0][k++] = mode_dev(*optics, 1u << bit);
+    Work w = carve(ws, bl.fwd, p->status);
+    w.slotmap = reinterpret_cast<int32_t *>(static_cast<char *>(ws) + bl.slotmap);
+    w.slotmap_ppp = ppp;
+    float *part = reinterpret_cast<float *>(static_cast<char *>(ws) + bl.part);
+    float *opart = reinterpret_cast<float *>(static_cast<char *>(ws) + bl.opart);
+
+    // Forward recomputation up to the filtered columns Q_m.
+    rc = run_kernel(p, OSOG_KERNEL_BIN_COUNT, st, [&] { return launch_bin_count(soa, ld, gd, geo, w, st); });
+    if (rc) return rc;
+    rc = run_kernel(p, OSOG_KERNEL_BIN_SCAN, st, [&] { return launch_bin_scan(gd, geo, w, st); });
+    if (rc) return rc;
+    rc = run_kernel(p, OSOG_KERNEL_BIN_FILL, st, [&] { return launch_bin_fill(gd, geo, w, st); });
+    if (rc) return rc;
+    StripArgs sa{};
+    sa.geo = geo;
+    sa.w = w;
+    sa.tw = p->tw_w;
+    sa.S = 1;
+    sa.sc[0] = sc;
+    rc = run_kernel(p, OSOG_KERNEL_STRIP_FORWARD, st, [&] { return launch_strip_forward(sa, kStripRender, st); });
+    if (rc) return rc;
+    ColumnArgs ca{};
+    ca.geo = geo;
+    ca.w = w;
+    ca.tw = p->tw_h;
+    ca.S = 1;
+    ca.K = K;
+    for (int k = 0; k < K; ++k) ca.md[0][k] = gd.md[0][k];
+    rc = run_kernel(p, OSOG_KERNEL_COLUMN, st, [&] { return launch_column(ca, st); });
+    if (rc) return rc;
+
+    // Adjoint passes.
+    BwdRowsArgs ra{};
+    ra.geo = geo;
+    ra.w = w;
+    ra.tw = p->tw_w;
+    ra.grad_image = grad_image;
+    ra.S = 1;
+    ra.K = K;
+    rc = run_kernel(p, OSOG_KERNEL_BWD_ROWS, st, [&] { return launch_bwd_rows(ra, st); });
+    if (rc) return rc;
+    BwdColumnArgs bc{};
+    bc.geo = geo;
+    bc.w = w;
+    bc.tw = p->tw_h;
+    bc.opart = opart;
+    bc.S = 1;
+    bc.K = K;
+    for (int k = 0; k < K; ++k) bc.md[0][k] = gd.md[0][k];
+    rc = run_kernel(p, OSOG_KERNEL_BWD_COLUMN, st, [&] { return launch_bwd_column(bc, st); });
+    if (rc) return rc;
+    BwdStripArgs bs{};
+    bs.geo = geo;
+    bs.w = w;
+    bs.tw = p->tw_w;
+    bs.part = part;
+    bs.S = 1;
+    bs.sc[0] = sc;
+    rc = run_kernel(p, OSOG_KERNEL_BWD_STRIP, st, [&] { return launch_bwd_strip(bs, st); });
+    if (rc) return rc;
+    BwdReduceArgs br{};
+    br.geo = geo;
+    br.w = w;
+    br.part = part;
+    br.opart = opart;
+    br.grad_soa = grad_soa;
+    br.ld = ld;
+    br.grad_optics = grad_optics;
+    br.S = 1;
+    br.nchunks = (int32_t)chunks;
+    br.sc[0] = sc;
+    return run_kernel(p, OSOG_KERNEL_BWD_REDUCE, st, [&] { return launch_bwd_reduce(br, st); });
 }
 
 int osog_sync_status(osog_plan_t *p, osog_stream_t stream) {

@@ -255,6 +255,8 @@ k_bin_fill(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
         if (in) {
             const int slot = off[b] + pre[b] + wpre[warp][b] + __popc(m & lt);
             if (slot < sc.pair_cap) w.pairs[sc.pair0 + slot] = p;
+            if (w.slotmap && b - b0 < w.slotmap_ppp)
+                w.slotmap[(size_t)p * w.slotmap_ppp + (b - b0)] = slot < sc.pair_cap ? slot : -1;
         }
     }
 }

@@ -91,7 +91,7 @@ struct ModeDev {
     float dsx, dsy, bias;
     float scale;          // 1 / (H W)
     int32_t dic;          // 1 for the DIC factor
-    int32_t pad_;
+    float dsx1, dsy1;     // d(dsx, dsy) / d(shear_px): dx (cos, sin)(shear_angle) / 2
 };
 
 struct GroupDev {
@@ -114,6 +114,9 @@ struct Work {
     float2 *Q;          // [S][K][W/B][H][B] filtered columns
     int2 *chord;        // [S][K][W] rows [lo, hi] inside the pupil per column
     int2 *colrange;     // [S] signed column frequencies [lo, hi] any pupil passes
+    int32_t *slotmap;   // [n][pairs per particle] band-list slot of each (particle,
+                        // band); written by the fill pass when not null (adjoint)
+    int32_t slotmap_ppp;
     int32_t *status;    // plan status word
 };
 

@@ -34,6 +34,45 @@ struct InverseArgs {
     int32_t S, K;
 };
 
+// Adjoint passes (osog_render_backward).
+struct BwdRowsArgs {  // dL/dQ_m = DFT_rows(2 gI_m E_m), written over Q_m
+    Geometry geo;
+    Work w;
+    const float2 *tw;          // W-point tables
+    const float *grad_image;   // [S][K][H][W]
+    int32_t S, K;
+};
+
+struct BwdColumnArgs {  // dL/dG = IDFT_cols(sum_m conj(H_m) DFT_cols(dL/dQ_m)), over G
+    Geometry geo;
+    Work w;
+    const float2 *tw;          // H-point tables
+    float *opart;              // [S][W/B][4] per-block optics partials
+    int32_t S, K;
+    ModeDev md[kMaxScenes][kMaxModes];
+};
+
+struct BwdStripArgs {  // per-(band slot, strip) particle partials
+    Geometry geo;
+    Work w;
+    const float2 *tw;          // W-point tables
+    float *part;               // [pair slots][strips per band][8]
+    int32_t S;
+    SceneDev sc[kMaxScenes];
+};
+
+struct BwdReduceArgs {  // fixed-order sums into the particle and optics gradients
+    Geometry geo;
+    Work w;
+    const float *part;
+    const float *opart;
+    float *grad_soa;           // [9][ld], columns of this group
+    int64_t ld;
+    float *grad_optics;        // [S][4]
+    int32_t S, nchunks;
+    SceneDev sc[kMaxScenes];
+};
+
 cudaError_t launch_bin_count(const float *soa, int64_t ld, const GroupDev &gd,
                              const Geometry &geo, const Work &w, cudaStream_t st);
 cudaError_t launch_bin_scan(const GroupDev &gd, const Geometry &geo, const Work &w,
@@ -48,5 +87,13 @@ cudaError_t prepare_kernels(int H, int W);  // opt-in shared memory sizes
 cudaError_t launch_strip_forward(const StripArgs &a, StripMode mode, cudaStream_t st);
 cudaError_t launch_column(const ColumnArgs &a, cudaStream_t st);
 cudaError_t launch_strip_inverse(const InverseArgs &a, cudaStream_t st);
+
+size_t bwd_column_smem(int H);
+size_t bwd_strip_smem(int W);
+cudaError_t prepare_backward(int H, int W);
+cudaError_t launch_bwd_rows(const BwdRowsArgs &a, cudaStream_t st);
+cudaError_t launch_bwd_column(const BwdColumnArgs &a, cudaStream_t st);
+cudaError_t launch_bwd_strip(const BwdStripArgs &a, cudaStream_t st);
+cudaError_t launch_bwd_reduce(const BwdReduceArgs &a, cudaStream_t st);
 
 }  // namespace osog

@@ -135,6 +135,8 @@ extern "C" int osog_render_noalloc(const float *soa, int64_t ld, int32_t n,
     w.Q = reinterpret_cast<float2 *>(st->scratch + o_Q);
     w.chord = reinterpret_cast<int2 *>(st->scratch + o_chord);
     w.colrange = reinterpret_cast<int2 *>(st->scratch + o_colrange);
+    w.slotmap = nullptr;
+    w.slotmap_ppp = 0;
     w.status = st->status;
 
     // Scene and transfer-function constants (double precision on the host).

@@ -17,156 +17,11 @@
 //                  I = |E|^2 (Sec. III.B), float32 image rows.
 #include <math.h>
 
-#include "osog_fft.cuh"
-#include "osog_kernels.h"
+#include "osog_strip.cuh"
 
 namespace osog {
 
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ unsigned lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
-__device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
-
-// Accumulate one particle's OPD / ATT over the pixels [xa, xb] x [ya, yb]
-// of the strip buffer.  The warp's lanes cover the particle's rows (the
-// next power of two of their count, at most 32) times 32 / that many
-// consecutive columns, stepping across the columns.
-//   ellipsoid: t = T sqrt(1 - rho^2), rho^2 = u'^2 + v'^2 with
-//              u' = (c ex + s ey) / a, v' = (-s ex + c ey) / b, evaluated
-//              in float32 and redone in float-float inside the rim band;
-//   prism:     t = clamp(g min(hx - |u|, hy - |v|), 0, T), g = 2 s_b dx.
-__device__ __forceinline__ void raster_particle(float2 *buf, int LS, int y0, const PRec &r,
-                                                int xa, int xb, int ya, int yb, int lane) {
-    const int bh = yb - ya + 1;
-    const int lyn = bh >= 32 ? 32 : (bh <= 1 ? 1 : 1 << (32 - __clz(bh - 1)));
-    const int lxn = 32 / lyn;
-    const int shx = ilog2(lxn);
-    const int lx = lane & (lxn - 1), ly = lane >> shx;
-    if (r.g > 0.f) {
-        for (int yy = ya + ly; yy <= yb; yy += lyn) {
-            const float ey = ((float)yy + 0.5f) - r.cy;
-            const float s_ey = r.sh * ey, c_ey = r.ch * ey;
-            float2 *row = buf + (yy - y0) * LS;
-            for (int xx = xa + lx; xx <= xb; xx += lxn) {
-                const float ex = ((float)xx + 0.5f) - r.cx;
-                const float u = fmaf(r.ch, ex, s_ey);
-                const float v = fmaf(-r.sh, ex, c_ey);
-                const float d = fminf(r.p0h - fabsf(u), r.p1h - fabsf(v));
-                const float t = fminf(fmaxf(r.g * d, 0.f), r.T);
-                float2 acc = row[pad16(xx)];
-                acc.x = fmaf(r.dn, t, acc.x);
-                acc.y = fmaf(r.mu, t, acc.y);
-                row[pad16(xx)] = acc;
-            }
-        }
-    } else {
-        const float cia = r.ch * r.p0h, sia = r.sh * r.p0h;
-        const float cib = r.ch * r.p1h, sib = r.sh * r.p1h;
-        for (int yy = ya + ly; yy <= yb; yy += lyn) {
-            const float yc = (float)yy + 0.5f;
-            const float ey = yc - r.cy;
-            const float u0 = sia * ey, v0 = cib * ey;
-            float2 *row = buf + (yy - y0) * LS;
-            for (int xx = xa + lx; xx <= xb; xx += lxn) {
-                const float xc = (float)xx + 0.5f;
-                const float ex = xc - r.cx;
-                const float ua = fmaf(cia, ex, u0);
-                const float vb = fmaf(-sib, ex, v0);
-                float delta = 1.f - fmaf(ua, ua, vb * vb);
-                if (delta < kRimBand) {
-                    if (delta <= -kRimBand) continue;
-                    delta = ellipse_delta_ff(r, xc, yc);
-                    if (!(delta > 0.f)) continue;
-                }
-                const float t = r.T * delta * rsqrtf(delta);
-                float2 acc = row[pad16(xx)];
-                acc.x = fmaf(r.dn, t, acc.x);
-                acc.y = fmaf(r.mu, t, acc.y);
-                row[pad16(xx)] = acc;
-            }
-        }
-    }
-}
-
-// OPD/ATT of the strip [y0, y0 + R) into buf, particles in list order.
-// The band list is consumed kThreads entries at a time: every thread tests
-// one entry against the strip's rows and the kept entries are compacted, in
-// order, into shared memory together with their records (one parallel
-// global load per round instead of one dependent load per particle).  Each
-// warp then rasterises, in order, the staged particles that overlap its own
-// N/8 columns.
-template <int N>
-__device__ void raster_strip(const StripArgs &a, int s, int y0, float2 *buf, PRec *srec,
-                             Rect *srect, int *wsum) {
-    constexpr int LS = line_stride(N);
-    constexpr int NW = kThreads / 32;
-    const Geometry &geo = a.geo;
-    const SceneDev &sc = a.sc[s];
-    const int band = y0 / geo.BH;
-    const int32_t *off = a.w.band_off + (size_t)s * (geo.nbands + 1);
-    const int hi = min(off[band + 1], sc.pair_cap);
-    const int lo = min(off[band], hi);
-    const int32_t *ids = a.w.pairs + sc.pair0;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cw = N / NW;
-    const int c0 = warp * cw, c1 = c0 + cw - 1;
-    const int ylast = y0 + geo.R - 1;
-    const unsigned lt = lanemask_lt();
-    for (int base = lo; base < hi; base += kThreads) {
-        const int i = base + threadIdx.x;
-        int id = 0;
-        Rect q = {1, 0, 1, 0};
-        if (i < hi) {
-            id = ids[i];
-            q = a.w.rect[id];
-        }
-        const bool keep = i < hi && q.y0 <= ylast && q.y1 >= y0;
-        const unsigned m = __ballot_sync(kFull, keep);
-        if (lane == 0) wsum[warp] = __popc(m);
-        __syncthreads();
-        int before = 0, nl = 0;
-#pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            const int c = wsum[k];
-            before += k < warp ? c : 0;
-            nl += c;
-        }
-        if (keep) {
-            const int slot = before + __popc(m & lt);
-            srect[slot] = q;
-            srec[slot] = a.w.rec[id];
-        }
-        __syncthreads();
-        for (int i0 = 0; i0 < nl; i0 += 32) {
-            const int k = i0 + lane;
-            Rect r = {1, 0, 1, 0};
-            if (k < nl) r = srect[k];
-            unsigned mm = __ballot_sync(kFull, k < nl && r.x0 <= c1 && r.x1 >= c0);
-            while (mm) {
-                const int src = __ffs(mm) - 1;
-                mm &= mm - 1;
-                const Rect rq = srect[i0 + src];
-                const PRec rec = srec[i0 + src];
-                raster_particle(buf, LS, y0, rec, max((int)rq.x0, c0), min((int)rq.x1, c1),
-                                max((int)rq.y0, y0), min((int)rq.y1, ylast), lane);
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// Elements of an 8192-sample set handled by each thread in the copy loops;
-// the loops are fully unrolled so that every thread has all of its global
-// loads in flight at once.
-constexpr int kEPT = kSetElems / kThreads;
 
 template <int N, int MODE>
 __global__ void __launch_bounds__(kThreads, 2) k_strip_forward(const __grid_constant__ StripArgs a) {
@@ -199,7 +54,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_strip_forward(const __grid_cons
         float4 *b4 = reinterpret_cast<float4 *>(buf);
         for (int i = threadIdx.x; i < R * LS / 2; i += kThreads) b4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
-        raster_strip<N>(a, s, y0, buf, srec, srect, wsum);
+        raster_strip<N>(a.geo, a.w, a.sc[s], s, y0, buf, srec, srect, wsum);
     }
     __syncthreads();
     if constexpr (MODE == kStripOpdOnly) {
@@ -238,28 +93,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_strip_forward(const __grid_cons
                 G[((size_t)bk * geo.H + y0 + r) * B + c] = buf[r * LS + pad16(kx)];
         }
     }
-}
-
-// ------------------------------------------------------------ optical head
-// Transfer function at signed frequency (fx, fy) inside the pupil chord,
-// including 1/(HW):
-// pupil circ * exp(i dz (sqrt(k0^2 - |q|^2) - k0)) at q = k + k_ill (Eq. 3,
-// oblique shift), times 2i sin(k . ds + theta) for DIC (Eq. 5).  The defocus
-// phase is evaluated as -dz |q|^2 / (sqrt(k0^2 - |q|^2) + k0), which has no
-// cancellation for small |q|.
-__device__ __forceinline__ float2 transfer(const ModeDev &md, int fx, int fy) {
-    const float kx = (float)fx * md.kstep_x, ky = (float)fy * md.kstep_y;
-    const float qx = kx + md.qoff_x, qy = ky + md.qoff_y;
-    const float q2 = fmaf(qx, qx, qy * qy);
-    const float chi = -md.dz * q2 / (sqrtf(fmaxf(fmaf(md.k0, md.k0, -q2), 0.f)) + md.k0);
-    float sn, cs;
-    sincosf(chi, &sn, &cs);
-    float2 h = make_float2(cs, sn);
-    if (md.dic) {
-        const float g = 2.f * sinf(fmaf(kx, md.dsx, fmaf(ky, md.dsy, md.bias)));
-        h = make_float2(-sn * g, cs * g);
-    }
-    return make_float2(h.x * md.scale, h.y * md.scale);
 }
 
 template <int N, bool MULTI>
@@ -373,20 +206,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_strip_inverse(const __grid_cons
             const float2 v = buf[(e / N) * LS + pad16(e % N)];
             img[e] = fmaf(v.x, v.x, v.y * v.y);
         }
-    }
-}
-
-template <template <int> class F, typename... Args>
-cudaError_t dispatch_n(int n, Args &&...args) {
-    switch (n) {
-        case 32: return F<32>::run(args...);
-        case 64: return F<64>::run(args...);
-        case 128: return F<128>::run(args...);
-        case 256: return F<256>::run(args...);
-        case 512: return F<512>::run(args...);
-        case 1024: return F<1024>::run(args...);
-        case 2048: return F<2048>::run(args...);
-        default: return cudaErrorInvalidValue;
     }
 }
 

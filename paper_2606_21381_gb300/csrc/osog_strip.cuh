@@ -1,0 +1,369 @@
+// Device pieces shared by the forward and adjoint render kernels: the
+// ordered strip raster, the transfer functions of the optical head, and a
+// dispatcher over the power-of-two transform sizes.
+#pragma once
+
+#include "osog_fft.cuh"
+#include "osog_kernels.h"
+
+namespace osog {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
+
+// Accumulate one particle's OPD / ATT over the pixels [xa, xb] x [ya, yb]
+// of the strip buffer.  The warp's lanes cover the particle's rows (the
+// next power of two of their count, at most 32) times 32 / that many
+// consecutive columns, stepping across the columns.
+//   ellipsoid: t = T sqrt(1 - rho^2), rho^2 = u'^2 + v'^2 with
+//              u' = (c ex + s ey) / a, v' = (-s ex + c ey) / b, evaluated
+//              in float32 and redone in float-float inside the rim band;
+//   prism:     t = clamp(g min(hx - |u|, hy - |v|), 0, T), g = 2 s_b dx.
+__device__ __forceinline__ void raster_particle(float2 *buf, int LS, int y0, const PRec &r,
+                                                int xa, int xb, int ya, int yb, int lane) {
+    const int bh = yb - ya + 1;
+    const int lyn = bh >= 32 ? 32 : (bh <= 1 ? 1 : 1 << (32 - __clz(bh - 1)));
+    const int lxn = 32 / lyn;
+    const int shx = ilog2(lxn);
+    const int lx = lane & (lxn - 1), ly = lane >> shx;
+    if (r.g > 0.f) {
+        for (int yy = ya + ly; yy <= yb; yy += lyn) {
+            const float ey = ((float)yy + 0.5f) - r.cy;
+            const float s_ey = r.sh * ey, c_ey = r.ch * ey;
+            float2 *row = buf + (yy - y0) * LS;
+            for (int xx = xa + lx; xx <= xb; xx += lxn) {
+                const float ex = ((float)xx + 0.5f) - r.cx;
+                const float u = fmaf(r.ch, ex, s_ey);
+                const float v = fmaf(-r.sh, ex, c_ey);
+                const float d = fminf(r.p0h - fabsf(u), r.p1h - fabsf(v));
+                const float t = fminf(fmaxf(r.g * d, 0.f), r.T);
+                float2 acc = row[pad16(xx)];
+                acc.x = fmaf(r.dn, t, acc.x);
+                acc.y = fmaf(r.mu, t, acc.y);
+                row[pad16(xx)] = acc;
+            }
+        }
+    } else {
+        const float cia = r.ch * r.p0h, sia = r.sh * r.p0h;
+        const float cib = r.ch * r.p1h, sib = r.sh * r.p1h;
+        for (int yy = ya + ly; yy <= yb; yy += lyn) {
+            const float yc = (float)yy + 0.5f;
+            const float ey = yc - r.cy;
+            const float u0 = sia * ey, v0 = cib * ey;
+            float2 *row = buf + (yy - y0) * LS;
+            for (int xx = xa + lx; xx <= xb; xx += lxn) {
+                const float xc = (float)xx + 0.5f;
+                const float ex = xc - r.cx;
+                const float ua = fmaf(cia, ex, u0);
+                const float vb = fmaf(-sib, ex, v0);
+                float delta = 1.f - fmaf(ua, ua, vb * vb);
+                if (delta < kRimBand) {
+                    if (delta <= -kRimBand) continue;
+                    delta = ellipse_delta_ff(r, xc, yc);
+                    if (!(delta > 0.f)) continue;
+                }
+                const float t = r.T * delta * rsqrtf(delta);
+                float2 acc = row[pad16(xx)];
+                acc.x = fmaf(r.dn, t, acc.x);
+                acc.y = fmaf(r.mu, t, acc.y);
+                row[pad16(xx)] = acc;
+            }
+        }
+    }
+}
+
+// OPD/ATT of the strip [y0, y0 + R) into buf, particles in list order.
+// The band list is consumed kThreads entries at a time: every thread tests
+// one entry against the strip's rows and the kept entries are compacted, in
+// order, into shared memory together with their records (one parallel
+// global load per round instead of one dependent load per particle).  Each
+// warp then rasterises, in order, the staged particles that overlap its own
+// N/8 columns.
+template <int N>
+__device__ void raster_strip(const Geometry &geo, const Work &w, const SceneDev &sc, int s,
+                             int y0, float2 *buf, PRec *srec, Rect *srect, int *wsum) {
+    constexpr int LS = line_stride(N);
+    constexpr int NW = kThreads / 32;
+    const int band = y0 / geo.BH;
+    const int32_t *off = w.band_off + (size_t)s * (geo.nbands + 1);
+    const int hi = min(off[band + 1], sc.pair_cap);
+    const int lo = min(off[band], hi);
+    const int32_t *ids = w.pairs + sc.pair0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cw = N / NW;
+    const int c0 = warp * cw, c1 = c0 + cw - 1;
+    const int ylast = y0 + geo.R - 1;
+    const unsigned lt = lanemask_lt();
+    for (int base = lo; base < hi; base += kThreads) {
+        const int i = base + threadIdx.x;
+        int id = 0;
+        Rect q = {1, 0, 1, 0};
+        if (i < hi) {
+            id = ids[i];
+            q = w.rect[id];
+        }
+        const bool keep = i < hi && q.y0 <= ylast && q.y1 >= y0;
+        const unsigned m = __ballot_sync(kFull, keep);
+        if (lane == 0) wsum[warp] = __popc(m);
+        __syncthreads();
+        int before = 0, nl = 0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            const int c = wsum[k];
+            before += k < warp ? c : 0;
+            nl += c;
+        }
+        if (keep) {
+            const int slot = before + __popc(m & lt);
+            srect[slot] = q;
+            srec[slot] = w.rec[id];
+        }
+        __syncthreads();
+        for (int i0 = 0; i0 < nl; i0 += 32) {
+            const int k = i0 + lane;
+            Rect r = {1, 0, 1, 0};
+            if (k < nl) r = srect[k];
+            unsigned mm = __ballot_sync(kFull, k < nl && r.x0 <= c1 && r.x1 >= c0);
+            while (mm) {
+                const int src = __ffs(mm) - 1;
+                mm &= mm - 1;
+                const Rect rq = srect[i0 + src];
+                const PRec rec = srec[i0 + src];
+                raster_particle(buf, LS, y0, rec, max((int)rq.x0, c0), min((int)rq.x1, c1),
+                                max((int)rq.y0, y0), min((int)rq.y1, ylast), lane);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Elements of an 8192-sample set handled by each thread in the copy loops;
+// the loops are fully unrolled so that every thread has all of its global
+// loads in flight at once.
+constexpr int kEPT = kSetElems / kThreads;
+
+// ------------------------------------------------------------ optical head
+// Transfer function at signed frequency (fx, fy) inside the pupil chord,
+// including 1/(HW):
+// pupil circ * exp(i dz (sqrt(k0^2 - |q|^2) - k0)) at q = k + k_ill (Eq. 3,
+// oblique shift), times 2i sin(k . ds + theta) for DIC (Eq. 5).  The defocus
+// phase is evaluated as -dz |q|^2 / (sqrt(k0^2 - |q|^2) + k0), which has no
+// cancellation for small |q|.
+__device__ __forceinline__ float2 transfer(const ModeDev &md, int fx, int fy) {
+    const float kx = (float)fx * md.kstep_x, ky = (float)fy * md.kstep_y;
+    const float qx = kx + md.qoff_x, qy = ky + md.qoff_y;
+    const float q2 = fmaf(qx, qx, qy * qy);
+    const float chi = -md.dz * q2 / (sqrtf(fmaxf(fmaf(md.k0, md.k0, -q2), 0.f)) + md.k0);
+    float sn, cs;
+    sincosf(chi, &sn, &cs);
+    float2 h = make_float2(cs, sn);
+    if (md.dic) {
+        const float g = 2.f * sinf(fmaf(kx, md.dsx, fmaf(ky, md.dsy, md.bias)));
+        h = make_float2(-sn * g, cs * g);
+    }
+    return make_float2(h.x * md.scale, h.y * md.scale);
+}
+
+// ---------------------------------------------------------------- layouts
+// A row-strip [y0, y0 + R) of a column-blocked array [W/B][H][B] (complex)
+// to and from the padded shared lines of an N = W point set.  Columns whose
+// signed frequency lies outside [cr.x, cr.y] (no pupil passes them) are
+// neither read (zero-filled) nor written.
+template <int N>
+__device__ __forceinline__ void load_strip_blocked(float2 *buf, const float2 *src,
+                                                   const Geometry &geo, int y0, int2 cr) {
+    constexpr int LS = line_stride(N);
+    const int R = geo.R, B = geo.B, lb = ilog2(B), lr = ilog2(R), RN = R * N;
+    float2 v[kEPT];
+#pragma unroll
+    for (int i = 0; i < kEPT; ++i) {
+        const int e = threadIdx.x + i * kThreads;
+        const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
+        const int kx = bk * B + c, fx = kx < N / 2 ? kx : kx - N;
+        v[i] = e < RN && fx >= cr.x && fx <= cr.y ? src[((size_t)bk * geo.H + y0 + r) * B + c]
+                                                  : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < kEPT; ++i) {
+        const int e = threadIdx.x + i * kThreads;
+        const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
+        if (e < RN) buf[r * LS + pad16(bk * B + c)] = v[i];
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void store_strip_blocked(const float2 *buf, float2 *dst,
+                                                    const Geometry &geo, int y0, int2 cr) {
+    constexpr int LS = line_stride(N);
+    const int R = geo.R, B = geo.B, lb = ilog2(B), lr = ilog2(R), RN = R * N;
+#pragma unroll
+    for (int i = 0; i < kEPT; ++i) {
+        const int e = threadIdx.x + i * kThreads;
+        const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
+        const int kx = bk * B + c, fx = kx < N / 2 ? kx : kx - N;
+        if (e < RN && fx >= cr.x && fx <= cr.y)
+            dst[((size_t)bk * geo.H + y0 + r) * B + c] = buf[r * LS + pad16(kx)];
+    }
+}
+
+// A column block (B columns, N = H rows, contiguous [H][B]) to and from the
+// padded shared lines (line c = column c).  Inactive columns load as zero.
+template <int N>
+__device__ __forceinline__ void load_block(float2 *buf, const float2 *src, const Geometry &geo,
+                                           int bk, int2 cr) {
+    constexpr int LS = line_stride(N);
+    const int B = geo.B, lb = ilog2(B), NB = N * B, half = geo.W / 2;
+    float2 v[kEPT];
+#pragma unroll
+    for (int i = 0; i < kEPT; ++i) {
+        const int e = threadIdx.x + i * kThreads;
+        const int kx = bk * B + (e & (B - 1)), fx = kx < half ? kx : kx - geo.W;
+        v[i] = e < NB && fx >= cr.x && fx <= cr.y ? src[e] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < kEPT; ++i) {
+        const int e = threadIdx.x + i * kThreads;
+        if (e < NB) buf[(e & (B - 1)) * LS + pad16(e >> lb)] = v[i];
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void store_block(const float2 *buf, float2 *dst, const Geometry &geo) {
+    constexpr int LS = line_stride(N);
+    const int B = geo.B, lb = ilog2(B), NB = N * B;
+#pragma unroll
+    for (int i = 0; i < kEPT; ++i) {
+        const int e = threadIdx.x + i * kThreads;
+        if (e < NB) dst[e] = buf[(e & (B - 1)) * LS + pad16(e >> lb)];
+    }
+}
+
+// True if some column of block bk has a signed frequency inside cr.
+__device__ __forceinline__ bool block_active(const Geometry &geo, int bk, int2 cr) {
+    const int u0 = bk * geo.B, u1 = u0 + geo.B - 1, half = geo.W / 2;
+    const bool lo = u0 < half && u0 <= cr.y && min(u1, half - 1) >= cr.x;
+    const bool hi = u1 >= half && max(u0, half) - geo.W <= cr.y && u1 - geo.W >= cr.x;
+    return lo || hi;
+}
+
+// Transfer function and its derivatives with respect to (defocus,
+// shear_px, shear_angle, bias) at signed frequency (fx, fy) inside the
+// pupil chord, including 1/(HW).  With kappa = sqrt(k0^2 - |q|^2) - k0 the
+// pupil is P = exp(i dz kappa) and dP/ddz = i kappa P; DIC multiplies by
+// i g, g = 2 sin(a), a = k.ds + theta, whose derivatives are 2 cos(a) da.
+__device__ __forceinline__ void transfer_grad(const ModeDev &md, int fx, int fy, float2 &h,
+                                              float2 dh[4]) {
+    const float kx = (float)fx * md.kstep_x, ky = (float)fy * md.kstep_y;
+    const float qx = kx + md.qoff_x, qy = ky + md.qoff_y;
+    const float q2 = fmaf(qx, qx, qy * qy);
+    const float kappa = -q2 / (sqrtf(fmaxf(fmaf(md.k0, md.k0, -q2), 0.f)) + md.k0);
+    float sn, cs;
+    sincosf(md.dz * kappa, &sn, &cs);
+    const float sc = md.scale;
+    if (!md.dic) {
+        h = make_float2(cs * sc, sn * sc);
+        dh[0] = make_float2(-sn * kappa * sc, cs * kappa * sc);
+        dh[1] = dh[2] = dh[3] = make_float2(0.f, 0.f);
+        return;
+    }
+    float sa, ca;
+    sincosf(fmaf(kx, md.dsx, fmaf(ky, md.dsy, md.bias)), &sa, &ca);
+    const float g = 2.f * sa, gp = 2.f * ca;
+    h = make_float2(-sn * g * sc, cs * g * sc);
+    dh[0] = make_float2(-cs * kappa * g * sc, -sn * kappa * g * sc);
+    const float da[3] = {fmaf(kx, md.dsx1, ky * md.dsy1), fmaf(-kx, md.dsy, ky * md.dsx), 1.f};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dh[k + 1] = make_float2(-sn * gp * da[k] * sc, cs * gp * da[k] * sc);
+}
+
+// Adds to acc[0..7] the contribution of one pixel to dL/d(cx, cy, theta,
+// a|hx, b|hy, T, dn, mu) of particle r, given go = dL/dOPD and
+// ga = dL/dATT at the pixel centre (x, y): dn and mu collect t go and
+// t ga; the geometry collects (dn go + mu ga) dt/d(field).
+//   ellipsoid: t = T sqrt(delta), delta = 1 - u'^2 - v'^2, u' = u/a,
+//     v' = v/b; d delta/d(cx, cy) = 2 (u' c/a - v' s/b, u' s/a + v' c/b),
+//     d delta/d theta = 2 u' v' (a/b - b/a), d delta/d(a, b) = 2 (u'^2/a,
+//     v'^2/b); delta comes from float-float inside the rim band.
+//   prism: t = clamp(g d, 0, T), d = min(hx - |u|, hy - |v|): on the ramp
+//     dt = g dd with dd/d(hx or hy) = 1 and the chain through |u| or |v|;
+//     on the plateau dt/dT = 1.
+__device__ __forceinline__ void thickness_grad(const PRec &r, float xc, float yc, float go,
+                                               float ga, float acc[8]) {
+    const float ex = xc - r.cx, ey = yc - r.cy;
+    const float wgt = fmaf(r.dn, go, r.mu * ga);
+    if (r.g > 0.f) {
+        const float u = fmaf(r.ch, ex, r.sh * ey);
+        const float v = fmaf(-r.sh, ex, r.ch * ey);
+        const float du = r.p0h - fabsf(u), dv = r.p1h - fabsf(v);
+        const float gd = r.g * fminf(du, dv);
+        if (!(gd > 0.f)) return;
+        const float t = fminf(gd, r.T);
+        acc[6] = fmaf(go, t, acc[6]);
+        acc[7] = fmaf(ga, t, acc[7]);
+        if (gd >= r.T) {
+            acc[5] += wgt;
+            return;
+        }
+        const float q = wgt * r.g;
+        if (du <= dv) {
+            const float sq = u >= 0.f ? q : -q;
+            acc[0] = fmaf(sq, r.ch, acc[0]);
+            acc[1] = fmaf(sq, r.sh, acc[1]);
+            acc[2] = fmaf(-sq, v, acc[2]);
+            acc[3] += q;
+        } else {
+            const float sq = v >= 0.f ? q : -q;
+            acc[0] = fmaf(-sq, r.sh, acc[0]);
+            acc[1] = fmaf(sq, r.ch, acc[1]);
+            acc[2] = fmaf(sq, u, acc[2]);
+            acc[4] += q;
+        }
+        return;
+    }
+    const float cia = r.ch * r.p0h, sia = r.sh * r.p0h;
+    const float cib = r.ch * r.p1h, sib = r.sh * r.p1h;
+    const float ua = fmaf(cia, ex, sia * ey);
+    const float vb = fmaf(-sib, ex, cib * ey);
+    float delta = 1.f - fmaf(ua, ua, vb * vb);
+    if (delta < kRimBand) {
+        if (delta <= -kRimBand) return;
+        delta = ellipse_delta_ff(r, xc, yc);
+        if (!(delta > 0.f)) return;
+    }
+    const float rs = rsqrtf(delta);
+    const float sq = delta * rs;
+    const float t = r.T * sq;
+    acc[6] = fmaf(go, t, acc[6]);
+    acc[7] = fmaf(ga, t, acc[7]);
+    acc[5] = fmaf(wgt, sq, acc[5]);
+    const float q = wgt * r.T * rs;  // 2 * wgt * dt/ddelta
+    acc[0] = fmaf(q, fmaf(ua, cia, -vb * sib), acc[0]);
+    acc[1] = fmaf(q, fmaf(ua, sia, vb * cib), acc[1]);
+    acc[2] = fmaf(q * ua * vb, r.p1h / r.p0h - r.p0h / r.p1h, acc[2]);
+    acc[3] = fmaf(q * ua * ua, r.p0h, acc[3]);
+    acc[4] = fmaf(q * vb * vb, r.p1h, acc[4]);
+}
+
+template <template <int> class F, typename... Args>
+cudaError_t dispatch_n(int n, Args &&...args) {
+    switch (n) {
+        case 32: return F<32>::run(args...);
+        case 64: return F<64>::run(args...);
+        case 128: return F<128>::run(args...);
+        case 256: return F<256>::run(args...);
+        case 512: return F<512>::run(args...);
+        case 1024: return F<1024>::run(args...);
+        case 2048: return F<2048>::run(args...);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace osog

@@ -88,6 +88,29 @@ class Renderer:
               "osog_render")
         return out
 
+    def backward(self, soa: torch.Tensor, n: int | None, optics: dict, grad_image: torch.Tensor,
+                 stream=None):
+        """osog_render_backward: (dL/dsoa (9, ld), dL/d(defocus, shear_px,
+        shear_angle, bias_phase) (4,)) for grad_image = dL/dI of shape (K, H, W)."""
+        self._check_soa(soa)
+        n = soa.shape[1] if n is None else int(n)
+        K = n_modes(optics)
+        if grad_image.shape != (K, self.H, self.W) or grad_image.dtype != torch.float32 \
+                or not grad_image.is_contiguous() or grad_image.device.type != "cuda":
+            raise ValueError("grad_image must be a contiguous cuda float32 (K, H, W) tensor")
+        gsoa = torch.zeros_like(soa)
+        gopt = torch.zeros(4, dtype=torch.float32, device=self.device)
+        nbytes = int(self._L.osog_backward_workspace_size(self.plan, n, K))
+        if nbytes == 0:
+            raise OsogError(1, "osog_backward_workspace_size")
+        ws = self.workspace(nbytes)
+        o = optics_struct(optics)
+        check(self._L.osog_render_backward(self.plan, _ptr(soa), soa.shape[1], n, ctypes.byref(o),
+                                           _ptr(grad_image), _ptr(gsoa), _ptr(gopt), _ptr(ws),
+                                           ws.numel(), _stream(stream)),
+              "osog_render_backward")
+        return gsoa, gopt
+
     def render_opd(self, soa: torch.Tensor, n: int | None, optics: dict, out=None, stream=None):
         """osog_render_opd: (H, W, 2) float32 OPD / ATT map."""
         self._check_soa(soa)
@@ -164,7 +187,8 @@ class Renderer:
         check(self._L.osog_profile_begin(self.plan), "osog_profile_begin")
 
     def profile_end(self, stream=None) -> dict:
-        ms = (ctypes.c_float * 6)()
-        cnt = (ctypes.c_int32 * 6)()
+        nk = len(_lib.KERNEL_CLASSES)
+        ms = (ctypes.c_float * nk)()
+        cnt = (ctypes.c_int32 * nk)()
         check(self._L.osog_profile_end(self.plan, _stream(stream), ms, cnt), "osog_profile_end")
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(_lib.KERNEL_CLASSES)}
