@@ -273,6 +273,26 @@ def run_gpu(args, rank, world, local_rank):
             stream.synchronize()
             single40k.append(a.elapsed_time(b))
 
+        # ---- forward + adjoint of the inverse-rendering scene (512^2, 200
+        #      particles, brightfield + DIC), one loss gradient per iteration
+        fb_soa, fb_o = scenes.inverse_512()
+        fb_r = Renderer(512, 512, dev)
+        fb_x = torch.from_numpy(fb_soa).to(dev)
+        fb_w = torch.randn((2, 512, 512), device=dev)
+        fb_ms = []
+        for i in range(max(5, min(args.steps, 50)) + 3):
+            a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+            a.record(stream)
+            img = fb_r.render(fb_x, None, fb_o, stream=stream)
+            fb_r.backward(fb_x, None, fb_o, fb_w, stream=stream)
+            b.record(stream)
+            stream.synchronize()
+            if i >= 3:
+                fb_ms.append(a.elapsed_time(b))
+        if fb_r.sync_status(stream) != 0:
+            raise RuntimeError("device status set in the forward + adjoint run")
+        del img
+
         # ---- end to end from pinned host buffers through the public API
         soa_host = torch.from_numpy(soa_all).pin_memory()
         img_host = torch.empty((SCENES, K, SIZE, SIZE), dtype=torch.float32).pin_memory()
@@ -291,11 +311,12 @@ def run_gpu(args, rank, world, local_rank):
         if status != 0:
             raise RuntimeError(f"device status {status} after the timed runs")
     return finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms,
-                  single40k, e2e_ms, launches, clocks, wall, K, soas=soas, optics=optics)
+                  single40k, e2e_ms, launches, clocks, wall, K, soas=soas, optics=optics,
+                  fwd_bwd_ms=fb_ms)
 
 
 def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms, single40k,
-           e2e_ms, launches, clocks, wall, K, soas=None, optics=None):
+           e2e_ms, launches, clocks, wall, K, soas=None, optics=None, fwd_bwd_ms=None):
     import torch
     import torch.distributed as dist
 
@@ -310,9 +331,8 @@ def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms
         return None
 
     # dominant kernel and its roofline
-    kernels = {k: {"ms_total": v[0], "launches": v[1],
-                   "ms_per_launch": v[0] / v[1] if v[1] else None}
-               for k, v in prof.items()}
+    kernels = {k: {"ms_total": v[0], "launches": v[1], "ms_per_launch": v[0] / v[1]}
+               for k, v in prof.items() if v[1] > 0}
     tot = sum(v["ms_total"] for v in kernels.values()) or 1.0
     for v in kernels.values():
         v["share"] = v["ms_total"] / tot
@@ -354,6 +374,10 @@ def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms
                 "value": round(SCENES / (statistics.median(e2e_ms) / 1e3), 2), "unit": "frames/s",
                 "h2d_bytes_per_step": int(soa_all.nbytes),
                 "d2h_bytes_per_step": int(SCENES * K * SIZE * SIZE * 4)},
+        "fwd_bwd": None if not fwd_bwd_ms else {
+            "ms": round(statistics.median(fwd_bwd_ms), 4),
+            "workload": "512x512, 200 particles, brightfield + DIC: osog_render + "
+                        "osog_render_backward (recomputed forward, adjoint)"},
         "gpu_launches": int(launches),
         "clocks": clocks.summary(),
         "wall_s_timed": round(wall, 4),

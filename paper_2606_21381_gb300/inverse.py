@@ -1,0 +1,159 @@
+"""Differentiable inverse rendering (the paper's DiffOSOG, Sec. IV.B), driven
+by the hand-written adjoint.
+
+Given target images of a scene, recover each particle's dn, thickness T,
+centre and orientation plus the global defocus and DIC shear by gradient
+descent on the image misfit, starting from perturbed guesses.  As in the
+paper's curriculum (coarse structure first, then detail), the misfit is
+taken through a low-pass filter whose cut-off rises from a small numerical
+aperture to the objective's over the first part of the run; both the model
+and the target images pass through the same filter.
+
+The render and its gradient run in libosog; the loss, the filter and Adam
+are plain torch on the device.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from .autograd import OPTICS_PARAMS, render
+from .render import Renderer
+
+# particle-tensor rows the solver updates: cx, cy, theta, T, dn
+FREE_ROWS = (0, 1, 2, 5, 6)
+
+
+@dataclass
+class SolveConfig:
+    steps: int = 500
+    na_start: float = 0.1            # curriculum: low-pass cut-off at step 0 (NA units)
+    curriculum_frac: float = 0.6     # fraction of steps over which the cut-off rises
+    lr_pos: float = 0.05             # px
+    lr_theta: float = 0.01           # rad
+    lr_T: float = 0.01               # um
+    lr_dn: float = 4e-4
+    lr_defocus: float = 0.02         # um
+    lr_shear: float = 0.01           # px
+    betas: tuple = (0.9, 0.99)
+    log_every: int = 0
+
+
+@dataclass
+class SolveResult:
+    soa: np.ndarray                  # recovered particle tensor (9, n)
+    optics_params: np.ndarray        # recovered (defocus, shear_px, shear_angle, bias)
+    losses: list = field(default_factory=list)
+    seconds: float = 0.0
+    steps: int = 0
+
+
+def lowpass_mask(H: int, W: int, dx: float, lam: float, na: float, device) -> torch.Tensor:
+    """rfft2 mask keeping spatial frequencies below 2 NA / lambda (the
+    intensity band of a coherent image through a pupil of that NA)."""
+    fy = torch.fft.fftfreq(H, dx, device=device)[:, None]
+    fx = torch.fft.rfftfreq(W, dx, device=device)[None, :]
+    return ((fx * fx + fy * fy) <= (2.0 * na / lam) ** 2).float()
+
+
+def filtered(img: torch.Tensor, mask: torch.Tensor) -> torch.Tensor:
+    return torch.fft.irfft2(torch.fft.rfft2(img) * mask, s=img.shape[-2:])
+
+
+def perturb(soa: np.ndarray, optics: dict, rng: np.random.Generator, frac: float = 0.2):
+    """Initial guess: dn, T multiplied by U(1 - frac, 1 + frac); centres moved
+    by up to frac times the mean semi-axis; angles by up to frac rad; the
+    defocus and shear length multiplied likewise."""
+    s = soa.copy()
+    n = s.shape[1]
+    for row in (5, 6):
+        s[row] *= rng.uniform(1 - frac, 1 + frac, n).astype(np.float32)
+    r = 0.5 * (s[3] + s[4])
+    for row in (0, 1):
+        s[row] += (rng.uniform(-frac, frac, n) * r).astype(np.float32)
+    s[2] += rng.uniform(-frac, frac, n).astype(np.float32)
+    o = dict(optics)
+    o["defocus"] = optics["defocus"] * rng.uniform(1 - frac, 1 + frac) if optics["defocus"] else \
+        rng.uniform(-frac, frac)
+    o["shear_px"] = optics["shear_px"] * rng.uniform(1 - frac, 1 + frac)
+    return s, o
+
+
+def solve(target: torch.Tensor, soa0: np.ndarray, optics0: dict, renderer: Renderer,
+          cfg: SolveConfig | None = None, fixed_optics: bool = False) -> SolveResult:
+    """Adam on the curriculum-filtered squared image misfit.  target is the
+    (K, H, W) measured image; soa0 / optics0 the initial guess."""
+    cfg = cfg or SolveConfig()
+    dev = renderer.device
+    soa = torch.from_numpy(np.ascontiguousarray(soa0, dtype=np.float32)).to(dev)
+    free = torch.zeros_like(soa, dtype=torch.bool)
+    free[list(FREE_ROWS)] = True
+    x = soa.clone().requires_grad_(True)
+    params = torch.tensor([float(optics0[k]) for k in OPTICS_PARAMS], dtype=torch.float64,
+                          requires_grad=not fixed_optics)
+    lr = torch.zeros_like(soa)
+    lr[0] = lr[1] = cfg.lr_pos
+    lr[2] = cfg.lr_theta
+    lr[5] = cfg.lr_T
+    lr[6] = cfg.lr_dn
+    plr = torch.tensor([cfg.lr_defocus, cfg.lr_shear, 0.0, 0.0], dtype=torch.float64)
+    m1, m2 = torch.zeros_like(soa), torch.zeros_like(soa)
+    p1, p2 = torch.zeros_like(params), torch.zeros_like(params)
+    b1, b2 = cfg.betas
+    H, W = target.shape[-2:]
+    norm = float(target.numel())
+    res = SolveResult(soa=None, optics_params=None)
+    t0 = time.perf_counter()
+    ramp = max(1, int(cfg.steps * cfg.curriculum_frac))
+    for it in range(cfg.steps):
+        na = cfg.na_start + (optics0["NA"] - cfg.na_start) * min(1.0, it / ramp)
+        mask = lowpass_mask(H, W, optics0["dx"], optics0["lambda_um"], na, dev)
+        img = render(x, optics0, renderer, params)
+        loss = ((filtered(img, mask) - filtered(target, mask)) ** 2).sum() / norm
+        gx, gp = torch.autograd.grad(loss, (x, params), allow_unused=True)
+        with torch.no_grad():
+            t = it + 1
+            m1.mul_(b1).add_(gx, alpha=1 - b1)
+            m2.mul_(b2).addcmul_(gx, gx, value=1 - b2)
+            step = lr * (m1 / (1 - b1 ** t)) / (torch.sqrt(m2 / (1 - b2 ** t)) + 1e-30)
+            x.sub_(torch.where(free, step, torch.zeros_like(step)))
+            x[5].clamp_(min=1e-3)
+            if gp is not None and not fixed_optics:
+                gp = gp.cpu()
+                p1.mul_(b1).add_(gp, alpha=1 - b1)
+                p2.mul_(b2).addcmul_(gp, gp, value=1 - b2)
+                params.sub_(plr * (p1 / (1 - b1 ** t)) / (torch.sqrt(p2 / (1 - b2 ** t)) + 1e-30))
+        res.losses.append(float(loss.detach()))
+        if cfg.log_every and it % cfg.log_every == 0:
+            print(f"step {it:4d} NA {na:.3f} loss {float(loss):.3e}")
+    torch.cuda.synchronize(dev)
+    res.seconds = time.perf_counter() - t0
+    res.steps = cfg.steps
+    res.soa = x.detach().cpu().numpy()
+    res.optics_params = params.detach().numpy()
+    return res
+
+
+def errors(est: np.ndarray, truth: np.ndarray, est_params=None, truth_optics=None) -> dict:
+    """Recovery errors: median relative error of dn, T and dn T; median
+    centre error (px); median angle error (rad, modulo pi); the fraction of
+    particles with both dn and T within 1%; defocus (um) and relative shear
+    errors when the optics are given."""
+    d = {}
+    d["dn_rel_median"] = float(np.median(np.abs(est[6] - truth[6]) / np.abs(truth[6])))
+    d["T_rel_median"] = float(np.median(np.abs(est[5] - truth[5]) / np.abs(truth[5])))
+    d["dnT_rel_median"] = float(np.median(np.abs(est[6] * est[5] - truth[6] * truth[5])
+                                          / np.abs(truth[6] * truth[5])))
+    d["centre_px_median"] = float(np.median(np.hypot(est[0] - truth[0], est[1] - truth[1])))
+    dth = np.abs((est[2] - truth[2] + math.pi / 2) % math.pi - math.pi / 2)
+    d["theta_rad_median"] = float(np.median(dth))
+    d["frac_dn_T_within_1pct"] = float(np.mean((np.abs(est[6] - truth[6]) <= 0.01 * np.abs(truth[6]))
+                                               & (np.abs(est[5] - truth[5]) <= 0.01 * np.abs(truth[5]))))
+    if est_params is not None and truth_optics is not None:
+        d["defocus_abs"] = float(abs(est_params[0] - truth_optics["defocus"]))
+        d["shear_rel"] = float(abs(est_params[1] - truth_optics["shear_px"]) / truth_optics["shear_px"])
+    return d
