@@ -180,6 +180,9 @@ def algorithmic_bytes(kernel: str, counts, H: int, W: int, K: int, pairs: int,
         "strip_forward": px * 8 * active + n * (64 + 8) + pairs * 4,
         "column": px * (8 + 8 * K) * active,
         "strip_inverse": px * 8 * K * active + px * 4 * K,
+        # the three render stages in one launch: their bytes together
+        "persistent": px * 8 * active + n * (64 + 8) + pairs * 4 + px * (8 + 8 * K) * active
+        + px * 8 * K * active + px * 4 * K,
     }[kernel])
 
 
@@ -209,6 +212,9 @@ def run_gpu(args, rank, world, local_rank):
         r.batch(soa_dev, offs, optics, out=out, tuning=tuning, stream=stream)
 
     with torch.cuda.stream(stream):
+        # the project's autotuner picks band height, pair reservation and
+        # launch mode for this batch shape; later submits use its choice
+        tuned = r.autotune(soa_dev, offs, optics, out=out, stream=stream)
         for _ in range(max(3, args.warmup)):
             flush.fill_(1)
             step()
@@ -236,12 +242,32 @@ def run_gpu(args, rank, world, local_rank):
         step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
         timed_ms = float(sum(step_ms))
 
-        # ---- per-kernel times (same batch, direct launches, events per kernel)
+        # ---- per-kernel times: the timed configuration (direct launches,
+        #      events per kernel), then the three-launch breakdown
         r.profile_begin()
         for i in range(args.steps):
             flush.fill_(i & 0xff)
-            step()
+            step({"use_graph": 0})
         prof = r.profile_end(stream)
+        r.profile_begin()
+        for i in range(min(args.steps, 20)):
+            flush.fill_(i & 0xff)
+            step({"use_graph": 0, "persistent": -1})
+        prof3 = r.profile_end(stream)
+
+        # ---- both launch modes of the batched path (graph replays)
+        modes_ms = {}
+        for name, pers in (("three_launch", -1), ("persistent", 1)):
+            t = []
+            for i in range(max(3, min(args.steps, 20))):
+                flush.fill_(1)
+                a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+                a.record(stream)
+                step({"persistent": pers})
+                b.record(stream)
+                stream.synchronize()
+                t.append(a.elapsed_time(b))
+            modes_ms[name] = round(statistics.median(t[1:]), 4)
 
         # ---- per-scene launches of the same batch (osog_render per scene)
         per_scene_ms, single40k, e2e_ms = [float("nan")], [float("nan")], [float("nan")]
@@ -250,7 +276,8 @@ def run_gpu(args, rank, world, local_rank):
             if status != 0:
                 raise RuntimeError(f"device status {status} after the timed runs")
             return finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms,
-                          single40k, e2e_ms, launches, clocks, wall, K)
+                          single40k, e2e_ms, launches, clocks, wall, K,
+                          extra={"autotuned": tuned, "kernels_three_launch": prof3})
         per_scene_ms = []
         singles = [torch.from_numpy(s).to(dev) for s in soas]
         for i in range(max(2, args.steps // 4)):
@@ -312,11 +339,13 @@ def run_gpu(args, rank, world, local_rank):
             raise RuntimeError(f"device status {status} after the timed runs")
     return finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms,
                   single40k, e2e_ms, launches, clocks, wall, K, soas=soas, optics=optics,
-                  fwd_bwd_ms=fb_ms)
+                  fwd_bwd_ms=fb_ms, extra={"autotuned": tuned, "batched_modes_ms": modes_ms,
+                                           "kernels_three_launch": prof3})
 
 
 def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms, single40k,
-           e2e_ms, launches, clocks, wall, K, soas=None, optics=None, fwd_bwd_ms=None):
+           e2e_ms, launches, clocks, wall, K, soas=None, optics=None, fwd_bwd_ms=None,
+           extra=None):
     import torch
     import torch.distributed as dist
 
@@ -351,7 +380,8 @@ def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded scenes shaped like the paper's workloads)",
-        "config": dict(workload_config(counts), parallelism=f"replicas x{world}"),
+        "config": dict(workload_config(counts), parallelism=f"replicas x{world}",
+                       tuning=(extra or {}).get("autotuned")),
         "particles_per_s": round(sum(counts) * args.steps * world / (timed_max / 1e3), 1),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -362,6 +392,10 @@ def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms
                           "achieved_gbs": round(step_bytes / (ms_step / 1e3) / 1e9, 1),
                           "frac": round(step_bytes / (ms_step / 1e3) / 1e9 / peak, 4)},
         "kernels": kernels,
+        "kernels_three_launch": {k: {"ms_per_launch": v[0] / v[1], "share": v[0] / max(
+            sum(x[0] for x in (extra or {}).get("kernels_three_launch", {}).values()), 1e-30)}
+            for k, v in (extra or {}).get("kernels_three_launch", {}).items() if v[1] > 0},
+        "batched_modes_ms": (extra or {}).get("batched_modes_ms"),
         "per_scene_launches": None if args.quick else {
                                "ms_per_batch": round(statistics.median(per_scene_ms), 4),
                                "frames_per_s": round(SCENES / (statistics.median(per_scene_ms) / 1e3), 2),

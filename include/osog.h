@@ -76,7 +76,8 @@ extern "C" {
 #define OSOG_KERNEL_BWD_COLUMN 7
 #define OSOG_KERNEL_BWD_STRIP 8
 #define OSOG_KERNEL_BWD_REDUCE 9
-#define OSOG_KERNEL_CLASS_COUNT 10
+#define OSOG_KERNEL_PERSISTENT 10
+#define OSOG_KERNEL_CLASS_COUNT 11
 
 typedef struct osog_plan osog_plan_t;
 /* Binary-compatible with cudaStream_t; NULL is the legacy default stream. */
@@ -110,15 +111,25 @@ typedef struct {
 
 /*
  * Tuning of the batched path (osog_batch_submit).  Zero fields take the
- * autotuned or default value.
+ * value osog_autotune stored in the plan for this batch shape, else the
+ * default.
  *   pairs_per_particle  particle-band pairs reserved per particle (default 8)
  *   use_graph           1: replay the launch sequence as a CUDA graph that the
- *                       plan caches per batch shape; 0: launch directly
+ *                       plan caches per batch shape; 0 (or -1): launch directly
+ *   persistent          1: the three render stages of each group of up to 32
+ *                       scenes run as one persistent launch that pulls work
+ *                       items from a device queue (square canvases only);
+ *                       -1: three launches (default)
+ *   band_rows           rows per binning band (the raster's tile height): a
+ *                       multiple of the strip height 8192 / W that divides H
+ *                       and gives at most 64 bands; 0 = smallest such value
  */
 typedef struct {
     int32_t pairs_per_particle;
     int32_t use_graph;
-    int32_t reserved[6];
+    int32_t persistent;
+    int32_t band_rows;
+    int32_t reserved[4];
 } osog_tuning_t;
 
 /*
@@ -215,6 +226,23 @@ int osog_batch_submit(osog_plan_t *plan, const float *soa_all, int64_t ld,
                       const osog_optics_t *optics, float *images,
                       const osog_tuning_t *tuning, void *ws, size_t ws_bytes,
                       osog_stream_t stream);
+
+/*
+ * Autotuner of the batched path.  For this batch shape it measures, for
+ * each candidate band height (the smallest valid one and up to three
+ * doublings), the exact particle-band pairs per particle the batch needs (a
+ * binning dry run), then times the batch three times with three launches
+ * per group and, on square canvases, with the persistent launch, and keeps
+ * the fastest.  The choice is stored in the plan for (S, total particles,
+ * K) and used by later osog_batch_submit calls of that shape whose tuning
+ * leaves the fields at 0; it is also written to *out when out is not NULL.
+ * Arguments as for osog_batch_submit; images receive a valid render.  This
+ * call synchronises the stream and must not be captured into a graph.
+ */
+int osog_autotune(osog_plan_t *plan, const float *soa_all, int64_t ld,
+                  const int32_t *offsets, int32_t S, const osog_optics_t *optics,
+                  float *images, void *ws, size_t ws_bytes, osog_stream_t stream,
+                  osog_tuning_t *out);
 
 /* Synchronise `stream`, return the first device-latched status since the
  * last call (OSOG_OK if none) and clear it. */

@@ -14,7 +14,8 @@ from . import build as _build
 
 MODE_BF, MODE_OBLIQUE, MODE_DIC = 1, 2, 4
 KERNEL_CLASSES = ("bin_count", "bin_scan", "bin_fill", "strip_forward", "column",
-                  "strip_inverse", "bwd_rows", "bwd_column", "bwd_strip", "bwd_reduce")
+                  "strip_inverse", "bwd_rows", "bwd_column", "bwd_strip", "bwd_reduce",
+                  "persistent")
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_SIZE", 3: "WORKSPACE",
           4: "BIN_OVERFLOW", 5: "NONFINITE_INPUT", 6: "TIMEOUT", 7: "CUDA",
           8: "INVALID_PARTICLE"}
@@ -23,7 +24,7 @@ EXPORTS = ("osog_plan_create", "osog_plan_destroy", "osog_workspace_size", "osog
            "osog_render_opd", "osog_optics_from_opd", "osog_batch_submit",
            "osog_sync_status", "osog_last_error", "osog_plan_launch_count",
            "osog_profile_begin", "osog_profile_end", "osog_render_noalloc",
-           "osog_backward_workspace_size", "osog_render_backward")
+           "osog_backward_workspace_size", "osog_render_backward", "osog_autotune")
 
 
 class OsogError(RuntimeError):
@@ -46,7 +47,8 @@ class Optics(ctypes.Structure):
 class Tuning(ctypes.Structure):
     """Mirror of osog_tuning_t."""
     _fields_ = [("pairs_per_particle", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("persistent", ctypes.c_int32), ("band_rows", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 def optics_struct(o: dict) -> Optics:
@@ -109,6 +111,8 @@ def lib(build_if_missing: bool = True):
     L.osog_backward_workspace_size.restype = sz
     L.osog_render_backward.argtypes = [vp, vp, i64, i32, P(Optics), vp, vp, vp, vp, sz, vp]
     L.osog_render_backward.restype = ctypes.c_int
+    L.osog_autotune.argtypes = [vp, vp, i64, P(i32), i32, P(Optics), vp, vp, sz, vp, P(Tuning)]
+    L.osog_autotune.restype = ctypes.c_int
     L.osog_render_noalloc.argtypes = [vp, i64, i32, P(Optics), vp, vp]
     L.osog_render_noalloc.restype = ctypes.c_int
     _lib = L

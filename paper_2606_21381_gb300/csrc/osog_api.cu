@@ -25,6 +25,14 @@ struct osog_plan {
     std::vector<int> ev_cls;
     int ev_used = 0;
     int32_t prof_launches[OSOG_KERNEL_CLASS_COUNT] = {};
+    // autotuned choices per batch shape (scenes, particles, modalities)
+    struct Tuned {
+        int S;
+        int64_t n;
+        int K;
+        int ppp, persistent, band_rows;
+    };
+    std::vector<Tuned> tuned;
     // cached graph of the last batched launch sequence
     cudaGraphExec_t gexec = nullptr;
     std::vector<unsigned char> gkey;
@@ -54,7 +62,7 @@ constexpr int kMaxTimed = 8192;
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t rec, rect, cnt, band_off, pairs, G, Q, chord, colrange, total;
+    size_t rec, rect, cnt, band_off, pairs, G, Q, chord, colrange, ctr, total;
 };
 
 // Workspace regions for a launch group of up to S scenes, n records,
@@ -81,6 +89,8 @@ Layout make_layout(const Geometry &geo, int64_t n, int64_t nchunks, int S, int K
     o = align256(o + (size_t)S * kMaxModes * geo.W * sizeof(int2));
     l.colrange = o;
     o = align256(o + (size_t)S * sizeof(int2));
+    l.ctr = o;
+    o = align256(o + (size_t)(1 + 2 * S) * sizeof(int32_t));
     l.total = o;
     return l;
 }
@@ -188,14 +198,38 @@ int run_kernel(osog_plan *p, int cls, cudaStream_t st, F &&launch) {
     return OSOG_OK;
 }
 
-enum Stage { kFull, kOpdOnly, kFromMap };
+enum Stage { kFull, kOpdOnly, kFromMap, kBinOnly };
+
+// Per-call choices of the batched path (see osog_tuning_t).
+struct GroupOpts {
+    int ppp = kDefaultPairs;
+    bool persistent = false;
+    int band_rows = 0;
+    std::vector<int32_t> *band_off_out = nullptr;  // kBinOnly: host copy of band_off
+};
+
+// The plan's geometry with the binning band height replaced by band_rows
+// (0 keeps it).  False if band_rows is not a multiple of the strip height
+// that divides H into at most kMaxBands bands.
+bool band_geometry(const Geometry &base, int band_rows, Geometry &g) {
+    g = base;
+    if (band_rows <= 0) return true;
+    if (band_rows % base.R || base.H % band_rows || base.H / band_rows > kMaxBands) return false;
+    g.BH = band_rows;
+    g.nbands = base.H / band_rows;
+    return true;
+}
 
 // One launch group: up to kMaxScenes scenes whose records start at soa.
 int enqueue_group(osog_plan *p, const float *soa, int64_t ld, const int32_t *counts, int S,
-                  const osog_optics_t *optics, int K, int pairs_per_particle, void *ws,
+                  const osog_optics_t *optics, int K, const GroupOpts &opt, void *ws,
                   size_t ws_bytes, float *images, const float *opd_att, float *opd_out,
                   Stage stage, cudaStream_t st) {
-    const Geometry &geo = p->geo;
+    Geometry geo;
+    if (!band_geometry(p->geo, opt.band_rows, geo))
+        return fail(OSOG_ERR_INVALID_ARG, "band_rows must be a multiple of the strip height "
+                                          "dividing H into at most 64 bands");
+    const int pairs_per_particle = opt.ppp;
     GroupDev gd{};
     gd.S = S;
     gd.K = K;
@@ -228,6 +262,14 @@ int enqueue_group(osog_plan *p, const float *soa, int64_t ld, const int32_t *cou
     // The scan also tabulates the pupil chords used by the render kernels.
     rc = run_kernel(p, OSOG_KERNEL_BIN_SCAN, st, [&] { return launch_bin_scan(gd, geo, w, st); });
     if (rc) return rc;
+    if (stage == kBinOnly) {  // autotuner dry run: the per-band pair totals only
+        opt.band_off_out->resize((size_t)S * (geo.nbands + 1));
+        cudaError_t e = cudaMemcpyAsync(opt.band_off_out->data(), w.band_off,
+                                        sizeof(int32_t) * opt.band_off_out->size(),
+                                        cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        return e == cudaSuccess ? OSOG_OK : cuda_fail(e, "autotune dry run");
+    }
     if (stage != kFromMap) {
         rc = run_kernel(p, OSOG_KERNEL_BIN_FILL, st, [&] { return launch_bin_fill(gd, geo, w, st); });
         if (rc) return rc;
@@ -240,9 +282,6 @@ int enqueue_group(osog_plan *p, const float *soa, int64_t ld, const int32_t *cou
     sa.opd_out = reinterpret_cast<float2 *>(opd_out);
     sa.S = S;
     for (int s = 0; s < S; ++s) sa.sc[s] = gd.sc[s];
-    const StripMode sm = stage == kOpdOnly ? kStripOpdOnly : stage == kFromMap ? kStripFromMap : kStripRender;
-    rc = run_kernel(p, OSOG_KERNEL_STRIP_FORWARD, st, [&] { return launch_strip_forward(sa, sm, st); });
-    if (rc || stage == kOpdOnly) return rc;
     ColumnArgs ca{};
     ca.geo = geo;
     ca.w = w;
@@ -251,8 +290,6 @@ int enqueue_group(osog_plan *p, const float *soa, int64_t ld, const int32_t *cou
     ca.K = K;
     for (int s = 0; s < S; ++s)
         for (int k = 0; k < K; ++k) ca.md[s][k] = gd.md[s][k];
-    rc = run_kernel(p, OSOG_KERNEL_COLUMN, st, [&] { return launch_column(ca, st); });
-    if (rc) return rc;
     InverseArgs ia{};
     ia.geo = geo;
     ia.w = w;
@@ -260,6 +297,22 @@ int enqueue_group(osog_plan *p, const float *soa, int64_t ld, const int32_t *cou
     ia.images = images;
     ia.S = S;
     ia.K = K;
+    if (opt.persistent && stage == kFull && geo.H == geo.W) {
+        PersistArgs pa{};
+        pa.sa = sa;
+        pa.ca = ca;
+        pa.ia = ia;
+        pa.ctr = reinterpret_cast<int32_t *>(static_cast<char *>(ws) + l.ctr);
+        pa.total = S * (geo.nstrips + geo.nblocks + K * geo.nstrips);
+        cudaError_t e = cudaMemsetAsync(pa.ctr, 0, sizeof(int32_t) * (1 + 2 * S), st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        return run_kernel(p, OSOG_KERNEL_PERSISTENT, st, [&] { return launch_persistent(pa, st); });
+    }
+    const StripMode sm = stage == kOpdOnly ? kStripOpdOnly : stage == kFromMap ? kStripFromMap : kStripRender;
+    rc = run_kernel(p, OSOG_KERNEL_STRIP_FORWARD, st, [&] { return launch_strip_forward(sa, sm, st); });
+    if (rc || stage == kOpdOnly) return rc;
+    rc = run_kernel(p, OSOG_KERNEL_COLUMN, st, [&] { return launch_column(ca, st); });
+    if (rc) return rc;
     return run_kernel(p, OSOG_KERNEL_STRIP_INVERSE, st, [&] { return launch_strip_inverse(ia, st); });
 }
 
@@ -367,7 +420,7 @@ static int render_stage(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
     const int nn = stage == kFromMap ? 0 : n;
     rc = check_ws(ws, ws_need(p, nn, stage == kOpdOnly ? 0 : K, 1, kDefaultPairs), ws_bytes);
     if (rc) return rc;
-    return enqueue_group(p, soa, ld, &nn, 1, optics, K, kDefaultPairs, ws, ws_bytes, image,
+    return enqueue_group(p, soa, ld, &nn, 1, optics, K, GroupOpts{}, ws, ws_bytes, image,
                          opd_att, opd_out, stage, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -391,17 +444,30 @@ int osog_optics_from_opd(osog_plan_t *p, const float *opd_att, const osog_optics
 }
 
 static int batch_enqueue(osog_plan_t *p, const float *soa_all, int64_t ld, const int32_t *offsets,
-                         int32_t S, const osog_optics_t *optics, float *images, int K, int ppp,
-                         void *ws, size_t ws_bytes, cudaStream_t st) {
+                         int32_t S, const osog_optics_t *optics, float *images, int K,
+                         const GroupOpts &opt, void *ws, size_t ws_bytes, cudaStream_t st,
+                         Stage stage = kFull, int *ppp_needed = nullptr) {
     const size_t img_scene = (size_t)K * p->H * p->W;
     for (int g0 = 0; g0 < S; g0 += kMaxScenes) {
         const int Sg = S - g0 < kMaxScenes ? S - g0 : kMaxScenes;
         int32_t counts[kMaxScenes];
         for (int s = 0; s < Sg; ++s) counts[s] = offsets[g0 + s + 1] - offsets[g0 + s];
         const float *soa_g = soa_all ? soa_all + offsets[g0] : nullptr;
-        int rc = enqueue_group(p, soa_g, ld, counts, Sg, optics + g0, K, ppp, ws, ws_bytes,
-                               images + (size_t)g0 * img_scene, nullptr, nullptr, kFull, st);
+        std::vector<int32_t> offs;
+        GroupOpts o = opt;
+        o.band_off_out = &offs;
+        int rc = enqueue_group(p, soa_g, ld, counts, Sg, optics + g0, K, o, ws, ws_bytes,
+                               images + (size_t)g0 * img_scene, nullptr, nullptr, stage, st);
         if (rc) return rc;
+        if (stage == kBinOnly && ppp_needed) {
+            const int nb = (int)(offs.size() / Sg) - 1;
+            for (int s = 0; s < Sg; ++s)
+                if (counts[s] > 0) {
+                    const int64_t tot = offs[(size_t)s * (nb + 1) + nb];
+                    const int need = (int)((tot + counts[s] - 1) / counts[s]);
+                    if (need > *ppp_needed) *ppp_needed = need;
+                }
+        }
     }
     return OSOG_OK;
 }
@@ -425,8 +491,23 @@ int osog_batch_submit(osog_plan_t *p, const float *soa_all, int64_t ld, const in
     const int64_t n_total = (int64_t)offsets[S] - offsets[0];
     if (n_total > 0 && !soa_all) return fail(OSOG_ERR_INVALID_ARG, "soa_all is NULL");
     const int K = popcount3(optics[0].modes);
-    const int ppp = tuning && tuning->pairs_per_particle > 0 ? tuning->pairs_per_particle : kDefaultPairs;
-    const bool use_graph = !tuning || tuning->use_graph != 0;
+    // Options: explicit tuning fields first, then the autotuned values for
+    // this batch shape, then the defaults.
+    GroupOpts opt;
+    for (const auto &t : p->tuned)
+        if (t.S == S && t.n == n_total && t.K == K) {
+            opt.ppp = t.ppp;
+            opt.persistent = t.persistent > 0;
+            opt.band_rows = t.band_rows;
+        }
+    bool use_graph = true;
+    if (tuning) {
+        if (tuning->pairs_per_particle > 0) opt.ppp = tuning->pairs_per_particle;
+        if (tuning->persistent != 0) opt.persistent = tuning->persistent > 0;
+        if (tuning->band_rows > 0) opt.band_rows = tuning->band_rows;
+        use_graph = tuning->use_graph > 0;
+    }
+    const int ppp = opt.ppp;
     int rc = check_ws(ws, ws_need(p, n_total, K, S, ppp), ws_bytes);
     if (rc) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -434,7 +515,7 @@ int osog_batch_submit(osog_plan_t *p, const float *soa_all, int64_t ld, const in
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (st) cudaStreamIsCapturing(st, &cs);
     if (!use_graph || p->prof || !st || cs != cudaStreamCaptureStatusNone)
-        return batch_enqueue(p, soa_all, ld, offsets, S, optics, images, K, ppp, ws, ws_bytes, st);
+        return batch_enqueue(p, soa_all, ld, offsets, S, optics, images, K, opt, ws, ws_bytes, st);
 
     // Key of the launch sequence: every argument that ends up in a kernel.
     std::vector<unsigned char> key;
@@ -450,12 +531,14 @@ int osog_batch_submit(osog_plan_t *p, const float *soa_all, int64_t ld, const in
     put(&images, sizeof images);
     put(&ws, sizeof ws);
     put(&ws_bytes, sizeof ws_bytes);
-    put(&ppp, sizeof ppp);
+    put(&opt.ppp, sizeof opt.ppp);
+    put(&opt.persistent, sizeof opt.persistent);
+    put(&opt.band_rows, sizeof opt.band_rows);
     if (!(p->gexec && key == p->gkey)) {
         const int64_t before = p->launches;
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-        rc = batch_enqueue(p, soa_all, ld, offsets, S, optics, images, K, ppp, ws, ws_bytes, st);
+        rc = batch_enqueue(p, soa_all, ld, offsets, S, optics, images, K, opt, ws, ws_bytes, st);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(st, &g);
         p->graph_kernels = p->launches - before;
@@ -597,6 +680,79 @@ int osog_render_backward(osog_plan_t *p, const float *soa, int64_t ld, int32_t n
     br.nchunks = (int32_t)chunks;
     br.sc[0] = sc;
     return run_kernel(p, OSOG_KERNEL_BWD_REDUCE, st, [&] { return launch_bwd_reduce(br, st); });
+}
+
+int osog_autotune(osog_plan_t *p, const float *soa_all, int64_t ld, const int32_t *offsets,
+                  int32_t S, const osog_optics_t *optics, float *images, void *ws,
+                  size_t ws_bytes, osog_stream_t stream, osog_tuning_t *out) {
+    // Validate once through the direct path (it also warms the kernels up).
+    osog_tuning_t base{};
+    base.use_graph = -1;
+    base.persistent = -1;
+    int rc = osog_batch_submit(p, soa_all, ld, offsets, S, optics, images, &base, ws, ws_bytes, stream);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int K = popcount3(optics[0].modes);
+    const int64_t n_total = (int64_t)offsets[S] - offsets[0];
+    std::vector<int> bands;
+    for (int bh = p->geo.BH; bh <= p->H && bands.size() < 4; bh *= 2) bands.push_back(bh);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(OSOG_ERR_CUDA, "cudaEventCreate");
+    float best = 1e30f;
+    GroupOpts chosen;
+    for (int bh : bands) {
+        GroupOpts o;
+        o.band_rows = bh;
+        int need = 1;
+        rc = batch_enqueue(p, soa_all, ld, offsets, S, optics, images, K, o, ws, ws_bytes, st,
+                           kBinOnly, &need);
+        if (rc) break;
+        o.ppp = need;
+        if (ws_need(p, n_total, K, S, o.ppp) > ws_bytes) continue;
+        for (int pers = 0; pers < (p->H == p->W ? 2 : 1); ++pers) {
+            o.persistent = pers == 1;
+            float t[3];
+            for (int r = 0; r < 3 && rc == OSOG_OK; ++r) {
+                cudaEventRecord(e0, st);
+                rc = batch_enqueue(p, soa_all, ld, offsets, S, optics, images, K, o, ws, ws_bytes, st);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t[r], e0, e1) != cudaSuccess)
+                    rc = fail(OSOG_ERR_CUDA, "autotune timing");
+            }
+            if (rc) break;
+            const float med = t[0] + t[1] + t[2] - fminf(t[0], fminf(t[1], t[2])) -
+                              fmaxf(t[0], fmaxf(t[1], t[2]));
+            if (med < best) {
+                best = med;
+                chosen = o;
+            }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // The dry runs may have latched a bin overflow for candidates they then
+    // sized exactly: clear the status word.
+    cudaMemsetAsync(p->status, 0, sizeof(int32_t), st);
+    cudaStreamSynchronize(st);
+    if (rc) return rc;
+    bool found = false;
+    for (auto &t : p->tuned)
+        if (t.S == S && t.n == n_total && t.K == K) {
+            t = {S, n_total, K, chosen.ppp, chosen.persistent ? 1 : -1, chosen.band_rows};
+            found = true;
+        }
+    if (!found)
+        p->tuned.push_back({S, n_total, K, chosen.ppp, chosen.persistent ? 1 : -1, chosen.band_rows});
+    if (out) {
+        *out = osog_tuning_t{};
+        out->pairs_per_particle = chosen.ppp;
+        out->use_graph = 1;
+        out->persistent = chosen.persistent ? 1 : -1;
+        out->band_rows = chosen.band_rows;
+    }
+    return OSOG_OK;
 }
 
 int osog_sync_status(osog_plan_t *p, osog_stream_t stream) {

@@ -34,6 +34,17 @@ struct InverseArgs {
     int32_t S, K;
 };
 
+// The three render stages of a launch group in one persistent launch
+// (square canvases).  ctr[0] hands out work items; ctr[1 + s] counts the
+// finished strips of scene s, ctr[1 + S + s] its finished column blocks.
+struct PersistArgs {
+    StripArgs sa;
+    ColumnArgs ca;
+    InverseArgs ia;
+    int32_t *ctr;      // [1 + 2 S], zero at launch
+    int32_t total;     // work items
+};
+
 // Adjoint passes (osog_render_backward).
 struct BwdRowsArgs {  // dL/dQ_m = DFT_rows(2 gI_m E_m), written over Q_m
     Geometry geo;
@@ -87,6 +98,9 @@ cudaError_t prepare_kernels(int H, int W);  // opt-in shared memory sizes
 cudaError_t launch_strip_forward(const StripArgs &a, StripMode mode, cudaStream_t st);
 cudaError_t launch_column(const ColumnArgs &a, cudaStream_t st);
 cudaError_t launch_strip_inverse(const InverseArgs &a, cudaStream_t st);
+
+size_t persistent_smem(int N, int K);
+cudaError_t launch_persistent(const PersistArgs &a, cudaStream_t st);
 
 size_t bwd_column_smem(int H);
 size_t bwd_strip_smem(int W);

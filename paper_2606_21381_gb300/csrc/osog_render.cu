@@ -23,18 +23,18 @@ namespace osog {
 
 namespace {
 
+// One strip (rows [strip R, strip R + R)) of scene s.
 template <int N, int MODE>
-__global__ void __launch_bounds__(kThreads, 2) k_strip_forward(const __grid_constant__ StripArgs a) {
+__device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, int strip,
+                                                   unsigned char *smem_raw) {
     constexpr int L = kSetElems / N;
     constexpr int LS = line_stride(N);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
     PRec *srec = reinterpret_cast<PRec *>(buf + L * LS);
     Rect *srect = reinterpret_cast<Rect *>(srec + kThreads);
     int *wsum = reinterpret_cast<int *>(srect + kThreads);
     const Geometry &geo = a.geo;
-    const int s = blockIdx.y;
-    const int y0 = blockIdx.x * geo.R;
+    const int y0 = strip * geo.R;
     const int R = geo.R;
     const int RN = R * N;  // <= kSetElems; lines R..L-1 are never read back
     if constexpr (MODE == kStripFromMap) {
@@ -95,16 +95,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_strip_forward(const __grid_cons
     }
 }
 
+template <int N, int MODE>
+__global__ void __launch_bounds__(kThreads, 2) k_strip_forward(const __grid_constant__ StripArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    strip_forward_item<N, MODE>(a, blockIdx.y, blockIdx.x, smem_raw);
+}
+
+// One column block bk of scene s.
 template <int N, bool MULTI>
-__global__ void __launch_bounds__(kThreads, 2) k_column(const __grid_constant__ ColumnArgs a) {
+__device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
+                                            unsigned char *smem_raw) {
     constexpr int L = kSetElems / N;
     constexpr int LS = line_stride(N);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *buf0 = reinterpret_cast<float2 *>(smem_raw);
     float2 *buf1 = MULTI ? buf0 + L * LS : buf0;
     int2 *chords = reinterpret_cast<int2 *>(buf1 + L * LS);
     const Geometry &geo = a.geo;
-    const int s = blockIdx.y, bk = blockIdx.x;
     const int B = geo.B, lb = ilog2(B), K = a.K;
     const int2 cr = a.w.colrange[s];
     // A block whose columns all lie outside every pupil has nothing to filter:
@@ -165,16 +171,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_column(const __grid_constant__ 
     }
 }
 
+template <int N, bool MULTI>
+__global__ void __launch_bounds__(kThreads, 2) k_column(const __grid_constant__ ColumnArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    column_item<N, MULTI>(a, blockIdx.y, blockIdx.x, smem_raw);
+}
+
+// One strip of the image sm = s K + m.
 template <int N>
-__global__ void __launch_bounds__(kThreads, 2) k_strip_inverse(const __grid_constant__ InverseArgs a) {
+__device__ __forceinline__ void inverse_item(const InverseArgs &a, int sm, int strip,
+                                             unsigned char *smem_raw) {
     constexpr int L = kSetElems / N;
     constexpr int LS = line_stride(N);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
     const Geometry &geo = a.geo;
     const int K = a.K;
-    const int sm = blockIdx.y;
-    const int y0 = blockIdx.x * geo.R;
+    const int y0 = strip * geo.R;
     const int R = geo.R, B = geo.B, lb = ilog2(B), lr = ilog2(R);
     const float2 *Qm = a.w.Q + (size_t)sm * geo.nblocks * geo.H * B;
     const int2 cr = a.w.colrange[sm / K];
@@ -208,6 +220,126 @@ __global__ void __launch_bounds__(kThreads, 2) k_strip_inverse(const __grid_cons
         }
     }
 }
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 2) k_strip_inverse(const __grid_constant__ InverseArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    inverse_item<N>(a, blockIdx.y, blockIdx.x, smem_raw);
+}
+
+// ------------------------------------------------------------ persistent
+// Bounded wait on a completion counter: thread 0 polls until it reaches
+// target or the iteration limit runs out (then the status word records a
+// timeout and the item proceeds on whatever is there, so the launch always
+// ends); the fence orders the producer's writes before this CTA's reads.
+constexpr int kSpinLimit = 1 << 24;
+
+__device__ __forceinline__ void wait_count(const int32_t *cnt, int target, int32_t *status) {
+    if (threadIdx.x == 0) {
+        int spins = 0;
+        while (*reinterpret_cast<const volatile int32_t *>(cnt) < target) {
+            __nanosleep(100);
+            if (++spins >= kSpinLimit) {
+                latch(status, OSOG_ERR_TIMEOUT);
+                break;
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// Work items in dispatch order: wave t holds the strips of scene t, the
+// column blocks of scene t - 1 and the inverse strips of scene t - 2, so a
+// column (inverse) item of scene s is handed out only after every strip
+// (column block) item of s, to CTAs that are already running.
+__device__ __forceinline__ void decode_item(int it, int S, int na, int nb, int nc, int &stage,
+                                            int &s, int &idx) {
+    for (int t = 0; t < S + 2; ++t) {
+        const int sa = t < S ? na : 0;
+        const int sb = t >= 1 && t - 1 < S ? nb : 0;
+        const int sc = t >= 2 && t - 2 < S ? nc : 0;
+        if (it < sa) { stage = 0; s = t; idx = it; return; }
+        it -= sa;
+        if (it < sb) { stage = 1; s = t - 1; idx = it; return; }
+        it -= sb;
+        if (it < sc) { stage = 2; s = t - 2; idx = it; return; }
+        it -= sc;
+    }
+    stage = 3;
+}
+
+// Two CTAs per SM when one modality keeps the largest stage (the strip
+// kernel) within half of the shared memory, as the separate kernels run.
+template <int N, bool MULTI>
+__global__ void __launch_bounds__(kThreads, MULTI ? 1 : 2) k_persistent(const __grid_constant__ PersistArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int item[3];
+    const Geometry &geo = a.sa.geo;
+    const int S = a.sa.S, K = a.ca.K;
+    const int na = geo.nstrips, nb = geo.nblocks, nc = K * geo.nstrips;
+    int32_t *doneA = a.ctr + 1, *doneB = a.ctr + 1 + S;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int it = atomicAdd(a.ctr, 1);
+            int stage = 3, s = 0, idx = 0;
+            if (it < a.total) decode_item(it, S, na, nb, nc, stage, s, idx);
+            item[0] = stage;
+            item[1] = s;
+            item[2] = idx;
+        }
+        __syncthreads();
+        const int stage = item[0], s = item[1], idx = item[2];
+        __syncthreads();
+        if (stage == 3) break;
+        if (stage == 0) {
+            strip_forward_item<N, kStripRender>(a.sa, s, idx, smem_raw);
+        } else if (stage == 1) {
+            wait_count(doneA + s, na, a.sa.w.status);
+            column_item<N, MULTI>(a.ca, s, idx, smem_raw);
+        } else {
+            wait_count(doneB + s, nb, a.sa.w.status);
+            inverse_item<N>(a.ia, s * K + idx / na, idx % na, smem_raw);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && stage < 2) {
+            __threadfence();
+            atomicAdd(stage == 0 ? doneA + s : doneB + s, 1);
+        }
+    }
+}
+
+template <int N>
+struct PersistLaunch {
+    static cudaError_t run(const PersistArgs &a, cudaStream_t st) {
+        const size_t smem = persistent_smem(N, a.ca.K);
+        int dev = 0, sms = 0, per = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        if (a.ca.K > 1)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent<N, true>, kThreads, smem);
+        else
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent<N, false>, kThreads, smem);
+        if (e != cudaSuccess) return e;
+        const int grid = max(1, min(a.total, max(per, 1) * sms));
+        if (a.ca.K > 1)
+            k_persistent<N, true><<<grid, kThreads, smem, st>>>(a);
+        else
+            k_persistent<N, false><<<grid, kThreads, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    static cudaError_t prepare() {
+        cudaError_t e = cudaFuncSetAttribute(k_persistent<N, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)persistent_smem(N, 1));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_persistent<N, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)persistent_smem(N, 3));
+        return e;
+    }
+};
 
 template <int N>
 struct StripFwdLaunch {
@@ -273,6 +405,7 @@ struct Prepare {
         (void)other;
         if (which == 0) return StripFwdLaunch<N>::prepare(strip_forward_smem(N));
         if (which == 1) return ColumnLaunch<N>::prepare(column_smem(N, 1), column_smem(N, 3));
+        if (which == 3) return PersistLaunch<N>::prepare();
         return InverseLaunch<N>::prepare(strip_inverse_smem(N));
     }
 };
@@ -296,11 +429,22 @@ size_t strip_inverse_smem(int W) {
     return (size_t)L * line_stride(W) * sizeof(float2);
 }
 
+size_t persistent_smem(int N, int K) {
+    const size_t a = strip_forward_smem(N), b = column_smem(N, K), c = strip_inverse_smem(N);
+    return a > b ? (a > c ? a : c) : (b > c ? b : c);
+}
+
 cudaError_t prepare_kernels(int H, int W) {
     cudaError_t e = dispatch_n<Prepare>(W, 0, 0);
     if (e == cudaSuccess) e = dispatch_n<Prepare>(H, 1, 0);
     if (e == cudaSuccess) e = dispatch_n<Prepare>(W, 2, 0);
+    if (e == cudaSuccess && H == W) e = dispatch_n<Prepare>(W, 3, 0);
     return e;
+}
+
+cudaError_t launch_persistent(const PersistArgs &a, cudaStream_t st) {
+    if (a.sa.geo.H != a.sa.geo.W) return cudaErrorInvalidValue;
+    return dispatch_n<PersistLaunch>(a.sa.geo.W, a, st);
 }
 
 cudaError_t launch_strip_forward(const StripArgs &a, StripMode mode, cudaStream_t st) {

@@ -156,6 +156,8 @@ class Renderer:
         if tuning:
             t.pairs_per_particle = int(tuning.get("pairs_per_particle", 0))
             t.use_graph = int(tuning.get("use_graph", 1))
+            t.persistent = int(tuning.get("persistent", 0))
+            t.band_rows = int(tuning.get("band_rows", 0))
         need = self.workspace_size(n_total, K, S)
         if t.pairs_per_particle > 8:
             need = int(need * t.pairs_per_particle / 8) + (1 << 20)
@@ -166,6 +168,27 @@ class Renderer:
             offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), S, arr, _ptr(out),
             ctypes.byref(t), _ptr(ws), ws.numel(), _stream(stream)), "osog_batch_submit")
         return out
+
+    def autotune(self, soa_all: torch.Tensor, offsets, optics_list: list[dict], out=None,
+                 stream=None) -> dict:
+        """osog_autotune: time the batched path's candidate band heights and
+        launch modes for this batch shape, keep the fastest in the plan and
+        return it as a tuning dict."""
+        self._check_soa(soa_all)
+        offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+        S = len(optics_list)
+        K = n_modes(optics_list[0])
+        if out is None:
+            out = torch.empty((S, K, self.H, self.W), dtype=torch.float32, device=self.device)
+        ws = self.workspace(self.workspace_size(int(offs[-1] - offs[0]), K, S))
+        arr = (Optics * S)(*[optics_struct(o) for o in optics_list])
+        t = Tuning()
+        check(self._L.osog_autotune(
+            self.plan, _ptr(soa_all), soa_all.shape[1],
+            offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), S, arr, _ptr(out),
+            _ptr(ws), ws.numel(), _stream(stream), ctypes.byref(t)), "osog_autotune")
+        return {"pairs_per_particle": t.pairs_per_particle, "use_graph": t.use_graph,
+                "persistent": t.persistent, "band_rows": t.band_rows}
 
     def render_host(self, soa_host: torch.Tensor, n: int, optics: dict,
                     image_host: torch.Tensor, stream=None):

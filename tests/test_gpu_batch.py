@@ -1,0 +1,76 @@
+"""Batched path: the persistent launch, band-height choices and the
+autotuner give results bitwise identical to the three-launch path (the
+same arithmetic in the same order per pixel), and match the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_21381_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+_renderers = {}
+
+
+def renderer(H, W):
+    from paper_2606_21381_gb300.render import Renderer
+    if (H, W) not in _renderers:
+        _renderers[(H, W)] = Renderer(H, W)
+    return _renderers[(H, W)]
+
+
+def batch(seed, S, size, modes, lo=0, hi=600):
+    rng = np.random.default_rng(seed)
+    soas = [scenes.draw_particles(rng, int(c), size, size, mu=(0, 0.02))
+            for c in rng.integers(lo, hi, S)]
+    optics = [scenes.optics(size, size, modes=modes, defocus=rng.uniform(-1, 1)) for _ in range(S)]
+    soa_all, offs = scenes.concat(soas)
+    return soas, optics, torch.from_numpy(soa_all).cuda(), offs
+
+
+@pytest.mark.parametrize("modes,S", [(2, 5), (3, 4), (1, 37)])
+def test_persistent_launch_is_bitwise_identical(modes, S):
+    soas, optics, dev, offs = batch(modes * 10 + S, S, 256, modes)
+    r = renderer(256, 256)
+    base = r.batch(dev, offs, optics, tuning={"use_graph": 0, "persistent": -1}).clone()
+    pers = r.batch(dev, offs, optics, tuning={"use_graph": 0, "persistent": 1}).clone()
+    graph = r.batch(dev, offs, optics, tuning={"use_graph": 1, "persistent": 1}).clone()
+    assert r.sync_status() == 0
+    assert torch.equal(base, pers) and torch.equal(base, graph)
+    s = S - 1
+    ref = oracle.render(soas[s], soas[s].shape[1], oracle.make_optics(**optics[s]))["images"]
+    assert np.abs(pers[s].cpu().numpy().astype(np.float64) - ref).max() <= 2e-4
+
+
+@pytest.mark.parametrize("band_rows", [64, 128, 256])
+def test_band_height_does_not_change_results(band_rows):
+    soas, optics, dev, offs = batch(3, 4, 512, 1, 100, 2000)
+    r = renderer(512, 512)
+    base = r.batch(dev, offs, optics, tuning={"use_graph": 0}).clone()
+    other = r.batch(dev, offs, optics, tuning={"use_graph": 0, "band_rows": band_rows,
+                                              "pairs_per_particle": 8}).clone()
+    assert r.sync_status() == 0
+    assert torch.equal(base, other)
+
+
+def test_invalid_band_height_is_rejected_on_the_host():
+    from paper_2606_21381_gb300._lib import OsogError
+    soas, optics, dev, offs = batch(4, 2, 512, 1)
+    r = renderer(512, 512)
+    with pytest.raises(OsogError) as e:
+        r.batch(dev, offs, optics, tuning={"use_graph": 0, "band_rows": 12})
+    assert e.value.code == 1
+
+
+def test_autotuner_choice_is_used_and_exact():
+    soas, optics, dev, offs = batch(5, 8, 1024, 2, 500, 5000)
+    r = renderer(1024, 1024)
+    base = r.batch(dev, offs, optics, tuning={"use_graph": 0, "persistent": -1}).clone()
+    t = r.autotune(dev, offs, optics)
+    assert r.sync_status() == 0
+    assert t["band_rows"] in (16, 32, 64, 128) and 1 <= t["pairs_per_particle"] <= 8
+    assert t["persistent"] in (1, -1)
+    tuned = r.batch(dev, offs, optics).clone()   # picks the stored choice
+    assert r.sync_status() == 0                  # the exact reservation does not overflow
+    assert torch.equal(base, tuned)
