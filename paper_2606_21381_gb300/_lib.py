@@ -44,6 +44,16 @@ class Optics(ctypes.Structure):
                 ("bias_phase", ctypes.c_double), ("bevel_slope", ctypes.c_double)]
 
 
+class ConvShape(ctypes.Structure):
+    """Mirror of osog_conv_shape_t."""
+    _fields_ = [(k, ctypes.c_int32) for k in ("N", "H", "W", "C", "K", "R", "S", "stride", "pad")]
+
+
+CNN_EXPORTS = ("osog_conv_out_h", "osog_conv_out_w", "osog_conv2d_forward",
+               "osog_conv2d_backward_data", "osog_conv2d_backward_filter_workspace",
+               "osog_conv2d_backward_filter", "osog_relu_backward")
+
+
 class Tuning(ctypes.Structure):
     """Mirror of osog_tuning_t."""
     _fields_ = [("pairs_per_particle", ctypes.c_int32), ("use_graph", ctypes.c_int32),
@@ -114,6 +124,20 @@ def lib(build_if_missing: bool = True):
     L.osog_autotune.argtypes = [vp, vp, i64, P(i32), i32, P(Optics), vp, vp, sz, vp, P(Tuning)]
     L.osog_autotune.restype = ctypes.c_int
     L.osog_render_noalloc.argtypes = [vp, i64, i32, P(Optics), vp, vp]
+    L.osog_conv_out_h.argtypes = [P(ConvShape)]
+    L.osog_conv_out_h.restype = i32
+    L.osog_conv_out_w.argtypes = [P(ConvShape)]
+    L.osog_conv_out_w.restype = i32
+    L.osog_conv2d_forward.argtypes = [P(ConvShape), vp, vp, vp, i32, vp, vp, vp]
+    L.osog_conv2d_forward.restype = ctypes.c_int
+    L.osog_conv2d_backward_data.argtypes = [P(ConvShape), vp, vp, vp, vp, vp, vp]
+    L.osog_conv2d_backward_data.restype = ctypes.c_int
+    L.osog_conv2d_backward_filter_workspace.argtypes = [P(ConvShape)]
+    L.osog_conv2d_backward_filter_workspace.restype = sz
+    L.osog_conv2d_backward_filter.argtypes = [P(ConvShape), vp, vp, vp, vp, vp, sz, vp]
+    L.osog_conv2d_backward_filter.restype = ctypes.c_int
+    L.osog_relu_backward.argtypes = [vp, vp, vp, i64, vp]
+    L.osog_relu_backward.restype = ctypes.c_int
     L.osog_render_noalloc.restype = ctypes.c_int
     _lib = L
     return L

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libosog.so")
 SOURCES = ("osog_api.cu", "osog_bin.cu", "osog_render.cu", "osog_backward.cu",
-           "osog_noalloc.cu")
+           "osog_noalloc.cu", "osog_cnn.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
          "--expt-relaxed-constexpr"]
@@ -40,6 +40,7 @@ def _inputs() -> list[str]:
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)
              if f.endswith((".cu", ".cuh", ".h"))]
     files.append(os.path.join(INCLUDE, "osog.h"))
+    files.append(os.path.join(INCLUDE, "osog_cnn.h"))
     return files
 
 

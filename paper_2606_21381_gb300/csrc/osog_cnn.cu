@@ -1,0 +1,412 @@
+// Convolutions of the learned warm start as implicit GEMMs on the tensor
+// cores (BF16 operands, FP32 accumulation).
+//
+//   forward  Y[m = (n,p,q)][k]   = sum_{j = (r,s,c)} X(im2col)[m][j] W[k][j]
+//   data     dX[m = (n,h,w)][c]  = sum_{j = (r,s,k)} dY(gathered)[m][j] Wt[c][j]
+//   filter   dW[k][j = (r,s,c)]  = sum_{m = (n,p,q)} dY[m][k] X(im2col)[m][j]
+//
+// A CTA computes a 64 x 64 tile of the product from 32-wide slices of the
+// reduction: both operands are gathered from NHWC tensors (8 channels per
+// 16-byte vector, zero outside the image or for strides that skip a tap),
+// staged in shared memory as [row][reduction] and fed to mma.m16n8k16
+// through ldmatrix; four warps each own a 32 x 32 sub-tile.  The filter
+// gradient splits its pixel reduction across CTAs and sums the partial tiles
+// in a fixed order, so every result is bitwise reproducible.
+#include <cuda_bf16.h>
+
+#include "osog_cnn.h"
+
+namespace osog {
+namespace cnn {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 32, LDS = BK + 8;  // smem row: 40 bf16 = 80 bytes
+constexpr int NT = 128;
+constexpr int kSplitPixels = 2048;  // pixels per CTA in the filter-gradient reduction
+
+enum Pass { kFwd = 0, kDgrad = 1, kWgrad = 2 };
+
+struct Geo {
+    int N, H, W, C, K, R, S, stride, pad, P, Q;
+};
+
+struct Args {
+    Geo g;
+    const __nv_bfloat16 *x;     // fwd: X, dgrad: dY, wgrad: dY
+    const __nv_bfloat16 *w;     // fwd: W [K][RSC], dgrad: Wt [C][RSK], wgrad: X
+    const float *bias;
+    const __nv_bfloat16 *mask;  // dgrad: activation whose ReLU derivative applies
+    __nv_bfloat16 *y;
+    float *y32;
+    float *part;                // wgrad partial tiles [splits][M][N]
+    int relu;
+    int M, Ncols, Kred;         // GEMM sizes
+};
+
+__device__ __forceinline__ uint4 zero4() { return make_uint4(0u, 0u, 0u, 0u); }
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3,
+                                        const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0,
+                                         unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// ---------------------------------------------------------------- gathers
+// Forward A: 8 reduction entries j..j+7 (same tap, 8 channels) of output
+// pixel m.
+__device__ __forceinline__ uint4 fwd_a(const Args &a, int m, int j) {
+    const Geo &g = a.g;
+    if (m >= a.M || j >= a.Kred) return zero4();
+    const int q = m % g.Q, t = m / g.Q, p = t % g.P, n = t / g.P;
+    const int rs = j / g.C, c = j - rs * g.C, r = rs / g.S, s = rs - r * g.S;
+    const int h = p * g.stride + r - g.pad, w = q * g.stride + s - g.pad;
+    if (h < 0 || h >= g.H || w < 0 || w >= g.W) return zero4();
+    return *reinterpret_cast<const uint4 *>(a.x + (((size_t)n * g.H + h) * g.W + w) * g.C + c);
+}
+
+// Data-gradient A: dY at the output pixel that tap (r, s) of input pixel m
+// reads, 8 output channels; zero where the stride skips it.
+__device__ __forceinline__ uint4 dgrad_a(const Args &a, int m, int j) {
+    const Geo &g = a.g;
+    if (m >= a.M || j >= a.Kred) return zero4();
+    const int w = m % g.W, t = m / g.W, h = t % g.H, n = t / g.H;
+    const int rs = j / g.K, k = j - rs * g.K, r = rs / g.S, s = rs - r * g.S;
+    const int hp = h + g.pad - r, wq = w + g.pad - s;
+    if (hp < 0 || wq < 0 || hp % g.stride || wq % g.stride) return zero4();
+    const int p = hp / g.stride, q = wq / g.stride;
+    if (p >= g.P || q >= g.Q) return zero4();
+    return *reinterpret_cast<const uint4 *>(a.x + (((size_t)n * g.P + p) * g.Q + q) * g.K + k);
+}
+
+// Row-major operand rows (8 consecutive reduction entries of row r).
+__device__ __forceinline__ uint4 rows_b(const __nv_bfloat16 *base, int rows, int ld, int r, int j) {
+    if (r >= rows || j >= ld) return zero4();
+    return *reinterpret_cast<const uint4 *>(base + (size_t)r * ld + j);
+}
+
+// Filter gradient: A(k, pixel) = dY[pixel][k..k+7] (a vector across 8 rows
+// of the A tile); B(j, pixel) = X(im2col)[pixel][j..j+7] (across 8 rows of
+// the B tile).
+__device__ __forceinline__ uint4 wgrad_a(const Args &a, int k, int pix) {
+    if (k >= a.M || pix >= a.Kred) return zero4();
+    return *reinterpret_cast<const uint4 *>(a.x + (size_t)pix * a.g.K + k);
+}
+__device__ __forceinline__ uint4 wgrad_b(const Args &a, int j, int pix) {
+    const Geo &g = a.g;
+    if (j >= a.Ncols || pix >= a.Kred) return zero4();
+    const int q = pix % g.Q, t = pix / g.Q, p = t % g.P, n = t / g.P;
+    const int rs = j / g.C, c = j - rs * g.C, r = rs / g.S, s = rs - r * g.S;
+    const int h = p * g.stride + r - g.pad, w = q * g.stride + s - g.pad;
+    if (h < 0 || h >= g.H || w < 0 || w >= g.W) return zero4();
+    return *reinterpret_cast<const uint4 *>(a.w + (((size_t)n * g.H + h) * g.W + w) * g.C + c);
+}
+
+// ---------------------------------------------------------------- GEMM
+template <int PASS>
+__global__ void __launch_bounds__(NT) k_conv_gemm(const __grid_constant__ Args a) {
+    __shared__ __align__(16) __nv_bfloat16 As[2][BM][LDS];
+    __shared__ __align__(16) __nv_bfloat16 Bs[2][BN][LDS];
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    int kbeg = 0, kend = a.Kred;
+    if constexpr (PASS == kWgrad) {
+        kbeg = blockIdx.z * kSplitPixels;
+        kend = min(a.Kred, kbeg + kSplitPixels);
+    }
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wm = warp & 1, wn = warp >> 1;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+    uint4 ra[2], rb[2];
+
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int v = tid + i * NT;
+            if constexpr (PASS == kWgrad) {
+                const int kc = v & 31, rg = v >> 5;
+                ra[i] = wgrad_a(a, m0 + rg * 8, k0 + kc);
+                rb[i] = wgrad_b(a, n0 + rg * 8, k0 + kc);
+            } else {
+                const int row = v >> 2, kv = v & 3;
+                ra[i] = PASS == kFwd ? fwd_a(a, m0 + row, k0 + kv * 8) : dgrad_a(a, m0 + row, k0 + kv * 8);
+                rb[i] = rows_b(a.w, a.Ncols, a.Kred, n0 + row, k0 + kv * 8);
+            }
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int v = tid + i * NT;
+            if constexpr (PASS == kWgrad) {
+                const int kc = v & 31, rg = v >> 5;
+                const __nv_bfloat16 *ea = reinterpret_cast<const __nv_bfloat16 *>(&ra[i]);
+                const __nv_bfloat16 *eb = reinterpret_cast<const __nv_bfloat16 *>(&rb[i]);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    As[buf][rg * 8 + e][kc] = ea[e];
+                    Bs[buf][rg * 8 + e][kc] = eb[e];
+                }
+            } else {
+                const int row = v >> 2, kv = v & 3;
+                *reinterpret_cast<uint4 *>(&As[buf][row][kv * 8]) = ra[i];
+                *reinterpret_cast<uint4 *>(&Bs[buf][row][kv * 8]) = rb[i];
+            }
+        }
+    };
+
+    load(kbeg);
+    store(0);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        const bool more = k0 + BK < kend;
+        if (more) load(k0 + BK);  // global loads in flight during the MMAs
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            unsigned af[2][4], bf[4][2];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+                ldsm_x4(af[mt][0], af[mt][1], af[mt][2], af[mt][3],
+                        &As[buf][wm * 32 + mt * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
+#pragma unroll
+            for (int np = 0; np < 2; ++np)
+                ldsm_x4(bf[2 * np][0], bf[2 * np][1], bf[2 * np + 1][0], bf[2 * np + 1][1],
+                        &Bs[buf][wn * 32 + np * 16 + (lane & 7) + (lane >> 4) * 8]
+                           [kk + ((lane >> 3) & 1) * 8]);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bf[nt][0], bf[nt][1]);
+        }
+        if (more) store(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+    }
+
+    // epilogue: thread holds rows (lane / 4) and (lane / 4 + 8) of each
+    // 16 x 8 tile, columns 2 (lane % 4) and +1
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int row = m0 + wm * 32 + mt * 16 + (lane >> 2) + half * 8;
+                const int col = n0 + wn * 32 + nt * 8 + (lane & 3) * 2;
+                if (row >= a.M || col >= a.Ncols) continue;
+                float v0 = acc[mt][nt][half * 2], v1 = acc[mt][nt][half * 2 + 1];
+                const size_t o = (size_t)row * a.Ncols + col;
+                if constexpr (PASS == kFwd) {
+                    v0 += a.bias[col];
+                    v1 += a.bias[col + 1];
+                    if (a.relu) {
+                        v0 = fmaxf(v0, 0.f);
+                        v1 = fmaxf(v1, 0.f);
+                    }
+                    *reinterpret_cast<__nv_bfloat162 *>(a.y + o) = __floats2bfloat162_rn(v0, v1);
+                    if (a.y32) *reinterpret_cast<float2 *>(a.y32 + o) = make_float2(v0, v1);
+                } else if constexpr (PASS == kDgrad) {
+                    if (a.mask) {
+                        const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(a.mask + o);
+                        if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
+                        if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
+                    }
+                    *reinterpret_cast<__nv_bfloat162 *>(a.y + o) = __floats2bfloat162_rn(v0, v1);
+                } else {
+                    *reinterpret_cast<float2 *>(a.part + (size_t)blockIdx.z * a.M * a.Ncols + o) =
+                        make_float2(v0, v1);
+                }
+            }
+}
+
+// Sum of the filter-gradient partial tiles over the pixel splits, in split
+// order.
+__global__ void k_sum_splits(const float *part, int splits, int64_t count, float *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += part[(int64_t)z * count + i];
+    out[i] = s;
+}
+
+// dbias[k] = sum over pixels of dy[pixel][k]: one CTA per channel, a fixed
+// strided partition and a fixed tree.
+__global__ void k_bias_grad(const __nv_bfloat16 *dy, int64_t pixels, int K, float *db) {
+    __shared__ float red[256];
+    const int k = blockIdx.x;
+    float s = 0.f;
+    for (int64_t p = threadIdx.x; p < pixels; p += blockDim.x) s += __bfloat162float(dy[p * K + k]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int d = blockDim.x / 2; d > 0; d >>= 1) {
+        if (threadIdx.x < d) red[threadIdx.x] += red[threadIdx.x + d];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[k] = red[0];
+}
+
+// W [K][R][S][C] -> Wt [C][R][S][K].
+__global__ void k_filter_transpose(const __nv_bfloat16 *w, int K, int RS, int C, __nv_bfloat16 *wt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)K * RS * C;
+    if (i >= total) return;
+    const int c = i % C;
+    const int64_t t = i / C;
+    const int rs = t % RS, k = t / RS;
+    wt[((int64_t)c * RS + rs) * K + k] = w[i];
+}
+
+__global__ void k_relu_backward(const __nv_bfloat16 *dy, const __nv_bfloat16 *act, int64_t n,
+                                __nv_bfloat16 *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __bfloat162float(act[i]) > 0.f ? dy[i] : __float2bfloat16(0.f);
+}
+
+}  // namespace
+}  // namespace cnn
+}  // namespace osog
+
+using namespace osog::cnn;
+
+namespace {
+
+bool shape_ok(const osog_conv_shape_t *s) {
+    return s && s->N > 0 && s->H > 0 && s->W > 0 && s->C > 0 && s->C % 8 == 0 && s->K > 0 &&
+           s->K % 8 == 0 && s->R > 0 && s->S > 0 && (s->stride == 1 || s->stride == 2) &&
+           s->pad >= 0 && s->H + 2 * s->pad >= s->R && s->W + 2 * s->pad >= s->S;
+}
+
+Geo geo_of(const osog_conv_shape_t *s) {
+    Geo g;
+    g.N = s->N;
+    g.H = s->H;
+    g.W = s->W;
+    g.C = s->C;
+    g.K = s->K;
+    g.R = s->R;
+    g.S = s->S;
+    g.stride = s->stride;
+    g.pad = s->pad;
+    g.P = (s->H + 2 * s->pad - s->R) / s->stride + 1;
+    g.Q = (s->W + 2 * s->pad - s->S) / s->stride + 1;
+    return g;
+}
+
+int splits_of(const Geo &g) {
+    const int64_t pix = (int64_t)g.N * g.P * g.Q;
+    return (int)((pix + kSplitPixels - 1) / kSplitPixels);
+}
+
+int status_of(cudaError_t e) { return e == cudaSuccess ? OSOG_OK : OSOG_ERR_CUDA; }
+
+const __nv_bfloat16 *bf(const uint16_t *p) { return reinterpret_cast<const __nv_bfloat16 *>(p); }
+__nv_bfloat16 *bf(uint16_t *p) { return reinterpret_cast<__nv_bfloat16 *>(p); }
+
+}  // namespace
+
+extern "C" {
+
+int32_t osog_conv_out_h(const osog_conv_shape_t *s) { return shape_ok(s) ? geo_of(s).P : 0; }
+int32_t osog_conv_out_w(const osog_conv_shape_t *s) { return shape_ok(s) ? geo_of(s).Q : 0; }
+
+int osog_conv2d_forward(const osog_conv_shape_t *shape, const uint16_t *x, const uint16_t *w,
+                        const float *bias, int32_t relu, uint16_t *y, float *y_f32,
+                        osog_stream_t stream) {
+    if (!shape_ok(shape) || !x || !w || !bias || !y) return OSOG_ERR_INVALID_ARG;
+    Args a{};
+    a.g = geo_of(shape);
+    a.x = bf(x);
+    a.w = bf(w);
+    a.bias = bias;
+    a.y = bf(y);
+    a.y32 = y_f32;
+    a.relu = relu;
+    a.M = a.g.N * a.g.P * a.g.Q;
+    a.Ncols = a.g.K;
+    a.Kred = a.g.R * a.g.S * a.g.C;
+    dim3 grid((a.M + BM - 1) / BM, (a.Ncols + BN - 1) / BN);
+    k_conv_gemm<kFwd><<<grid, NT, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
+    return status_of(cudaGetLastError());
+}
+
+int osog_conv2d_backward_data(const osog_conv_shape_t *shape, const uint16_t *dy,
+                              const uint16_t *w, const uint16_t *x_act, uint16_t *dx,
+                              uint16_t *w_t, osog_stream_t stream) {
+    if (!shape_ok(shape) || !dy || !w || !dx || !w_t) return OSOG_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const Geo g = geo_of(shape);
+    const int64_t nw = (int64_t)g.K * g.R * g.S * g.C;
+    k_filter_transpose<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(bf(w), g.K, g.R * g.S, g.C, bf(w_t));
+    Args a{};
+    a.g = g;
+    a.x = bf(dy);
+    a.w = bf(w_t);
+    a.mask = x_act ? bf(x_act) : nullptr;
+    a.y = bf(dx);
+    a.M = g.N * g.H * g.W;
+    a.Ncols = g.C;
+    a.Kred = g.R * g.S * g.K;
+    dim3 grid((a.M + BM - 1) / BM, (a.Ncols + BN - 1) / BN);
+    k_conv_gemm<kDgrad><<<grid, NT, 0, st>>>(a);
+    return status_of(cudaGetLastError());
+}
+
+size_t osog_conv2d_backward_filter_workspace(const osog_conv_shape_t *shape) {
+    if (!shape_ok(shape)) return 0;
+    const Geo g = geo_of(shape);
+    return (size_t)splits_of(g) * g.K * g.R * g.S * g.C * sizeof(float);
+}
+
+int osog_conv2d_backward_filter(const osog_conv_shape_t *shape, const uint16_t *dy,
+                                const uint16_t *x, float *dw, float *dbias, void *ws,
+                                size_t ws_bytes, osog_stream_t stream) {
+    if (!shape_ok(shape) || !dy || !x || !dw || !dbias) return OSOG_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < osog_conv2d_backward_filter_workspace(shape)) return OSOG_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const Geo g = geo_of(shape);
+    Args a{};
+    a.g = g;
+    a.x = bf(dy);
+    a.w = bf(x);
+    a.part = static_cast<float *>(ws);
+    a.M = g.K;
+    a.Ncols = g.R * g.S * g.C;
+    a.Kred = g.N * g.P * g.Q;
+    const int splits = splits_of(g);
+    dim3 grid((a.M + BM - 1) / BM, (a.Ncols + BN - 1) / BN, splits);
+    k_conv_gemm<kWgrad><<<grid, NT, 0, st>>>(a);
+    const int64_t count = (int64_t)a.M * a.Ncols;
+    k_sum_splits<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(a.part, splits, count, dw);
+    k_bias_grad<<<g.K, 256, 0, st>>>(bf(dy), (int64_t)g.N * g.P * g.Q, g.K, dbias);
+    return status_of(cudaGetLastError());
+}
+
+int osog_relu_backward(const uint16_t *dy, const uint16_t *act, uint16_t *dy_out, int64_t count,
+                       osog_stream_t stream) {
+    if (!dy || !act || !dy_out || count < 0) return OSOG_ERR_INVALID_ARG;
+    if (count == 0) return OSOG_OK;
+    k_relu_backward<<<(unsigned)((count + 255) / 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        bf(dy), bf(act), count, bf(dy_out));
+    return status_of(cudaGetLastError());
+}
+
+}  // extern "C"

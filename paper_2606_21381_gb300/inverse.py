@@ -41,6 +41,7 @@ class SolveConfig:
     lr_shear: float = 0.01           # px
     betas: tuple = (0.9, 0.99)
     log_every: int = 0
+    record_every: int = 0            # with a ground truth: error history every n steps
 
 
 @dataclass
@@ -50,6 +51,9 @@ class SolveResult:
     losses: list = field(default_factory=list)
     seconds: float = 0.0
     steps: int = 0
+    # (step, seconds since start, median rel. dn error, median rel. T error,
+    #  fraction of particles with dn and T within 1%)
+    history: list = field(default_factory=list)
 
 
 def lowpass_mask(H: int, W: int, dx: float, lam: float, na: float, device) -> torch.Tensor:
@@ -83,10 +87,20 @@ def perturb(soa: np.ndarray, optics: dict, rng: np.random.Generator, frac: float
     return s, o
 
 
+def _device_errors(x: torch.Tensor, truth: torch.Tensor) -> torch.Tensor:
+    rel_dn = (x[6] - truth[6]).abs() / truth[6].abs()
+    rel_T = (x[5] - truth[5]).abs() / truth[5].abs()
+    within = ((rel_dn <= 0.01) & (rel_T <= 0.01)).float().mean()
+    return torch.stack([rel_dn.median(), rel_T.median(), within])
+
+
 def solve(target: torch.Tensor, soa0: np.ndarray, optics0: dict, renderer: Renderer,
-          cfg: SolveConfig | None = None, fixed_optics: bool = False) -> SolveResult:
+          cfg: SolveConfig | None = None, fixed_optics: bool = False,
+          truth: np.ndarray | None = None) -> SolveResult:
     """Adam on the curriculum-filtered squared image misfit.  target is the
-    (K, H, W) measured image; soa0 / optics0 the initial guess."""
+    (K, H, W) measured image; soa0 / optics0 the initial guess.  With the
+    true particle tensor and cfg.record_every > 0 the error history is
+    recorded (the clock keeps running across the records)."""
     cfg = cfg or SolveConfig()
     dev = renderer.device
     soa = torch.from_numpy(np.ascontiguousarray(soa0, dtype=np.float32)).to(dev)
@@ -107,7 +121,13 @@ def solve(target: torch.Tensor, soa0: np.ndarray, optics0: dict, renderer: Rende
     H, W = target.shape[-2:]
     norm = float(target.numel())
     res = SolveResult(soa=None, optics_params=None)
+    truth_d = None
+    if truth is not None and cfg.record_every:
+        truth_d = torch.from_numpy(np.ascontiguousarray(truth, dtype=np.float32)).to(dev)
+    torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
+    if truth_d is not None:
+        res.history.append((0, 0.0, *_device_errors(x.detach(), truth_d).tolist()))
     ramp = max(1, int(cfg.steps * cfg.curriculum_frac))
     for it in range(cfg.steps):
         na = cfg.na_start + (optics0["NA"] - cfg.na_start) * min(1.0, it / ramp)
@@ -127,15 +147,28 @@ def solve(target: torch.Tensor, soa0: np.ndarray, optics0: dict, renderer: Rende
                 p1.mul_(b1).add_(gp, alpha=1 - b1)
                 p2.mul_(b2).addcmul_(gp, gp, value=1 - b2)
                 params.sub_(plr * (p1 / (1 - b1 ** t)) / (torch.sqrt(p2 / (1 - b2 ** t)) + 1e-30))
-        res.losses.append(float(loss.detach()))
+        res.losses.append(loss.detach())
+        if truth_d is not None and (it + 1) % cfg.record_every == 0:
+            e = _device_errors(x.detach(), truth_d).tolist()
+            res.history.append((it + 1, time.perf_counter() - t0, *e))
         if cfg.log_every and it % cfg.log_every == 0:
             print(f"step {it:4d} NA {na:.3f} loss {float(loss):.3e}")
     torch.cuda.synchronize(dev)
     res.seconds = time.perf_counter() - t0
     res.steps = cfg.steps
+    res.losses = [float(v) for v in torch.stack(res.losses).cpu()] if res.losses else []
     res.soa = x.detach().cpu().numpy()
     res.optics_params = params.detach().numpy()
     return res
+
+
+def time_to_error(history: list, tol: float = 0.01):
+    """(step, seconds) of the first record at which the median relative dn
+    and T errors are both <= tol; None if never."""
+    for step, sec, dn, T, _ in history:
+        if dn <= tol and T <= tol:
+            return step, sec
+    return None
 
 
 def errors(est: np.ndarray, truth: np.ndarray, est_params=None, truth_optics=None) -> dict:

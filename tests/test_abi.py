@@ -11,10 +11,10 @@ from paper_2606_21381_gb300 import _lib, build
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def header_functions():
-    text = open(os.path.join(ROOT, "include", "osog.h")).read()
+def header_functions(name="osog.h"):
+    text = open(os.path.join(ROOT, "include", name)).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(osog_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(osog_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
@@ -34,8 +34,17 @@ def test_header_declares_the_boundary():
 
 def test_library_exports_every_declared_symbol(L):
     raw = ctypes.CDLL(build.LIB)
-    for name in header_functions():
+    for name in header_functions() + header_functions("osog_cnn.h"):
         assert hasattr(raw, name), name
+    assert sorted(_lib.CNN_EXPORTS) == header_functions("osog_cnn.h")
+
+
+def test_conv_shape_checks_on_the_host(L):
+    s = _lib.ConvShape(2, 20, 20, 8, 16, 3, 3, 2, 1)
+    assert L.osog_conv_out_h(ctypes.byref(s)) == 10
+    bad = _lib.ConvShape(2, 20, 20, 6, 16, 3, 3, 1, 1)  # C not a multiple of 8
+    assert L.osog_conv_out_h(ctypes.byref(bad)) == 0
+    assert L.osog_conv2d_forward(ctypes.byref(bad), None, None, None, 1, None, None, None) == 1
 
 
 def test_library_is_built_for_sm103a():
