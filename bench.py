@@ -117,13 +117,15 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers
-def measured_peaks():
+def measured_peaks(kind: str = "hbm"):
+    """(peak, source): HBM copy GB/s, or dense bf16 TFLOP/s as a burst."""
+    key, fallback = {"hbm": ("hbm_gbs", 6800.0), "bf16": ("bf16_tflops", 1900.0)}[kind]
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d[key]), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return fallback, "fallback"
 
 
 def ncu_traffic(kernel: str):
@@ -319,7 +321,8 @@ def run_gpu(args, rank, world, local_rank):
         if fb_r.sync_status(stream) != 0:
             raise RuntimeError("device status set in the forward + adjoint run")
         del img
-
+    warm = None if (args.no_warm_start or rank != 0) else warm_start_bench(dev)
+    with torch.cuda.stream(stream):
         # ---- end to end from pinned host buffers through the public API
         soa_host = torch.from_numpy(soa_all).pin_memory()
         img_host = torch.empty((SCENES, K, SIZE, SIZE), dtype=torch.float32).pin_memory()
@@ -340,7 +343,107 @@ def run_gpu(args, rank, world, local_rank):
     return finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms,
                   single40k, e2e_ms, launches, clocks, wall, K, soas=soas, optics=optics,
                   fwd_bwd_ms=fb_ms, extra={"autotuned": tuned, "batched_modes_ms": modes_ms,
-                                           "kernels_three_launch": prof3})
+                                           "kernels_three_launch": prof3, "warm_start": warm})
+
+
+def conv_profile(net, x, reps: int = 10):
+    """Per-launch CUDA-event times of every convolution kernel call of one
+    training step (forward, data and filter gradients of each layer) on the
+    batch x, with the algorithmic FLOPs 2 N P Q K R S C of each."""
+    import torch
+
+    from paper_2606_21381_gb300 import cnn
+    out, acts = net.forward(x)
+    rows = []
+    for i, (cin, cout, k, stride, pad) in enumerate(net.specs):
+        a = acts[i]
+        y = acts[i + 1] if i + 1 < len(acts) else out.to(torch.bfloat16)
+        dy = torch.ones_like(y)
+        calls = [("fwd", lambda: cnn.conv2d(a, net.wb[i], net.b[i], stride, pad, True)),
+                 ("wgrad", lambda: cnn.conv2d_backward_filter(dy, a, tuple(net.w[i].shape),
+                                                              stride, pad))]
+        if i > 0:
+            calls.append(("dgrad", lambda: cnn.conv2d_backward_data(dy, net.wb[i], tuple(a.shape),
+                                                                    stride, pad, x_act=a)))
+        flops = 2.0 * a.shape[0] * y.shape[1] * y.shape[2] * cout * k * k * cin
+        for name, fn in calls:
+            fn()
+            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            rows.append({"layer": i, "pass": name, "ms": round(ms, 4),
+                         "tflops": round(flops / (ms / 1e3) / 1e12, 2)})
+    return rows
+
+
+def warm_start_bench(dev, samples: int = 200_000, seeds=(7, 9, 10)):
+    """Learned warm start on the 512^2 inverse-rendering scene: train the
+    network on `samples` rendered crops, then time the plain and the
+    warm-started solves to 1% median dn and T error from the same perturbed
+    guesses (500 curriculum steps)."""
+    import torch
+
+    from paper_2606_21381_gb300 import cnn, inverse
+    from paper_2606_21381_gb300.render import Renderer
+    r = Renderer(512, 512, dev)
+    net = cnn.WarmStartNet(dev, seed=0)
+    tr = cnn.train(net, cnn.TrainConfig(samples=samples), r)
+    ev = cnn.calibrate(net, r)
+    x, _, _ = cnn.RenderStream(r, 16, 256, seed=5).next()
+    convs = conv_profile(net, x)
+    soa, o = scenes.inverse_512()
+    o = dict(o, defocus=0.8, shear_px=1.0)
+    target = r.render(torch.from_numpy(soa).to(dev), None, o)
+    s0, o0 = inverse.perturb(soa, o, np.random.default_rng(seeds[0]))
+    inverse.solve(target, s0, o0, r, inverse.SolveConfig(steps=20))   # warm-up
+    arms = {"plain": [], "warm": []}
+    for seed in seeds:
+        s0, o0 = inverse.perturb(soa, o, np.random.default_rng(seed))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        sw, ow = cnn.warm_start(net, target, s0, o0)
+        torch.cuda.synchronize(dev)
+        t_inf = time.perf_counter() - t0
+        cfg = inverse.SolveConfig(steps=500, record_every=5)
+        for arm, (ss, oo, extra) in (("plain", (s0, o0, 0.0)), ("warm", (sw, ow, t_inf))):
+            res = inverse.solve(target, ss, oo, r, cfg, truth=soa)
+            hit = inverse.time_to_error(res.history)
+            e = inverse.errors(res.soa, soa, res.optics_params, o)
+            arms[arm].append({"seed": seed, "steps_to_1pct": hit[0] if hit else None,
+                              "seconds_to_1pct": round(hit[1] + extra, 4) if hit else None,
+                              "start_s": round(extra, 4),
+                              "final_frac_within_1pct": round(e["frac_dn_T_within_1pct"], 3)})
+    if r.sync_status() != 0:
+        raise RuntimeError("device status set in the warm-start run")
+    mean = lambda arm, k: (statistics.mean(a[k] for a in arms[arm])
+                           if all(a[k] is not None for a in arms[arm]) else None)
+    peak_t = measured_peaks(kind="bf16")
+    dom = max(convs, key=lambda c: c["ms"])
+    tot = sum(c["ms"] for c in convs)
+    flops_tot = sum(c["tflops"] * c["ms"] for c in convs)  # TF/s x ms = GFLOP
+    return {
+        "workload": "6-layer BF16 CNN (32-64-128-128-64-32, 3x3) on 256x256 brightfield + DIC "
+                    "crops of batched 512x512 renders, then the 512x512 / 200-particle inverse "
+                    "solve (500 curriculum steps) from perturbed guesses",
+        "train": {"samples": tr.samples, "steps": tr.steps, "seconds": round(tr.seconds, 2),
+                  "samples_per_s": round(tr.samples / tr.seconds, 1),
+                  "final_loss": round(float(tr.losses[-50:, 0].mean()), 4)},
+        "held_out_rms": {k: round(v, 5) for k, v in ev.items()},
+        "inverse_512": arms,
+        "mean_steps_to_1pct": {"plain": mean("plain", "steps_to_1pct"),
+                               "warm": mean("warm", "steps_to_1pct")},
+        "mean_seconds_to_1pct": {"plain": mean("plain", "seconds_to_1pct"),
+                                 "warm": mean("warm", "seconds_to_1pct")},
+        "conv_kernels": convs,
+        "roofline": {"bound": "tensor", "kernel": f"layer {dom['layer']} {dom['pass']}",
+                     "achieved": dom["tflops"], "peak": peak_t[0], "unit": "TFLOP/s",
+                     "frac": round(dom["tflops"] / peak_t[0], 4), "peak_source": peak_t[1],
+                     "step_convs_tflops": round(flops_tot / tot, 2)},
+    }
 
 
 def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms, single40k,
@@ -412,6 +515,7 @@ def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms
             "ms": round(statistics.median(fwd_bwd_ms), 4),
             "workload": "512x512, 200 particles, brightfield + DIC: osog_render + "
                         "osog_render_backward (recomputed forward, adjoint)"},
+        "warm_start": (extra or {}).get("warm_start"),
         "gpu_launches": int(launches),
         "clocks": clocks.summary(),
         "wall_s_timed": round(wall, 4),
@@ -483,6 +587,8 @@ def main():
     ap.add_argument("--impl", default="osog", choices=["osog", "reference"])
     ap.add_argument("--scenes", type=int, default=32,
                     help="scenes per batch (32 is the benchmarked workload)")
+    ap.add_argument("--no-warm-start", action="store_true",
+                    help="skip the learned warm-start benchmark (training + inverse solves)")
     ap.add_argument("--quick", action="store_true",
                     help="timed region and per-kernel pass only (profiling runs)")
     args = ap.parse_args()
