@@ -24,7 +24,7 @@ namespace osog {
 namespace {
 
 // One strip (rows [strip R, strip R + R)) of scene s.
-template <int N, int MODE>
+template <int N, int MODE, bool SQ = false>
 __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, int strip,
                                                    unsigned char *smem_raw) {
     constexpr int L = kSetElems / N;
@@ -34,8 +34,8 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
     Rect *srect = reinterpret_cast<Rect *>(srec + kThreads);
     int *wsum = reinterpret_cast<int *>(srect + kThreads);
     const Geometry &geo = a.geo;
-    const int y0 = strip * geo.R;
-    const int R = geo.R;
+    const int R = SQ ? sq_rb(N) : geo.R;
+    const int y0 = strip * R;
     const int RN = R * N;  // <= kSetElems; lines R..L-1 are never read back
     if constexpr (MODE == kStripFromMap) {
         const float2 *src = a.opd_att + (size_t)y0 * N;
@@ -73,16 +73,22 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
             if (e < RN) {
                 float2 *v = buf + (e / N) * LS + pad16(e % N);
                 const float2 oa = *v;
-                float sn, cs;
-                sincospif(oa.x * tol, &sn, &cs);
-                const float amp = expf(-oa.y);
-                *v = make_float2(amp * cs, amp * sn);
+                if (oa.x != 0.f || oa.y != 0.f) {  // empty pixels keep E = 1
+                    float sn, cs;
+                    sincospif(oa.x * tol, &sn, &cs);
+                    const float amp = expf(-oa.y);
+                    *v = make_float2(amp * cs, amp * sn);
+                } else {
+                    *v = make_float2(1.f, 0.f);
+                }
             }
         }
         __syncthreads();
         fft_lines<N, L, false>(buf, a.tw);
-        const int B = geo.B, lb = ilog2(B), lr = ilog2(R);
-        float2 *G = a.w.G + (size_t)s * geo.H * N;
+        const int B = SQ ? sq_rb(N) : geo.B;
+        const int lb = SQ ? clog2(sq_rb(N)) : ilog2(B), lr = SQ ? clog2(sq_rb(N)) : ilog2(R);
+        const int H = SQ ? N : geo.H;
+        float2 *G = a.w.G + (size_t)s * H * N;
         const int2 cr = a.w.colrange[s];
 #pragma unroll
         for (int i = 0; i < kEPT; ++i) {
@@ -90,19 +96,19 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
             const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
             const int kx = bk * B + c, fx = kx < N / 2 ? kx : kx - N;
             if (e < RN && fx >= cr.x && fx <= cr.y)  // columns outside every pupil are never read
-                G[((size_t)bk * geo.H + y0 + r) * B + c] = buf[r * LS + pad16(kx)];
+                G[((size_t)bk * H + y0 + r) * B + c] = buf[r * LS + pad16(kx)];
         }
     }
 }
 
-template <int N, int MODE>
+template <int N, int MODE, bool SQ>
 __global__ void __launch_bounds__(kThreads, 2) k_strip_forward(const __grid_constant__ StripArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    strip_forward_item<N, MODE>(a, blockIdx.y, blockIdx.x, smem_raw);
+    strip_forward_item<N, MODE, SQ>(a, blockIdx.y, blockIdx.x, smem_raw);
 }
 
 // One column block bk of scene s.
-template <int N, bool MULTI>
+template <int N, bool MULTI, bool SQ = false>
 __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
                                             unsigned char *smem_raw) {
     constexpr int L = kSetElems / N;
@@ -111,14 +117,15 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
     float2 *buf1 = MULTI ? buf0 + L * LS : buf0;
     int2 *chords = reinterpret_cast<int2 *>(buf1 + L * LS);
     const Geometry &geo = a.geo;
-    const int B = geo.B, lb = ilog2(B), K = a.K;
+    const int B = SQ ? sq_rb(N) : geo.B, lb = SQ ? clog2(sq_rb(N)) : ilog2(B), K = a.K;
+    const int W = SQ ? N : geo.W;
     const int2 cr = a.w.colrange[s];
     // A block whose columns all lie outside every pupil has nothing to filter:
     // its Q block is never read.  The block's unsigned columns [u0, u1] map to
     // signed frequencies [u0, min(u1, W/2 - 1)] and [max(u0, W/2), u1] - W.
-    const int u0 = bk * B, u1 = u0 + B - 1, half = geo.W / 2;
+    const int u0 = bk * B, u1 = u0 + B - 1, half = W / 2;
     const bool lo_part = u0 < half && u0 <= cr.y && min(u1, half - 1) >= cr.x;
-    const bool hi_part = u1 >= half && max(u0, half) - geo.W <= cr.y && u1 - geo.W >= cr.x;
+    const bool hi_part = u1 >= half && max(u0, half) - W <= cr.y && u1 - W >= cr.x;
     if (!lo_part && !hi_part) return;
     const float2 *G = a.w.G + ((size_t)s * geo.nblocks + bk) * N * B;
     const int NB_ = N * B;  // <= kSetElems; lines B..L-1 are never read back
@@ -127,7 +134,7 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
 #pragma unroll
         for (int i = 0; i < kEPT; ++i) {
             const int e = threadIdx.x + i * kThreads;
-            const int kx = u0 + (e & (B - 1)), fx = kx < half ? kx : kx - geo.W;
+            const int kx = u0 + (e & (B - 1)), fx = kx < half ? kx : kx - W;
             v[i] = e < NB_ && fx >= cr.x && fx <= cr.y ? G[e] : make_float2(0.f, 0.f);
         }
 #pragma unroll
@@ -138,7 +145,7 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
     }
     for (int j = threadIdx.x; j < K * B; j += kThreads) {
         const int m = j >> lb, c = j & (B - 1);
-        chords[m * L + c] = a.w.chord[((size_t)s * K + m) * geo.W + bk * B + c];
+        chords[m * L + c] = a.w.chord[((size_t)s * K + m) * W + bk * B + c];
     }
     __syncthreads();
     fft_lines<N, L, false>(buf0, a.tw);
@@ -150,7 +157,7 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
             const int c = e / N, y = e % N;
             if (c < B) {
                 const int kx = bk * B + c;
-                const int fx = kx < half ? kx : kx - geo.W;
+                const int fx = kx < half ? kx : kx - W;
                 const int fy = y < N / 2 ? y : y - N;
                 const int2 ch = chords[m * L + c];
                 float2 v = make_float2(0.f, 0.f);
@@ -171,14 +178,14 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
     }
 }
 
-template <int N, bool MULTI>
+template <int N, bool MULTI, bool SQ>
 __global__ void __launch_bounds__(kThreads, 2) k_column(const __grid_constant__ ColumnArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    column_item<N, MULTI>(a, blockIdx.y, blockIdx.x, smem_raw);
+    column_item<N, MULTI, SQ>(a, blockIdx.y, blockIdx.x, smem_raw);
 }
 
 // One strip of the image sm = s K + m.
-template <int N>
+template <int N, bool SQ = false>
 __device__ __forceinline__ void inverse_item(const InverseArgs &a, int sm, int strip,
                                              unsigned char *smem_raw) {
     constexpr int L = kSetElems / N;
@@ -186,9 +193,11 @@ __device__ __forceinline__ void inverse_item(const InverseArgs &a, int sm, int s
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
     const Geometry &geo = a.geo;
     const int K = a.K;
-    const int y0 = strip * geo.R;
-    const int R = geo.R, B = geo.B, lb = ilog2(B), lr = ilog2(R);
-    const float2 *Qm = a.w.Q + (size_t)sm * geo.nblocks * geo.H * B;
+    const int R = SQ ? sq_rb(N) : geo.R, B = SQ ? sq_rb(N) : geo.B;
+    const int lb = SQ ? clog2(sq_rb(N)) : ilog2(B), lr = SQ ? clog2(sq_rb(N)) : ilog2(R);
+    const int H = SQ ? N : geo.H;
+    const int y0 = strip * R;
+    const float2 *Qm = a.w.Q + (size_t)sm * geo.nblocks * H * B;
     const int2 cr = a.w.colrange[sm / K];
     const int RN = R * N;  // <= kSetElems; lines R..L-1 are never read back
     {
@@ -198,7 +207,7 @@ __device__ __forceinline__ void inverse_item(const InverseArgs &a, int sm, int s
             const int e = threadIdx.x + i * kThreads;
             const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
             const int kx = bk * B + c, fx = kx < N / 2 ? kx : kx - N;
-            v[i] = e < RN && fx >= cr.x && fx <= cr.y ? Qm[((size_t)bk * geo.H + y0 + r) * B + c]
+            v[i] = e < RN && fx >= cr.x && fx <= cr.y ? Qm[((size_t)bk * H + y0 + r) * B + c]
                                                       : make_float2(0.f, 0.f);
         }
 #pragma unroll
@@ -210,7 +219,7 @@ __device__ __forceinline__ void inverse_item(const InverseArgs &a, int sm, int s
     }
     __syncthreads();
     fft_lines<N, L, true>(buf, a.tw);
-    float *img = a.images + ((size_t)sm * geo.H + y0) * N;
+    float *img = a.images + ((size_t)sm * H + y0) * N;
 #pragma unroll
     for (int i = 0; i < kEPT; ++i) {
         const int e = threadIdx.x + i * kThreads;
@@ -221,10 +230,10 @@ __device__ __forceinline__ void inverse_item(const InverseArgs &a, int sm, int s
     }
 }
 
-template <int N>
+template <int N, bool SQ>
 __global__ void __launch_bounds__(kThreads, 2) k_strip_inverse(const __grid_constant__ InverseArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    inverse_item<N>(a, blockIdx.y, blockIdx.x, smem_raw);
+    inverse_item<N, SQ>(a, blockIdx.y, blockIdx.x, smem_raw);
 }
 
 // ------------------------------------------------------------ persistent
@@ -345,22 +354,27 @@ template <int N>
 struct StripFwdLaunch {
     static cudaError_t run(const StripArgs &a, StripMode mode, cudaStream_t st, size_t smem) {
         dim3 grid(a.geo.nstrips, a.S);
-        if (mode == kStripRender)
-            k_strip_forward<N, kStripRender><<<grid, kThreads, smem, st>>>(a);
+        if (mode == kStripRender && a.geo.H == a.geo.W)
+            k_strip_forward<N, kStripRender, true><<<grid, kThreads, smem, st>>>(a);
+        else if (mode == kStripRender)
+            k_strip_forward<N, kStripRender, false><<<grid, kThreads, smem, st>>>(a);
         else if (mode == kStripOpdOnly)
-            k_strip_forward<N, kStripOpdOnly><<<grid, kThreads, smem, st>>>(a);
+            k_strip_forward<N, kStripOpdOnly, false><<<grid, kThreads, smem, st>>>(a);
         else
-            k_strip_forward<N, kStripFromMap><<<grid, kThreads, smem, st>>>(a);
+            k_strip_forward<N, kStripFromMap, false><<<grid, kThreads, smem, st>>>(a);
         return cudaGetLastError();
     }
     static cudaError_t prepare(size_t smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_strip_forward<N, kStripRender>,
+        cudaError_t e = cudaFuncSetAttribute(k_strip_forward<N, kStripRender, true>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_strip_forward<N, kStripOpdOnly>,
+            e = cudaFuncSetAttribute(k_strip_forward<N, kStripRender, false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_strip_forward<N, kStripFromMap>,
+            e = cudaFuncSetAttribute(k_strip_forward<N, kStripOpdOnly, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_strip_forward<N, kStripFromMap, false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         return e;
     }
@@ -370,18 +384,26 @@ template <int N>
 struct ColumnLaunch {
     static cudaError_t run(const ColumnArgs &a, cudaStream_t st, size_t smem) {
         dim3 grid(a.geo.nblocks, a.S);
-        if (a.K > 1)
-            k_column<N, true><<<grid, kThreads, smem, st>>>(a);
+        const bool sq = a.geo.H == a.geo.W;
+        if (a.K > 1 && sq)
+            k_column<N, true, true><<<grid, kThreads, smem, st>>>(a);
+        else if (a.K > 1)
+            k_column<N, true, false><<<grid, kThreads, smem, st>>>(a);
+        else if (sq)
+            k_column<N, false, true><<<grid, kThreads, smem, st>>>(a);
         else
-            k_column<N, false><<<grid, kThreads, smem, st>>>(a);
+            k_column<N, false, false><<<grid, kThreads, smem, st>>>(a);
         return cudaGetLastError();
     }
     static cudaError_t prepare(size_t smem1, size_t smem2) {
-        cudaError_t e = cudaFuncSetAttribute(k_column<N, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_column<N, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        cudaError_t e = cudaSuccess;
+        for (int sq = 0; sq < 2 && e == cudaSuccess; ++sq) {
+            e = cudaFuncSetAttribute(sq ? k_column<N, false, true> : k_column<N, false, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(sq ? k_column<N, true, true> : k_column<N, true, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        }
         return e;
     }
 };
@@ -390,12 +412,19 @@ template <int N>
 struct InverseLaunch {
     static cudaError_t run(const InverseArgs &a, cudaStream_t st, size_t smem) {
         dim3 grid(a.geo.nstrips, a.S * a.K);
-        k_strip_inverse<N><<<grid, kThreads, smem, st>>>(a);
+        if (a.geo.H == a.geo.W)
+            k_strip_inverse<N, true><<<grid, kThreads, smem, st>>>(a);
+        else
+            k_strip_inverse<N, false><<<grid, kThreads, smem, st>>>(a);
         return cudaGetLastError();
     }
     static cudaError_t prepare(size_t smem) {
-        return cudaFuncSetAttribute(k_strip_inverse<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_strip_inverse<N, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_strip_inverse<N, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return e;
     }
 };
 

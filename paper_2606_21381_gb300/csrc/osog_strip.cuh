@@ -17,6 +17,12 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 __device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
+__host__ __device__ constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v >> 1); }
+
+// Rows per strip and columns per column block of a square N x N canvas
+// (both min(kSetElems / N, N)); kernels specialised for square canvases use
+// these compile-time values instead of the geometry's.
+__host__ __device__ constexpr int sq_rb(int n) { return kSetElems / n < n ? kSetElems / n : n; }
 
 // Accumulate one particle's OPD / ATT over the pixels [xa, xb] x [ya, yb]
 // of the strip buffer.  The warp's lanes cover the particle's rows (the
@@ -33,21 +39,30 @@ __device__ __forceinline__ void raster_particle(float2 *buf, int LS, int y0, con
     const int lxn = 32 / lyn;
     const int shx = ilog2(lxn);
     const int lx = lane & (lxn - 1), ly = lane >> shx;
+    // Two pixels per lane and step (x and x + lxn): both chords first, then
+    // both shared-memory updates, so that the loads of the pair overlap.
+    // A pixel outside the footprint is skipped (t < 0).
     if (r.g > 0.f) {
         for (int yy = ya + ly; yy <= yb; yy += lyn) {
             const float ey = ((float)yy + 0.5f) - r.cy;
             const float s_ey = r.sh * ey, c_ey = r.ch * ey;
             float2 *row = buf + (yy - y0) * LS;
-            for (int xx = xa + lx; xx <= xb; xx += lxn) {
+            auto chord = [&](int xx) {
                 const float ex = ((float)xx + 0.5f) - r.cx;
                 const float u = fmaf(r.ch, ex, s_ey);
                 const float v = fmaf(-r.sh, ex, c_ey);
                 const float d = fminf(r.p0h - fabsf(u), r.p1h - fabsf(v));
-                const float t = fminf(fmaxf(r.g * d, 0.f), r.T);
-                float2 acc = row[pad16(xx)];
-                acc.x = fmaf(r.dn, t, acc.x);
-                acc.y = fmaf(r.mu, t, acc.y);
-                row[pad16(xx)] = acc;
+                return fminf(fmaxf(r.g * d, 0.f), r.T);
+            };
+            for (int xx = xa + lx; xx <= xb; xx += 2 * lxn) {
+                const int x2 = xx + lxn;
+                const float t1 = chord(xx);
+                const float t2 = x2 <= xb ? chord(x2) : -1.f;
+                float2 *p1 = row + pad16(xx), *p2 = row + pad16(x2);
+                float2 a1 = *p1, a2;
+                if (t2 >= 0.f) a2 = *p2;
+                *p1 = make_float2(fmaf(r.dn, t1, a1.x), fmaf(r.mu, t1, a1.y));
+                if (t2 >= 0.f) *p2 = make_float2(fmaf(r.dn, t2, a2.x), fmaf(r.mu, t2, a2.y));
             }
         }
     } else {
@@ -58,22 +73,29 @@ __device__ __forceinline__ void raster_particle(float2 *buf, int LS, int y0, con
             const float ey = yc - r.cy;
             const float u0 = sia * ey, v0 = cib * ey;
             float2 *row = buf + (yy - y0) * LS;
-            for (int xx = xa + lx; xx <= xb; xx += lxn) {
+            auto chord = [&](int xx) {
                 const float xc = (float)xx + 0.5f;
                 const float ex = xc - r.cx;
                 const float ua = fmaf(cia, ex, u0);
                 const float vb = fmaf(-sib, ex, v0);
                 float delta = 1.f - fmaf(ua, ua, vb * vb);
                 if (delta < kRimBand) {
-                    if (delta <= -kRimBand) continue;
+                    if (delta <= -kRimBand) return -1.f;
                     delta = ellipse_delta_ff(r, xc, yc);
-                    if (!(delta > 0.f)) continue;
+                    if (!(delta > 0.f)) return -1.f;
                 }
-                const float t = r.T * delta * rsqrtf(delta);
-                float2 acc = row[pad16(xx)];
-                acc.x = fmaf(r.dn, t, acc.x);
-                acc.y = fmaf(r.mu, t, acc.y);
-                row[pad16(xx)] = acc;
+                return r.T * delta * rsqrtf(delta);
+            };
+            for (int xx = xa + lx; xx <= xb; xx += 2 * lxn) {
+                const int x2 = xx + lxn;
+                const float t1 = chord(xx);
+                const float t2 = x2 <= xb ? chord(x2) : -1.f;
+                float2 *p1 = row + pad16(xx), *p2 = row + pad16(x2);
+                float2 a1, a2;
+                if (t1 >= 0.f) a1 = *p1;
+                if (t2 >= 0.f) a2 = *p2;
+                if (t1 >= 0.f) *p1 = make_float2(fmaf(r.dn, t1, a1.x), fmaf(r.mu, t1, a1.y));
+                if (t2 >= 0.f) *p2 = make_float2(fmaf(r.dn, t2, a2.x), fmaf(r.mu, t2, a2.y));
             }
         }
     }
@@ -177,18 +199,20 @@ __device__ __forceinline__ float2 transfer(const ModeDev &md, int fx, int fy) {
 // to and from the padded shared lines of an N = W point set.  Columns whose
 // signed frequency lies outside [cr.x, cr.y] (no pupil passes them) are
 // neither read (zero-filled) nor written.
-template <int N>
+template <int N, bool SQ = false>
 __device__ __forceinline__ void load_strip_blocked(float2 *buf, const float2 *src,
                                                    const Geometry &geo, int y0, int2 cr) {
     constexpr int LS = line_stride(N);
-    const int R = geo.R, B = geo.B, lb = ilog2(B), lr = ilog2(R), RN = R * N;
+    const int R = SQ ? sq_rb(N) : geo.R, B = SQ ? sq_rb(N) : geo.B;
+    const int lb = SQ ? clog2(sq_rb(N)) : ilog2(B), lr = SQ ? clog2(sq_rb(N)) : ilog2(R);
+    const int RN = R * N, H = SQ ? N : geo.H;
     float2 v[kEPT];
 #pragma unroll
     for (int i = 0; i < kEPT; ++i) {
         const int e = threadIdx.x + i * kThreads;
         const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
         const int kx = bk * B + c, fx = kx < N / 2 ? kx : kx - N;
-        v[i] = e < RN && fx >= cr.x && fx <= cr.y ? src[((size_t)bk * geo.H + y0 + r) * B + c]
+        v[i] = e < RN && fx >= cr.x && fx <= cr.y ? src[((size_t)bk * H + y0 + r) * B + c]
                                                   : make_float2(0.f, 0.f);
     }
 #pragma unroll
@@ -199,18 +223,20 @@ __device__ __forceinline__ void load_strip_blocked(float2 *buf, const float2 *sr
     }
 }
 
-template <int N>
+template <int N, bool SQ = false>
 __device__ __forceinline__ void store_strip_blocked(const float2 *buf, float2 *dst,
                                                     const Geometry &geo, int y0, int2 cr) {
     constexpr int LS = line_stride(N);
-    const int R = geo.R, B = geo.B, lb = ilog2(B), lr = ilog2(R), RN = R * N;
+    const int R = SQ ? sq_rb(N) : geo.R, B = SQ ? sq_rb(N) : geo.B;
+    const int lb = SQ ? clog2(sq_rb(N)) : ilog2(B), lr = SQ ? clog2(sq_rb(N)) : ilog2(R);
+    const int RN = R * N, H = SQ ? N : geo.H;
 #pragma unroll
     for (int i = 0; i < kEPT; ++i) {
         const int e = threadIdx.x + i * kThreads;
         const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
         const int kx = bk * B + c, fx = kx < N / 2 ? kx : kx - N;
         if (e < RN && fx >= cr.x && fx <= cr.y)
-            dst[((size_t)bk * geo.H + y0 + r) * B + c] = buf[r * LS + pad16(kx)];
+            dst[((size_t)bk * H + y0 + r) * B + c] = buf[r * LS + pad16(kx)];
     }
 }
 
