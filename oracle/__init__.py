@@ -84,6 +84,10 @@ def _load():
         lib.orc_transfer.argtypes = [ctypes.POINTER(_Optics), i32, d, d]
         lib.orc_images.argtypes = [ctypes.POINTER(_Optics), d, d, d]
         lib.orc_render.argtypes = [d, i64, i32, ctypes.POINTER(_Optics), d, d, d, d, d]
+        lib.orc_opd_att_poly.argtypes = [d, i64, i32, i32, i32, ctypes.c_double,
+                                         ctypes.c_double, i32, d, d, d, d]
+        lib.orc_render_poly.argtypes = [d, i64, i32, d, d, ctypes.POINTER(_Optics), d, d, d,
+                                        d, d]
         lib.orc_render_grad.argtypes = [d, i64, i32, ctypes.POINTER(_Optics), d, d, d]
         _lib = lib
     return _lib
@@ -141,14 +145,33 @@ def halfspace_chord(A: np.ndarray, b: np.ndarray, u: float, v: float) -> float:
     return _load().orc_halfspace_chord(_p(A), _p(b), len(b), float(u), float(v))
 
 
+def _planes(planes, plane_off, n: int):
+    """float64 (P, 4) planes and int32 (n + 1,) offsets of kind-2 particles."""
+    pl = np.ascontiguousarray(planes, dtype=np.float64).reshape(-1, 4)
+    off = np.ascontiguousarray(plane_off, dtype=np.int32)
+    if off.shape != (n + 1,) or off[0] < 0 or np.any(np.diff(off) < 0) or off[-1] > len(pl):
+        raise ValueError("plane_off must be non-decreasing offsets [n + 1] into planes")
+    return pl, off
+
+
 def opd_att(soa: np.ndarray, n: int, H: int, W: int, dx: float = 0.5,
-            bevel_slope: float = 1.0, full_canvas: bool = False):
-    """OPD (um) and absorption-thickness maps, each (H, W) float64."""
+            bevel_slope: float = 1.0, full_canvas: bool = False, planes=None,
+            plane_off=None):
+    """OPD (um) and absorption-thickness maps, each (H, W) float64.  Kind-2
+    particles (general polyhedra) take their half-spaces from planes
+    (rows (a_x, a_y, a_z, b), local frame in um) and plane_off [n + 1]."""
     soa, ld = _soa(soa)
     opd = np.zeros((H, W))
     att = np.zeros((H, W))
-    _load().orc_opd_att(_p(soa), ld, int(n), H, W, dx, bevel_slope,
-                        int(full_canvas), _p(opd), _p(att))
+    if planes is None:
+        if np.any(soa[8, :n] > 1.5):
+            raise ValueError("kind-2 particles need planes")
+        _load().orc_opd_att(_p(soa), ld, int(n), H, W, dx, bevel_slope,
+                            int(full_canvas), _p(opd), _p(att))
+    else:
+        pl, off = _planes(planes, plane_off, n)
+        _load().orc_opd_att_poly(_p(soa), ld, int(n), H, W, dx, bevel_slope,
+                                 int(full_canvas), _p(pl), _p(off), _p(opd), _p(att))
     return opd, att
 
 
@@ -215,8 +238,9 @@ def images_from_field(o: dict, E: np.ndarray) -> np.ndarray:
     return out
 
 
-def render(soa: np.ndarray, n: int, o: dict) -> dict:
-    """Whole forward model: returns dict(opd, att, field, images)."""
+def render(soa: np.ndarray, n: int, o: dict, planes=None, plane_off=None) -> dict:
+    """Whole forward model: returns dict(opd, att, field, images).  planes /
+    plane_off as for opd_att (kind-2 particles)."""
     soa, ld = _soa(soa)
     s = _optics_struct(o)
     H, W = o["H"], o["W"]
@@ -225,8 +249,15 @@ def render(soa: np.ndarray, n: int, o: dict) -> dict:
     er = np.empty_like(opd)
     ei = np.empty_like(opd)
     img = np.empty((n_modes(o), H, W))
-    _load().orc_render(_p(soa), ld, int(n), ctypes.byref(s), _p(opd), _p(att),
-                       _p(er), _p(ei), _p(img))
+    if planes is None:
+        if np.any(soa[8, :n] > 1.5):
+            raise ValueError("kind-2 particles need planes")
+        _load().orc_render(_p(soa), ld, int(n), ctypes.byref(s), _p(opd), _p(att),
+                           _p(er), _p(ei), _p(img))
+    else:
+        pl, off = _planes(planes, plane_off, n)
+        _load().orc_render_poly(_p(soa), ld, int(n), _p(pl), _p(off), ctypes.byref(s),
+                                _p(opd), _p(att), _p(er), _p(ei), _p(img))
     return dict(opd=opd, att=att, field=er + 1j * ei, images=img)
 
 

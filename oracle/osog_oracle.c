@@ -8,9 +8,10 @@
  * in double precision, slowly and in the paper's order.
  *
  * What it computes (paper sections / equations):
- *   - particle geometry: ellipsoids (quadric chord) and bevelled rectangular
+ *   - particle geometry: ellipsoids (quadric chord), bevelled rectangular
  *     prisms as an intersection of M = 14 half-spaces, P = {x : A x <= b}
- *     (Sec. III.A, Eq. 1);
+ *     (Sec. III.A, Eq. 1), and general convex polyhedra given by the
+ *     caller's own M planes (kind 2, Eq. 1);
  *   - OPD and absorption maps: sum over particles of dn_p * t_p and
  *     mu_p * t_p, overlaps add (Eq. 2's integral over z; Eq. 7's
  *     accumulate=True composition, Sec. III.C);
@@ -116,15 +117,37 @@ void orc_prism_halfspaces(double hx_um, double hy_um, double T, double s,
     }
 }
 
+/* Planes of the general polyhedra (kind 2): particle p owns rows
+ * off[p] .. off[p+1]-1 of planes, each (a_x, a_y, a_z, b) of one half-space
+ * a . (u, v, z) <= b in the particle's local frame (um). */
+typedef struct {
+    const double *planes;
+    const int32_t *off;
+} orc_planes;
+
 /* Thickness t (um) of particle p (fields widened from fp32) at the canvas
  * point (x, y) px. */
-static double particle_thickness(const double *q, double dx, double bevel,
-                                 double x, double y)
+static double particle_thickness(const double *q, int p, const orc_planes *pl,
+                                 double dx, double bevel, double x, double y)
 {
     double c = cos(q[F_TH]), s = sin(q[F_TH]);
     double ex = x - q[F_CX], ey = y - q[F_CY];
     double u = c * ex + s * ey;
     double v = -s * ex + c * ey;
+    if (q[F_KIND] > 1.5) {
+        if (!pl || !pl->planes) return 0.0;
+        int m = pl->off[p + 1] - pl->off[p];
+        double A[3 * 64], b[64];
+        if (m > 64) m = 64;
+        for (int i = 0; i < m; ++i) {
+            const double *r = pl->planes + 4 * (size_t)(pl->off[p] + i);
+            A[3 * i] = r[0];
+            A[3 * i + 1] = r[1];
+            A[3 * i + 2] = r[2];
+            b[i] = r[3];
+        }
+        return orc_halfspace_chord(A, b, m, u * dx, v * dx);
+    }
     if (q[F_KIND] > 0.5) {
         double A[42], b[14];
         orc_prism_halfspaces(q[F_A] * dx, q[F_B] * dx, q[F_T], bevel, A, b);
@@ -145,9 +168,9 @@ static void load_particle(const float *soa, int64_t ld, int p, double *q)
  * particles added in ascending index.  Each particle is evaluated on the
  * pixels of its circumscribed square plus one pixel (t is zero outside it)
  * unless full_canvas is set, in which case every pixel is evaluated. */
-void orc_opd_att(const float *soa, int64_t ld, int n, int H, int W,
-                 double dx, double bevel, int full_canvas,
-                 double *opd, double *att)
+static void opd_att_planes(const float *soa, int64_t ld, int n, int H, int W,
+                           double dx, double bevel, int full_canvas,
+                           const orc_planes *pl, double *opd, double *att)
 {
     memset(opd, 0, sizeof(double) * (size_t)H * W);
     memset(att, 0, sizeof(double) * (size_t)H * W);
@@ -156,7 +179,9 @@ void orc_opd_att(const float *soa, int64_t ld, int n, int H, int W,
         load_particle(soa, ld, p, q);
         int j0 = 0, j1 = W - 1, i0 = 0, i1 = H - 1;
         if (!full_canvas) {
-            double R = q[F_KIND] > 0.5 ? sqrt(q[F_A] * q[F_A] + q[F_B] * q[F_B])
+            /* kind 2: a is the footprint's circumscribed radius (px) */
+            double R = q[F_KIND] > 1.5 ? q[F_A]
+                     : q[F_KIND] > 0.5 ? sqrt(q[F_A] * q[F_A] + q[F_B] * q[F_B])
                                        : fmax(q[F_A], q[F_B]);
             double jl = floor(q[F_CX] - R - 1.5), jh = ceil(q[F_CX] + R + 0.5);
             double il = floor(q[F_CY] - R - 1.5), ih = ceil(q[F_CY] + R + 0.5);
@@ -168,13 +193,31 @@ void orc_opd_att(const float *soa, int64_t ld, int n, int H, int W,
         }
         for (int i = i0; i <= i1; ++i)
             for (int j = j0; j <= j1; ++j) {
-                double t = particle_thickness(q, dx, bevel, j + 0.5, i + 0.5);
+                double t = particle_thickness(q, p, pl, dx, bevel, j + 0.5, i + 0.5);
                 if (t != 0.0) {
                     opd[(size_t)i * W + j] += q[F_DN] * t;
                     att[(size_t)i * W + j] += q[F_MU] * t;
                 }
             }
     }
+}
+
+void orc_opd_att(const float *soa, int64_t ld, int n, int H, int W,
+                 double dx, double bevel, int full_canvas,
+                 double *opd, double *att)
+{
+    opd_att_planes(soa, ld, n, H, W, dx, bevel, full_canvas, NULL, opd, att);
+}
+
+/* As orc_opd_att with the plane sets of kind-2 particles (planes: rows of
+ * (a_x, a_y, a_z, b); off: [n + 1] row offsets). */
+void orc_opd_att_poly(const float *soa, int64_t ld, int n, int H, int W,
+                      double dx, double bevel, int full_canvas,
+                      const double *planes, const int32_t *off,
+                      double *opd, double *att)
+{
+    orc_planes pl = {planes, off};
+    opd_att_planes(soa, ld, n, H, W, dx, bevel, full_canvas, &pl, opd, att);
 }
 
 /* OPD at a list of pixels by brute force over every particle (no window):
@@ -190,7 +233,7 @@ void orc_opd_at(const float *soa, int64_t ld, int n, double dx, double bevel,
         for (int p = 0; p < n; ++p) {
             double q[F_COUNT];
             load_particle(soa, ld, p, q);
-            double t = particle_thickness(q, dx, bevel, j + 0.5, i + 0.5);
+            double t = particle_thickness(q, p, NULL, dx, bevel, j + 0.5, i + 0.5);
             so += q[F_DN] * t;
             sa += q[F_MU] * t;
         }
@@ -393,6 +436,17 @@ void orc_render(const float *soa, int64_t ld, int n, const orc_optics *o,
                 double *images)
 {
     orc_opd_att(soa, ld, n, o->H, o->W, o->dx, o->bevel_slope, 0, opd, att);
+    orc_field(opd, att, (int64_t)o->H * o->W, o->lambda, ere, eim);
+    orc_images(o, ere, eim, images);
+}
+
+/* orc_render with kind-2 particles and their planes. */
+void orc_render_poly(const float *soa, int64_t ld, int n, const double *planes,
+                     const int32_t *off, const orc_optics *o, double *opd,
+                     double *att, double *ere, double *eim, double *images)
+{
+    orc_opd_att_poly(soa, ld, n, o->H, o->W, o->dx, o->bevel_slope, 0, planes,
+                     off, opd, att);
     orc_field(opd, att, (int64_t)o->H * o->W, o->lambda, ere, eim);
     orc_images(o, ere, eim, images);
 }

@@ -65,6 +65,55 @@ def draw_particles(rng: np.random.Generator, n: int, H: int, W: int,
     return soa
 
 
+def draw_polyhedra(rng: np.random.Generator, n: int, H: int, W: int, dn=(0.01, 0.05),
+                   mu=(0.0, 0.0), sides=(5, 8), dist=(3.0, 10.0), thickness=(0.5, 3.0),
+                   slope: float = 1.0, dx: float = 0.5):
+    """n general polyhedra (kind 2): bevelled convex polygons.  Each has k ~
+    U{sides} edges with outward normals at angles 2 pi j / k jittered by up
+    to a quarter of the spacing and distances U(dist) px from the centre, a
+    top and a bottom face at +-T/2 and, on every edge, a top and a bottom
+    chamfer plane of the given slope (2 + 2k half-spaces, no vertical wall).
+    Returns (soa (9, n) float32, planes (P, 4) float32 of (a_x, a_y, a_z, b)
+    in the local frame (um), offsets (n + 1,) int32); soa row 3 (and 4)
+    holds the footprint's circumscribed radius in px."""
+    soa = np.zeros((9, n), dtype=np.float32)
+    soa[0] = rng.uniform(0.0, W, n)
+    soa[1] = rng.uniform(0.0, H, n)
+    soa[2] = rng.uniform(0.0, math.pi, n)
+    soa[5] = rng.uniform(*thickness, size=n)
+    soa[6] = rng.uniform(*dn, size=n)
+    soa[7] = rng.uniform(*mu, size=n) if mu[1] > mu[0] else mu[0]
+    soa[8] = 2.0
+    planes, offsets = [], [0]
+    for p in range(n):
+        k = int(rng.integers(sides[0], sides[1] + 1))
+        ang = 2 * math.pi * np.arange(k) / k + rng.uniform(-0.25, 0.25, k) * (2 * math.pi / k)
+        d = rng.uniform(*dist, size=k) * dx
+        nx, ny = np.cos(ang), np.sin(ang)
+        T = float(soa[5, p])
+        rows = [(0.0, 0.0, 1.0, 0.5 * T), (0.0, 0.0, -1.0, 0.5 * T)]
+        for j in range(k):
+            rows.append((slope * nx[j], slope * ny[j], 1.0, slope * d[j]))
+            rows.append((slope * nx[j], slope * ny[j], -1.0, slope * d[j]))
+        # circumscribed radius: the farthest vertex of the polygon
+        # {n_j . x <= d_j}, among the pairwise line intersections that
+        # satisfy every edge
+        r2 = 0.0
+        for i in range(k):
+            for j in range(i + 1, k):
+                det = nx[i] * ny[j] - ny[i] * nx[j]
+                if abs(det) < 1e-12:
+                    continue
+                x = (d[i] * ny[j] - ny[i] * d[j]) / det
+                y = (nx[i] * d[j] - d[i] * nx[j]) / det
+                if np.all(nx * x + ny * y <= d + 1e-9):
+                    r2 = max(r2, x * x + y * y)
+        soa[3, p] = soa[4, p] = math.sqrt(r2) / dx
+        planes.extend(rows)
+        offsets.append(len(planes))
+    return soa, np.asarray(planes, dtype=np.float32), np.asarray(offsets, dtype=np.int32)
+
+
 # ------------------------------------------------------------------ workloads
 def plain_256(seed: int = 0):
     """256 x 256, 64 particles, brightfield + oblique (offset 0.3 NA)."""
@@ -108,6 +157,14 @@ def batch_2048(scenes: int = 32, size: int = 2048, seed: int = 100):
     counts = batch_2048_counts(seed, scenes)
     out = [batch_2048_scene(s, c, size) for s, c in enumerate(counts)]
     return [a for a, _ in out], [o for _, o in out]
+
+
+def polyhedra_256(seed: int = 5, n: int = 48):
+    """256 x 256, n bevelled convex polygons given as planes (kind 2),
+    brightfield + oblique, NA 0.4."""
+    rng = np.random.default_rng(seed)
+    soa, planes, off = draw_polyhedra(rng, n, 256, 256)
+    return soa, planes, off, optics(256, 256, NA=0.4, modes=MODE_BF | MODE_OBLIQUE)
 
 
 def inverse_512(seed: int = 3, n: int = 200):
