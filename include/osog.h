@@ -24,7 +24,8 @@
  *       3 a | hx (px)  4 b | hy (px)  5 T (um)  6 dn  7 mu (1/um)
  *       8 kind (0 = ellipsoid with semi-axes a, b and full thickness T;
  *               1 = rectangular prism with half-lengths hx, hy, thickness T
- *               and chamfers of slope bevel_slope on all top/bottom edges).
+ *               and chamfers of slope bevel_slope on all top/bottom edges;
+ *               2 = general convex polyhedron, osog_render_polyhedra only).
  *   - Pixel (i, j) is sampled at its centre (x, y) = (j + 0.5, i + 0.5) px;
  *     rows are y.  Images are float32 [K][H][W], K = number of bits set in
  *     optics->modes, in bit order brightfield, oblique, DIC.
@@ -58,7 +59,8 @@ extern "C" {
 #define OSOG_ERR_NONFINITE_INPUT 5    /* NaN or Inf in a particle field */
 #define OSOG_ERR_TIMEOUT 6            /* a bounded device wait gave up */
 #define OSOG_ERR_CUDA 7               /* a CUDA runtime call failed */
-#define OSOG_ERR_INVALID_PARTICLE 8   /* a <= 0, b <= 0, T < 0 or unknown kind */
+#define OSOG_ERR_INVALID_PARTICLE 8   /* a <= 0, b <= 0, T < 0, unknown kind, or a
+                                         kind-2 particle without a valid plane range */
 
 /* Modality bits of osog_optics_t.modes. */
 #define OSOG_MODE_BRIGHTFIELD 1u
@@ -165,6 +167,33 @@ size_t osog_workspace_size(const osog_plan_t *plan, int32_t n_max, int32_t K,
 int osog_render(osog_plan_t *plan, const float *soa, int64_t ld, int32_t n,
                 const osog_optics_t *optics, float *image, void *ws,
                 size_t ws_bytes, osog_stream_t stream);
+
+/*
+ * Forward render of one scene that may hold general convex polyhedra
+ * (kind 2): each is the intersection of its own half-spaces
+ * a_x u + a_y v + a_z z <= b (Eq. 1 with the caller's M planes), u, v in um
+ * in the particle's frame (centre cx, cy; rotated by theta), z in um along
+ * the optical axis; its thickness is the vertical chord through the pixel
+ * centre.  Kinds 0 and 1 render as in osog_render.
+ *   planes         device float32 [n_planes][4] rows (a_x, a_y, a_z, b),
+ *                  16-byte aligned
+ *   plane_offsets  device int32 [n + 1]: particle p owns rows
+ *                  plane_offsets[p] .. plane_offsets[p+1]-1 (1..32 of them
+ *                  for kind 2; ignored for kinds 0 and 1)
+ *   soa rows 3 and 4 of a kind-2 particle hold the circumscribed radius of
+ *   its footprint in px (both > 0); T is not used.
+ *   ws             >= osog_polyhedra_workspace_size(plan, n, K, n_planes)
+ * A kind-2 particle with a bad plane range latches
+ * OSOG_ERR_INVALID_PARTICLE, non-finite planes OSOG_ERR_NONFINITE_INPUT,
+ * and is skipped.  Other arguments and errors as for osog_render.  The
+ * adjoint (osog_render_backward) covers kinds 0 and 1 only.
+ */
+size_t osog_polyhedra_workspace_size(const osog_plan_t *plan, int32_t n_max, int32_t K,
+                                     int32_t n_planes);
+int osog_render_polyhedra(osog_plan_t *plan, const float *soa, int64_t ld, int32_t n,
+                          const float *planes, const int32_t *plane_offsets,
+                          int32_t n_planes, const osog_optics_t *optics, float *image,
+                          void *ws, size_t ws_bytes, osog_stream_t stream);
 
 /*
  * Stage entry: rasterise only.  Writes the OPD and ATT maps of Eq. 2 as a

@@ -137,6 +137,7 @@ SceneDev scene_dev(const osog_optics_t &o) {
     SceneDev s{};
     s.two_over_lambda = (float)(2.0 / o.lambda_um);
     s.prism_g = (float)(2.0 * o.bevel_slope * o.dx_um);
+    s.dx_um = (float)o.dx_um;
     return s;
 }
 
@@ -206,6 +207,9 @@ struct GroupOpts {
     bool persistent = false;
     int band_rows = 0;
     std::vector<int32_t> *band_off_out = nullptr;  // kBinOnly: host copy of band_off
+    const float4 *planes = nullptr;                 // kind-2 particles (single scene)
+    const int32_t *plane_off = nullptr;
+    int32_t n_planes = 0;
 };
 
 // The plan's geometry with the binning band height replaced by band_rows
@@ -253,7 +257,16 @@ int enqueue_group(osog_plan *p, const float *soa, int64_t ld, const int32_t *cou
     gd.nchunks = (int32_t)chunks;
     const Layout l = make_layout(geo, n, chunks, S, stage == kFull || stage == kFromMap ? K : 0, pairs);
     if (l.total > ws_bytes) return fail(OSOG_ERR_WORKSPACE, "workspace too small");
-    const Work w = carve(ws, l, p->status);
+    Work w = carve(ws, l, p->status);
+    if (opt.planes) {  // the planes' pixel-affine bounds follow the regions above
+        const size_t coef = align256(l.total);
+        if (coef + (size_t)opt.n_planes * sizeof(float4) > ws_bytes)
+            return fail(OSOG_ERR_WORKSPACE, "workspace too small for the planes");
+        w.planes = opt.planes;
+        w.plane_off = opt.plane_off;
+        w.n_planes = opt.n_planes;
+        w.plane_coef = reinterpret_cast<float4 *>(static_cast<char *>(ws) + coef);
+    }
     int rc;
     if (stage != kFromMap) {
         rc = run_kernel(p, OSOG_KERNEL_BIN_COUNT, st, [&] { return launch_bin_count(soa, ld, gd, geo, w, st); });
@@ -428,6 +441,37 @@ int osog_render(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
                 const osog_optics_t *optics, float *image, void *ws, size_t ws_bytes,
                 osog_stream_t stream) {
     return render_stage(p, soa, ld, n, optics, image, nullptr, nullptr, ws, ws_bytes, stream, kFull);
+}
+
+size_t osog_polyhedra_workspace_size(const osog_plan_t *p, int32_t n_max, int32_t K,
+                                     int32_t n_planes) {
+    if (!p || n_max < 0 || K < 1 || K > 3 || n_planes < 0) return 0;
+    return align256(ws_need(p, n_max, K, 1, kDefaultPairs)) + (size_t)n_planes * sizeof(float4);
+}
+
+int osog_render_polyhedra(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
+                          const float *planes, const int32_t *plane_offsets, int32_t n_planes,
+                          const osog_optics_t *optics, float *image, void *ws, size_t ws_bytes,
+                          osog_stream_t stream) {
+    if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    int rc = check_optics(p, optics);
+    if (rc) return rc;
+    if (n < 0 || (int64_t)n > ld) return fail(OSOG_ERR_INVALID_ARG, "need 0 <= n <= ld");
+    if (n > 0 && !soa) return fail(OSOG_ERR_INVALID_ARG, "soa is NULL");
+    if (!image) return fail(OSOG_ERR_INVALID_ARG, "image is NULL");
+    if (n_planes < 0 || (n_planes > 0 && !planes) || !plane_offsets)
+        return fail(OSOG_ERR_INVALID_ARG, "planes / plane_offsets missing");
+    if (reinterpret_cast<uintptr_t>(planes) & 15)
+        return fail(OSOG_ERR_INVALID_ARG, "planes must be 16-byte aligned");
+    const int K = popcount3(optics->modes);
+    rc = check_ws(ws, osog_polyhedra_workspace_size(p, n, K, n_planes), ws_bytes);
+    if (rc) return rc;
+    GroupOpts o;
+    o.planes = reinterpret_cast<const float4 *>(planes);
+    o.plane_off = plane_offsets;
+    o.n_planes = n_planes;
+    return enqueue_group(p, soa, ld, &n, 1, optics, K, o, ws, ws_bytes, image, nullptr, nullptr,
+                         kFull, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int osog_render_opd(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,

@@ -52,9 +52,34 @@ __device__ __forceinline__ void band_range(const Rect &r, int BH, int &b0, int &
     }
 }
 
+// Kind-2 setup: every plane a . (u, v, z) <= b of the particle, with the
+// local frame u = dx (c ex + s ey), v = dx (-s ex + c ey) of the pixel
+// offset (ex, ey) from the centre, becomes a bound affine in (ex, ey):
+//   a . (u, v) = kx ex + ky ey,  kx = dx (a_x c - a_y s),  ky = dx (a_x s + a_y c),
+//   a_z > 0:  z <= (b - kx ex - ky ey) / a_z      (w = +1)
+//   a_z < 0:  z >= (b - kx ex - ky ey) / a_z      (w = -1)
+//   a_z = 0:  inside iff b - kx ex - ky ey >= 0   (w =  0)
+// stored as (c0, cx, cy, w) with the bound c0 - cx ex - cy ey, in double
+// precision rounded once.  False if a plane is not finite.
+__device__ bool setup_planes(const Work &w, int off, int m, double c, double s, double dx) {
+    for (int i = 0; i < m; ++i) {
+        const float4 pl = __ldg(w.planes + off + i);
+        if (!isfinite(pl.x) || !isfinite(pl.y) || !isfinite(pl.z) || !isfinite(pl.w)) return false;
+        const double kx = dx * ((double)pl.x * c - (double)pl.y * s);
+        const double ky = dx * ((double)pl.x * s + (double)pl.y * c);
+        const double az = pl.z;
+        const double d = az != 0.0 ? az : 1.0;
+        w.plane_coef[off + i] = make_float4((float)((double)pl.w / d), (float)(kx / d),
+                                            (float)(ky / d), az > 0.0 ? 1.f : (az < 0.0 ? -1.f : 0.f));
+    }
+    return true;
+}
+
 // Setup of one particle: validation, FP64-rounded record, bounding rect.
 __device__ Rect setup_particle(const float *soa, int64_t ld, int p, const SceneDev &sc,
-                               const Geometry &geo, PRec *rec, int32_t *status) {
+                               const Geometry &geo, const Work &w) {
+    PRec *rec = w.rec;
+    int32_t *status = w.status;
     float f[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) f[k] = __ldg(soa + (int64_t)k * ld + p);
@@ -68,9 +93,22 @@ __device__ Rect setup_particle(const float *soa, int64_t ld, int p, const SceneD
     }
     const float cx = f[0], cy = f[1], th = f[2], a = f[3], b = f[4], T = f[5];
     const float kind = f[8];
-    if (!(a > 0.f) || !(b > 0.f) || !(T >= 0.f) || !(kind == 0.f || kind == 1.f)) {
+    if (!(a > 0.f) || !(b > 0.f) || !(T >= 0.f) || !(kind == 0.f || kind == 1.f || kind == 2.f)) {
         latch(status, OSOG_ERR_INVALID_PARTICLE);
         return empty;
+    }
+    int poff = 0, pcnt = 0;
+    if (kind == 2.f) {  // planes given, 1..kMaxPlanes of them, inside the list
+        if (!w.planes || !w.plane_off || !w.plane_coef) {
+            latch(status, OSOG_ERR_INVALID_PARTICLE);
+            return empty;
+        }
+        poff = __ldg(w.plane_off + p);
+        pcnt = __ldg(w.plane_off + p + 1) - poff;
+        if (poff < 0 || pcnt < 1 || pcnt > kMaxPlanes || poff + pcnt > w.n_planes) {
+            latch(status, OSOG_ERR_INVALID_PARTICLE);
+            return empty;
+        }
     }
     double sd, cd;
     sincos((double)th, &sd, &cd);
@@ -86,7 +124,18 @@ __device__ Rect setup_particle(const float *soa, int64_t ld, int p, const SceneD
     r.mu = f[7];
     float ex, ey;
     const float c = fabsf(r.ch), s = fabsf(r.sh);
-    if (kind == 1.f) {
+    if (kind == 2.f) {
+        if (!setup_planes(w, poff, pcnt, cd, sd, (double)sc.dx_um)) {
+            latch(status, OSOG_ERR_NONFINITE_INPUT);
+            return empty;
+        }
+        r.p0h = __int_as_float(poff);
+        r.p0l = 0.f;
+        r.p1h = __int_as_float(pcnt);
+        r.p1l = 0.f;
+        r.g = -1.f;  // marks a general polyhedron
+        ex = ey = a;  // circumscribed radius of the footprint (px)
+    } else if (kind == 1.f) {
         r.p0h = a;
         r.p0l = 0.f;
         r.p1h = b;
@@ -133,7 +182,7 @@ k_bin_count(const float *__restrict__ soa, int64_t ld, const __grid_constant__ G
     for (int i = threadIdx.x; i < (kChunk / 32) * kMaxBands; i += kChunk) (&wcnt[0][0])[i] = 0;
     int b0 = 1, b1 = 0;
     if (mine) {
-        Rect r = setup_particle(soa, ld, p, sc, geo, w.rec, w.status);
+        Rect r = setup_particle(soa, ld, p, sc, geo, w);
         w.rect[p] = r;
         band_range(r, geo.BH, b0, b1);
     }

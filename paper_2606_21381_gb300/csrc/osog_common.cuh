@@ -18,6 +18,7 @@ constexpr int kChunk = 256;            // particles per binning CTA
 constexpr int kMaxBands = 64;          // bands (binning rows) per canvas
 constexpr int kMaxScenes = 32;         // scenes per launch group
 constexpr int kMaxModes = 3;
+constexpr int kMaxPlanes = 32;         // half-spaces per general polyhedron
 
 // Shared-memory index of element i of an FFT line: one float2 of padding
 // after every 16 keeps the strided Stockham accesses free of bank conflicts.
@@ -76,7 +77,7 @@ struct SceneDev {
     int32_t pair_cap;  // slots reserved for the scene
     float two_over_lambda;
     float prism_g;     // 2 s_b dx
-    float pad_;
+    float dx_um;       // pixel pitch (um)
 };
 
 // Transfer-function constants of one (scene, modality).
@@ -118,6 +119,13 @@ struct Work {
                         // band); written by the fill pass when not null (adjoint)
     int32_t slotmap_ppp;
     int32_t *status;    // plan status word
+    // General polyhedra (kind 2): the caller's planes (a_x, a_y, a_z, b),
+    // per-particle row offsets [n + 1], and their per-particle pixel-affine
+    // bounds written by the setup pass (see setup_particle()).
+    const float4 *planes = nullptr;
+    const int32_t *plane_off = nullptr;
+    int32_t n_planes = 0;
+    float4 *plane_coef = nullptr;
 };
 
 // ---------------------------------------------------------------- pupil

@@ -31,9 +31,12 @@ __host__ __device__ constexpr int sq_rb(int n) { return kSetElems / n < n ? kSet
 //   ellipsoid: t = T sqrt(1 - rho^2), rho^2 = u'^2 + v'^2 with
 //              u' = (c ex + s ey) / a, v' = (-s ex + c ey) / b, evaluated
 //              in float32 and redone in float-float inside the rim band;
-//   prism:     t = clamp(g min(hx - |u|, hy - |v|), 0, T), g = 2 s_b dx.
+//   prism:     t = clamp(g min(hx - |u|, hy - |v|), 0, T), g = 2 s_b dx;
+//   polyhedron (g < 0): t = z_hi - z_lo over the particle's pixel-affine
+//              plane bounds coef[off .. off + m) (Eq. 1), 0 outside a wall.
 __device__ __forceinline__ void raster_particle(float2 *buf, int LS, int y0, const PRec &r,
-                                                int xa, int xb, int ya, int yb, int lane) {
+                                                const float4 *__restrict__ coef, int xa, int xb,
+                                                int ya, int yb, int lane) {
     const int bh = yb - ya + 1;
     const int lyn = bh >= 32 ? 32 : (bh <= 1 ? 1 : 1 << (32 - __clz(bh - 1)));
     const int lxn = 32 / lyn;
@@ -42,7 +45,35 @@ __device__ __forceinline__ void raster_particle(float2 *buf, int LS, int y0, con
     // Two pixels per lane and step (x and x + lxn): both chords first, then
     // both shared-memory updates, so that the loads of the pair overlap.
     // A pixel outside the footprint is skipped (t < 0).
-    if (r.g > 0.f) {
+    if (r.g < 0.f) {
+        const float4 *pc = coef + __float_as_int(r.p0h);
+        const int m = __float_as_int(r.p1h);
+        for (int yy = ya + ly; yy <= yb; yy += lyn) {
+            const float ey = ((float)yy + 0.5f) - r.cy;
+            float2 *row = buf + (yy - y0) * LS;
+            for (int xx = xa + lx; xx <= xb; xx += lxn) {
+                const float ex = ((float)xx + 0.5f) - r.cx;
+                float zlo = -INFINITY, zhi = INFINITY;
+                bool inside = true;
+                for (int i = 0; i < m; ++i) {
+                    const float4 q = __ldg(pc + i);  // same address in every lane
+                    const float z = fmaf(-q.y, ex, fmaf(-q.z, ey, q.x));
+                    if (q.w > 0.f)
+                        zhi = fminf(zhi, z);
+                    else if (q.w < 0.f)
+                        zlo = fmaxf(zlo, z);
+                    else
+                        inside = inside && z >= 0.f;
+                }
+                if (!inside || !(zhi > zlo)) continue;
+                const float t = zhi - zlo;
+                float2 acc = row[pad16(xx)];
+                acc.x = fmaf(r.dn, t, acc.x);
+                acc.y = fmaf(r.mu, t, acc.y);
+                row[pad16(xx)] = acc;
+            }
+        }
+    } else if (r.g > 0.f) {
         for (int yy = ya + ly; yy <= yb; yy += lyn) {
             const float ey = ((float)yy + 0.5f) - r.cy;
             const float s_ey = r.sh * ey, c_ey = r.ch * ey;
@@ -158,7 +189,8 @@ __device__ void raster_strip(const Geometry &geo, const Work &w, const SceneDev 
                 mm &= mm - 1;
                 const Rect rq = srect[i0 + src];
                 const PRec rec = srec[i0 + src];
-                raster_particle(buf, LS, y0, rec, max((int)rq.x0, c0), min((int)rq.x1, c1),
+                raster_particle(buf, LS, y0, rec, w.plane_coef, max((int)rq.x0, c0),
+                                min((int)rq.x1, c1),
                                 max((int)rq.y0, y0), min((int)rq.y1, ylast), lane);
                 __syncwarp();
             }

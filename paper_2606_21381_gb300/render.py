@@ -88,6 +88,32 @@ class Renderer:
               "osog_render")
         return out
 
+    def render_polyhedra(self, soa: torch.Tensor, n: int | None, planes: torch.Tensor,
+                         plane_offsets: torch.Tensor, optics: dict, out=None, stream=None):
+        """osog_render_polyhedra: one scene with general polyhedra (kind 2)
+        whose half-spaces are the rows (a_x, a_y, a_z, b) of planes
+        (float32 (P, 4)), particle p owning rows plane_offsets[p] ..
+        plane_offsets[p+1]-1 (int32 (n + 1,))."""
+        self._check_soa(soa)
+        n = soa.shape[1] if n is None else int(n)
+        if planes.device.type != "cuda" or planes.dtype != torch.float32 or planes.dim() != 2 \
+                or planes.shape[1] != 4 or not planes.is_contiguous():
+            raise ValueError("planes must be a contiguous CUDA float32 (P, 4) tensor")
+        if plane_offsets.device.type != "cuda" or plane_offsets.dtype != torch.int32 \
+                or plane_offsets.shape != (n + 1,):
+            raise ValueError("plane_offsets must be a CUDA int32 (n + 1,) tensor")
+        K = n_modes(optics)
+        if out is None:
+            out = torch.empty((K, self.H, self.W), dtype=torch.float32, device=self.device)
+        P = planes.shape[0]
+        ws = self.workspace(self._L.osog_polyhedra_workspace_size(self.plan, n, K, P))
+        o = optics_struct(optics)
+        check(self._L.osog_render_polyhedra(self.plan, _ptr(soa), soa.shape[1], n, _ptr(planes),
+                                            _ptr(plane_offsets), P, ctypes.byref(o), _ptr(out),
+                                            _ptr(ws), ws.numel(), _stream(stream)),
+              "osog_render_polyhedra")
+        return out
+
     def backward(self, soa: torch.Tensor, n: int | None, optics: dict, grad_image: torch.Tensor,
                  stream=None):
         """osog_render_backward: (dL/dsoa (9, ld), dL/d(defocus, shear_px,
