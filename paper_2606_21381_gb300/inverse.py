@@ -41,6 +41,7 @@ class SolveConfig:
     lr_shear: float = 0.01           # px
     betas: tuple = (0.9, 0.99)
     log_every: int = 0
+    spectral_weight: float = 0.0     # weight of the log-amplitude spectral loss (Eq. 8)
     record_every: int = 0            # with a ground truth: error history every n steps
 
 
@@ -66,6 +67,15 @@ def lowpass_mask(H: int, W: int, dx: float, lam: float, na: float, device) -> to
 
 def filtered(img: torch.Tensor, mask: torch.Tensor) -> torch.Tensor:
     return torch.fft.irfft2(torch.fft.rfft2(img) * mask, s=img.shape[-2:])
+
+
+def spectral_loss(img: torch.Tensor, target: torch.Tensor, eps: float = 1e-6) -> torch.Tensor:
+    """Eq. 8: squared difference of the log amplitude spectra of the images
+    (mean over the (K, H, W) frequencies; eps guards log 0).  Invariant to
+    circular shifts of either image."""
+    a = torch.log(torch.abs(torch.fft.fft2(img)) + eps)
+    b = torch.log(torch.abs(torch.fft.fft2(target)) + eps)
+    return ((a - b) ** 2).mean()
 
 
 def perturb(soa: np.ndarray, optics: dict, rng: np.random.Generator, frac: float = 0.2):
@@ -134,6 +144,8 @@ def solve(target: torch.Tensor, soa0: np.ndarray, optics0: dict, renderer: Rende
         mask = lowpass_mask(H, W, optics0["dx"], optics0["lambda_um"], na, dev)
         img = render(x, optics0, renderer, params)
         loss = ((filtered(img, mask) - filtered(target, mask)) ** 2).sum() / norm
+        if cfg.spectral_weight:
+            loss = loss + cfg.spectral_weight * spectral_loss(img, target)
         gx, gp = torch.autograd.grad(loss, (x, params), allow_unused=True)
         with torch.no_grad():
             t = it + 1

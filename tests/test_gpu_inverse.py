@@ -30,3 +30,20 @@ def test_inverse_solve_recovers_parameters():
     assert res.losses[-1] < 1e-2 * res.losses[0]
     # fixed particles (a, b, mu, kind) are untouched
     assert np.array_equal(res.soa[[3, 4, 7, 8]], s0[[3, 4, 7, 8]])
+
+
+def test_solve_with_the_spectral_loss_term():
+    # Eq. 8's log-amplitude term added to the misfit: the solve still
+    # recovers the particles (the term is shift-invariant, so it only helps
+    # alongside the pixel misfit)
+    from paper_2606_21381_gb300 import inverse
+    from paper_2606_21381_gb300.render import Renderer
+    soa, o = scenes.inverse_512()
+    o = dict(o, defocus=0.8, shear_px=1.0)
+    r = Renderer(512, 512)
+    target = r.render(torch.from_numpy(soa).cuda(), None, o)
+    s0, o0 = inverse.perturb(soa, o, np.random.default_rng(8))
+    res = inverse.solve(target, s0, o0, r, inverse.SolveConfig(steps=300, spectral_weight=1e-3))
+    e = inverse.errors(res.soa, soa, res.optics_params, o)
+    assert e["dn_rel_median"] < 0.01 and e["T_rel_median"] < 0.01
+    assert res.losses[-1] < 1e-2 * res.losses[0]
