@@ -84,6 +84,7 @@ def _load():
         lib.orc_transfer.argtypes = [ctypes.POINTER(_Optics), i32, d, d]
         lib.orc_images.argtypes = [ctypes.POINTER(_Optics), d, d, d]
         lib.orc_render.argtypes = [d, i64, i32, ctypes.POINTER(_Optics), d, d, d, d, d]
+        lib.orc_dic_incoherent.argtypes = [ctypes.POINTER(_Optics), d, d, d]
         lib.orc_opd_att_poly.argtypes = [d, i64, i32, i32, i32, ctypes.c_double,
                                          ctypes.c_double, i32, d, d, d, d]
         lib.orc_render_poly.argtypes = [d, i64, i32, d, d, ctypes.POINTER(_Optics), d, d, d,
@@ -236,6 +237,24 @@ def images_from_field(o: dict, E: np.ndarray) -> np.ndarray:
     out = np.empty((n_modes(o), o["H"], o["W"]))
     _load().orc_images(ctypes.byref(s), _p(re), _p(im), _p(out))
     return out
+
+
+def dic_incoherent(o: dict, E: np.ndarray) -> np.ndarray:
+    """Eq. 5 read literally: |U(r + ds) e^{i theta} - U(r - ds) e^{-i theta}|^2
+    blurred by the unit-sum intensity PSF of the brightfield pupil; (H, W)."""
+    s = _optics_struct(o)
+    re = np.ascontiguousarray(E.real, dtype=np.float64)
+    im = np.ascontiguousarray(E.imag, dtype=np.float64)
+    out = np.empty((o["H"], o["W"]))
+    _load().orc_dic_incoherent(ctypes.byref(s), _p(re), _p(im), _p(out))
+    return out
+
+
+def render_dic_incoherent(soa: np.ndarray, n: int, o: dict) -> np.ndarray:
+    """Incoherent DIC image of a scene (H, W): OPD/ATT maps, exit wave, then
+    dic_incoherent."""
+    opd, att = opd_att(soa, n, o["H"], o["W"], o["dx"], o["bevel_slope"])
+    return dic_incoherent(o, field(opd, att, o["lambda_um"]))
 
 
 def render(soa: np.ndarray, n: int, o: dict, planes=None, plane_off=None) -> dict:

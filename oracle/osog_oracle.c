@@ -21,7 +21,8 @@
  *     and the coherent image I = |E * h_obj|^2 (Sec. III.B, brightfield);
  *     oblique illumination as the pupil shifted by k_ill (Fig. 2 discussion:
  *     "asymmetric Fourier pupil"); DIC as the sheared-field difference of
- *     Eq. 5 taken coherently through the pupil;
+ *     Eq. 5 taken coherently through the pupil, and in the literal
+ *     incoherent reading of Eq. 5 (orc_dic_incoherent);
  *   - an own radix-2 FFT and a brute-force DFT (used to pin the FFT);
  *   - the gradient of a linear functional of the images with respect to
  *     every particle field and to the optics scalars, by the analytic
@@ -428,6 +429,71 @@ void orc_images(const orc_optics *o, const double *ere, const double *eim,
         ++k;
     }
     free(fr); free(fi); free(hr); free(hi); free(zr); free(zi);
+}
+
+/* DIC read literally from Eq. 5 (incoherent reading): the exit wave itself,
+ * not the filtered field, is sheared and interfered,
+ *   J(r) = | U(r + ds) e^{i theta} - U(r - ds) e^{-i theta} |^2,
+ * computed as D = IDFT2( DFT2(U) * 2i sin(k . ds + theta) ) / (H W) (shift
+ * theorem; every frequency, no pupil), and the intensity is then blurred by
+ * the objective's intensity point spread function |h|^2, h = IDFT2(P) /
+ * (H W) with P the brightfield pupil of Eq. 3 (NA, defocus), normalised to
+ * unit sum so that a uniform J stays uniform:
+ *   I = J (*) |h|^2 / sum |h|^2   (circular convolution, via the DFT).
+ * out is H x W. */
+void orc_dic_incoherent(const orc_optics *o, const double *ere, const double *eim,
+                        double *out)
+{
+    int H = o->H, W = o->W;
+    size_t N = (size_t)H * W;
+    double *dr = (double *)malloc(sizeof(double) * N), *di = (double *)malloc(sizeof(double) * N);
+    double *hr = (double *)malloc(sizeof(double) * N), *hi = (double *)malloc(sizeof(double) * N);
+    double *jr = (double *)malloc(sizeof(double) * N), *ji = (double *)malloc(sizeof(double) * N);
+    double dsx = 0.5 * o->shear_px * o->dx * cos(o->shear_angle);
+    double dsy = 0.5 * o->shear_px * o->dx * sin(o->shear_angle);
+    /* D and J = |D|^2 */
+    memcpy(dr, ere, sizeof(double) * N);
+    memcpy(di, eim, sizeof(double) * N);
+    orc_fft2(dr, di, H, W, -1);
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j) {
+            size_t q = (size_t)i * W + j;
+            double g = 2.0 * sin(kfreq(j, W, o->dx) * dsx + kfreq(i, H, o->dx) * dsy + o->bias_phase);
+            double r = -di[q] * g, m = dr[q] * g; /* (dr + i di) * (i g) */
+            dr[q] = r;
+            di[q] = m;
+        }
+    orc_fft2(dr, di, H, W, +1);
+    for (size_t q = 0; q < N; ++q) {
+        double a = dr[q] / (double)N, b = di[q] / (double)N;
+        jr[q] = a * a + b * b;
+        ji[q] = 0.0;
+    }
+    /* |h|^2 of the brightfield pupil, normalised to unit sum */
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j)
+            pupil(o, kfreq(j, W, o->dx), kfreq(i, H, o->dx), &hr[(size_t)i * W + j],
+                  &hi[(size_t)i * W + j]);
+    orc_fft2(hr, hi, H, W, +1);
+    double sum = 0.0;
+    for (size_t q = 0; q < N; ++q) {
+        double a = hr[q] / (double)N, b = hi[q] / (double)N;
+        hr[q] = a * a + b * b;
+        hi[q] = 0.0;
+        sum += hr[q];
+    }
+    for (size_t q = 0; q < N; ++q) hr[q] /= sum;
+    /* circular convolution J (*) psf by the DFT */
+    orc_fft2(jr, ji, H, W, -1);
+    orc_fft2(hr, hi, H, W, -1);
+    for (size_t q = 0; q < N; ++q) {
+        double r = jr[q] * hr[q] - ji[q] * hi[q], m = jr[q] * hi[q] + ji[q] * hr[q];
+        jr[q] = r;
+        ji[q] = m;
+    }
+    orc_fft2(jr, ji, H, W, +1);
+    for (size_t q = 0; q < N; ++q) out[q] = jr[q] / (double)N;
+    free(dr); free(di); free(hr); free(hi); free(jr); free(ji);
 }
 
 /* Whole forward model f(Theta) = I: OPD/ATT maps, exit wave, images. */
