@@ -196,6 +196,24 @@ int osog_render_polyhedra(osog_plan_t *plan, const float *soa, int64_t ld, int32
                           void *ws, size_t ws_bytes, osog_stream_t stream);
 
 /*
+ * DIC image of one scene in the literal (incoherent) reading of Eq. 5: the
+ * exit wave U itself is sheared by +-ds (ds = shear_px / 2 pixels along
+ * shear_angle) and interfered at bias theta,
+ *   J = |U(r + ds) e^{i theta} - U(r - ds) e^{-i theta}|^2,
+ * and J is convolved with the intensity point spread function |h|^2 of the
+ * brightfield pupil (NA, defocus; h = IDFT2(P)), normalised to unit sum:
+ *   image = J (*) |h|^2 / sum |h|^2   (device float32 [H][W]).
+ * optics->modes is ignored; oblique settings are not used.  Workspace:
+ * osog_dic_incoherent_workspace_size(plan, n).  Errors as for osog_render.
+ * (osog_render's DIC modality is the coherent reading: the sheared
+ * difference taken through the pupil.)
+ */
+size_t osog_dic_incoherent_workspace_size(const osog_plan_t *plan, int32_t n_max);
+int osog_render_dic_incoherent(osog_plan_t *plan, const float *soa, int64_t ld, int32_t n,
+                               const osog_optics_t *optics, float *image, void *ws,
+                               size_t ws_bytes, osog_stream_t stream);
+
+/*
  * Stage entry: rasterise only.  Writes the OPD and ATT maps of Eq. 2 as a
  * device float32 [H][W][2] array (opd, att per pixel), in the same order of
  * summation as osog_render.  Workspace as for osog_render with K = 1.

@@ -25,7 +25,8 @@ EXPORTS = ("osog_plan_create", "osog_plan_destroy", "osog_workspace_size", "osog
            "osog_sync_status", "osog_last_error", "osog_plan_launch_count",
            "osog_profile_begin", "osog_profile_end", "osog_render_noalloc",
            "osog_backward_workspace_size", "osog_render_backward", "osog_autotune",
-           "osog_polyhedra_workspace_size", "osog_render_polyhedra")
+           "osog_polyhedra_workspace_size", "osog_render_polyhedra",
+           "osog_dic_incoherent_workspace_size", "osog_render_dic_incoherent")
 
 
 class OsogError(RuntimeError):
@@ -129,6 +130,10 @@ def lib(build_if_missing: bool = True):
     L.osog_polyhedra_workspace_size.restype = sz
     L.osog_render_polyhedra.argtypes = [vp, vp, i64, i32, vp, vp, i32, P(Optics), vp, vp, sz, vp]
     L.osog_render_polyhedra.restype = ctypes.c_int
+    L.osog_dic_incoherent_workspace_size.argtypes = [vp, i32]
+    L.osog_dic_incoherent_workspace_size.restype = sz
+    L.osog_render_dic_incoherent.argtypes = [vp, vp, i64, i32, P(Optics), vp, vp, sz, vp]
+    L.osog_render_dic_incoherent.restype = ctypes.c_int
     L.osog_conv_out_h.argtypes = [P(ConvShape)]
     L.osog_conv_out_h.restype = i32
     L.osog_conv_out_w.argtypes = [P(ConvShape)]

@@ -474,6 +474,133 @@ int osog_render_polyhedra(osog_plan_t *p, const float *soa, int64_t ld, int32_t 
                          kFull, reinterpret_cast<cudaStream_t>(stream));
 }
 
+// Workspace of the incoherent DIC render: the one-scene, one-modality
+// regions, then a float [H][W] intensity buffer and the complex [H][W]
+// optical transfer function table (column-blocked like Q).
+struct DicLayout {
+    Layout l;
+    size_t img, otf, total;
+};
+
+DicLayout dic_layout(const Geometry &geo, int64_t n) {
+    DicLayout d;
+    d.l = make_layout(geo, n, (n + kChunk - 1) / kChunk + 1, 1, 1, n * kDefaultPairs);
+    size_t o = d.l.total;
+    d.img = o;
+    o = align256(o + (size_t)geo.H * geo.W * sizeof(float));
+    d.otf = o;
+    o = align256(o + (size_t)geo.H * geo.W * sizeof(float2));
+    d.total = o;
+    return d;
+}
+
+size_t osog_dic_incoherent_workspace_size(const osog_plan_t *p, int32_t n_max) {
+    if (!p || n_max < 0) return 0;
+    return dic_layout(p->geo, n_max).total;
+}
+
+int osog_render_dic_incoherent(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
+                               const osog_optics_t *optics, float *image, void *ws,
+                               size_t ws_bytes, osog_stream_t stream) {
+    if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    int rc = check_optics(p, optics);
+    if (rc) return rc;
+    if (n < 0 || (int64_t)n > ld) return fail(OSOG_ERR_INVALID_ARG, "need 0 <= n <= ld");
+    if (n > 0 && !soa) return fail(OSOG_ERR_INVALID_ARG, "soa is NULL");
+    if (!image) return fail(OSOG_ERR_INVALID_ARG, "image is NULL");
+    const Geometry &geo = p->geo;
+    const DicLayout dl = dic_layout(geo, n);
+    rc = check_ws(ws, dl.total, ws_bytes);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const Work w = carve(ws, dl.l, p->status);
+    float *J = reinterpret_cast<float *>(static_cast<char *>(ws) + dl.img);
+    float2 *otf = reinterpret_cast<float2 *>(static_cast<char *>(ws) + dl.otf);
+
+    GroupDev gd{};
+    gd.S = 1;
+    gd.K = 1;
+    gd.sc[0] = scene_dev(*optics);  // no particles until step 3
+    StripArgs sa{};
+    sa.geo = geo;
+    sa.w = w;
+    sa.tw = p->tw_w;
+    sa.S = 1;
+    ColumnArgs ca{};
+    ca.geo = geo;
+    ca.w = w;
+    ca.tw = p->tw_h;
+    ca.S = 1;
+    ca.K = 1;
+    InverseArgs ia{};
+    ia.geo = geo;
+    ia.w = w;
+    ia.tw = p->tw_w;
+    ia.S = 1;
+    ia.K = 1;
+    // Each step tabulates its modality's chords (full for every op but the
+    // pupil) before the render kernels run.
+    auto use_mode = [&](const ModeDev &md) {
+        gd.md[0][0] = md;
+        ca.md[0][0] = md;
+        sa.sc[0] = gd.sc[0];
+        return run_kernel(p, OSOG_KERNEL_BIN_SCAN, st, [&] { return launch_bin_scan(gd, geo, w, st); });
+    };
+    auto column = [&] { return run_kernel(p, OSOG_KERNEL_COLUMN, st, [&] { return launch_column(ca, st); }); };
+    auto inverse = [&] {
+        return run_kernel(p, OSOG_KERNEL_STRIP_INVERSE, st, [&] { return launch_strip_inverse(ia, st); });
+    };
+    auto strip = [&](StripMode m) {
+        return run_kernel(p, OSOG_KERNEL_STRIP_FORWARD, st, [&] { return launch_strip_forward(sa, m, st); });
+    };
+
+    // 1. |h|^2: unit spectrum times the brightfield pupil (NA, defocus),
+    //    inverse transform, squared modulus (h = IDFT2(P) / (H W)).
+    const ModeDev bf = mode_dev(*optics, OSOG_MODE_BRIGHTFIELD);
+    ca.unit_input = 1;
+    ia.images = J;
+    ia.real_out = 0;
+    if ((rc = use_mode(bf)) || (rc = column()) || (rc = inverse())) return rc;
+    // 2. OTF = DFT2(|h|^2), kept as a table (its DC term is sum |h|^2).
+    ModeDev sp{};
+    sp.op = kOpSpectrum;
+    sp.tab = otf;
+    sp.scale = 1.f;
+    ca.unit_input = 0;
+    sa.opd_att = reinterpret_cast<const float2 *>(J);
+    if ((rc = use_mode(sp)) || (rc = strip(kStripFromReal)) || (rc = column())) return rc;
+    // 3. J = |D|^2, D = IDFT2(DFT2(U) 2i sin(k . ds + theta)) / (H W): the
+    //    exit wave sheared and interfered on every frequency (Eq. 5).
+    ModeDev dic = mode_dev(*optics, OSOG_MODE_DIC);
+    dic.op = kOpAllPass;
+    dic.dz = 0.f;
+    const int64_t chunks = (n + kChunk - 1) / kChunk;
+    gd.nchunks = (int32_t)chunks;
+    gd.sc[0].n = n;
+    gd.sc[0].pair_cap = (int32_t)((int64_t)n * kDefaultPairs);
+    if ((rc = run_kernel(p, OSOG_KERNEL_BIN_COUNT, st,
+                         [&] { return launch_bin_count(soa, ld, gd, geo, w, st); })))
+        return rc;
+    if ((rc = use_mode(dic))) return rc;
+    if ((rc = run_kernel(p, OSOG_KERNEL_BIN_FILL, st, [&] { return launch_bin_fill(gd, geo, w, st); })))
+        return rc;
+    if ((rc = strip(kStripRender)) || (rc = column()) || (rc = inverse())) return rc;
+    // 4. I = IDFT2(DFT2(J) OTF / OTF(0)) / (H W): J blurred by the unit-sum
+    //    intensity PSF; the result is real.
+    ModeDev tb{};
+    tb.op = kOpTable;
+    tb.tab = otf;
+    tb.scale = (float)(1.0 / ((double)geo.H * geo.W));
+    gd.nchunks = 0;
+    gd.sc[0].n = 0;
+    gd.sc[0].pair_cap = 0;
+    ia.images = image;
+    ia.real_out = 1;
+    if ((rc = use_mode(tb)) || (rc = strip(kStripFromReal)) || (rc = column()) || (rc = inverse()))
+        return rc;
+    return OSOG_OK;
+}
+
 int osog_render_opd(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
                     const osog_optics_t *optics, float *opd_att, void *ws, size_t ws_bytes,
                     osog_stream_t stream) {

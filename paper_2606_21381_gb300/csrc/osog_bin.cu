@@ -250,7 +250,9 @@ k_bin_scan(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
         const int fx = kx < geo.W / 2 ? kx : kx - geo.W;
         bool act = false;
         for (int m = 0; m < gd.K; ++m) {
-            const int2 ch = pupil_chord(gd.md[s][m], fx);
+            const ModeDev &md = gd.md[s][m];
+            const int2 ch = md.op == kOpPupil ? pupil_chord(md, fx)
+                                              : make_int2(-geo.H / 2, geo.H / 2 - 1);
             w.chord[((size_t)s * gd.K + m) * geo.W + kx] = ch;
             act = act || ch.x <= ch.y;
         }

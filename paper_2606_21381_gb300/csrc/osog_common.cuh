@@ -93,7 +93,19 @@ struct ModeDev {
     float scale;          // 1 / (H W)
     int32_t dic;          // 1 for the DIC factor
     float dsx1, dsy1;     // d(dsx, dsy) / d(shear_px): dx (cos, sin)(shear_angle) / 2
+    int32_t op;           // kOpPupil, kOpAllPass, kOpTable or kOpSpectrum
+    float2 *tab;          // kOpTable: multiplier table; kOpSpectrum: output
+                          // (both column-blocked [W/B][H][B] like Q)
 };
+
+// What the column pass does with one (scene, modality):
+//   kOpPupil     multiply by the transfer function inside the pupil chord
+//   kOpAllPass   the same transfer function (without the pupil circle) on
+//                every frequency
+//   kOpTable     multiply every frequency by tab / tab[0] (real DC term)
+//   kOpSpectrum  write the forward column spectrum times scale to tab (no
+//                inverse transform, Q untouched)
+enum { kOpPupil = 0, kOpAllPass = 1, kOpTable = 2, kOpSpectrum = 3 };
 
 struct GroupDev {
     int32_t S;

@@ -6,7 +6,9 @@
 namespace osog {
 
 // Stage selector of the forward strip kernel.
-enum StripMode { kStripRender = 0, kStripOpdOnly = 1, kStripFromMap = 2 };
+// kStripFromReal: the strip's field is a real image [H][W] (float, read
+// from opd_att), used as (value, 0) without an exit-wave step.
+enum StripMode { kStripRender = 0, kStripOpdOnly = 1, kStripFromMap = 2, kStripFromReal = 3 };
 
 struct StripArgs {
     Geometry geo;
@@ -23,6 +25,7 @@ struct ColumnArgs {
     Work w;
     const float2 *tw;        // H-point twiddles
     int32_t S, K;
+    int32_t unit_input;      // 1: the column spectrum is 1 everywhere (no G read, no DFT)
     ModeDev md[kMaxScenes][kMaxModes];
 };
 
@@ -32,6 +35,7 @@ struct InverseArgs {
     const float2 *tw;        // W-point twiddles
     float *images;           // [S][K][H][W]
     int32_t S, K;
+    int32_t real_out;        // 1: write Re(E) instead of |E|^2
 };
 
 // The three render stages of a launch group in one persistent launch

@@ -37,7 +37,20 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
     const int R = SQ ? sq_rb(N) : geo.R;
     const int y0 = strip * R;
     const int RN = R * N;  // <= kSetElems; lines R..L-1 are never read back
-    if constexpr (MODE == kStripFromMap) {
+    if constexpr (MODE == kStripFromReal) {
+        const float *src = reinterpret_cast<const float *>(a.opd_att) + (size_t)y0 * N;
+        float v[kEPT];
+#pragma unroll
+        for (int i = 0; i < kEPT; ++i) {
+            const int e = threadIdx.x + i * kThreads;
+            if (e < RN) v[i] = src[e];
+        }
+#pragma unroll
+        for (int i = 0; i < kEPT; ++i) {
+            const int e = threadIdx.x + i * kThreads;
+            if (e < RN) buf[(e / N) * LS + pad16(e % N)] = make_float2(v[i], 0.f);
+        }
+    } else if constexpr (MODE == kStripFromMap) {
         const float2 *src = a.opd_att + (size_t)y0 * N;
         float2 v[kEPT];
 #pragma unroll
@@ -70,7 +83,7 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
 #pragma unroll
         for (int i = 0; i < kEPT; ++i) {
             const int e = threadIdx.x + i * kThreads;
-            if (e < RN) {
+            if (MODE != kStripFromReal && e < RN) {
                 float2 *v = buf + (e / N) * LS + pad16(e % N);
                 const float2 oa = *v;
                 if (oa.x != 0.f || oa.y != 0.f) {  // empty pixels keep E = 1
@@ -129,7 +142,13 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
     if (!lo_part && !hi_part) return;
     const float2 *G = a.w.G + ((size_t)s * geo.nblocks + bk) * N * B;
     const int NB_ = N * B;  // <= kSetElems; lines B..L-1 are never read back
-    {
+    if (a.unit_input) {  // the spectrum of a unit impulse: 1 at every frequency
+#pragma unroll
+        for (int i = 0; i < kEPT; ++i) {
+            const int e = threadIdx.x + i * kThreads;
+            if (e < NB_) buf0[(e & (B - 1)) * LS + pad16(e >> lb)] = make_float2(1.f, 0.f);
+        }
+    } else {
         float2 v[kEPT];
 #pragma unroll
         for (int i = 0; i < kEPT; ++i) {
@@ -148,9 +167,23 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
         chords[m * L + c] = a.w.chord[((size_t)s * K + m) * W + bk * B + c];
     }
     __syncthreads();
-    fft_lines<N, L, false>(buf0, a.tw);
+    if (!a.unit_input) fft_lines<N, L, false>(buf0, a.tw);
     for (int m = 0; m < K; ++m) {
         const ModeDev &md = a.md[s][m];
+        if (md.op == kOpSpectrum) {  // the forward spectrum itself, to md.tab
+            float2 *T = md.tab + (size_t)bk * N * B;
+#pragma unroll
+            for (int i = 0; i < kEPT; ++i) {
+                const int e = threadIdx.x + i * kThreads;
+                if (e < NB_) {
+                    const float2 v = buf0[(e & (B - 1)) * LS + pad16(e >> lb)];
+                    T[e] = make_float2(v.x * md.scale, v.y * md.scale);
+                }
+            }
+            continue;  // buf0 is only read: the next modality may still use it
+        }
+        const float2 *T = md.op == kOpTable ? md.tab + (size_t)bk * N * B : nullptr;
+        const float tnorm = md.op == kOpTable ? md.scale / md.tab[0].x : 0.f;
 #pragma unroll 4
         for (int i = 0; i < kEPT; ++i) {
             const int e = threadIdx.x + i * kThreads;  // line-major: consecutive y
@@ -161,8 +194,12 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
                 const int fy = y < N / 2 ? y : y - N;
                 const int2 ch = chords[m * L + c];
                 float2 v = make_float2(0.f, 0.f);
-                if (fy >= ch.x && fy <= ch.y)
+                if (T) {
+                    const float2 t = T[y * B + c];
+                    v = cmul(buf0[c * LS + pad16(y)], make_float2(t.x * tnorm, t.y * tnorm));
+                } else if (fy >= ch.x && fy <= ch.y) {
                     v = cmul(buf0[c * LS + pad16(y)], transfer(md, fx, fy));
+                }
                 buf1[c * LS + pad16(y)] = v;
             }
         }
@@ -225,7 +262,7 @@ __device__ __forceinline__ void inverse_item(const InverseArgs &a, int sm, int s
         const int e = threadIdx.x + i * kThreads;
         if (e < RN) {
             const float2 v = buf[(e / N) * LS + pad16(e % N)];
-            img[e] = fmaf(v.x, v.x, v.y * v.y);
+            img[e] = a.real_out ? v.x : fmaf(v.x, v.x, v.y * v.y);
         }
     }
 }
@@ -360,6 +397,8 @@ struct StripFwdLaunch {
             k_strip_forward<N, kStripRender, false><<<grid, kThreads, smem, st>>>(a);
         else if (mode == kStripOpdOnly)
             k_strip_forward<N, kStripOpdOnly, false><<<grid, kThreads, smem, st>>>(a);
+        else if (mode == kStripFromReal)
+            k_strip_forward<N, kStripFromReal, false><<<grid, kThreads, smem, st>>>(a);
         else
             k_strip_forward<N, kStripFromMap, false><<<grid, kThreads, smem, st>>>(a);
         return cudaGetLastError();
@@ -375,6 +414,9 @@ struct StripFwdLaunch {
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_strip_forward<N, kStripFromMap, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_strip_forward<N, kStripFromReal, false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         return e;
     }

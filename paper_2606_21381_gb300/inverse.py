@@ -69,12 +69,17 @@ def filtered(img: torch.Tensor, mask: torch.Tensor) -> torch.Tensor:
     return torch.fft.irfft2(torch.fft.rfft2(img) * mask, s=img.shape[-2:])
 
 
-def spectral_loss(img: torch.Tensor, target: torch.Tensor, eps: float = 1e-6) -> torch.Tensor:
+def spectral_loss(img: torch.Tensor, target: torch.Tensor, eps_rel: float = 1e-6) -> torch.Tensor:
     """Eq. 8: squared difference of the log amplitude spectra of the images
-    (mean over the (K, H, W) frequencies; eps guards log 0).  Invariant to
+    (mean over the (K, H, W) frequencies).  The guard eps added inside the
+    logarithms is eps_rel times the largest target amplitude of each
+    modality, so frequencies where both spectra are only rounding noise
+    (beyond the band the pupil passes) do not dominate.  Invariant to
     circular shifts of either image."""
+    fb = torch.abs(torch.fft.fft2(target)).detach()
+    eps = eps_rel * fb.amax(dim=(-2, -1), keepdim=True)
     a = torch.log(torch.abs(torch.fft.fft2(img)) + eps)
-    b = torch.log(torch.abs(torch.fft.fft2(target)) + eps)
+    b = torch.log(fb + eps)
     return ((a - b) ** 2).mean()
 
 

@@ -88,6 +88,22 @@ class Renderer:
               "osog_render")
         return out
 
+    def render_dic_incoherent(self, soa: torch.Tensor, n: int | None, optics: dict, out=None,
+                              stream=None):
+        """osog_render_dic_incoherent: (H, W) DIC image in the literal
+        reading of Eq. 5 (sheared exit wave, intensity blurred by |h|^2)."""
+        self._check_soa(soa)
+        n = soa.shape[1] if n is None else int(n)
+        if out is None:
+            out = torch.empty((self.H, self.W), dtype=torch.float32, device=self.device)
+        ws = self.workspace(self._L.osog_dic_incoherent_workspace_size(self.plan, n))
+        o = optics_struct(optics)
+        check(self._L.osog_render_dic_incoherent(self.plan, _ptr(soa), soa.shape[1], n,
+                                                 ctypes.byref(o), _ptr(out), _ptr(ws),
+                                                 ws.numel(), _stream(stream)),
+              "osog_render_dic_incoherent")
+        return out
+
     def render_polyhedra(self, soa: torch.Tensor, n: int | None, planes: torch.Tensor,
                          plane_offsets: torch.Tensor, optics: dict, out=None, stream=None):
         """osog_render_polyhedra: one scene with general polyhedra (kind 2)

@@ -1,0 +1,48 @@
+"""The literal (incoherent) reading of Eq. 5 through
+osog_render_dic_incoherent against the FP64 oracle: square and non-square
+canvases, defocus, an all-pass pupil, and the empty field."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_21381_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-4  # of the empty-field background 4 sin^2(theta)
+
+
+def _case(H, W, n, seed, **kw):
+    rng = np.random.default_rng(seed)
+    soa = scenes.draw_particles(rng, n, H, W, mu=(0.0, 0.02))
+    o = scenes.optics(H, W, **dict(dict(modes=scenes.MODE_DIC, NA=0.5, shear_px=1.0), **kw))
+    return soa, o
+
+
+@pytest.mark.parametrize("H,W,n,kw", [
+    (256, 256, 64, dict(defocus=0.7)),
+    (128, 256, 40, dict(defocus=-1.2, shear_angle=0.3, bias_phase=1.1)),
+    (256, 256, 64, dict(NA=0.8, defocus=0.0, shear_px=2.0, shear_angle=0.0)),
+])
+def test_matches_the_oracle(H, W, n, kw):
+    from paper_2606_21381_gb300.render import Renderer
+    soa, o = _case(H, W, n, 31 + H + n, **kw)
+    want = oracle.render_dic_incoherent(soa, n, o)
+    r = Renderer(H, W)
+    got = r.render_dic_incoherent(torch.from_numpy(soa).cuda(), None, o).cpu().numpy()
+    assert r.sync_status() == 0
+    bg = 4 * math.sin(o["bias_phase"]) ** 2
+    assert np.abs(want - bg).max() > 0.05 * bg  # contrast
+    assert np.abs(got - want).max() <= TOL * bg
+
+
+def test_empty_field_is_the_bias_background():
+    from paper_2606_21381_gb300.render import Renderer
+    r = Renderer(128, 128)
+    o = scenes.optics(128, 128, modes=scenes.MODE_DIC, NA=0.45, defocus=1.0)
+    img = r.render_dic_incoherent(torch.zeros((9, 1), device="cuda"), 0, o).cpu().numpy()
+    assert r.sync_status() == 0
+    np.testing.assert_allclose(img, 4 * math.sin(o["bias_phase"]) ** 2, rtol=0, atol=1e-5)

@@ -43,7 +43,11 @@ def test_solve_with_the_spectral_loss_term():
     r = Renderer(512, 512)
     target = r.render(torch.from_numpy(soa).cuda(), None, o)
     s0, o0 = inverse.perturb(soa, o, np.random.default_rng(8))
-    res = inverse.solve(target, s0, o0, r, inverse.SolveConfig(steps=300, spectral_weight=1e-3))
+    res = inverse.solve(target, s0, o0, r, inverse.SolveConfig(steps=300, spectral_weight=1e-5))
     e = inverse.errors(res.soa, soa, res.optics_params, o)
     assert e["dn_rel_median"] < 0.01 and e["T_rel_median"] < 0.01
     assert res.losses[-1] < 1e-2 * res.losses[0]
+    x0 = torch.from_numpy(s0).cuda()
+    x1 = torch.from_numpy(res.soa).cuda()
+    assert float(inverse.spectral_loss(r.render(x1, None, o), target)) < \
+        0.1 * float(inverse.spectral_loss(r.render(x0, None, o0), target))
