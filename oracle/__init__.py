@@ -84,6 +84,14 @@ def _load():
         lib.orc_transfer.argtypes = [ctypes.POINTER(_Optics), i32, d, d]
         lib.orc_images.argtypes = [ctypes.POINTER(_Optics), d, d, d]
         lib.orc_render.argtypes = [d, i64, i32, ctypes.POINTER(_Optics), d, d, d, d, d]
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        lib.orc_philox4x32.argtypes = [u32p, u32p, u32p]
+        lib.orc_poisson.argtypes = [ctypes.c_double, ctypes.c_uint64, i64]
+        lib.orc_poisson.restype = i64
+        lib.orc_normal.argtypes = [ctypes.c_uint64, i64]
+        lib.orc_normal.restype = ctypes.c_double
+        lib.orc_sensor_noise.argtypes = [ctypes.POINTER(ctypes.c_float), i64, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_uint64, d]
         lib.orc_dic_incoherent.argtypes = [ctypes.POINTER(_Optics), d, d, d]
         lib.orc_opd_att_poly.argtypes = [d, i64, i32, i32, i32, ctypes.c_double,
                                          ctypes.c_double, i32, d, d, d, d]
@@ -255,6 +263,33 @@ def render_dic_incoherent(soa: np.ndarray, n: int, o: dict) -> np.ndarray:
     dic_incoherent."""
     opd, att = opd_att(soa, n, o["H"], o["W"], o["dx"], o["bevel_slope"])
     return dic_incoherent(o, field(opd, att, o["lambda_um"]))
+
+
+def philox4x32(ctr, key) -> tuple:
+    """Philox4x32-10 of a 4-word counter and 2-word key."""
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    _load().orc_philox4x32(c, k, o)
+    return tuple(o)
+
+
+def poisson(lam: float, seed: int, index: int) -> int:
+    """The Poisson sample of element `index` (see orc_poisson)."""
+    return int(_load().orc_poisson(float(lam), int(seed), int(index)))
+
+
+def normal(seed: int, index: int) -> float:
+    return float(_load().orc_normal(int(seed), int(index)))
+
+
+def sensor_noise(img: np.ndarray, photons: float, read_sigma: float, seed: int) -> np.ndarray:
+    """(Poisson(g max(I, 0)) + sigma N(0, 1)) / g per element, float64."""
+    x = np.ascontiguousarray(img, dtype=np.float32)
+    out = np.empty(x.shape)
+    _load().orc_sensor_noise(x.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), x.size,
+                             float(photons), float(read_sigma), int(seed), _p(out))
+    return out
 
 
 def render(soa: np.ndarray, n: int, o: dict, planes=None, plane_off=None) -> dict:

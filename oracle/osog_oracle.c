@@ -755,3 +755,112 @@ void orc_render_grad(const float *soa, int64_t ld, int n, const orc_optics *o,
     free(opd); free(att); free(er); free(ei); free(fr); free(fi);
     free(zr); free(zi); free(gr); free(gi); free(hr); free(hi);
 }
+
+/* ------------------------------------------------------------------ */
+/* Sensor noise (Sec. III.C: Poisson shot plus Gaussian read noise)    */
+/* ------------------------------------------------------------------ */
+
+/* Philox4x32-10, the counter-based generator of Salmon, Moraes, Dror and
+ * Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC 2011): ten rounds
+ * of two 32x32->64-bit multiplications on a 4-word counter with a 2-word
+ * key bumped by the Weyl constants between rounds. */
+void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform in (0, 1) from 32 random bits. */
+static double unit_open(uint32_t x) { return ((double)x + 0.5) * (1.0 / 4294967296.0); }
+
+/* The uniforms of element i, round r (four per round). */
+static void noise_round(uint64_t seed, int64_t i, uint32_t r, double u[4])
+{
+    uint32_t ctr[4] = {(uint32_t)(uint64_t)i, (uint32_t)((uint64_t)i >> 32), r, 0x6E6F6973u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t o[4];
+    orc_philox4x32(ctr, key, o);
+    for (int k = 0; k < 4; ++k) u[k] = unit_open(o[k]);
+}
+
+#define ORC_NOISE_ROUNDS 64
+
+/* Poisson(lam) sample of element i: round 0 holds (u0, u1) for the normal
+ * deviate and (u2, u3) for the first Poisson attempt, rounds 1.. two more
+ * attempts each.
+ *   lam < 10:  inversion by sequential search with u2 (pmf recursion
+ *              p_k = p_{k-1} lam / k from p_0 = exp(-lam));
+ *   lam >= 10: Hormann's transformed rejection with squeeze (PTRS; W.
+ *              Hormann, "The transformed rejection method for generating
+ *              Poisson random variables", Insurance: Mathematics and
+ *              Economics 12, 1993), attempts from (u2, u3), (u4, u5), ...
+ * If every attempt of ORC_NOISE_ROUNDS rounds is rejected the sample is
+ * floor(lam). */
+int64_t orc_poisson(double lam, uint64_t seed, int64_t i)
+{
+    double u[4];
+    noise_round(seed, i, 0, u);
+    if (!(lam > 0.0)) return 0;
+    if (lam < 10.0) {
+        double p = exp(-lam), F = p;
+        int64_t k = 0;
+        while (u[2] > F && k < 1000) {
+            ++k;
+            p *= lam / (double)k;
+            F += p;
+        }
+        return k;
+    }
+    const double slam = sqrt(lam), loglam = log(lam);
+    const double b = 0.931 + 2.53 * slam;
+    const double a = -0.059 + 0.02483 * b;
+    const double invalpha = 1.1239 + 1.1328 / (b - 3.4);
+    const double vr = 0.9277 - 3.6224 / (b - 2.0);
+    for (uint32_t r = 0; r < ORC_NOISE_ROUNDS; ++r) {
+        if (r > 0) noise_round(seed, i, r, u);
+        for (int h = (r == 0 ? 1 : 0); h < 2; ++h) {
+            const double U = u[2 * h] - 0.5, V = u[2 * h + 1];
+            const double us = 0.5 - fabs(U);
+            const double k = floor((2.0 * a / us + b) * U + lam + 0.43);
+            if (us >= 0.07 && V <= vr) return (int64_t)k;
+            if (k < 0.0 || (us < 0.013 && V > us)) continue;
+            if (log(V * invalpha / (a / (us * us) + b)) <= -lam + k * loglam - lgamma(k + 1.0))
+                return (int64_t)k;
+        }
+    }
+    return (int64_t)floor(lam);
+}
+
+/* Standard normal deviate of element i by the Box-Muller transform of
+ * round 0's (u0, u1). */
+double orc_normal(uint64_t seed, int64_t i)
+{
+    double u[4];
+    noise_round(seed, i, 0, u);
+    return sqrt(-2.0 * log(u[0])) * cos(2.0 * M_PI * u[1]);
+}
+
+/* Noisy image: out_i = (Poisson(g max(I_i, 0)) + sigma Z_i) / g, with g the
+ * photo-electrons per unit intensity and sigma the read noise (electrons),
+ * so that the noiseless mean is I. */
+void orc_sensor_noise(const float *img, int64_t count, double g, double sigma,
+                      uint64_t seed, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < count; ++i) {
+        double lam = g * (img[i] > 0.0f ? (double)img[i] : 0.0);
+        out[i] = ((double)orc_poisson(lam, seed, i) + sigma * orc_normal(seed, i)) / g;
+    }
+}
