@@ -214,6 +214,22 @@ int osog_render_dic_incoherent(osog_plan_t *plan, const float *soa, int64_t ld, 
                                size_t ws_bytes, osog_stream_t stream);
 
 /*
+ * Sensor noise (Sec. III.C: Poisson photon shot noise plus Gaussian read
+ * noise, N ~ P(lambda) + G(0, sigma^2)) applied to `count` intensities:
+ *   out[i] = (Poisson(g max(image[i], 0)) + read_sigma Z_i) / g,
+ * g = photons_per_unit (photo-electrons per unit intensity, 0 < g <= 1e12),
+ * read_sigma >= 0 in electrons, Z_i standard normal; the noiseless mean is
+ * the input.  Random numbers: Philox4x32-10 keyed by `seed`, counter (i,
+ * round, tag), so each element's draw depends only on (seed, i) and not on
+ * the launch; Poisson by inversion below rate 10 and by transformed
+ * rejection (PTRS) above, decided in double precision.  image and out are
+ * device float32 arrays (may be the same).  Returns OSOG_ERR_INVALID_ARG for
+ * bad arguments.
+ */
+int osog_sensor_noise(const float *image, int64_t count, double photons_per_unit,
+                      double read_sigma, uint64_t seed, float *out, osog_stream_t stream);
+
+/*
  * Stage entry: rasterise only.  Writes the OPD and ATT maps of Eq. 2 as a
  * device float32 [H][W][2] array (opd, att per pixel), in the same order of
  * summation as osog_render.  Workspace as for osog_render with K = 1.

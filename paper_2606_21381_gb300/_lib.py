@@ -26,7 +26,8 @@ EXPORTS = ("osog_plan_create", "osog_plan_destroy", "osog_workspace_size", "osog
            "osog_profile_begin", "osog_profile_end", "osog_render_noalloc",
            "osog_backward_workspace_size", "osog_render_backward", "osog_autotune",
            "osog_polyhedra_workspace_size", "osog_render_polyhedra",
-           "osog_dic_incoherent_workspace_size", "osog_render_dic_incoherent")
+           "osog_dic_incoherent_workspace_size", "osog_render_dic_incoherent",
+           "osog_sensor_noise")
 
 
 class OsogError(RuntimeError):
@@ -134,6 +135,9 @@ def lib(build_if_missing: bool = True):
     L.osog_dic_incoherent_workspace_size.restype = sz
     L.osog_render_dic_incoherent.argtypes = [vp, vp, i64, i32, P(Optics), vp, vp, sz, vp]
     L.osog_render_dic_incoherent.restype = ctypes.c_int
+    L.osog_sensor_noise.argtypes = [vp, i64, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                    vp, vp]
+    L.osog_sensor_noise.restype = ctypes.c_int
     L.osog_conv_out_h.argtypes = [P(ConvShape)]
     L.osog_conv_out_h.restype = i32
     L.osog_conv_out_w.argtypes = [P(ConvShape)]

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libosog.so")
 SOURCES = ("osog_api.cu", "osog_bin.cu", "osog_render.cu", "osog_backward.cu",
-           "osog_noalloc.cu", "osog_cnn.cu")
+           "osog_noalloc.cu", "osog_cnn.cu", "osog_noise.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
          "--expt-relaxed-constexpr"]
