@@ -179,10 +179,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_strip(const __grid_constant
         if (e < RN) {
             const int idx = (e / N) * LS + pad16(e % N);
             const float2 oa = bufO[idx], g = bufG[idx];
-            float sn, cs;
-            sincospif(oa.x * tol, &sn, &cs);
-            const float amp = expf(-oa.y);
-            const float ex = amp * cs, ey = amp * sn;
+            const float2 E = exit_wave(oa.x, oa.y, tol);
+            const float ex = E.x, ey = E.y;
             bufO[idx] = make_float2(k2pi * fmaf(g.y, ex, -g.x * ey), -fmaf(g.x, ex, g.y * ey));
         }
     }

@@ -87,10 +87,7 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
                 float2 *v = buf + (e / N) * LS + pad16(e % N);
                 const float2 oa = *v;
                 if (oa.x != 0.f || oa.y != 0.f) {  // empty pixels keep E = 1
-                    float sn, cs;
-                    sincospif(oa.x * tol, &sn, &cs);
-                    const float amp = expf(-oa.y);
-                    *v = make_float2(amp * cs, amp * sn);
+                    *v = exit_wave(oa.x, oa.y, tol);
                 } else {
                     *v = make_float2(1.f, 0.f);
                 }

@@ -204,6 +204,28 @@ __device__ void raster_strip(const Geometry &geo, const Work &w, const SceneDev 
 // loads in flight at once.
 constexpr int kEPT = kSetElems / kThreads;
 
+// ------------------------------------------------------------ fast phases
+// sin and cos of x with the hardware approximations: x is first reduced to
+// [-pi, pi] (x - 2 pi rint(x / 2 pi)), where __sincosf's absolute error is a
+// few 1e-7; each turn removed adds at most 1.8e-7 (2 pi rounded to float).
+// The transfer-function phases stay within a few turns.
+__device__ __forceinline__ void phase_sincos(float x, float *s, float *c) {
+    const float r = fmaf(-6.28318530717958648f, rintf(x * 0.159154943091895336f), x);
+    __sincosf(r, s, c);
+}
+
+// Exit wave (Eq. 2 with the Beer-Lambert amplitude of Eq. 4):
+// exp(-att) (cos, sin)(pi opd two_over_lambda), the phase reduced exactly
+// in half-turns (x - 2 rint(x / 2)) before the hardware sin / cos.
+__device__ __forceinline__ float2 exit_wave(float opd, float att, float two_over_lambda) {
+    const float x = opd * two_over_lambda;
+    const float r = fmaf(-2.f, rintf(0.5f * x), x);
+    float s, c;
+    __sincosf(3.14159265358979323846f * r, &s, &c);
+    const float a = __expf(-att);
+    return make_float2(a * c, a * s);
+}
+
 // ------------------------------------------------------------ optical head
 // Transfer function at signed frequency (fx, fy) inside the pupil chord,
 // including 1/(HW):
@@ -215,12 +237,14 @@ __device__ __forceinline__ float2 transfer(const ModeDev &md, int fx, int fy) {
     const float kx = (float)fx * md.kstep_x, ky = (float)fy * md.kstep_y;
     const float qx = kx + md.qoff_x, qy = ky + md.qoff_y;
     const float q2 = fmaf(qx, qx, qy * qy);
-    const float chi = -md.dz * q2 / (sqrtf(fmaxf(fmaf(md.k0, md.k0, -q2), 0.f)) + md.k0);
+    const float chi = __fdividef(-md.dz * q2, sqrtf(fmaxf(fmaf(md.k0, md.k0, -q2), 0.f)) + md.k0);
     float sn, cs;
-    sincosf(chi, &sn, &cs);
+    phase_sincos(chi, &sn, &cs);
     float2 h = make_float2(cs, sn);
     if (md.dic) {
-        const float g = 2.f * sinf(fmaf(kx, md.dsx, fmaf(ky, md.dsy, md.bias)));
+        float sa, ca;
+        phase_sincos(fmaf(kx, md.dsx, fmaf(ky, md.dsy, md.bias)), &sa, &ca);
+        const float g = 2.f * sa;
         h = make_float2(-sn * g, cs * g);
     }
     return make_float2(h.x * md.scale, h.y * md.scale);
@@ -322,9 +346,9 @@ __device__ __forceinline__ void transfer_grad(const ModeDev &md, int fx, int fy,
     const float kx = (float)fx * md.kstep_x, ky = (float)fy * md.kstep_y;
     const float qx = kx + md.qoff_x, qy = ky + md.qoff_y;
     const float q2 = fmaf(qx, qx, qy * qy);
-    const float kappa = -q2 / (sqrtf(fmaxf(fmaf(md.k0, md.k0, -q2), 0.f)) + md.k0);
+    const float kappa = __fdividef(-q2, sqrtf(fmaxf(fmaf(md.k0, md.k0, -q2), 0.f)) + md.k0);
     float sn, cs;
-    sincosf(md.dz * kappa, &sn, &cs);
+    phase_sincos(md.dz * kappa, &sn, &cs);
     const float sc = md.scale;
     if (!md.dic) {
         h = make_float2(cs * sc, sn * sc);
@@ -333,7 +357,7 @@ __device__ __forceinline__ void transfer_grad(const ModeDev &md, int fx, int fy,
         return;
     }
     float sa, ca;
-    sincosf(fmaf(kx, md.dsx, fmaf(ky, md.dsy, md.bias)), &sa, &ca);
+    phase_sincos(fmaf(kx, md.dsx, fmaf(ky, md.dsy, md.bias)), &sa, &ca);
     const float g = 2.f * sa, gp = 2.f * ca;
     h = make_float2(-sn * g * sc, cs * g * sc);
     dh[0] = make_float2(-cs * kappa * g * sc, -sn * kappa * g * sc);
