@@ -143,13 +143,18 @@ def ncu_traffic(kernel: str):
     return None
 
 
+RENDER_SOURCES = ("osog_api.cu", "osog_bin.cu", "osog_render.cu", "osog_common.cuh",
+                  "osog_fft.cuh", "osog_strip.cuh", "osog_kernels.h")
+
+
 def source_digest() -> str:
+    """Hash of the sources the render kernels and their launches are built
+    from (the convolution and noise kernels do not enter)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2606_21381_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in RENDER_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:12]
 
 
