@@ -257,3 +257,66 @@ class Renderer:
         cnt = (ctypes.c_int32 * nk)()
         check(self._L.osog_profile_end(self.plan, _stream(stream), ms, cnt), "osog_profile_end")
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(_lib.KERNEL_CLASSES)}
+
+
+class HostBatchPipeline:
+    """Batches given in pinned host memory rendered into pinned host images,
+    with each batch's copies overlapping the renders of its neighbours: two
+    device slots, one stream for the renders, one for host-to-device copies
+    and `out_streams` streams that copy parts of each image batch back in
+    parallel (several copy engines), ordered by events.  submit() returns
+    the events that mark the batch's images as copied to the host."""
+
+    def __init__(self, renderer: Renderer, n_max: int, S: int, K: int, slots: int = 2,
+                 out_streams: int = 4):
+        dev = renderer.device
+        self.r = renderer
+        self.slots = slots
+        self.render_stream = torch.cuda.Stream(dev)
+        self.in_stream = torch.cuda.Stream(dev)
+        self.out_streams = [torch.cuda.Stream(dev) for _ in range(max(1, min(out_streams, S)))]
+        self.soa = [torch.empty((9, n_max), dtype=torch.float32, device=dev) for _ in range(slots)]
+        self.out = [torch.empty((S, K, renderer.H, renderer.W), dtype=torch.float32, device=dev)
+                    for _ in range(slots)]
+        self.rendered = [None] * slots
+        self.copied = [None] * slots
+        self.count = 0
+
+    def submit(self, soa_host: torch.Tensor, offsets, optics_list: list[dict],
+               image_host: torch.Tensor, tuning: dict | None = None):
+        k = self.count % self.slots
+        self.count += 1
+        n = soa_host.shape[1]
+        if n > self.soa[k].shape[1]:
+            raise ValueError("more particles than the pipeline was built for")
+        if self.rendered[k] is not None:  # the slot's previous render has read soa[k]
+            self.in_stream.wait_event(self.rendered[k])
+        with torch.cuda.stream(self.in_stream):
+            self.soa[k][:, :n].copy_(soa_host, non_blocking=True)
+        loaded = torch.cuda.Event()
+        loaded.record(self.in_stream)
+        self.render_stream.wait_event(loaded)
+        for ev in self.copied[k] or ():  # out[k] has reached the host
+            self.render_stream.wait_event(ev)
+        self.r.batch(self.soa[k], offsets, optics_list, out=self.out[k], tuning=tuning,
+                     stream=self.render_stream)
+        done = torch.cuda.Event()
+        done.record(self.render_stream)
+        self.rendered[k] = done
+        S = self.out[k].shape[0]
+        c = len(self.out_streams)
+        copied = []
+        for j, st in enumerate(self.out_streams):
+            a, b = j * S // c, (j + 1) * S // c
+            st.wait_event(done)
+            with torch.cuda.stream(st):
+                image_host[a:b].copy_(self.out[k][a:b], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(st)
+            copied.append(ev)
+        self.copied[k] = copied
+        return copied
+
+    def synchronize(self) -> None:
+        for s in (self.in_stream, self.render_stream, *self.out_streams):
+            s.synchronize()

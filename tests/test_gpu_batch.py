@@ -74,3 +74,29 @@ def test_autotuner_choice_is_used_and_exact():
     tuned = r.batch(dev, offs, optics).clone()   # picks the stored choice
     assert r.sync_status() == 0                  # the exact reservation does not overflow
     assert torch.equal(base, tuned)
+
+
+def test_host_pipeline_matches_batch():
+    # three batches through the two-slot pipeline (slot reuse included)
+    # equal the same batches rendered one at a time
+    from paper_2606_21381_gb300.render import HostBatchPipeline, Renderer
+    r = Renderer(256, 256)
+    rng = np.random.default_rng(41)
+    batches = []
+    for b in range(3):
+        soas = [scenes.draw_particles(rng, int(c), 256, 256, mu=(0.0, 0.02)) for c in (50, 120, 7)]
+        optics = [scenes.optics(256, 256, modes=scenes.MODE_BF | scenes.MODE_OBLIQUE,
+                                defocus=0.3 * b + 0.1 * s) for s in range(3)]
+        soa_all, offs = scenes.concat(soas)
+        batches.append((soa_all, offs, optics))
+    pipe = HostBatchPipeline(r, 200, 3, 2)
+    outs = []
+    for soa_all, offs, optics in batches:
+        h = torch.empty((3, 2, 256, 256)).pin_memory()
+        pipe.submit(torch.from_numpy(soa_all).pin_memory(), offs, optics, h)
+        outs.append(h)
+    pipe.synchronize()
+    assert r.sync_status() == 0
+    for (soa_all, offs, optics), h in zip(batches, outs):
+        want = r.batch(torch.from_numpy(soa_all).cuda(), offs, optics).cpu()
+        assert torch.equal(h, want)
