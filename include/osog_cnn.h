@@ -7,8 +7,8 @@
  *
  * Layouts (all device memory owned by the caller):
  *   activations  bf16 NHWC [N][H][W][C], C a multiple of 8
- *   filters      bf16 [K][R][S][C] (K output channels, R x S window),
- *                K a multiple of 8
+ *   filters      bf16 [K][R][S][C] (K output channels, R x S window,
+ *                R, S <= 8), K a multiple of 8
  *   bias         fp32 [K]
  *   gradients    d(activations) bf16 NHWC; d(filters) and d(bias) fp32
  * Convolutions are cross-correlations with zero padding `pad` and stride

@@ -24,7 +24,10 @@ constexpr int BM = 64, BN = 64, BK = 32, LDS = BK + 8;  // smem row: 40 bf16 = 8
 constexpr int NT = 128;
 constexpr int kSplitPixels = 2048;  // pixels per CTA in the filter-gradient reduction
 
-enum Pass { kFwd = 0, kDgrad = 1, kWgrad = 2 };
+// kDgrad2: the data gradient of a stride-2 convolution for the input
+// pixels of one parity class (h mod 2, w mod 2), reduced over the taps that
+// reach them only (the other taps of that class are zero).
+enum Pass { kFwd = 0, kDgrad = 1, kWgrad = 2, kDgrad2 = 3 };
 
 struct Geo {
     int N, H, W, C, K, R, S, stride, pad, P, Q;
@@ -41,6 +44,9 @@ struct Args {
     float *part;                // wgrad partial tiles [splits][M][N]
     int relu;
     int M, Ncols, Kred;         // GEMM sizes
+    // kDgrad2: parity class, its pixel grid and its taps
+    int ph, pw, Hc, Wc, nr, ns;
+    int rtap[4], stap[4];
 };
 
 __device__ __forceinline__ uint4 zero4() { return make_uint4(0u, 0u, 0u, 0u); }
@@ -52,6 +58,13 @@ __device__ __forceinline__ unsigned smem_u32(const void *p) {
 __device__ __forceinline__ void ldsm_x4(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3,
                                         const void *p) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3,
+                                          const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
                  : "r"(smem_u32(p)));
 }
@@ -92,6 +105,31 @@ __device__ __forceinline__ uint4 dgrad_a(const Args &a, int m, int j) {
     return *reinterpret_cast<const uint4 *>(a.x + (((size_t)n * g.P + p) * g.Q + q) * g.K + k);
 }
 
+// Stride-2 data gradient, parity class (ph, pw): class pixel m = (n, i, j)
+// is input pixel (n, 2 i + ph, 2 j + pw); reduction entry (tap, k) with tap
+// = (ri, si) reads dY at ((h + pad - r) / 2, (w + pad - s) / 2), which the
+// class's taps make exact.
+__device__ __forceinline__ uint4 dgrad2_a(const Args &a, int m, int j) {
+    const Geo &g = a.g;
+    if (m >= a.M || j >= a.Kred) return zero4();
+    const int wi = m % a.Wc, t = m / a.Wc, hi = t % a.Hc, n = t / a.Hc;
+    const int tap = j / g.K, k = j - tap * g.K, ri = tap / a.ns, si = tap - ri * a.ns;
+    const int p = (2 * hi + a.ph + g.pad - a.rtap[ri]) >> 1;
+    const int q = (2 * wi + a.pw + g.pad - a.stap[si]) >> 1;
+    if (p < 0 || q < 0 || p >= g.P || q >= g.Q) return zero4();
+    return *reinterpret_cast<const uint4 *>(a.x + (((size_t)n * g.P + p) * g.Q + q) * g.K + k);
+}
+
+// Filters reordered [C][R][S][K], row c, reduction entry (tap, k) of the
+// class's taps.
+__device__ __forceinline__ uint4 dgrad2_b(const Args &a, int c, int j) {
+    const Geo &g = a.g;
+    if (c >= a.Ncols || j >= a.Kred) return zero4();
+    const int tap = j / g.K, k = j - tap * g.K, ri = tap / a.ns, si = tap - ri * a.ns;
+    const int rs = a.rtap[ri] * g.S + a.stap[si];
+    return *reinterpret_cast<const uint4 *>(a.w + ((size_t)c * g.R * g.S + rs) * g.K + k);
+}
+
 // Row-major operand rows (8 consecutive reduction entries of row r).
 __device__ __forceinline__ uint4 rows_b(const __nv_bfloat16 *base, int rows, int ld, int r, int j) {
     if (r >= rows || j >= ld) return zero4();
@@ -116,10 +154,23 @@ __device__ __forceinline__ uint4 wgrad_b(const Args &a, int j, int pix) {
 }
 
 // ---------------------------------------------------------------- GEMM
+// The filter gradient reduces over pixels, the outer index of both NHWC
+// operands: its tiles are kept as [pixel][row] (16-byte vector stores) and
+// its fragments are read transposed (ldmatrix .trans).
+constexpr int LDT = BM + 8;  // 72 bf16 = 144 bytes per pixel row
+
 template <int PASS>
 __global__ void __launch_bounds__(NT) k_conv_gemm(const __grid_constant__ Args a) {
-    __shared__ __align__(16) __nv_bfloat16 As[2][BM][LDS];
-    __shared__ __align__(16) __nv_bfloat16 Bs[2][BN][LDS];
+    constexpr bool T = PASS == kWgrad;
+    __shared__ __align__(16) __nv_bfloat16 smA[2 * (T ? BK * LDT : BM * LDS)];
+    __shared__ __align__(16) __nv_bfloat16 smB[2 * (T ? BK * LDT : BN * LDS)];
+    // element (row, k) of stage buf: [row][k] tiles, or [k][row] for T
+    auto As = [&](int buf, int row, int k) -> __nv_bfloat16 * {
+        return T ? smA + buf * BK * LDT + k * LDT + row : smA + buf * BM * LDS + row * LDS + k;
+    };
+    auto Bs = [&](int buf, int row, int k) -> __nv_bfloat16 * {
+        return T ? smB + buf * BK * LDT + k * LDT + row : smB + buf * BN * LDS + row * LDS + k;
+    };
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     int kbeg = 0, kend = a.Kred;
     if constexpr (PASS == kWgrad) {
@@ -147,8 +198,14 @@ __global__ void __launch_bounds__(NT) k_conv_gemm(const __grid_constant__ Args a
                 rb[i] = wgrad_b(a, n0 + rg * 8, k0 + kc);
             } else {
                 const int row = v >> 2, kv = v & 3;
-                ra[i] = PASS == kFwd ? fwd_a(a, m0 + row, k0 + kv * 8) : dgrad_a(a, m0 + row, k0 + kv * 8);
-                rb[i] = rows_b(a.w, a.Ncols, a.Kred, n0 + row, k0 + kv * 8);
+                if constexpr (PASS == kDgrad2) {
+                    ra[i] = dgrad2_a(a, m0 + row, k0 + kv * 8);
+                    rb[i] = dgrad2_b(a, n0 + row, k0 + kv * 8);
+                } else {
+                    ra[i] = PASS == kFwd ? fwd_a(a, m0 + row, k0 + kv * 8)
+                                         : dgrad_a(a, m0 + row, k0 + kv * 8);
+                    rb[i] = rows_b(a.w, a.Ncols, a.Kred, n0 + row, k0 + kv * 8);
+                }
             }
         }
     };
@@ -158,17 +215,12 @@ __global__ void __launch_bounds__(NT) k_conv_gemm(const __grid_constant__ Args a
             const int v = tid + i * NT;
             if constexpr (PASS == kWgrad) {
                 const int kc = v & 31, rg = v >> 5;
-                const __nv_bfloat16 *ea = reinterpret_cast<const __nv_bfloat16 *>(&ra[i]);
-                const __nv_bfloat16 *eb = reinterpret_cast<const __nv_bfloat16 *>(&rb[i]);
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    As[buf][rg * 8 + e][kc] = ea[e];
-                    Bs[buf][rg * 8 + e][kc] = eb[e];
-                }
+                *reinterpret_cast<uint4 *>(As(buf, rg * 8, kc)) = ra[i];
+                *reinterpret_cast<uint4 *>(Bs(buf, rg * 8, kc)) = rb[i];
             } else {
                 const int row = v >> 2, kv = v & 3;
-                *reinterpret_cast<uint4 *>(&As[buf][row][kv * 8]) = ra[i];
-                *reinterpret_cast<uint4 *>(&Bs[buf][row][kv * 8]) = rb[i];
+                *reinterpret_cast<uint4 *>(As(buf, row, kv * 8)) = ra[i];
+                *reinterpret_cast<uint4 *>(Bs(buf, row, kv * 8)) = rb[i];
             }
         }
     };
@@ -183,15 +235,26 @@ __global__ void __launch_bounds__(NT) k_conv_gemm(const __grid_constant__ Args a
 #pragma unroll
         for (int kk = 0; kk < BK; kk += 16) {
             unsigned af[2][4], bf[4][2];
+            const int q = lane >> 3, r8 = lane & 7;
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-                ldsm_x4(af[mt][0], af[mt][1], af[mt][2], af[mt][3],
-                        &As[buf][wm * 32 + mt * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
+            for (int mt = 0; mt < 2; ++mt) {
+                if constexpr (T)  // 8x8 blocks (m 0-7 | 8-15) x (k 0-7 | 8-15), stored [k][m]
+                    ldsm_x4_t(af[mt][0], af[mt][1], af[mt][2], af[mt][3],
+                              As(buf, wm * 32 + mt * 16 + (q & 1) * 8, kk + r8 + (q >> 1) * 8));
+                else
+                    ldsm_x4(af[mt][0], af[mt][1], af[mt][2], af[mt][3],
+                            As(buf, wm * 32 + mt * 16 + (lane & 15), kk + (lane >> 4) * 8));
+            }
 #pragma unroll
-            for (int np = 0; np < 2; ++np)
-                ldsm_x4(bf[2 * np][0], bf[2 * np][1], bf[2 * np + 1][0], bf[2 * np + 1][1],
-                        &Bs[buf][wn * 32 + np * 16 + (lane & 7) + (lane >> 4) * 8]
-                           [kk + ((lane >> 3) & 1) * 8]);
+            for (int np = 0; np < 2; ++np) {
+                if constexpr (T)  // (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, k 0-7), (n 8-15, k 8-15)
+                    ldsm_x4_t(bf[2 * np][0], bf[2 * np][1], bf[2 * np + 1][0], bf[2 * np + 1][1],
+                              Bs(buf, wn * 32 + np * 16 + (q >> 1) * 8, kk + r8 + (q & 1) * 8));
+                else
+                    ldsm_x4(bf[2 * np][0], bf[2 * np][1], bf[2 * np + 1][0], bf[2 * np + 1][1],
+                            Bs(buf, wn * 32 + np * 16 + (lane & 7) + (lane >> 4) * 8,
+                               kk + ((lane >> 3) & 1) * 8));
+            }
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -214,7 +277,11 @@ __global__ void __launch_bounds__(NT) k_conv_gemm(const __grid_constant__ Args a
                 const int col = n0 + wn * 32 + nt * 8 + (lane & 3) * 2;
                 if (row >= a.M || col >= a.Ncols) continue;
                 float v0 = acc[mt][nt][half * 2], v1 = acc[mt][nt][half * 2 + 1];
-                const size_t o = (size_t)row * a.Ncols + col;
+                size_t o = (size_t)row * a.Ncols + col;
+                if constexpr (PASS == kDgrad2) {  // class pixel -> input pixel
+                    const int wi = row % a.Wc, t = row / a.Wc, hi = t % a.Hc, n = t / a.Hc;
+                    o = (((size_t)n * a.g.H + 2 * hi + a.ph) * a.g.W + 2 * wi + a.pw) * a.Ncols + col;
+                }
                 if constexpr (PASS == kFwd) {
                     v0 += a.bias[col];
                     v1 += a.bias[col + 1];
@@ -224,7 +291,7 @@ __global__ void __launch_bounds__(NT) k_conv_gemm(const __grid_constant__ Args a
                     }
                     *reinterpret_cast<__nv_bfloat162 *>(a.y + o) = __floats2bfloat162_rn(v0, v1);
                     if (a.y32) *reinterpret_cast<float2 *>(a.y32 + o) = make_float2(v0, v1);
-                } else if constexpr (PASS == kDgrad) {
+                } else if constexpr (PASS == kDgrad || PASS == kDgrad2) {
                     if (a.mask) {
                         const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(a.mask + o);
                         if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
@@ -248,8 +315,30 @@ __global__ void k_sum_splits(const float *part, int splits, int64_t count, float
     out[i] = s;
 }
 
-// dbias[k] = sum over pixels of dy[pixel][k]: one CTA per channel, a fixed
-// strided partition and a fixed tree.
+// Partial bias gradients for K dividing 256: CTA c sums the pixels
+// [c chunk, (c + 1) chunk), chunk = kBiasIter 256 / K, with 256 / K pixel
+// lanes per channel (coalesced rows), then a fixed tree over the lanes:
+// part[c][k].
+constexpr int kBiasIter = 64;
+__host__ __device__ constexpr int bias_chunk(int K) { return kBiasIter * (256 / K); }
+__global__ void k_bias_partial(const __nv_bfloat16 *dy, int64_t pixels, int K, float *part) {
+    __shared__ float red[256];
+    const int lanes = 256 / K, t = threadIdx.x, k = t % K, pl = t / K;
+    const int64_t p0 = (int64_t)blockIdx.x * bias_chunk(K);
+    const int64_t p1 = p0 + bias_chunk(K) < pixels ? p0 + bias_chunk(K) : pixels;
+    float acc = 0.f;
+    for (int64_t p = p0 + pl; p < p1; p += lanes) acc += __bfloat162float(dy[p * K + k]);
+    red[t] = acc;
+    __syncthreads();
+    for (int d = lanes / 2; d > 0; d >>= 1) {
+        if (pl < d) red[t] += red[t + d * K];
+        __syncthreads();
+    }
+    if (pl == 0) part[(int64_t)blockIdx.x * K + k] = red[t];
+}
+
+// dbias[k] = sum over pixels of dy[pixel][k] for other K: one CTA per
+// channel, a fixed strided partition and a fixed tree.
 __global__ void k_bias_grad(const __nv_bfloat16 *dy, int64_t pixels, int K, float *db) {
     __shared__ float red[256];
     const int k = blockIdx.x;
@@ -291,7 +380,8 @@ namespace {
 
 bool shape_ok(const osog_conv_shape_t *s) {
     return s && s->N > 0 && s->H > 0 && s->W > 0 && s->C > 0 && s->C % 8 == 0 && s->K > 0 &&
-           s->K % 8 == 0 && s->R > 0 && s->S > 0 && (s->stride == 1 || s->stride == 2) &&
+           s->K % 8 == 0 && s->R > 0 && s->S > 0 && s->R <= 8 && s->S <= 8 &&
+           (s->stride == 1 || s->stride == 2) &&
            s->pad >= 0 && s->H + 2 * s->pad >= s->R && s->W + 2 * s->pad >= s->S;
 }
 
@@ -362,18 +452,44 @@ int osog_conv2d_backward_data(const osog_conv_shape_t *shape, const uint16_t *dy
     a.w = bf(w_t);
     a.mask = x_act ? bf(x_act) : nullptr;
     a.y = bf(dx);
-    a.M = g.N * g.H * g.W;
     a.Ncols = g.C;
+    if (g.stride == 2) {  // four parity classes, each over its own taps
+        for (int ph = 0; ph < 2; ++ph)
+            for (int pw = 0; pw < 2; ++pw) {
+                a.ph = ph;
+                a.pw = pw;
+                a.Hc = (g.H - ph + 1) / 2;
+                a.Wc = (g.W - pw + 1) / 2;
+                a.nr = a.ns = 0;
+                for (int r = 0; r < g.R; ++r)
+                    if (((ph + g.pad - r) & 1) == 0) a.rtap[a.nr++] = r;
+                for (int sx = 0; sx < g.S; ++sx)
+                    if (((pw + g.pad - sx) & 1) == 0) a.stap[a.ns++] = sx;
+                a.M = g.N * a.Hc * a.Wc;
+                a.Kred = a.nr * a.ns * g.K;
+                if (a.M == 0) continue;
+                dim3 grid((a.M + BM - 1) / BM, (a.Ncols + BN - 1) / BN);
+                k_conv_gemm<kDgrad2><<<grid, NT, 0, st>>>(a);
+            }
+        return status_of(cudaGetLastError());
+    }
+    a.M = g.N * g.H * g.W;
     a.Kred = g.R * g.S * g.K;
     dim3 grid((a.M + BM - 1) / BM, (a.Ncols + BN - 1) / BN);
     k_conv_gemm<kDgrad><<<grid, NT, 0, st>>>(a);
     return status_of(cudaGetLastError());
 }
 
+static int bias_chunks(const Geo &g) {
+    if (256 % g.K) return 0;
+    return (int)(((int64_t)g.N * g.P * g.Q + bias_chunk(g.K) - 1) / bias_chunk(g.K));
+}
+
 size_t osog_conv2d_backward_filter_workspace(const osog_conv_shape_t *shape) {
     if (!shape_ok(shape)) return 0;
     const Geo g = geo_of(shape);
-    return (size_t)splits_of(g) * g.K * g.R * g.S * g.C * sizeof(float);
+    return ((size_t)splits_of(g) * g.K * g.R * g.S * g.C + (size_t)bias_chunks(g) * g.K) *
+           sizeof(float);
 }
 
 int osog_conv2d_backward_filter(const osog_conv_shape_t *shape, const uint16_t *dy,
@@ -396,7 +512,15 @@ int osog_conv2d_backward_filter(const osog_conv_shape_t *shape, const uint16_t *
     k_conv_gemm<kWgrad><<<grid, NT, 0, st>>>(a);
     const int64_t count = (int64_t)a.M * a.Ncols;
     k_sum_splits<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(a.part, splits, count, dw);
-    k_bias_grad<<<g.K, 256, 0, st>>>(bf(dy), (int64_t)g.N * g.P * g.Q, g.K, dbias);
+    const int64_t pixels = (int64_t)g.N * g.P * g.Q;
+    if (256 % g.K == 0) {
+        float *bpart = a.part + (size_t)splits * count;
+        const int chunks = bias_chunks(g);
+        k_bias_partial<<<chunks, 256, 0, st>>>(bf(dy), pixels, g.K, bpart);
+        k_sum_splits<<<(unsigned)((g.K + 255) / 256), 256, 0, st>>>(bpart, chunks, g.K, dbias);
+    } else {
+        k_bias_grad<<<g.K, 256, 0, st>>>(bf(dy), pixels, g.K, dbias);
+    }
     return status_of(cudaGetLastError());
 }
 

@@ -19,6 +19,9 @@ SHAPES = [
     (2, 9, 13, 32, 8, 1, 1, 1, 0),
     (1, 66, 70, 64, 128, 3, 3, 1, 1),
     (1, 30, 30, 16, 16, 3, 3, 2, 0),
+    (2, 15, 17, 16, 8, 1, 1, 2, 0),   # stride 2, 1 x 1: two parity classes see no tap
+    (1, 21, 19, 8, 16, 5, 5, 2, 2),
+    (1, 64, 64, 32, 64, 3, 3, 2, 1),  # the network's second layer at small size
 ]
 
 
