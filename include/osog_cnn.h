@@ -66,6 +66,19 @@ int osog_conv2d_backward_filter(const osog_conv_shape_t *shape, const uint16_t *
                                 const uint16_t *x, float *dw, float *dbias, void *ws,
                                 size_t ws_bytes, osog_stream_t stream);
 
+/* Engine of osog_conv2d_forward and osog_conv2d_backward_data for later
+ * calls of this process: 1 (default) the fifth-generation tensor cores
+ * (tcgen05.mma with the accumulator in tensor memory), 0 the warp-level
+ * MMA (mma.sync).  Both compute the same products in BF16 with FP32
+ * accumulation; summation order inside the tensor core differs.  The
+ * filter gradient always uses the warp-level MMA. */
+void osog_conv_use_tcgen05(int32_t enable);
+
+/* Synchronise `stream` and report a latched device error of the
+ * convolution kernels (OSOG_ERR_TIMEOUT: a bounded wait for the tensor
+ * cores gave up; results of that call are invalid), clearing it. */
+int osog_conv_sync_status(osog_stream_t stream);
+
 /* Derivative of a ReLU: dy_out[i] = dy[i] where act[i] > 0, else 0 (bf16). */
 int osog_relu_backward(const uint16_t *dy, const uint16_t *act, uint16_t *dy_out, int64_t count,
                        osog_stream_t stream);

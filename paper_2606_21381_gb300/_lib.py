@@ -54,7 +54,8 @@ class ConvShape(ctypes.Structure):
 
 CNN_EXPORTS = ("osog_conv_out_h", "osog_conv_out_w", "osog_conv2d_forward",
                "osog_conv2d_backward_data", "osog_conv2d_backward_filter_workspace",
-               "osog_conv2d_backward_filter", "osog_relu_backward")
+               "osog_conv2d_backward_filter", "osog_relu_backward", "osog_conv_use_tcgen05",
+               "osog_conv_sync_status")
 
 
 class Tuning(ctypes.Structure):
@@ -150,6 +151,10 @@ def lib(build_if_missing: bool = True):
     L.osog_conv2d_backward_filter_workspace.restype = sz
     L.osog_conv2d_backward_filter.argtypes = [P(ConvShape), vp, vp, vp, vp, vp, sz, vp]
     L.osog_conv2d_backward_filter.restype = ctypes.c_int
+    L.osog_conv_use_tcgen05.argtypes = [i32]
+    L.osog_conv_use_tcgen05.restype = None
+    L.osog_conv_sync_status.argtypes = [vp]
+    L.osog_conv_sync_status.restype = ctypes.c_int
     L.osog_relu_backward.argtypes = [vp, vp, vp, i64, vp]
     L.osog_relu_backward.restype = ctypes.c_int
     L.osog_render_noalloc.restype = ctypes.c_int

@@ -124,6 +124,18 @@ def conv2d_backward_filter(dy, x, w_shape, stride: int, pad: int, ws=None):
     return dw, db
 
 
+def use_tcgen05(enable: bool) -> None:
+    """Engine of the forward and data-gradient convolutions (process-wide):
+    tcgen05 tensor cores (default) or the warp-level MMA."""
+    _lib.lib().osog_conv_use_tcgen05(1 if enable else 0)
+
+
+def sync_status(device=None) -> int:
+    """Synchronise and return (and clear) a latched convolution error."""
+    dev = torch.device(device or "cuda")
+    return int(_lib.lib().osog_conv_sync_status(_stream(dev)))
+
+
 def relu_backward(dy, act):
     _require(dy, torch.bfloat16, "dy")
     _require(act, torch.bfloat16, "act")

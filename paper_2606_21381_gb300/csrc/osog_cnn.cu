@@ -1,5 +1,8 @@
 // Convolutions of the learned warm start as implicit GEMMs on the tensor
-// cores (BF16 operands, FP32 accumulation).
+// cores (BF16 operands, FP32 accumulation): forward and data gradients on
+// tcgen05 (TMEM accumulators, shared-memory descriptors, mbarrier
+// completion), filter gradients on the warp-level MMA (mma.sync), which
+// also remains selectable for the other two.
 //
 //   forward  Y[m = (n,p,q)][k]   = sum_{j = (r,s,c)} X(im2col)[m][j] W[k][j]
 //   data     dX[m = (n,h,w)][c]  = sum_{j = (r,s,k)} dY(gathered)[m][j] Wt[c][j]
@@ -81,59 +84,80 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
 // ---------------------------------------------------------------- gathers
 // Forward A: 8 reduction entries j..j+7 (same tap, 8 channels) of output
 // pixel m.
-__device__ __forceinline__ uint4 fwd_a(const Args &a, int m, int j) {
+__device__ __forceinline__ const __nv_bfloat16 *fwd_a_src(const Args &a, int m, int j) {
     const Geo &g = a.g;
-    if (m >= a.M || j >= a.Kred) return zero4();
+    if (m >= a.M || j >= a.Kred) return nullptr;
     const int q = m % g.Q, t = m / g.Q, p = t % g.P, n = t / g.P;
     const int rs = j / g.C, c = j - rs * g.C, r = rs / g.S, s = rs - r * g.S;
     const int h = p * g.stride + r - g.pad, w = q * g.stride + s - g.pad;
-    if (h < 0 || h >= g.H || w < 0 || w >= g.W) return zero4();
-    return *reinterpret_cast<const uint4 *>(a.x + (((size_t)n * g.H + h) * g.W + w) * g.C + c);
+    if (h < 0 || h >= g.H || w < 0 || w >= g.W) return nullptr;
+    return a.x + (((size_t)n * g.H + h) * g.W + w) * g.C + c;
+}
+__device__ __forceinline__ uint4 fwd_a(const Args &a, int m, int j) {
+    const __nv_bfloat16 *p = fwd_a_src(a, m, j);
+    return p ? *reinterpret_cast<const uint4 *>(p) : zero4();
 }
 
 // Data-gradient A: dY at the output pixel that tap (r, s) of input pixel m
 // reads, 8 output channels; zero where the stride skips it.
-__device__ __forceinline__ uint4 dgrad_a(const Args &a, int m, int j) {
+__device__ __forceinline__ const __nv_bfloat16 *dgrad_a_src(const Args &a, int m, int j) {
     const Geo &g = a.g;
-    if (m >= a.M || j >= a.Kred) return zero4();
+    if (m >= a.M || j >= a.Kred) return nullptr;
     const int w = m % g.W, t = m / g.W, h = t % g.H, n = t / g.H;
     const int rs = j / g.K, k = j - rs * g.K, r = rs / g.S, s = rs - r * g.S;
     const int hp = h + g.pad - r, wq = w + g.pad - s;
-    if (hp < 0 || wq < 0 || hp % g.stride || wq % g.stride) return zero4();
+    if (hp < 0 || wq < 0 || hp % g.stride || wq % g.stride) return nullptr;
     const int p = hp / g.stride, q = wq / g.stride;
-    if (p >= g.P || q >= g.Q) return zero4();
-    return *reinterpret_cast<const uint4 *>(a.x + (((size_t)n * g.P + p) * g.Q + q) * g.K + k);
+    if (p >= g.P || q >= g.Q) return nullptr;
+    return a.x + (((size_t)n * g.P + p) * g.Q + q) * g.K + k;
+}
+__device__ __forceinline__ uint4 dgrad_a(const Args &a, int m, int j) {
+    const __nv_bfloat16 *p = dgrad_a_src(a, m, j);
+    return p ? *reinterpret_cast<const uint4 *>(p) : zero4();
 }
 
 // Stride-2 data gradient, parity class (ph, pw): class pixel m = (n, i, j)
 // is input pixel (n, 2 i + ph, 2 j + pw); reduction entry (tap, k) with tap
 // = (ri, si) reads dY at ((h + pad - r) / 2, (w + pad - s) / 2), which the
 // class's taps make exact.
-__device__ __forceinline__ uint4 dgrad2_a(const Args &a, int m, int j) {
+__device__ __forceinline__ const __nv_bfloat16 *dgrad2_a_src(const Args &a, int m, int j) {
     const Geo &g = a.g;
-    if (m >= a.M || j >= a.Kred) return zero4();
+    if (m >= a.M || j >= a.Kred) return nullptr;
     const int wi = m % a.Wc, t = m / a.Wc, hi = t % a.Hc, n = t / a.Hc;
     const int tap = j / g.K, k = j - tap * g.K, ri = tap / a.ns, si = tap - ri * a.ns;
     const int p = (2 * hi + a.ph + g.pad - a.rtap[ri]) >> 1;
     const int q = (2 * wi + a.pw + g.pad - a.stap[si]) >> 1;
-    if (p < 0 || q < 0 || p >= g.P || q >= g.Q) return zero4();
-    return *reinterpret_cast<const uint4 *>(a.x + (((size_t)n * g.P + p) * g.Q + q) * g.K + k);
+    if (p < 0 || q < 0 || p >= g.P || q >= g.Q) return nullptr;
+    return a.x + (((size_t)n * g.P + p) * g.Q + q) * g.K + k;
+}
+__device__ __forceinline__ uint4 dgrad2_a(const Args &a, int m, int j) {
+    const __nv_bfloat16 *p = dgrad2_a_src(a, m, j);
+    return p ? *reinterpret_cast<const uint4 *>(p) : zero4();
 }
 
 // Filters reordered [C][R][S][K], row c, reduction entry (tap, k) of the
 // class's taps.
-__device__ __forceinline__ uint4 dgrad2_b(const Args &a, int c, int j) {
+__device__ __forceinline__ const __nv_bfloat16 *dgrad2_b_src(const Args &a, int c, int j) {
     const Geo &g = a.g;
-    if (c >= a.Ncols || j >= a.Kred) return zero4();
+    if (c >= a.Ncols || j >= a.Kred) return nullptr;
     const int tap = j / g.K, k = j - tap * g.K, ri = tap / a.ns, si = tap - ri * a.ns;
     const int rs = a.rtap[ri] * g.S + a.stap[si];
-    return *reinterpret_cast<const uint4 *>(a.w + ((size_t)c * g.R * g.S + rs) * g.K + k);
+    return a.w + ((size_t)c * g.R * g.S + rs) * g.K + k;
+}
+__device__ __forceinline__ uint4 dgrad2_b(const Args &a, int c, int j) {
+    const __nv_bfloat16 *p = dgrad2_b_src(a, c, j);
+    return p ? *reinterpret_cast<const uint4 *>(p) : zero4();
 }
 
 // Row-major operand rows (8 consecutive reduction entries of row r).
+__device__ __forceinline__ const __nv_bfloat16 *rows_src(const __nv_bfloat16 *base, int rows, int ld,
+                                                         int r, int j) {
+    if (r >= rows || j >= ld) return nullptr;
+    return base + (size_t)r * ld + j;
+}
 __device__ __forceinline__ uint4 rows_b(const __nv_bfloat16 *base, int rows, int ld, int r, int j) {
-    if (r >= rows || j >= ld) return zero4();
-    return *reinterpret_cast<const uint4 *>(base + (size_t)r * ld + j);
+    const __nv_bfloat16 *p = rows_src(base, rows, ld, r, j);
+    return p ? *reinterpret_cast<const uint4 *>(p) : zero4();
 }
 
 // Filter gradient: A(k, pixel) = dY[pixel][k..k+7] (a vector across 8 rows
@@ -151,6 +175,75 @@ __device__ __forceinline__ uint4 wgrad_b(const Args &a, int j, int pix) {
     const int h = p * g.stride + r - g.pad, w = q * g.stride + s - g.pad;
     if (h < 0 || h >= g.H || w < 0 || w >= g.W) return zero4();
     return *reinterpret_cast<const uint4 *>(a.w + (((size_t)n * g.H + h) * g.W + w) * g.C + c);
+}
+
+// Output of two adjacent columns (col, col + 1) of GEMM row `row`.
+template <int PASS>
+__device__ __forceinline__ void epilogue_pair(const Args &a, int row, int col, float v0, float v1) {
+    size_t o = (size_t)row * a.Ncols + col;
+    if constexpr (PASS == kDgrad2) {  // class pixel -> input pixel
+        const int wi = row % a.Wc, t = row / a.Wc, hi = t % a.Hc, n = t / a.Hc;
+        o = (((size_t)n * a.g.H + 2 * hi + a.ph) * a.g.W + 2 * wi + a.pw) * a.Ncols + col;
+    }
+    if constexpr (PASS == kFwd) {
+        v0 += a.bias[col];
+        v1 += a.bias[col + 1];
+        if (a.relu) {
+            v0 = fmaxf(v0, 0.f);
+            v1 = fmaxf(v1, 0.f);
+        }
+        *reinterpret_cast<__nv_bfloat162 *>(a.y + o) = __floats2bfloat162_rn(v0, v1);
+        if (a.y32) *reinterpret_cast<float2 *>(a.y32 + o) = make_float2(v0, v1);
+    } else if constexpr (PASS == kDgrad || PASS == kDgrad2) {
+        if (a.mask) {
+            const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(a.mask + o);
+            if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
+            if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
+        }
+        *reinterpret_cast<__nv_bfloat162 *>(a.y + o) = __floats2bfloat162_rn(v0, v1);
+    } else {
+        *reinterpret_cast<float2 *>(a.part + (size_t)blockIdx.z * a.M * a.Ncols + o) =
+            make_float2(v0, v1);
+    }
+}
+
+// Output of eight consecutive columns col .. col + 7 (col a multiple of 8)
+// of GEMM row `row`, forward or data gradient, as 16-byte accesses.
+template <int PASS>
+__device__ __forceinline__ void epilogue_vec8(const Args &a, int row, int col, const float *v) {
+    size_t o = (size_t)row * a.Ncols + col;
+    if constexpr (PASS == kDgrad2) {
+        const int wi = row % a.Wc, t = row / a.Wc, hi = t % a.Hc, n = t / a.Hc;
+        o = (((size_t)n * a.g.H + 2 * hi + a.ph) * a.g.W + 2 * wi + a.pw) * a.Ncols + col;
+    }
+    float x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = v[j];
+    if constexpr (PASS == kFwd) {
+        const float4 b0 = *reinterpret_cast<const float4 *>(a.bias + col);
+        const float4 b1 = *reinterpret_cast<const float4 *>(a.bias + col + 4);
+        const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            x[j] += bb[j];
+            if (a.relu) x[j] = fmaxf(x[j], 0.f);
+        }
+        if (a.y32) {
+            *reinterpret_cast<float4 *>(a.y32 + o) = make_float4(x[0], x[1], x[2], x[3]);
+            *reinterpret_cast<float4 *>(a.y32 + o + 4) = make_float4(x[4], x[5], x[6], x[7]);
+        }
+    } else if (a.mask) {
+        const uint4 mk = *reinterpret_cast<const uint4 *>(a.mask + o);
+        const __nv_bfloat16 *m8 = reinterpret_cast<const __nv_bfloat16 *>(&mk);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (!(__bfloat162float(m8[j]) > 0.f)) x[j] = 0.f;
+    }
+    uint4 out;
+    __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(&out);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o2[j] = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+    *reinterpret_cast<uint4 *>(a.y + o) = out;
 }
 
 // ---------------------------------------------------------------- GEMM
@@ -276,33 +369,223 @@ __global__ void __launch_bounds__(NT) k_conv_gemm(const __grid_constant__ Args a
                 const int row = m0 + wm * 32 + mt * 16 + (lane >> 2) + half * 8;
                 const int col = n0 + wn * 32 + nt * 8 + (lane & 3) * 2;
                 if (row >= a.M || col >= a.Ncols) continue;
-                float v0 = acc[mt][nt][half * 2], v1 = acc[mt][nt][half * 2 + 1];
-                size_t o = (size_t)row * a.Ncols + col;
-                if constexpr (PASS == kDgrad2) {  // class pixel -> input pixel
-                    const int wi = row % a.Wc, t = row / a.Wc, hi = t % a.Hc, n = t / a.Hc;
-                    o = (((size_t)n * a.g.H + 2 * hi + a.ph) * a.g.W + 2 * wi + a.pw) * a.Ncols + col;
-                }
-                if constexpr (PASS == kFwd) {
-                    v0 += a.bias[col];
-                    v1 += a.bias[col + 1];
-                    if (a.relu) {
-                        v0 = fmaxf(v0, 0.f);
-                        v1 = fmaxf(v1, 0.f);
-                    }
-                    *reinterpret_cast<__nv_bfloat162 *>(a.y + o) = __floats2bfloat162_rn(v0, v1);
-                    if (a.y32) *reinterpret_cast<float2 *>(a.y32 + o) = make_float2(v0, v1);
-                } else if constexpr (PASS == kDgrad || PASS == kDgrad2) {
-                    if (a.mask) {
-                        const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(a.mask + o);
-                        if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
-                        if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
-                    }
-                    *reinterpret_cast<__nv_bfloat162 *>(a.y + o) = __floats2bfloat162_rn(v0, v1);
-                } else {
-                    *reinterpret_cast<float2 *>(a.part + (size_t)blockIdx.z * a.M * a.Ncols + o) =
-                        make_float2(v0, v1);
+                epilogue_pair<PASS>(a, row, col, acc[mt][nt][half * 2], acc[mt][nt][half * 2 + 1]);
+            }
+}
+
+// ---------------------------------------------------------------- tcgen05
+// Forward and data-gradient convolutions on the fifth-generation tensor
+// cores.  A CTA of UNT threads owns a tile of UM = 128 GEMM rows (pixels) by
+// BNU columns (output channels rounded up to 16, at most 128); the FP32
+// accumulator lives in tensor memory (TMEM, one lane per row).  Each
+// reduction slice of UBK = 64 is copied by all threads (cp.async, 16 bytes,
+// zero-filled outside the image) into one of UST shared stages in the
+// canonical K-major layout without swizzle -- 8-row x 16-byte
+// core matrices, contiguous along K (LBO = 128 bytes) and 8-row groups
+// UBK / 8 core matrices apart (SBO = 1024 bytes) -- then one thread issues
+// four tcgen05.mma (M 128, N BNU, K 16) with shared-memory descriptors and
+// commits them to the stage's mbarrier; a stage is refilled once its
+// multiplications are done, while the next stage's are already queued, so
+// copies of UST - 1 stages overlap the multiplications.  Waits are bounded: a timeout latches
+// g_cnn_status and the kernel still releases its tensor memory.
+constexpr int UM = 128, UBK = 64, UST = 3, UKC = UBK / 8, UNT = 256;
+constexpr int kUStage = UM * UBK * 2;   // bytes of one operand stage (B <= 128 rows)
+constexpr int kSpinLimit = 1 << 22;
+
+__device__ int g_cnn_status;
+
+__device__ __forceinline__ int canon(int row, int k) {  // byte offset in a stage
+    return (row >> 3) * (UKC * 128) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) |
+           ((uint64_t)((UKC * 128) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// kind::f16 instruction descriptor: FP32 D, BF16 A and B, both K-major,
+// N >> 3 and M >> 4.
+__device__ __forceinline__ uint32_t umma_idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (int it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+        __nanosleep(32);
+    }
+    return false;
+}
+
+// 16-byte asynchronous copy to shared memory; a NULL source writes zeros.
+__device__ __forceinline__ void cp16(void *dst, const __nv_bfloat16 *src, const void *any) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n"
+                 :: "r"(smem_u32(dst)), "l"(src ? (const void *)src : any), "r"(src ? 16 : 0)
+                 : "memory");
+}
+
+template <int PASS>
+__device__ __forceinline__ void umma_load_stage(const Args &a, unsigned char *A, unsigned char *B,
+                                                int m0, int n0, int k0, int BNU, int tid) {
+#pragma unroll
+    for (int i = 0; i < UM * UKC / UNT; ++i) {
+        const int v = tid + i * UNT, row = v >> 3, kv = v & 7;
+        const __nv_bfloat16 *src = PASS == kFwd     ? fwd_a_src(a, m0 + row, k0 + kv * 8)
+                                 : PASS == kDgrad ? dgrad_a_src(a, m0 + row, k0 + kv * 8)
+                                                  : dgrad2_a_src(a, m0 + row, k0 + kv * 8);
+        cp16(A + canon(row, kv * 8), src, a.x);
+    }
+    for (int v = tid; v < BNU * UKC; v += UNT) {
+        const int row = v >> 3, kv = v & 7;
+        const __nv_bfloat16 *src = PASS == kDgrad2 ? dgrad2_b_src(a, n0 + row, k0 + kv * 8)
+                                                   : rows_src(a.w, a.Ncols, a.Kred, n0 + row, k0 + kv * 8);
+        cp16(B + canon(row, kv * 8), src, a.w);
+    }
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(UNT) k_conv_umma(const __grid_constant__ Args a, int BNU) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int bstage = BNU * UBK * 2;  // bytes of one B stage
+    unsigned char *stA = sm, *stB = sm + UST * kUStage;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(stB + UST * bstage);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + UST);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * UM, n0 = blockIdx.y * BNU;
+    const uint32_t ncols = BNU <= 32 ? 32u : BNU <= 64 ? 64u : 128u;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                     :: "r"(smem_u32(tslot)), "r"(ncols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int st = 0; st < UST; ++st)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(smem_u32(mbar + st)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    const int nk = (a.Kred + UBK - 1) / UBK;
+    // prologue: stages 0 .. UST-2 in flight, one commit group each
+    for (int kt = 0; kt < UST - 1; ++kt) {
+        if (kt < nk) umma_load_stage<PASS>(a, stA + kt * kUStage, stB + kt * bstage, m0, n0, kt * UBK, BNU, tid);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t taddr = *tslot;
+    const uint32_t idesc = umma_idesc(BNU);
+    bool ok = true;
+    for (int kt = 0; kt < nk; ++kt) {
+        const int st = kt % UST;
+        // this thread's copies of stage kt have landed (UST-2 newer groups may pend)
+        asm volatile("cp.async.wait_group %0;\n" :: "n"(UST - 2) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // visible to the tensor core
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            unsigned char *A = stA + st * kUStage, *B = stB + st * bstage;
+#pragma unroll
+            for (int s = 0; s < UBK / 16; ++s) {
+                const uint64_t ad = umma_desc(smem_u32(A) + s * 256);
+                const uint64_t bd = umma_desc(smem_u32(B) + s * 256);
+                const uint32_t acc = (kt > 0 || s > 0) ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             :: "r"(taddr), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                         :: "r"(smem_u32(mbar + st)) : "memory");
+        }
+        // refill the stage of step kt-1 with step kt+UST-1 once its
+        // multiplications are done (those of step kt are queued behind them)
+        const int nx = kt + UST - 1;
+        if (nx < nk) {
+            const int sx = nx % UST;
+            if (kt >= 1) ok = mbar_wait(smem_u32(mbar + sx), (uint32_t)(((kt - 1) / UST) & 1)) && ok;
+            umma_load_stage<PASS>(a, stA + sx * kUStage, stB + sx * bstage, m0, n0, nx * UBK, BNU, tid);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    // the last commit covers every multiplication issued before it (a
+    // reduction of length 0 issues none: the result is zero)
+    if (nk > 0) {
+        const int last = nk - 1;
+        ok = mbar_wait(smem_u32(mbar + last % UST), (uint32_t)((last / UST) & 1)) && ok;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (!ok && lane == 0) atomicExch(&g_cnn_status, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and the
+    // 32-column chunks c with c % (UNT / 128) == w / 4
+    const int quarter = warp & 3, group = warp >> 2;
+    const int row = m0 + quarter * 32 + lane;
+    for (int c0 = group * 32; c0 < BNU; c0 += 32 * (UNT / 128)) {
+        uint32_t v[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+            "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+              "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+              "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+              "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+              "=r"(v[31])
+            : "r"(taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (nk == 0) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = 0u;
+        }
+        if (row < a.M) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+                const int col = n0 + c0 + j;
+                if (c0 + j < BNU && col < a.Ncols) {
+                    float f[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) f[i] = __uint_as_float(v[j + i]);
+                    epilogue_vec8<PASS>(a, row, col, f);
                 }
             }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(taddr), "r"(ncols)
+                     : "memory");
+}
+
+constexpr int kUmmaSmem = 2 * UST * kUStage + 64;  // the largest (BNU = 128)
+__host__ __device__ constexpr int umma_smem(int bnu) { return UST * (kUStage + bnu * UBK * 2) + 64; }
+
+// One-time opt-in to the stages' dynamic shared memory.
+cudaError_t umma_prepare() {
+    static const cudaError_t e = [] {
+        cudaError_t r = cudaFuncSetAttribute(k_conv_umma<kFwd>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k_conv_umma<kDgrad>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k_conv_umma<kDgrad2>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
+        return r;
+    }();
+    return e;
+}
+
+template <int PASS>
+cudaError_t launch_umma(const Args &a, cudaStream_t st) {
+    cudaError_t e = umma_prepare();
+    if (e != cudaSuccess) return e;
+    const int bnu = ((a.Ncols + 15) / 16) * 16 < 128 ? ((a.Ncols + 15) / 16) * 16 : 128;
+    dim3 grid((a.M + UM - 1) / UM, (a.Ncols + bnu - 1) / bnu);
+    k_conv_umma<PASS><<<grid, UNT, umma_smem(bnu), st>>>(a, bnu);
+    return cudaGetLastError();
 }
 
 // Sum of the filter-gradient partial tiles over the pixel splits, in split
@@ -408,6 +691,10 @@ int splits_of(const Geo &g) {
 
 int status_of(cudaError_t e) { return e == cudaSuccess ? OSOG_OK : OSOG_ERR_CUDA; }
 
+// Engine of the forward and data-gradient convolutions: the tcgen05 kernel
+// (1, default) or the warp-level MMA kernel (0).
+int g_use_tcgen05 = 1;
+
 const __nv_bfloat16 *bf(const uint16_t *p) { return reinterpret_cast<const __nv_bfloat16 *>(p); }
 __nv_bfloat16 *bf(uint16_t *p) { return reinterpret_cast<__nv_bfloat16 *>(p); }
 
@@ -433,8 +720,10 @@ int osog_conv2d_forward(const osog_conv_shape_t *shape, const uint16_t *x, const
     a.M = a.g.N * a.g.P * a.g.Q;
     a.Ncols = a.g.K;
     a.Kred = a.g.R * a.g.S * a.g.C;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (g_use_tcgen05) return status_of(launch_umma<kFwd>(a, st));
     dim3 grid((a.M + BM - 1) / BM, (a.Ncols + BN - 1) / BN);
-    k_conv_gemm<kFwd><<<grid, NT, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
+    k_conv_gemm<kFwd><<<grid, NT, 0, st>>>(a);
     return status_of(cudaGetLastError());
 }
 
@@ -468,6 +757,11 @@ int osog_conv2d_backward_data(const osog_conv_shape_t *shape, const uint16_t *dy
                 a.M = g.N * a.Hc * a.Wc;
                 a.Kred = a.nr * a.ns * g.K;
                 if (a.M == 0) continue;
+                if (g_use_tcgen05) {
+                    const cudaError_t e = launch_umma<kDgrad2>(a, st);
+                    if (e != cudaSuccess) return status_of(e);
+                    continue;
+                }
                 dim3 grid((a.M + BM - 1) / BM, (a.Ncols + BN - 1) / BN);
                 k_conv_gemm<kDgrad2><<<grid, NT, 0, st>>>(a);
             }
@@ -475,6 +769,7 @@ int osog_conv2d_backward_data(const osog_conv_shape_t *shape, const uint16_t *dy
     }
     a.M = g.N * g.H * g.W;
     a.Kred = g.R * g.S * g.K;
+    if (g_use_tcgen05) return status_of(launch_umma<kDgrad>(a, st));
     dim3 grid((a.M + BM - 1) / BM, (a.Ncols + BN - 1) / BN);
     k_conv_gemm<kDgrad><<<grid, NT, 0, st>>>(a);
     return status_of(cudaGetLastError());
@@ -531,6 +826,18 @@ int osog_relu_backward(const uint16_t *dy, const uint16_t *act, uint16_t *dy_out
     k_relu_backward<<<(unsigned)((count + 255) / 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
         bf(dy), bf(act), count, bf(dy_out));
     return status_of(cudaGetLastError());
+}
+
+void osog_conv_use_tcgen05(int32_t enable) { g_use_tcgen05 = enable ? 1 : 0; }
+
+int osog_conv_sync_status(osog_stream_t stream) {
+    if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return OSOG_ERR_CUDA;
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_cnn_status, sizeof v) != cudaSuccess) return OSOG_ERR_CUDA;
+    if (!v) return OSOG_OK;
+    const int zero = 0;
+    if (cudaMemcpyToSymbol(g_cnn_status, &zero, sizeof zero) != cudaSuccess) return OSOG_ERR_CUDA;
+    return OSOG_ERR_TIMEOUT;
 }
 
 }  // extern "C"

@@ -43,10 +43,15 @@ def _inputs(shape, seed):
     return x, w, b, dy
 
 
-@pytest.fixture(scope="module")
-def cnn():
+@pytest.fixture(scope="module", params=["tcgen05", "mma_sync"])
+def cnn(request):
+    """The convolution module with the forward / data-gradient engine set to
+    the tcgen05 tensor cores or the warp-level MMA (every test runs on both)."""
     from paper_2606_21381_gb300 import cnn as m
-    return m
+    m.use_tcgen05(request.param == "tcgen05")
+    yield m
+    assert m.sync_status() == 0
+    m.use_tcgen05(True)
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -59,6 +64,7 @@ def test_conv_forward_matches_reference(cnn, shape, relu):
     bd = torch.from_numpy(b).to(dev)
     y, y32 = cnn.conv2d(xd, wd, bd, shape[7], shape[8], relu, want_f32=True)
     want = ref.conv_forward(x64, w64, b.astype(np.float64), shape[7], shape[8], relu)
+    assert cnn.sync_status() == 0
     got32 = y32.cpu().numpy().astype(np.float64)
     scale = np.abs(want).max()
     assert np.abs(got32 - want).max() <= 1e-5 * scale
@@ -80,6 +86,7 @@ def test_conv_backward_data_matches_reference(cnn, shape, masked):
     want, _, _ = ref.conv_grads(x64, w64, b.astype(np.float64), shape[7], shape[8], dy64)
     if masked:
         want = want * (x64 > 0)
+    assert cnn.sync_status() == 0
     got = dx.to(torch.float32).cpu().numpy().astype(np.float64)
     scale = np.abs(want).max()
     assert np.all(np.abs(got - want) <= 2.0 ** -8 * np.abs(want) + 1e-5 * scale)
