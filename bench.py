@@ -194,6 +194,28 @@ def algorithmic_bytes(kernel: str, counts, H: int, W: int, K: int, pairs: int,
 
 
 # ------------------------------------------------------------------ GPU arm
+def bind_to_gpu_numa_node(local_rank: int):
+    """Restrict this process to the CPUs of the GPU's NUMA node (from sysfs),
+    so that pinned host buffers are allocated next to the GPU's link.
+    Returns the node, or None where the topology is not exposed."""
+    import torch
+    try:
+        props = torch.cuda.get_device_properties(local_rank)
+        bus = f"{props.pci_domain_id:04x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
+        node = int(open(f"/sys/bus/pci/devices/{bus}/numa_node").read().strip())
+        if node < 0:
+            return None
+        cpus = set()
+        for part in open(f"/sys/devices/system/node/node{node}/cpulist").read().strip().split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+        return node
+    except Exception:
+        return None
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -202,6 +224,7 @@ def run_gpu(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    numa_node = bind_to_gpu_numa_node(local_rank)
     counts, soas, optics = workload(seed_offset=1000 * rank)
     soa_all, offs = scenes.concat(soas)
     K = 1
@@ -326,7 +349,6 @@ def run_gpu(args, rank, world, local_rank):
         if fb_r.sync_status(stream) != 0:
             raise RuntimeError("device status set in the forward + adjoint run")
         del img
-    warm = None if (args.no_warm_start or rank != 0) else warm_start_bench(dev)
     with torch.cuda.stream(stream):
         # ---- end to end from pinned host buffers through the public API:
         #      each step copies its particles in and its images out; the
@@ -357,14 +379,20 @@ def run_gpu(args, rank, world, local_rank):
         pipe.submit(soa_host, offs, optics, img_host[i % 2])
     pipe.synchronize()
     pipe_s = time.perf_counter() - t0
+    del pipe
     with torch.cuda.stream(stream):
         status = r.sync_status(stream)
         if status != 0:
             raise RuntimeError(f"device status {status} after the timed runs")
+    # the learned warm start last, in a process of its own: its training
+    # allocates and pins its own buffers, which should not share allocator
+    # state with the measurements above
+    warm = None if (args.no_warm_start or rank != 0) else warm_start_in_child(local_rank)
     return finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms,
                   single40k, e2e_ms, launches, clocks, wall, K, soas=soas, optics=optics,
                   fwd_bwd_ms=fb_ms, extra={"autotuned": tuned, "batched_modes_ms": modes_ms,
                                            "kernels_three_launch": prof3, "warm_start": warm,
+                                           "numa_node": numa_node,
                                            "e2e_pipelined": (n_pipe, pipe_s)})
 
 
@@ -402,6 +430,30 @@ def conv_profile(net, x, reps: int = 10):
     return rows
 
 
+def _warm_start_child(local_rank: int, queue) -> None:
+    import torch
+    torch.cuda.set_device(local_rank)
+    try:
+        queue.put(("ok", warm_start_bench(torch.device("cuda", local_rank))))
+    except Exception as e:  # reported by the parent
+        queue.put(("error", repr(e)))
+
+
+def warm_start_in_child(local_rank: int):
+    """warm_start_bench in a spawned process on the same GPU (the parent
+    waits idle)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_warm_start_child, args=(local_rank, q))
+    p.start()
+    status, result = q.get()
+    p.join()
+    if status != "ok":
+        raise RuntimeError(f"warm-start benchmark failed: {result}")
+    return result
+
+
 def warm_start_bench(dev, samples: int = 200_000, seeds=(7, 9, 10)):
     """Learned warm start on the 512^2 inverse-rendering scene: train the
     network on `samples` rendered crops, then time the plain and the
@@ -421,7 +473,8 @@ def warm_start_bench(dev, samples: int = 200_000, seeds=(7, 9, 10)):
     o = dict(o, defocus=0.8, shear_px=1.0)
     target = r.render(torch.from_numpy(soa).to(dev), None, o)
     s0, o0 = inverse.perturb(soa, o, np.random.default_rng(seeds[0]))
-    inverse.solve(target, s0, o0, r, inverse.SolveConfig(steps=20))   # warm-up
+    inverse.solve(target, s0, o0, r, inverse.SolveConfig(steps=20, record_every=5),
+                  truth=soa)  # warm-up of every code path the timed solves take
     arms = {"plain": [], "warm": []}
     for seed in seeds:
         s0, o0 = inverse.perturb(soa, o, np.random.default_rng(seed))
@@ -537,7 +590,8 @@ def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms
                 "how": "HostBatchPipeline: pinned host particles in, pinned host images out, "
                        "every step; copies of one step overlap the render of the next; "
                        "host wall clock over %d steps" % extra["e2e_pipelined"][0],
-                "serial_value": round(SCENES / (statistics.median(e2e_ms) / 1e3), 2)},
+                "serial_value": round(SCENES / (statistics.median(e2e_ms) / 1e3), 2),
+                "host_numa_node": extra.get("numa_node")},
         "fwd_bwd": None if not fwd_bwd_ms else {
             "ms": round(statistics.median(fwd_bwd_ms), 4),
             "workload": "512x512, 200 particles, brightfield + DIC: osog_render + "

@@ -309,9 +309,35 @@ def cell_targets(soas, optics_list, size: int, crop: int):
     return tgt, mask
 
 
-def _to_device(a: np.ndarray, dev) -> torch.Tensor:
-    """Asynchronous copy through pinned memory (the host may run ahead)."""
-    return torch.from_numpy(a).pin_memory().to(dev, non_blocking=True)
+class _PinnedStaging:
+    """Host-to-device copies through two reused pinned buffers per array
+    kind, so the host can run ahead without page-locking memory each step;
+    a slot is refilled only after its previous copy has finished."""
+
+    def __init__(self):
+        self.bufs, self.events, self.turn = {}, {}, 0
+
+    def next_turn(self) -> None:
+        self.turn ^= 1
+
+    def to_device(self, key: str, a: np.ndarray, dev) -> torch.Tensor:
+        src = torch.from_numpy(np.ascontiguousarray(a))
+        k = (key, self.turn)
+        buf = self.bufs.get(k)
+        if buf is None or buf.numel() < src.numel() or buf.dtype != src.dtype:
+            buf = torch.empty(max(src.numel(), 1), dtype=src.dtype, pin_memory=True)
+            self.bufs[k] = buf
+            self.events.pop(k, None)
+        ev = self.events.get(k)
+        if ev is not None:
+            ev.synchronize()
+        view = buf[:src.numel()].view(src.shape)
+        view.copy_(src)
+        out = view.to(dev, non_blocking=True)
+        e = torch.cuda.Event()
+        e.record(torch.cuda.current_stream(dev))
+        self.events[k] = e
+        return out
 
 
 class RenderStream:
@@ -325,6 +351,7 @@ class RenderStream:
         self.r, self.S, self.crop = renderer, scenes_per_batch, crop
         self.size = renderer.H
         self.rng = np.random.default_rng(seed)
+        self.staging = _PinnedStaging()
 
     @property
     def crops_per_batch(self) -> int:
@@ -335,10 +362,12 @@ class RenderStream:
         optics_list = [random_optics(self.rng, self.size) for _ in range(self.S)]
         soa_all, offsets = scenes.concat(soas)
         dev = self.r.device
-        imgs = self.r.batch(_to_device(soa_all, dev), offsets, optics_list)
+        st = self.staging
+        st.next_turn()
+        imgs = self.r.batch(st.to_device("soa", soa_all, dev), offsets, optics_list)
         x = pack_input(imgs, self.crop)
         tgt, mask = cell_targets(soas, optics_list, self.size, self.crop)
-        return x, _to_device(tgt, dev), _to_device(mask, dev)
+        return x, st.to_device("tgt", tgt, dev), st.to_device("mask", mask, dev)
 
 
 # ------------------------------------------------------------------ training
