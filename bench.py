@@ -454,6 +454,29 @@ def warm_start_in_child(local_rank: int):
     return result
 
 
+def convs_only(reps: int = 10) -> None:
+    """Per-launch times of the network's convolutions on a 64-crop batch
+    with the tcgen05 engine and with the warp-level MMA (random weights;
+    the kernels' work does not depend on their values)."""
+    import torch
+
+    from paper_2606_21381_gb300 import cnn
+    from paper_2606_21381_gb300.render import Renderer
+    dev = torch.device("cuda")
+    r = Renderer(512, 512, dev)
+    net = cnn.WarmStartNet(dev, seed=0)
+    x, _, _ = cnn.RenderStream(r, 16, 256, seed=5).next()
+    out = {}
+    for engine in ("tcgen05", "mma_sync"):
+        cnn.use_tcgen05(engine == "tcgen05")
+        out[engine] = conv_profile(net, x, reps)
+    cnn.use_tcgen05(True)
+    if cnn.sync_status() != 0:
+        raise RuntimeError("convolution status set")
+    print(json.dumps({"workload": "6-layer warm-start CNN, batch of 64 crops of 256x256",
+                      "conv_kernels": out}))
+
+
 def warm_start_bench(dev, samples: int = 200_000, seeds=(7, 9, 10)):
     """Learned warm start on the 512^2 inverse-rendering scene: train the
     network on `samples` rendered crops, then time the plain and the
@@ -668,6 +691,9 @@ def main():
     ap.add_argument("--impl", default="osog", choices=["osog", "reference"])
     ap.add_argument("--scenes", type=int, default=32,
                     help="scenes per batch (32 is the benchmarked workload)")
+    ap.add_argument("--convs-only", action="store_true",
+                    help="time the warm-start network's convolution kernels on one 64-crop "
+                         "batch (both tensor-core engines) and exit")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the learned warm-start benchmark (training + inverse solves)")
     ap.add_argument("--quick", action="store_true",
@@ -678,6 +704,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.convs_only:
+        convs_only()
+        return
     if args.impl == "reference":
         res = run_reference(args, rank, world)
     else:

@@ -70,8 +70,10 @@ int osog_conv2d_backward_filter(const osog_conv_shape_t *shape, const uint16_t *
  * calls of this process: 1 (default) the fifth-generation tensor cores
  * (tcgen05.mma with the accumulator in tensor memory), 0 the warp-level
  * MMA (mma.sync).  Both compute the same products in BF16 with FP32
- * accumulation; summation order inside the tensor core differs.  The
- * filter gradient always uses the warp-level MMA. */
+ * accumulation; summation order inside the tensor core differs.  With
+ * tcgen05 selected, forward convolutions whose reduction R S C is below 128
+ * still run on the warp-level MMA (faster there), and the filter gradient
+ * always does. */
 void osog_conv_use_tcgen05(int32_t enable);
 
 /* Synchronise `stream` and report a latched device error of the

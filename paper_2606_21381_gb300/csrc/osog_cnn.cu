@@ -427,24 +427,103 @@ __device__ __forceinline__ void cp16(void *dst, const __nv_bfloat16 *src, const 
                  : "memory");
 }
 
+// The operand copies of one thread.  Thread t copies the 8-element column
+// kv = t % 8 of every slice for the A rows t / 8 + 32 i (i < 4) and the B
+// rows t / 8 + 32 i below BNU.  The pixel of each A row is decoded once; the
+// tap and channel of the reduction entry j = k0 + 8 kv advance by UBK per
+// slice without divisions.
 template <int PASS>
-__device__ __forceinline__ void umma_load_stage(const Args &a, unsigned char *A, unsigned char *B,
-                                                int m0, int n0, int k0, int BNU, int tid) {
+struct UGather {
+    int kv;
+    int n[UM * UKC / UNT], y[UM * UKC / UNT], x[UM * UKC / UNT];  // n < 0: row past M
+    int t0, t1, ch;  // (r, s, c) forward, (r, s, k) data gradient, (ri, si, k) stride-2 class
+
+    __device__ __forceinline__ void init(const Args &a, int m0, int tid) {
+        const Geo &g = a.g;
+        kv = tid & 7;
+        const int cch = PASS == kFwd ? g.C : g.K, t1n = PASS == kDgrad2 ? a.ns : g.S;
+        const int j = kv * 8, tap = j / cch;
+        ch = j - tap * cch;
+        if (t1n > 0) {
+            t0 = tap / t1n;
+            t1 = tap - t0 * t1n;
+        } else {  // a parity class without taps: nothing to copy
+            t0 = 1 << 20;
+            t1 = 0;
+        }
 #pragma unroll
-    for (int i = 0; i < UM * UKC / UNT; ++i) {
-        const int v = tid + i * UNT, row = v >> 3, kv = v & 7;
-        const __nv_bfloat16 *src = PASS == kFwd     ? fwd_a_src(a, m0 + row, k0 + kv * 8)
-                                 : PASS == kDgrad ? dgrad_a_src(a, m0 + row, k0 + kv * 8)
-                                                  : dgrad2_a_src(a, m0 + row, k0 + kv * 8);
-        cp16(A + canon(row, kv * 8), src, a.x);
+        for (int i = 0; i < UM * UKC / UNT; ++i) {
+            const int m = m0 + (tid >> 3) + 32 * i;
+            n[i] = -1;
+            if (m >= a.M) continue;
+            if constexpr (PASS == kFwd) {
+                const int q = m % g.Q, t = m / g.Q, p = t % g.P;
+                n[i] = t / g.P;
+                y[i] = p * g.stride - g.pad;
+                x[i] = q * g.stride - g.pad;
+            } else if constexpr (PASS == kDgrad) {  // stride 1
+                const int w = m % g.W, t = m / g.W, h = t % g.H;
+                n[i] = t / g.H;
+                y[i] = h + g.pad;
+                x[i] = w + g.pad;
+            } else {
+                const int wi = m % a.Wc, t = m / a.Wc, hi = t % a.Hc;
+                n[i] = t / a.Hc;
+                y[i] = 2 * hi + a.ph + g.pad;
+                x[i] = 2 * wi + a.pw + g.pad;
+            }
+        }
     }
-    for (int v = tid; v < BNU * UKC; v += UNT) {
-        const int row = v >> 3, kv = v & 7;
-        const __nv_bfloat16 *src = PASS == kDgrad2 ? dgrad2_b_src(a, n0 + row, k0 + kv * 8)
-                                                   : rows_src(a.w, a.Ncols, a.Kred, n0 + row, k0 + kv * 8);
-        cp16(B + canon(row, kv * 8), src, a.w);
+
+    __device__ __forceinline__ void advance(const Args &a) {
+        const int cch = PASS == kFwd ? a.g.C : a.g.K, t1n = PASS == kDgrad2 ? a.ns : a.g.S;
+        ch += UBK;
+        while (ch >= cch) {
+            ch -= cch;
+            if (++t1 == t1n) {
+                t1 = 0;
+                ++t0;
+            }
+        }
     }
-}
+
+    __device__ __forceinline__ void load(const Args &a, unsigned char *A, unsigned char *B, int n0,
+                                         int k0, int BNU, int tid) const {
+        const Geo &g = a.g;
+        const bool live = t0 < (PASS == kDgrad2 ? a.nr : g.R);  // j < Kred
+        const int r = PASS == kDgrad2 ? a.rtap[live ? t0 : 0] : t0;
+        const int sx = PASS == kDgrad2 ? a.stap[t1] : t1;
+#pragma unroll
+        for (int i = 0; i < UM * UKC / UNT; ++i) {
+            const int row = (tid >> 3) + 32 * i;
+            const __nv_bfloat16 *src = nullptr;
+            if (live && n[i] >= 0) {
+                if constexpr (PASS == kFwd) {
+                    const int h = y[i] + r, w = x[i] + sx;
+                    if (h >= 0 && h < g.H && w >= 0 && w < g.W)
+                        src = a.x + (((size_t)n[i] * g.H + h) * g.W + w) * g.C + ch;
+                } else {
+                    const int p = PASS == kDgrad ? y[i] - r : (y[i] - r) >> 1;
+                    const int q = PASS == kDgrad ? x[i] - sx : (x[i] - sx) >> 1;
+                    if (p >= 0 && p < g.P && q >= 0 && q < g.Q)
+                        src = a.x + (((size_t)n[i] * g.P + p) * g.Q + q) * g.K + ch;
+                }
+            }
+            cp16(A + canon(row, kv * 8), src, a.x);
+        }
+        for (int row = tid >> 3; row < BNU; row += UNT / 8) {
+            const int b = n0 + row;
+            const __nv_bfloat16 *src = nullptr;
+            if (live && b < a.Ncols) {
+                if constexpr (PASS == kDgrad2)
+                    src = a.w + (((size_t)b * g.R + r) * g.S + sx) * g.K + ch;
+                else
+                    src = a.w + (size_t)b * a.Kred + k0 + kv * 8;
+            }
+            cp16(B + canon(row, kv * 8), src, a.w);
+        }
+    }
+};
 
 template <int PASS>
 __global__ void __launch_bounds__(UNT) k_conv_umma(const __grid_constant__ Args a, int BNU) {
@@ -467,9 +546,14 @@ __global__ void __launch_bounds__(UNT) k_conv_umma(const __grid_constant__ Args 
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     const int nk = (a.Kred + UBK - 1) / UBK;
+    UGather<PASS> ga;
+    ga.init(a, m0, tid);
     // prologue: stages 0 .. UST-2 in flight, one commit group each
     for (int kt = 0; kt < UST - 1; ++kt) {
-        if (kt < nk) umma_load_stage<PASS>(a, stA + kt * kUStage, stB + kt * bstage, m0, n0, kt * UBK, BNU, tid);
+        if (kt < nk) {
+            ga.load(a, stA + kt * kUStage, stB + kt * bstage, n0, kt * UBK, BNU, tid);
+            ga.advance(a);
+        }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -505,7 +589,8 @@ __global__ void __launch_bounds__(UNT) k_conv_umma(const __grid_constant__ Args 
         if (nx < nk) {
             const int sx = nx % UST;
             if (kt >= 1) ok = mbar_wait(smem_u32(mbar + sx), (uint32_t)(((kt - 1) / UST) & 1)) && ok;
-            umma_load_stage<PASS>(a, stA + sx * kUStage, stB + sx * bstage, m0, n0, nx * UBK, BNU, tid);
+            ga.load(a, stA + sx * kUStage, stB + sx * bstage, n0, nx * UBK, BNU, tid);
+            ga.advance(a);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
@@ -721,7 +806,9 @@ int osog_conv2d_forward(const osog_conv_shape_t *shape, const uint16_t *x, const
     a.Ncols = a.g.K;
     a.Kred = a.g.R * a.g.S * a.g.C;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (g_use_tcgen05) return status_of(launch_umma<kFwd>(a, st));
+    // reductions shorter than two slices feed the tensor cores too little per
+    // copied row (measured: the 8-channel first layer is faster on mma.sync)
+    if (g_use_tcgen05 && a.Kred >= 2 * UBK) return status_of(launch_umma<kFwd>(a, st));
     dim3 grid((a.M + BM - 1) / BM, (a.Ncols + BN - 1) / BN);
     k_conv_gemm<kFwd><<<grid, NT, 0, st>>>(a);
     return status_of(cudaGetLastError());
