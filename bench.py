@@ -544,19 +544,28 @@ def warm_start_bench(dev, samples: int = 200_000, seeds=(7, 9, 10)):
     }
 
 
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The largest value over all ranks (the slowest rank's timed region)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_step_per_rank: float, steps: int, world: int,
+                   max_ms: float) -> float:
+    """Whole-job units per second: every rank's units over the slowest
+    rank's time (weak scaling: each rank renders its own batch)."""
+    return units_per_step_per_rank * steps * world / (max_ms / 1e3)
+
+
 def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms, single40k,
            e2e_ms, launches, clocks, wall, K, soas=None, optics=None, fwd_bwd_ms=None,
            extra=None):
-    import torch
-    import torch.distributed as dist
-
-    # max over ranks of the timed region
-    t = torch.tensor([timed_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    timed_max = float(t.item())
-    frames = SCENES * args.steps * world
-    value = frames / (timed_max / 1e3)
+    timed_max = max_over_ranks(timed_ms, world, dev)
+    value = job_throughput(SCENES, args.steps, world, timed_max)
     if rank != 0:
         return None
 
