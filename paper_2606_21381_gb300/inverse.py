@@ -69,6 +69,34 @@ def filtered(img: torch.Tensor, mask: torch.Tensor) -> torch.Tensor:
     return torch.fft.irfft2(torch.fft.rfft2(img) * mask, s=img.shape[-2:])
 
 
+class SpectralMisfit:
+    """sum((filtered(img) - filtered(target))^2) / norm for the low-pass
+    masks of the curriculum, evaluated in the frequency domain (Parseval):
+    (1 / (H W norm)) sum over the rfft half-plane of w_k m_k |F(img)_k -
+    F(target)_k|^2, with w = 1 on the columns 0 and W/2 (their own
+    conjugates) and 2 elsewhere.  The target's spectrum and the squared
+    radii of the grid are computed once."""
+
+    def __init__(self, target: torch.Tensor, dx: float, norm: float):
+        H, W = target.shape[-2:]
+        dev = target.device
+        fy = torch.fft.fftfreq(H, dx, device=dev, dtype=torch.float64)[:, None]
+        fx = torch.fft.rfftfreq(W, dx, device=dev, dtype=torch.float64)[None, :]
+        self.r2 = fx * fx + fy * fy
+        w = torch.full((W // 2 + 1,), 2.0, device=dev, dtype=torch.float64)
+        w[0] = 1.0
+        if W % 2 == 0:
+            w[-1] = 1.0
+        self.w = w[None, :]
+        self.ft = torch.fft.rfft2(target)
+        self.scale = 1.0 / (H * W * norm)
+
+    def __call__(self, img: torch.Tensor, cutoff: float) -> torch.Tensor:
+        m = torch.where(self.r2 <= cutoff * cutoff, self.w, torch.zeros_like(self.w)).float()
+        d = torch.fft.rfft2(img) - self.ft
+        return (m * (d.real * d.real + d.imag * d.imag)).sum() * self.scale
+
+
 def spectral_loss(img: torch.Tensor, target: torch.Tensor, eps_rel: float = 1e-6) -> torch.Tensor:
     """Eq. 8: squared difference of the log amplitude spectra of the images
     (mean over the (K, H, W) frequencies).  The guard eps added inside the
@@ -144,11 +172,11 @@ def solve(target: torch.Tensor, soa0: np.ndarray, optics0: dict, renderer: Rende
     if truth_d is not None:
         res.history.append((0, 0.0, *_device_errors(x.detach(), truth_d).tolist()))
     ramp = max(1, int(cfg.steps * cfg.curriculum_frac))
+    misfit = SpectralMisfit(target, optics0["dx"], norm)
     for it in range(cfg.steps):
         na = cfg.na_start + (optics0["NA"] - cfg.na_start) * min(1.0, it / ramp)
-        mask = lowpass_mask(H, W, optics0["dx"], optics0["lambda_um"], na, dev)
         img = render(x, optics0, renderer, params)
-        loss = ((filtered(img, mask) - filtered(target, mask)) ** 2).sum() / norm
+        loss = misfit(img, 2.0 * na / optics0["lambda_um"])
         if cfg.spectral_weight:
             loss = loss + cfg.spectral_weight * spectral_loss(img, target)
         gx, gp = torch.autograd.grad(loss, (x, params), allow_unused=True)

@@ -31,3 +31,20 @@ def test_gradient_matches_central_differences():
         xm[idx] -= h
         fd = (float(spectral_loss(xp, t)) - float(spectral_loss(xm, t))) / (2 * h)
         assert abs(fd - float(gx[idx])) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_frequency_domain_misfit_equals_the_filtered_one():
+    # the solve's curriculum misfit, evaluated by Parseval on the rfft
+    # half-plane, equals the spatial sum of squared low-passed differences
+    from paper_2606_21381_gb300.inverse import SpectralMisfit, filtered, lowpass_mask
+    g = torch.Generator().manual_seed(3)
+    for H, W in ((32, 48), (64, 64), (16, 30)):
+        t = torch.rand((2, H, W), generator=g, dtype=torch.float64)
+        x = t + 0.3 * torch.rand((2, H, W), generator=g, dtype=torch.float64)
+        norm = float(t.numel())
+        mis = SpectralMisfit(t, 0.5, norm)
+        for na in (0.1, 0.25, 0.4):
+            mask = lowpass_mask(H, W, 0.5, 0.55, na, "cpu").double()
+            want = ((filtered(x, mask) - filtered(t, mask)) ** 2).sum() / norm
+            got = mis(x, 2.0 * na / 0.55)
+            assert abs(float(got) - float(want)) <= 1e-9 * max(1e-12, float(want)), (H, W, na)
