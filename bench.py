@@ -349,6 +349,29 @@ def run_gpu(args, rank, world, local_rank):
         if fb_r.sync_status(stream) != 0:
             raise RuntimeError("device status set in the forward + adjoint run")
         del img
+        # the same on one DIC 1024^2 image (4,000 particles, K = 1)
+        c1_soa, c1_o = scenes.dic_1024(0)
+        c1_r = Renderer(1024, 1024, dev)
+        c1_x = torch.from_numpy(c1_soa).to(dev)
+        c1_w = torch.randn((1, 1024, 1024), device=dev)
+        fb1_ms = []
+        for i in range(max(5, min(args.steps, 50)) + 3):
+            a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+            a.record(stream)
+            c1_r.render(c1_x, None, c1_o, stream=stream)
+            c1_r.backward(c1_x, None, c1_o, c1_w, stream=stream)
+            b.record(stream)
+            stream.synchronize()
+            if i >= 3:
+                fb1_ms.append(a.elapsed_time(b))
+        if c1_r.sync_status(stream) != 0:
+            raise RuntimeError("device status set in the DIC 1024 forward + adjoint run")
+        # bitwise determinism of the batched render: two renders, same bytes
+        step()
+        out2 = out.clone()
+        step()
+        deterministic = bool(torch.equal(out2, out))
+        del out2
     with torch.cuda.stream(stream):
         # ---- end to end from pinned host buffers through the public API:
         #      each step copies its particles in and its images out; the
@@ -392,7 +415,8 @@ def run_gpu(args, rank, world, local_rank):
                   single40k, e2e_ms, launches, clocks, wall, K, soas=soas, optics=optics,
                   fwd_bwd_ms=fb_ms, extra={"autotuned": tuned, "batched_modes_ms": modes_ms,
                                            "kernels_three_launch": prof3, "warm_start": warm,
-                                           "numa_node": numa_node,
+                                           "numa_node": numa_node, "fwd_bwd_dic1024_ms": fb1_ms,
+                                           "deterministic": deterministic,
                                            "e2e_pipelined": (n_pipe, pipe_s)})
 
 
@@ -627,7 +651,10 @@ def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms
         "fwd_bwd": None if not fwd_bwd_ms else {
             "ms": round(statistics.median(fwd_bwd_ms), 4),
             "workload": "512x512, 200 particles, brightfield + DIC: osog_render + "
-                        "osog_render_backward (recomputed forward, adjoint)"},
+                        "osog_render_backward (recomputed forward, adjoint)",
+            "dic_1024_ms": round(statistics.median(extra["fwd_bwd_dic1024_ms"]), 4),
+            "dic_1024_workload": "1024x1024, 4,000 particles, DIC (K = 1), defocus"},
+        "bitwise_deterministic": (extra or {}).get("deterministic"),
         "warm_start": (extra or {}).get("warm_start"),
         "gpu_launches": int(launches),
         "clocks": clocks.summary(),
@@ -653,6 +680,25 @@ def oracle_frames(soas, optics, budget_s: float, max_scenes: int, start: int = 0
     return done, parts, time.perf_counter() - t0
 
 
+def oracle_config_times(counts, soas, optics) -> dict:
+    """Seconds per frame of the oracle on the plain 256^2 scene, one DIC
+    1024^2 image and the 40,000-particle 2048^2 scene, on all host cores
+    and on one."""
+    import oracle
+    cases = {"plain_256": scenes.plain_256(),
+             "dic_1024_image": scenes.dic_1024(0),
+             "scene_2048_40k": (soas[int(np.argmax(counts))], optics[int(np.argmax(counts))])}
+    out = {}
+    for threads in (os.cpu_count(), 1):
+        oracle.set_threads(threads)
+        for name, (soa, o) in cases.items():
+            t0 = time.perf_counter()
+            oracle.render(soa, soa.shape[1], oracle.make_optics(**o))
+            out.setdefault(name, {})[f"s_{threads}_cores"] = round(time.perf_counter() - t0, 4)
+    oracle.set_threads(os.cpu_count())
+    return out
+
+
 def cpu_baseline(soas, optics, counts):
     import oracle
     oracle.build()
@@ -660,7 +706,8 @@ def cpu_baseline(soas, optics, counts):
     return {"value": round(n / dt, 4), "unit": "frames/s", "cores": os.cpu_count(),
             "kind": "oracle", "particles_per_s": round(parts / dt, 1),
             "sample": f"{n} of the {SCENES} scenes ({parts} particles), FP64 C oracle, "
-                      f"OpenMP over FFT lines, {dt:.1f} s"}
+                      f"OpenMP over FFT lines, {dt:.1f} s",
+            "per_config": oracle_config_times(counts, soas, optics)}
 
 
 def run_reference(args, rank, world):

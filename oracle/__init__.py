@@ -92,6 +92,7 @@ def _load():
         lib.orc_normal.restype = ctypes.c_double
         lib.orc_sensor_noise.argtypes = [ctypes.POINTER(ctypes.c_float), i64, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_uint64, d]
+        lib.orc_set_threads.argtypes = [i32]
         lib.orc_dic_incoherent.argtypes = [ctypes.POINTER(_Optics), d, d, d]
         lib.orc_opd_att_poly.argtypes = [d, i64, i32, i32, i32, ctypes.c_double,
                                          ctypes.c_double, i32, d, d, d, d]
@@ -263,6 +264,11 @@ def render_dic_incoherent(soa: np.ndarray, n: int, o: dict) -> np.ndarray:
     dic_incoherent."""
     opd, att = opd_att(soa, n, o["H"], o["W"], o["dx"], o["bevel_slope"])
     return dic_incoherent(o, field(opd, att, o["lambda_um"]))
+
+
+def set_threads(n: int) -> None:
+    """Number of OpenMP threads of the oracle's parallel loops."""
+    _load().orc_set_threads(int(n))
 
 
 def philox4x32(ctr, key) -> tuple:

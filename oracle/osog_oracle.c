@@ -864,3 +864,16 @@ void orc_sensor_noise(const float *img, int64_t count, double g, double sigma,
         out[i] = ((double)orc_poisson(lam, seed, i) + sigma * orc_normal(seed, i)) / g;
     }
 }
+
+/* Threads of the OpenMP loops above (timing on one core or all). */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
