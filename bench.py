@@ -147,6 +147,33 @@ RENDER_SOURCES = ("osog_api.cu", "osog_bin.cu", "osog_render.cu", "osog_common.c
                   "osog_fft.cuh", "osog_strip.cuh", "osog_kernels.h")
 
 
+def ncu_instructions(kernel: str):
+    """Warp instructions per launch of `kernel` from the committed ncu
+    summary, if taken on the current render sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_instructions.txt")
+    if not os.path.exists(path):
+        return None
+    digest = source_digest()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel \
+                and parts[1] == digest:
+            return float(parts[2])
+    return None
+
+
+def issue_peak_ginst():
+    """Warp-instruction issue peak (G/s): one warp instruction per clock
+    on each of the 4 sub-partitions of the 152 SMs at the measured maximum
+    SM clock."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        mhz = 2070.0
+    return 4 * 152 * mhz / 1e3
+
+
 def source_digest() -> str:
     """Hash of the sources the render kernels and their launches are built
     from (the convolution and noise kernels do not enter)."""
@@ -568,6 +595,23 @@ def warm_start_bench(dev, samples: int = 200_000, seeds=(7, 9, 10)):
     }
 
 
+def issue_roofline(kernels: dict):
+    """The bound the render kernels actually meet: warp instructions per
+    launch (committed ncu counts) over the live launch time, against the
+    issue peak."""
+    peak = issue_peak_ginst()
+    out = {}
+    for k in ("strip_forward", "column", "strip_inverse"):
+        inst = ncu_instructions(k)
+        if inst is None or k not in kernels:
+            continue
+        rate = inst / (kernels[k]["ms_per_launch"] / 1e3) / 1e9
+        out[k] = {"warp_instructions": inst, "achieved_ginst_s": round(rate, 1),
+                  "frac": round(rate / peak, 4)}
+    return {"bound": "issue", "unit": "G warp-instructions/s", "peak": round(peak, 1),
+            "kernels": out} if out else None
+
+
 def max_over_ranks(value: float, world: int, device) -> float:
     """The largest value over all ranks (the slowest rank's timed region)."""
     import torch
@@ -622,6 +666,7 @@ def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms
                      "traffic": traffic, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": bytes_dom,
                      "pupil_active_columns": round(act, 4)},
+        "issue_roofline": issue_roofline(kernels),
         "step_roofline": {"algorithmic_bytes": step_bytes,
                           "achieved_gbs": round(step_bytes / (ms_step / 1e3) / 1e9, 1),
                           "frac": round(step_bytes / (ms_step / 1e3) / 1e9 / peak, 4)},
