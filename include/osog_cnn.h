@@ -66,14 +66,16 @@ int osog_conv2d_backward_filter(const osog_conv_shape_t *shape, const uint16_t *
                                 const uint16_t *x, float *dw, float *dbias, void *ws,
                                 size_t ws_bytes, osog_stream_t stream);
 
-/* Engine of osog_conv2d_forward and osog_conv2d_backward_data for later
+/* Engine of osog_conv2d_forward, osog_conv2d_backward_data and
+ * osog_conv2d_backward_filter for later
  * calls of this process: 1 (default) the fifth-generation tensor cores
  * (tcgen05.mma with the accumulator in tensor memory), 0 the warp-level
  * MMA (mma.sync).  Both compute the same products in BF16 with FP32
  * accumulation; summation order inside the tensor core differs.  With
  * tcgen05 selected, forward convolutions whose reduction R S C is below 128
- * still run on the warp-level MMA (faster there), and the filter gradient
- * always does. */
+ * and filter gradients with fewer than 128 output channels still run on
+ * the warp-level MMA (faster there).  The switch also covers
+ * osog_conv2d_backward_filter. */
 void osog_conv_use_tcgen05(int32_t enable);
 
 /* Synchronise `stream` and report a latched device error of the

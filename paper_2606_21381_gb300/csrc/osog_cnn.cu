@@ -1,8 +1,9 @@
 // Convolutions of the learned warm start as implicit GEMMs on the tensor
-// cores (BF16 operands, FP32 accumulation): forward and data gradients on
-// tcgen05 (TMEM accumulators, shared-memory descriptors, mbarrier
-// completion), filter gradients on the warp-level MMA (mma.sync), which
-// also remains selectable for the other two.
+// cores (BF16 operands, FP32 accumulation): on tcgen05 (TMEM accumulators,
+// shared-memory descriptors, mbarrier completion) where it is faster --
+// forward and data gradients, and filter gradients with at least 128
+// output channels -- and on the warp-level MMA (mma.sync) otherwise; the
+// warp-level path stays selectable for all three.
 //
 //   forward  Y[m = (n,p,q)][k]   = sum_{j = (r,s,c)} X(im2col)[m][j] W[k][j]
 //   data     dX[m = (n,h,w)][c]  = sum_{j = (r,s,k)} dY(gathered)[m][j] Wt[c][j]
@@ -405,8 +406,18 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
 
 // kind::f16 instruction descriptor: FP32 D, BF16 A and B, both K-major,
 // N >> 3 and M >> 4.
-__device__ __forceinline__ uint32_t umma_idesc(int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+__device__ __forceinline__ uint32_t umma_idesc(int n, bool mn_major = false) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (mn_major ? (1u << 15) | (1u << 16) : 0u) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+}
+
+// MN-major canonical layout (both operands of the filter gradient): core
+// matrices of 8 reduction rows x 16 bytes (8 consecutive MN elements),
+// contiguous along the reduction (LBO 128 bytes), 8-element MN groups
+// UKC core matrices apart (SBO 1024 bytes) -- the same strides as the
+// K-major tiles, with the transpose bits of the instruction descriptor set.
+__device__ __forceinline__ int canon_mn(int mn, int k) {
+    return (mn >> 3) * (UKC * 128) + (k >> 3) * 128 + (k & 7) * 16 + (mn & 7) * 2;
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
@@ -644,6 +655,172 @@ __global__ void __launch_bounds__(UNT) k_conv_umma(const __grid_constant__ Args 
                      : "memory");
 }
 
+// Filter gradient on tcgen05: dW[k][j] = sum over pixels of dY[pixel][k]
+// X(im2col)[pixel][j] with the output channels k as the 128 GEMM rows
+// (zero past K), the filter entries j = (r, s, c) as up to 128 columns and
+// the pixels as the reduction, in chunks of kSplitPixels per CTA (grid.z)
+// whose partial tiles are summed in chunk order.  Both operands are copied
+// from NHWC rows as 16-byte vectors (8 channels of one pixel) into the
+// MN-major layout.
+__global__ void __launch_bounds__(UNT) k_wgrad_umma(const __grid_constant__ Args a, int BNU) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int bstage = BNU * UBK * 2;
+    unsigned char *stA = sm, *stB = sm + UST * kUStage;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(stB + UST * bstage);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + UST);
+    const Geo &g = a.g;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * UM, n0 = blockIdx.y * BNU;
+    const int pbeg = blockIdx.z * kSplitPixels;
+    const int pend = min(a.Kred, pbeg + kSplitPixels);
+    const uint32_t ncols = BNU <= 32 ? 32u : BNU <= 64 ? 64u : 128u;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                     :: "r"(smem_u32(tslot)), "r"(ncols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int st = 0; st < UST; ++st)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(smem_u32(mbar + st)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    const int nk = (pend - pbeg + UBK - 1) / UBK;
+    // Copies of slice kt.  Thread t owns channel group t % 16 of the 128
+    // rows (A: 8 output channels) and of the 128 columns (B: 8 channels of
+    // one tap, decoded once) and the pixels t / 16 + 16 i (i < 4) of every
+    // slice, whose coordinates advance by UBK per slice without divisions;
+    // consecutive threads read consecutive channel groups of one pixel.
+    constexpr int NV = UBK * 16 / UNT;  // pixels per thread and slice
+    const int grp = tid & 15, kq = tid >> 4;
+    const int m = m0 + grp * 8;
+    const int j = n0 + grp * 8;
+    const bool jok = j < a.Ncols;
+    int tr = 0, ts = 0, tc = 0;
+    if (jok) {
+        const int rs = j / g.C;
+        tc = j - rs * g.C;
+        tr = rs / g.S;
+        ts = rs - tr * g.S;
+    }
+    int pn[NV], pp[NV], pq[NV];  // image, output row, output column of each pixel
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        const int pix = pbeg + kq + 16 * i;
+        pq[i] = pix % g.Q;
+        const int t = pix / g.Q;
+        pp[i] = t % g.P;
+        pn[i] = t / g.P;
+    }
+    auto load = [&](int kt, int st) {
+        unsigned char *A = stA + st * kUStage, *B = stB + st * bstage;
+        const int p0 = pbeg + kt * UBK;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const int k = kq + 16 * i, pix = p0 + k;
+            const bool live = pix < pend;
+            const __nv_bfloat16 *sa = live && m < a.M ? a.x + (size_t)pix * g.K + m : nullptr;
+            cp16(A + canon_mn(grp * 8, k), sa, a.x);
+            const __nv_bfloat16 *sb = nullptr;
+            if (live && jok) {
+                const int h = pp[i] * g.stride + tr - g.pad, w = pq[i] * g.stride + ts - g.pad;
+                if (h >= 0 && h < g.H && w >= 0 && w < g.W)
+                    sb = a.w + (((size_t)pn[i] * g.H + h) * g.W + w) * g.C + tc;
+            }
+            cp16(B + canon_mn(grp * 8, k), sb, a.w);
+            // next slice: UBK pixels further
+            pq[i] += UBK;
+            while (pq[i] >= g.Q) {
+                pq[i] -= g.Q;
+                if (++pp[i] == g.P) {
+                    pp[i] = 0;
+                    ++pn[i];
+                }
+            }
+        }
+    };
+    for (int kt = 0; kt < UST - 1; ++kt) {
+        if (kt < nk) load(kt, kt);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t taddr = *tslot;
+    const uint32_t idesc = umma_idesc(BNU, true);
+    bool ok = true;
+    for (int kt = 0; kt < nk; ++kt) {
+        const int st = kt % UST;
+        asm volatile("cp.async.wait_group %0;\n" :: "n"(UST - 2) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            unsigned char *A = stA + st * kUStage, *B = stB + st * bstage;
+#pragma unroll
+            for (int s = 0; s < UBK / 16; ++s) {
+                const uint64_t ad = umma_desc(smem_u32(A) + s * 256);
+                const uint64_t bd = umma_desc(smem_u32(B) + s * 256);
+                const uint32_t acc = (kt > 0 || s > 0) ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             :: "r"(taddr), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                         :: "r"(smem_u32(mbar + st)) : "memory");
+        }
+        const int nx = kt + UST - 1;
+        if (nx < nk) {
+            const int sx = nx % UST;
+            if (kt >= 1) ok = mbar_wait(smem_u32(mbar + sx), (uint32_t)(((kt - 1) / UST) & 1)) && ok;
+            load(nx, sx);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    if (nk > 0) {
+        const int last = nk - 1;
+        ok = mbar_wait(smem_u32(mbar + last % UST), (uint32_t)((last / UST) & 1)) && ok;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (!ok && lane == 0) atomicExch(&g_cnn_status, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const int quarter = warp & 3, group = warp >> 2;
+    const int row = m0 + quarter * 32 + lane;  // output channel
+    float *part = a.part + (size_t)blockIdx.z * a.M * a.Ncols;
+    for (int c0 = group * 32; c0 < BNU; c0 += 32 * (UNT / 128)) {
+        uint32_t v[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+            "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+              "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+              "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+              "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+              "=r"(v[31])
+            : "r"(taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (row < a.M) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+                const int col = n0 + c0 + j;
+                if (c0 + j < BNU && col < a.Ncols) {  // Ncols is a multiple of 8
+                    const float f0 = nk ? __uint_as_float(v[j]) : 0.f;
+                    const float f1 = nk ? __uint_as_float(v[j + 1]) : 0.f;
+                    const float f2 = nk ? __uint_as_float(v[j + 2]) : 0.f;
+                    const float f3 = nk ? __uint_as_float(v[j + 3]) : 0.f;
+                    *reinterpret_cast<float4 *>(part + (size_t)row * a.Ncols + col) =
+                        make_float4(f0, f1, f2, f3);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(taddr), "r"(ncols)
+                     : "memory");
+}
+
 constexpr int kUmmaSmem = 2 * UST * kUStage + 64;  // the largest (BNU = 128)
 __host__ __device__ constexpr int umma_smem(int bnu) { return UST * (kUStage + bnu * UBK * 2) + 64; }
 
@@ -658,6 +835,9 @@ cudaError_t umma_prepare() {
         if (r == cudaSuccess)
             r = cudaFuncSetAttribute(k_conv_umma<kDgrad2>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k_wgrad_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kUmmaSmem);
         return r;
     }();
     return e;
@@ -890,8 +1070,16 @@ int osog_conv2d_backward_filter(const osog_conv_shape_t *shape, const uint16_t *
     a.Ncols = g.R * g.S * g.C;
     a.Kred = g.N * g.P * g.Q;
     const int splits = splits_of(g);
-    dim3 grid((a.M + BM - 1) / BM, (a.Ncols + BN - 1) / BN, splits);
-    k_conv_gemm<kWgrad><<<grid, NT, 0, st>>>(a);
+    // tcgen05 for 128 or more output channels (fewer would pad the 128 rows)
+    if (g_use_tcgen05 && a.M >= UM) {
+        const cudaError_t e = umma_prepare();
+        if (e != cudaSuccess) return status_of(e);
+        dim3 grid((a.M + UM - 1) / UM, (a.Ncols + 127) / 128, splits);
+        k_wgrad_umma<<<grid, UNT, umma_smem(128), st>>>(a, 128);
+    } else {
+        dim3 grid((a.M + BM - 1) / BM, (a.Ncols + BN - 1) / BN, splits);
+        k_conv_gemm<kWgrad><<<grid, NT, 0, st>>>(a);
+    }
     const int64_t count = (int64_t)a.M * a.Ncols;
     k_sum_splits<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(a.part, splits, count, dw);
     const int64_t pixels = (int64_t)g.N * g.P * g.Q;
