@@ -336,13 +336,13 @@ __global__ void __launch_bounds__(kThreads, MULTI ? 1 : 2) k_persistent(const __
         __syncthreads();
         if (stage == 3) break;
         if (stage == 0) {
-            strip_forward_item<N, kStripRender>(a.sa, s, idx, smem_raw);
+            strip_forward_item<N, kStripRender, true>(a.sa, s, idx, smem_raw);
         } else if (stage == 1) {
             wait_count(doneA + s, na, a.sa.w.status);
-            column_item<N, MULTI>(a.ca, s, idx, smem_raw);
+            column_item<N, MULTI, true>(a.ca, s, idx, smem_raw);
         } else {
             wait_count(doneB + s, nb, a.sa.w.status);
-            inverse_item<N>(a.ia, s * K + idx / na, idx % na, smem_raw);
+            inverse_item<N, true>(a.ia, s * K + idx / na, idx % na, smem_raw);
         }
         __syncthreads();
         if (threadIdx.x == 0 && stage < 2) {
