@@ -363,7 +363,20 @@ def run_gpu(args, rank, world, local_rank):
         fb_r = Renderer(512, 512, dev)
         fb_x = torch.from_numpy(fb_soa).to(dev)
         fb_w = torch.randn((2, 512, 512), device=dev)
-        fb_ms = []
+        # one training step's pair of calls: the forward keeps its
+        # intermediates (osog_render_keep), the adjoint reads them
+        # (osog_render_backward_kept); and the pair that recomputes them
+        fb_ms, fb_re_ms = [], []
+        fb_ws = None
+        for i in range(max(5, min(args.steps, 50)) + 3):
+            a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+            a.record(stream)
+            img, fb_ws = fb_r.render_keep(fb_x, None, fb_o, ws=fb_ws, stream=stream)
+            fb_r.backward_kept(fb_x, None, fb_o, fb_w, fb_ws, stream=stream)
+            b.record(stream)
+            stream.synchronize()
+            if i >= 3:
+                fb_ms.append(a.elapsed_time(b))
         for i in range(max(5, min(args.steps, 50)) + 3):
             a, b = torch.cuda.Event(True), torch.cuda.Event(True)
             a.record(stream)
@@ -372,7 +385,7 @@ def run_gpu(args, rank, world, local_rank):
             b.record(stream)
             stream.synchronize()
             if i >= 3:
-                fb_ms.append(a.elapsed_time(b))
+                fb_re_ms.append(a.elapsed_time(b))
         if fb_r.sync_status(stream) != 0:
             raise RuntimeError("device status set in the forward + adjoint run")
         del img
@@ -382,11 +395,12 @@ def run_gpu(args, rank, world, local_rank):
         c1_x = torch.from_numpy(c1_soa).to(dev)
         c1_w = torch.randn((1, 1024, 1024), device=dev)
         fb1_ms = []
+        c1_ws = None
         for i in range(max(5, min(args.steps, 50)) + 3):
             a, b = torch.cuda.Event(True), torch.cuda.Event(True)
             a.record(stream)
-            c1_r.render(c1_x, None, c1_o, stream=stream)
-            c1_r.backward(c1_x, None, c1_o, c1_w, stream=stream)
+            _, c1_ws = c1_r.render_keep(c1_x, None, c1_o, ws=c1_ws, stream=stream)
+            c1_r.backward_kept(c1_x, None, c1_o, c1_w, c1_ws, stream=stream)
             b.record(stream)
             stream.synchronize()
             if i >= 3:
@@ -443,6 +457,7 @@ def run_gpu(args, rank, world, local_rank):
                   fwd_bwd_ms=fb_ms, extra={"autotuned": tuned, "batched_modes_ms": modes_ms,
                                            "kernels_three_launch": prof3, "warm_start": warm,
                                            "numa_node": numa_node, "fwd_bwd_dic1024_ms": fb1_ms,
+                                           "fwd_bwd_recompute_ms": fb_re_ms,
                                            "deterministic": deterministic,
                                            "e2e_pipelined": (n_pipe, pipe_s)})
 
@@ -695,8 +710,10 @@ def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms
                 "host_numa_node": extra.get("numa_node")},
         "fwd_bwd": None if not fwd_bwd_ms else {
             "ms": round(statistics.median(fwd_bwd_ms), 4),
-            "workload": "512x512, 200 particles, brightfield + DIC: osog_render + "
-                        "osog_render_backward (recomputed forward, adjoint)",
+            "workload": "512x512, 200 particles, brightfield + DIC: osog_render_keep + "
+                        "osog_render_backward_kept (forward intermediates kept, adjoint)",
+            "ms_recomputed": round(statistics.median(extra["fwd_bwd_recompute_ms"]), 4),
+            "recomputed": "osog_render + osog_render_backward (the adjoint recomputes the forward)",
             "dic_1024_ms": round(statistics.median(extra["fwd_bwd_dic1024_ms"]), 4),
             "dic_1024_workload": "1024x1024, 4,000 particles, DIC (K = 1), defocus"},
         "bitwise_deterministic": (extra or {}).get("deterministic"),

@@ -123,8 +123,10 @@ typedef struct {
  *                       items from a device queue (square canvases only);
  *                       -1: three launches (default)
  *   band_rows           rows per binning band (the raster's tile height): a
- *                       multiple of the strip height 8192 / W that divides H
- *                       and gives at most 64 bands; 0 = smallest such value
+ *                       multiple of the strip height R that divides H and
+ *                       gives at most 64 bands (R = 8192 / W rows for
+ *                       W >= 1024, 4 for 128 <= W <= 512, 512 / W below);
+ *                       0 = the default max(H / 64, 16, R)
  */
 typedef struct {
     int32_t pairs_per_particle;
@@ -272,6 +274,36 @@ int osog_render_backward(osog_plan_t *plan, const float *soa, int64_t ld, int32_
                          const osog_optics_t *optics, const float *grad_image,
                          float *grad_soa, float *grad_optics, void *ws, size_t ws_bytes,
                          osog_stream_t stream);
+
+/*
+ * The forward render and its adjoint with the forward intermediates kept
+ * between the two calls instead of recomputed (the usual way a training or
+ * inverse-rendering step runs: one forward, then one backward).
+ *
+ * osog_render_keep writes the images exactly as osog_render does (same
+ * arguments, same results) and leaves the particle records, band bins and
+ * filtered spectra of the scene in ws, which must hold
+ * osog_backward_workspace_size(plan, n, K) bytes.
+ *
+ * osog_render_backward_kept then computes what osog_render_backward computes
+ * (same arguments, same results) from that state.  It accepts only the ws
+ * pointer and size, soa pointer, ld, n and optics (compared field by field)
+ * of an earlier osog_render_keep on this plan, and fails with
+ * OSOG_ERR_INVALID_ARG otherwise.  Any other call of this plan that writes
+ * the same ws drops the state, and the adjoint consumes it: a second
+ * backward needs a new osog_render_keep (or osog_render_backward, which
+ * recomputes).  The caller keeps the particle values and ws untouched
+ * between the two calls; a changed particle tensor at the same address is
+ * not detected.  The plan remembers the states of its last 64 workspaces.  Errors
+ * otherwise as for osog_render and osog_render_backward.
+ */
+int osog_render_keep(osog_plan_t *plan, const float *soa, int64_t ld, int32_t n,
+                     const osog_optics_t *optics, float *image, void *ws, size_t ws_bytes,
+                     osog_stream_t stream);
+int osog_render_backward_kept(osog_plan_t *plan, const float *soa, int64_t ld, int32_t n,
+                              const osog_optics_t *optics, const float *grad_image,
+                              float *grad_soa, float *grad_optics, void *ws, size_t ws_bytes,
+                              osog_stream_t stream);
 
 /*
  * Batched forward render of S scenes that share the plan's H x W and the

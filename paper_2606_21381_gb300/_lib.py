@@ -24,7 +24,8 @@ EXPORTS = ("osog_plan_create", "osog_plan_destroy", "osog_workspace_size", "osog
            "osog_render_opd", "osog_optics_from_opd", "osog_batch_submit",
            "osog_sync_status", "osog_last_error", "osog_plan_launch_count",
            "osog_profile_begin", "osog_profile_end", "osog_render_noalloc",
-           "osog_backward_workspace_size", "osog_render_backward", "osog_autotune",
+           "osog_backward_workspace_size", "osog_render_backward", "osog_render_keep",
+           "osog_render_backward_kept", "osog_autotune",
            "osog_polyhedra_workspace_size", "osog_render_polyhedra",
            "osog_dic_incoherent_workspace_size", "osog_render_dic_incoherent",
            "osog_sensor_noise")
@@ -125,6 +126,10 @@ def lib(build_if_missing: bool = True):
     L.osog_backward_workspace_size.restype = sz
     L.osog_render_backward.argtypes = [vp, vp, i64, i32, P(Optics), vp, vp, vp, vp, sz, vp]
     L.osog_render_backward.restype = ctypes.c_int
+    L.osog_render_keep.argtypes = [vp, vp, i64, i32, P(Optics), vp, vp, sz, vp]
+    L.osog_render_keep.restype = ctypes.c_int
+    L.osog_render_backward_kept.argtypes = [vp, vp, i64, i32, P(Optics), vp, vp, vp, vp, sz, vp]
+    L.osog_render_backward_kept.restype = ctypes.c_int
     L.osog_autotune.argtypes = [vp, vp, i64, P(i32), i32, P(Optics), vp, vp, sz, vp, P(Tuning)]
     L.osog_autotune.restype = ctypes.c_int
     L.osog_render_noalloc.argtypes = [vp, i64, i32, P(Optics), vp, vp]

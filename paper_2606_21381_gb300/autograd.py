@@ -1,5 +1,6 @@
 """Differentiable rendering: the forward render and its hand-written
-adjoint (osog_render / osog_render_backward) as a torch.autograd.Function.
+adjoint (osog_render_keep / osog_render_backward_kept) as a
+torch.autograd.Function.
 
 The paper's pipeline is differentiable end to end so that dI/dTheta drives
 inverse rendering (Sec. III.C, Sec. IV.B).  Here the particle tensor and the
@@ -30,17 +31,26 @@ class RenderFunction(torch.autograd.Function):
     def forward(ctx, soa, optics_params, renderer: Renderer, optics: dict):
         o = optics_with(optics, optics_params)
         soa_c = soa.detach().contiguous()
-        img = renderer.render(soa_c, None, o)
+        if any(ctx.needs_input_grad[:2]):
+            # the forward intermediates stay in a workspace of this call's
+            # own, so the adjoint need not recompute them
+            img, ws = renderer.render_keep(soa_c, None, o)
+        else:
+            img, ws = renderer.render(soa_c, None, o), None
         ctx.save_for_backward(soa_c)
-        ctx.renderer, ctx.optics = renderer, o
+        ctx.renderer, ctx.optics, ctx.ws = renderer, o, ws
         ctx.params_meta = (optics_params.dtype, optics_params.device)
         return img
 
     @staticmethod
     def backward(ctx, grad_image):
         (soa,) = ctx.saved_tensors
-        gsoa, gopt = ctx.renderer.backward(soa, None, ctx.optics,
-                                           grad_image.contiguous().float())
+        g = grad_image.contiguous().float()
+        if ctx.ws is not None:
+            gsoa, gopt = ctx.renderer.backward_kept(soa, None, ctx.optics, g, ctx.ws)
+            ctx.ws = None  # consumed: a second backward recomputes the forward
+        else:
+            gsoa, gopt = ctx.renderer.backward(soa, None, ctx.optics, g)
         dtype, device = ctx.params_meta
         return gsoa, gopt.to(device=device, dtype=dtype), None, None
 

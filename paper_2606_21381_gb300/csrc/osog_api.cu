@@ -37,6 +37,16 @@ struct osog_plan {
     cudaGraphExec_t gexec = nullptr;
     std::vector<unsigned char> gkey;
     int64_t graph_kernels = 0;
+    // forward states left by osog_render_keep, by workspace
+    struct Kept {
+        void *ws;
+        size_t ws_bytes;
+        const float *soa;
+        int64_t ld;
+        int32_t n;
+        osog_optics_t optics;
+    };
+    std::vector<Kept> kept;
 };
 
 namespace {
@@ -58,6 +68,7 @@ int popcount3(uint32_t m) { return (int)(m & 1u) + (int)((m >> 1) & 1u) + (int)(
 
 constexpr int kDefaultPairs = 8;
 constexpr int kMaxTimed = 8192;
+constexpr size_t kMaxKept = 64;  // forward states remembered per plan
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -365,6 +376,165 @@ BwdLayout make_bwd_layout(const Geometry &geo, int64_t n, int64_t chunks, int K,
     return b;
 }
 
+// One scene's forward pass laid out for the adjoint: the launch group, the
+// carved work regions and the adjoint's partial buffers.
+struct BwdState {
+    BwdLayout bl;
+    GroupDev gd;
+    SceneDev sc;
+    Work w;
+    float *part, *opart;
+    int K;
+    int64_t chunks;
+};
+
+int bwd_setup(osog_plan *p, const float *soa, int64_t ld, int32_t n, const osog_optics_t *optics,
+              void *ws, size_t ws_bytes, BwdState &b) {
+    if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    int rc = check_optics(p, optics);
+    if (rc) return rc;
+    if (n < 0 || (int64_t)n > ld) return fail(OSOG_ERR_INVALID_ARG, "need 0 <= n <= ld");
+    if (n > 0 && !soa) return fail(OSOG_ERR_INVALID_ARG, "soa is NULL");
+    b.K = popcount3(optics->modes);
+    b.chunks = (n + kChunk - 1) / kChunk;
+    const int ppp = kDefaultPairs;
+    b.bl = make_bwd_layout(p->geo, n, b.chunks, b.K, ppp);
+    rc = check_ws(ws, b.bl.total, ws_bytes);
+    if (rc) return rc;
+    b.gd = GroupDev{};
+    b.gd.S = 1;
+    b.gd.K = b.K;
+    b.gd.nchunks = (int32_t)b.chunks;
+    b.sc = scene_dev(*optics);
+    b.sc.p0 = 0;
+    b.sc.n = n;
+    b.sc.chunk0 = 0;
+    b.sc.pair0 = 0;
+    b.sc.pair_cap = (int32_t)((int64_t)n * ppp);
+    b.gd.sc[0] = b.sc;
+    for (int bit = 0, k = 0; bit < 3; ++bit)
+        if (optics->modes & (1u << bit)) b.gd.md[0][k++] = mode_dev(*optics, 1u << bit);
+    b.w = carve(ws, b.bl.fwd, p->status);
+    b.w.slotmap = reinterpret_cast<int32_t *>(static_cast<char *>(ws) + b.bl.slotmap);
+    b.w.slotmap_ppp = ppp;
+    b.part = reinterpret_cast<float *>(static_cast<char *>(ws) + b.bl.part);
+    b.opart = reinterpret_cast<float *>(static_cast<char *>(ws) + b.bl.opart);
+    return OSOG_OK;
+}
+
+int bwd_check_grads(const float *grad_image, const float *grad_soa, const float *grad_optics,
+                    int32_t n) {
+    if (n > 0 && !grad_soa) return fail(OSOG_ERR_INVALID_ARG, "grad_soa is NULL");
+    if (!grad_image || !grad_optics) return fail(OSOG_ERR_INVALID_ARG, "grad_image or grad_optics is NULL");
+    return OSOG_OK;
+}
+
+// Forward pass into the adjoint's layout: binning (with the slot map), the
+// strip and column passes up to the filtered columns Q_m, and, when image is
+// given, the inverse strip pass that writes the images.
+int bwd_forward(osog_plan *p, const float *soa, int64_t ld, const BwdState &b, float *image,
+                cudaStream_t st) {
+    const Geometry &geo = p->geo;
+    int rc = run_kernel(p, OSOG_KERNEL_BIN_COUNT, st,
+                        [&] { return launch_bin_count(soa, ld, b.gd, geo, b.w, st); });
+    if (rc) return rc;
+    rc = run_kernel(p, OSOG_KERNEL_BIN_SCAN, st, [&] { return launch_bin_scan(b.gd, geo, b.w, st); });
+    if (rc) return rc;
+    rc = run_kernel(p, OSOG_KERNEL_BIN_FILL, st, [&] { return launch_bin_fill(b.gd, geo, b.w, st); });
+    if (rc) return rc;
+    StripArgs sa{};
+    sa.geo = geo;
+    sa.w = b.w;
+    sa.tw = p->tw_w;
+    sa.S = 1;
+    sa.sc[0] = b.sc;
+    rc = run_kernel(p, OSOG_KERNEL_STRIP_FORWARD, st, [&] { return launch_strip_forward(sa, kStripRender, st); });
+    if (rc) return rc;
+    ColumnArgs ca{};
+    ca.geo = geo;
+    ca.w = b.w;
+    ca.tw = p->tw_h;
+    ca.S = 1;
+    ca.K = b.K;
+    for (int k = 0; k < b.K; ++k) ca.md[0][k] = b.gd.md[0][k];
+    rc = run_kernel(p, OSOG_KERNEL_COLUMN, st, [&] { return launch_column(ca, st); });
+    if (rc || !image) return rc;
+    InverseArgs ia{};
+    ia.geo = geo;
+    ia.w = b.w;
+    ia.tw = p->tw_w;
+    ia.images = image;
+    ia.S = 1;
+    ia.K = b.K;
+    return run_kernel(p, OSOG_KERNEL_STRIP_INVERSE, st, [&] { return launch_strip_inverse(ia, st); });
+}
+
+// The adjoint passes over a forward state left in the workspace by
+// bwd_forward: dL/dI -> dL/dQ_m (rows), -> dL/dG and the optics partials
+// (columns), -> per-(band slot, strip) particle partials (strips), and the
+// fixed-order sums into grad_soa and grad_optics.
+int bwd_adjoint(osog_plan *p, const BwdState &b, const float *grad_image, float *grad_soa,
+                int64_t ld, float *grad_optics, cudaStream_t st) {
+    const Geometry &geo = p->geo;
+    BwdRowsArgs ra{};
+    ra.geo = geo;
+    ra.w = b.w;
+    ra.tw = p->tw_w;
+    ra.grad_image = grad_image;
+    ra.S = 1;
+    ra.K = b.K;
+    int rc = run_kernel(p, OSOG_KERNEL_BWD_ROWS, st, [&] { return launch_bwd_rows(ra, st); });
+    if (rc) return rc;
+    BwdColumnArgs bc{};
+    bc.geo = geo;
+    bc.w = b.w;
+    bc.tw = p->tw_h;
+    bc.opart = b.opart;
+    bc.S = 1;
+    bc.K = b.K;
+    for (int k = 0; k < b.K; ++k) bc.md[0][k] = b.gd.md[0][k];
+    rc = run_kernel(p, OSOG_KERNEL_BWD_COLUMN, st, [&] { return launch_bwd_column(bc, st); });
+    if (rc) return rc;
+    BwdStripArgs bs{};
+    bs.geo = geo;
+    bs.w = b.w;
+    bs.tw = p->tw_w;
+    bs.part = b.part;
+    bs.S = 1;
+    bs.sc[0] = b.sc;
+    rc = run_kernel(p, OSOG_KERNEL_BWD_STRIP, st, [&] { return launch_bwd_strip(bs, st); });
+    if (rc) return rc;
+    BwdReduceArgs br{};
+    br.geo = geo;
+    br.w = b.w;
+    br.part = b.part;
+    br.opart = b.opart;
+    br.grad_soa = grad_soa;
+    br.ld = ld;
+    br.grad_optics = grad_optics;
+    br.S = 1;
+    br.nchunks = (int32_t)b.chunks;
+    br.sc[0] = b.sc;
+    return run_kernel(p, OSOG_KERNEL_BWD_REDUCE, st, [&] { return launch_bwd_reduce(br, st); });
+}
+
+// Field-by-field equality (the struct has padding).
+bool same_optics(const osog_optics_t &a, const osog_optics_t &b) {
+    return a.H == b.H && a.W == b.W && a.dx_um == b.dx_um && a.lambda_um == b.lambda_um &&
+           a.NA == b.NA && a.n_medium == b.n_medium && a.defocus_um == b.defocus_um &&
+           a.modes == b.modes && a.oblique_frac == b.oblique_frac &&
+           a.oblique_angle == b.oblique_angle && a.shear_px == b.shear_px &&
+           a.shear_angle == b.shear_angle && a.bias_phase == b.bias_phase &&
+           a.bevel_slope == b.bevel_slope;
+}
+
+// Drop the forward states that osog_render_keep left in workspace ws (any
+// other call that writes ws invalidates them).
+void forget_kept(osog_plan *p, const void *ws) {
+    for (size_t i = p->kept.size(); i-- > 0;)
+        if (p->kept[i].ws == ws) p->kept.erase(p->kept.begin() + i);
+}
+
 }  // namespace
 
 extern "C" {
@@ -422,6 +592,7 @@ static int render_stage(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
                         float *opd_out, void *ws, size_t ws_bytes, osog_stream_t stream,
                         Stage stage) {
     if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    forget_kept(p, ws);
     int rc = check_optics(p, optics);
     if (rc) return rc;
     if (n < 0 || (int64_t)n > ld) return fail(OSOG_ERR_INVALID_ARG, "need 0 <= n <= ld");
@@ -454,6 +625,7 @@ int osog_render_polyhedra(osog_plan_t *p, const float *soa, int64_t ld, int32_t 
                           const osog_optics_t *optics, float *image, void *ws, size_t ws_bytes,
                           osog_stream_t stream) {
     if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    forget_kept(p, ws);
     int rc = check_optics(p, optics);
     if (rc) return rc;
     if (n < 0 || (int64_t)n > ld) return fail(OSOG_ERR_INVALID_ARG, "need 0 <= n <= ld");
@@ -503,6 +675,7 @@ int osog_render_dic_incoherent(osog_plan_t *p, const float *soa, int64_t ld, int
                                const osog_optics_t *optics, float *image, void *ws,
                                size_t ws_bytes, osog_stream_t stream) {
     if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    forget_kept(p, ws);
     int rc = check_optics(p, optics);
     if (rc) return rc;
     if (n < 0 || (int64_t)n > ld) return fail(OSOG_ERR_INVALID_ARG, "need 0 <= n <= ld");
@@ -648,6 +821,7 @@ int osog_batch_submit(osog_plan_t *p, const float *soa_all, int64_t ld, const in
                       const osog_tuning_t *tuning, void *ws, size_t ws_bytes,
                       osog_stream_t stream) {
     if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    forget_kept(p, ws);
     if (S < 1 || !offsets || !optics || !images)
         return fail(OSOG_ERR_INVALID_ARG, "need S >= 1 and non-NULL offsets, optics, images");
     for (int s = 0; s < S; ++s) {
@@ -752,105 +926,59 @@ size_t osog_backward_workspace_size(const osog_plan_t *p, int32_t n_max, int32_t
 int osog_render_backward(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
                          const osog_optics_t *optics, const float *grad_image, float *grad_soa,
                          float *grad_optics, void *ws, size_t ws_bytes, osog_stream_t stream) {
-    if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
-    int rc = check_optics(p, optics);
+    BwdState b;
+    int rc = bwd_setup(p, soa, ld, n, optics, ws, ws_bytes, b);
     if (rc) return rc;
-    if (n < 0 || (int64_t)n > ld) return fail(OSOG_ERR_INVALID_ARG, "need 0 <= n <= ld");
-    if (n > 0 && (!soa || !grad_soa)) return fail(OSOG_ERR_INVALID_ARG, "soa or grad_soa is NULL");
-    if (!grad_image || !grad_optics) return fail(OSOG_ERR_INVALID_ARG, "grad_image or grad_optics is NULL");
-    const int K = popcount3(optics->modes);
-    const Geometry &geo = p->geo;
-    const int64_t chunks = (n + kChunk - 1) / kChunk;
-    const int ppp = kDefaultPairs;
-    const BwdLayout bl = make_bwd_layout(geo, n, chunks, K, ppp);
-    rc = check_ws(ws, bl.total, ws_bytes);
+    rc = bwd_check_grads(grad_image, grad_soa, grad_optics, n);
     if (rc) return rc;
+    forget_kept(p, ws);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    GroupDev gd{};
-    gd.S = 1;
-    gd.K = K;
-    gd.nchunks = (int32_t)chunks;
-    SceneDev sc = scene_dev(*optics);
-    sc.p0 = 0;
-    sc.n = n;
-    sc.chunk0 = 0;
-    sc.pair0 = 0;
-    sc.pair_cap = (int32_t)((int64_t)n * ppp);
-    gd.sc[0] = sc;
-    for (int bit = 0, k = 0; bit < 3; ++bit)
-        if (optics->modes & (1u << bit)) gd.md[0][k++] = mode_dev(*optics, 1u << bit);
-    Work w = carve(ws, bl.fwd, p->status);
-    w.slotmap = reinterpret_cast<int32_t *>(static_cast<char *>(ws) + bl.slotmap);
-    w.slotmap_ppp = ppp;
-    float *part = reinterpret_cast<float *>(static_cast<char *>(ws) + bl.part);
-    float *opart = reinterpret_cast<float *>(static_cast<char *>(ws) + bl.opart);
+    rc = bwd_forward(p, soa, ld, b, nullptr, st);  // recompute up to the filtered columns
+    if (rc) return rc;
+    return bwd_adjoint(p, b, grad_image, grad_soa, ld, grad_optics, st);
+}
 
-    // Forward recomputation up to the filtered columns Q_m.
-    rc = run_kernel(p, OSOG_KERNEL_BIN_COUNT, st, [&] { return launch_bin_count(soa, ld, gd, geo, w, st); });
+int osog_render_keep(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
+                     const osog_optics_t *optics, float *image, void *ws, size_t ws_bytes,
+                     osog_stream_t stream) {
+    BwdState b;
+    int rc = bwd_setup(p, soa, ld, n, optics, ws, ws_bytes, b);
     if (rc) return rc;
-    rc = run_kernel(p, OSOG_KERNEL_BIN_SCAN, st, [&] { return launch_bin_scan(gd, geo, w, st); });
+    if (!image) return fail(OSOG_ERR_INVALID_ARG, "image is NULL");
+    forget_kept(p, ws);
+    rc = bwd_forward(p, soa, ld, b, image, reinterpret_cast<cudaStream_t>(stream));
     if (rc) return rc;
-    rc = run_kernel(p, OSOG_KERNEL_BIN_FILL, st, [&] { return launch_bin_fill(gd, geo, w, st); });
-    if (rc) return rc;
-    StripArgs sa{};
-    sa.geo = geo;
-    sa.w = w;
-    sa.tw = p->tw_w;
-    sa.S = 1;
-    sa.sc[0] = sc;
-    rc = run_kernel(p, OSOG_KERNEL_STRIP_FORWARD, st, [&] { return launch_strip_forward(sa, kStripRender, st); });
-    if (rc) return rc;
-    ColumnArgs ca{};
-    ca.geo = geo;
-    ca.w = w;
-    ca.tw = p->tw_h;
-    ca.S = 1;
-    ca.K = K;
-    for (int k = 0; k < K; ++k) ca.md[0][k] = gd.md[0][k];
-    rc = run_kernel(p, OSOG_KERNEL_COLUMN, st, [&] { return launch_column(ca, st); });
-    if (rc) return rc;
+    osog_plan::Kept k{};
+    k.ws = ws;
+    k.ws_bytes = ws_bytes;
+    k.soa = soa;
+    k.ld = ld;
+    k.n = n;
+    k.optics = *optics;
+    if (p->kept.size() >= kMaxKept) p->kept.erase(p->kept.begin());  // the oldest goes
+    p->kept.push_back(k);
+    return OSOG_OK;
+}
 
-    // Adjoint passes.
-    BwdRowsArgs ra{};
-    ra.geo = geo;
-    ra.w = w;
-    ra.tw = p->tw_w;
-    ra.grad_image = grad_image;
-    ra.S = 1;
-    ra.K = K;
-    rc = run_kernel(p, OSOG_KERNEL_BWD_ROWS, st, [&] { return launch_bwd_rows(ra, st); });
+int osog_render_backward_kept(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
+                              const osog_optics_t *optics, const float *grad_image,
+                              float *grad_soa, float *grad_optics, void *ws, size_t ws_bytes,
+                              osog_stream_t stream) {
+    BwdState b;
+    int rc = bwd_setup(p, soa, ld, n, optics, ws, ws_bytes, b);
     if (rc) return rc;
-    BwdColumnArgs bc{};
-    bc.geo = geo;
-    bc.w = w;
-    bc.tw = p->tw_h;
-    bc.opart = opart;
-    bc.S = 1;
-    bc.K = K;
-    for (int k = 0; k < K; ++k) bc.md[0][k] = gd.md[0][k];
-    rc = run_kernel(p, OSOG_KERNEL_BWD_COLUMN, st, [&] { return launch_bwd_column(bc, st); });
+    rc = bwd_check_grads(grad_image, grad_soa, grad_optics, n);
     if (rc) return rc;
-    BwdStripArgs bs{};
-    bs.geo = geo;
-    bs.w = w;
-    bs.tw = p->tw_w;
-    bs.part = part;
-    bs.S = 1;
-    bs.sc[0] = sc;
-    rc = run_kernel(p, OSOG_KERNEL_BWD_STRIP, st, [&] { return launch_bwd_strip(bs, st); });
-    if (rc) return rc;
-    BwdReduceArgs br{};
-    br.geo = geo;
-    br.w = w;
-    br.part = part;
-    br.opart = opart;
-    br.grad_soa = grad_soa;
-    br.ld = ld;
-    br.grad_optics = grad_optics;
-    br.S = 1;
-    br.nchunks = (int32_t)chunks;
-    br.sc[0] = sc;
-    return run_kernel(p, OSOG_KERNEL_BWD_REDUCE, st, [&] { return launch_bwd_reduce(br, st); });
+    bool found = false;
+    for (const osog_plan::Kept &k : p->kept)
+        found = found || (k.ws == ws && k.ws_bytes == ws_bytes && k.soa == soa && k.ld == ld &&
+                          k.n == n && same_optics(k.optics, *optics));
+    if (!found)
+        return fail(OSOG_ERR_INVALID_ARG, "no forward state kept in this workspace for these "
+                                          "arguments (osog_render_keep)");
+    forget_kept(p, ws);  // the adjoint overwrites the kept spectra
+    return bwd_adjoint(p, b, grad_image, grad_soa, ld, grad_optics,
+                       reinterpret_cast<cudaStream_t>(stream));
 }
 
 int osog_autotune(osog_plan_t *p, const float *soa_all, int64_t ld, const int32_t *offsets,

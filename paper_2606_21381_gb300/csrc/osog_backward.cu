@@ -33,7 +33,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 template <int N>
 __global__ void __launch_bounds__(kThreads, 1) k_bwd_rows(const __grid_constant__ BwdRowsArgs a) {
-    constexpr int L = kSetElems / N;
+    constexpr int L = set_elems(N) / N;
     constexpr int LS = line_stride(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_rows(const __grid_constant_
     fft_lines<N, L, true>(buf, a.tw);  // E_m rows
     const float *gI = a.grad_image + ((size_t)sm * geo.H + y0) * N;
 #pragma unroll
-    for (int i = 0; i < kEPT; ++i) {
+    for (int i = 0; i < ept(N); ++i) {
         const int e = threadIdx.x + i * kThreads;
         if (e < RN) {
             float2 *v = buf + (e / N) * LS + pad16(e % N);
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_rows(const __grid_constant_
 
 template <int N>
 __global__ void __launch_bounds__(kThreads, 1) k_bwd_column(const __grid_constant__ BwdColumnArgs a) {
-    constexpr int L = kSetElems / N;
+    constexpr int L = set_elems(N) / N;
     constexpr int LS = line_stride(N);
     constexpr int NW = kThreads / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -89,9 +89,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_column(const __grid_constan
     }
     __syncthreads();
     fft_lines<N, L, false>(bufE, a.tw);  // E^ of the block's columns
-    float2 acc[kEPT];
+    float2 acc[ept(N)];
 #pragma unroll
-    for (int i = 0; i < kEPT; ++i) acc[i] = make_float2(0.f, 0.f);
+    for (int i = 0; i < ept(N); ++i) acc[i] = make_float2(0.f, 0.f);
     float po[4] = {0.f, 0.f, 0.f, 0.f};
     for (int m = 0; m < K; ++m) {
         const ModeDev &md = a.md[s][m];
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_column(const __grid_constan
         __syncthreads();
         fft_lines<N, L, false>(bufZ, a.tw);  // dL/dZ_m (adjoint of the inverse column DFT)
 #pragma unroll 4
-        for (int i = 0; i < kEPT; ++i) {
+        for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;  // line-major: consecutive rows
             const int c = e / N, y = e % N;
             if (c < B) {
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_column(const __grid_constan
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < kEPT; ++i) {
+    for (int i = 0; i < ept(N); ++i) {
         const int e = threadIdx.x + i * kThreads;
         const int c = e / N, y = e % N;
         if (c < B) bufZ[c * LS + pad16(y)] = acc[i];
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_column(const __grid_constan
 
 template <int N>
 __global__ void __launch_bounds__(kThreads, 1) k_bwd_strip(const __grid_constant__ BwdStripArgs a) {
-    constexpr int L = kSetElems / N;
+    constexpr int L = set_elems(N) / N;
     constexpr int LS = line_stride(N);
     constexpr int NW = kThreads / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_strip(const __grid_constant
     const float tol = sc.two_over_lambda;
     const float k2pi = 3.14159265358979323846f * tol;                   // 2 pi / lambda
 #pragma unroll
-    for (int i = 0; i < kEPT; ++i) {
+    for (int i = 0; i < ept(N); ++i) {
         const int e = threadIdx.x + i * kThreads;
         if (e < RN) {
             const int idx = (e / N) * LS + pad16(e % N);
@@ -249,13 +249,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_strip(const __grid_constant
 
 __global__ void __launch_bounds__(kChunk) k_bwd_reduce(const __grid_constant__ BwdReduceArgs a) {
     const Geometry &geo = a.geo;
-    if ((int)blockIdx.x >= a.nchunks) {  // optics: sum the per-block partials in order
+    if ((int)blockIdx.x >= a.nchunks) {  // optics: sum the per-block partials
+        // Warp f sums component f: lane l adds blocks l, l + 32, ... in
+        // double, then a fixed butterfly combines the lanes (same order on
+        // every run).
         const int s = blockIdx.x - a.nchunks;
-        if (threadIdx.x < 4) {
+        const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (f < 4) {
             double v = 0.0;
-            for (int bk = 0; bk < geo.nblocks; ++bk)
-                v += (double)a.opart[((size_t)s * geo.nblocks + bk) * 4 + threadIdx.x];
-            a.grad_optics[s * 4 + threadIdx.x] = (float)v;
+            for (int bk = lane; bk < geo.nblocks; bk += 32)
+                v += (double)a.opart[((size_t)s * geo.nblocks + bk) * 4 + f];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+            if (lane == 0) a.grad_optics[s * 4 + f] = (float)v;
         }
         return;
     }
@@ -335,13 +341,13 @@ struct BwdPrepare {
 }  // namespace
 
 size_t bwd_column_smem(int H) {
-    const int L = kSetElems / H;
+    const int L = set_elems(H) / H;
     return (size_t)2 * L * line_stride(H) * sizeof(float2) + (size_t)kMaxModes * L * sizeof(int2) +
            (kThreads / 32) * 4 * sizeof(float);
 }
 
 size_t bwd_strip_smem(int W) {
-    const int L = kSetElems / W;
+    const int L = set_elems(W) / W;
     return (size_t)2 * L * line_stride(W) * sizeof(float2) +
            kThreads * (sizeof(PRec) + sizeof(Rect) + sizeof(int)) + 64;
 }

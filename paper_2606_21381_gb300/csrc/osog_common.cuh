@@ -9,13 +9,21 @@
 namespace osog {
 
 // ---------------------------------------------------------------- layout
-// Every FFT-bearing kernel works on a set of 8192 complex samples held in
-// shared memory: a strip of R = 8192 / W full rows, or a block of
-// B = 8192 / H full columns (fewer when the canvas is smaller).
-constexpr int kSetElems = 8192;
+// Every FFT-bearing kernel works on a set of complex samples held in shared
+// memory: a strip of R = set_elems(W) / W full rows, or a block of
+// B = set_elems(H) / H full columns (fewer when the canvas is smaller).  A
+// set of an n-point transform holds 8192 samples for n >= 1024 (8 lines at
+// 1024, 4 at 2048) and kSetLines lines below that (at least kThreads
+// samples), so that a single small canvas still spreads over many CTAs.
+constexpr int kMaxSetElems = 8192;
+constexpr int kSetLines = 4;
 constexpr int kThreads = 512;          // threads of every FFT-bearing CTA
+__host__ __device__ constexpr int set_elems(int n) {
+    return n >= 1024 ? kMaxSetElems : kSetLines * n < kThreads ? kThreads : kSetLines * n;
+}
 constexpr int kChunk = 256;            // particles per binning CTA
 constexpr int kMaxBands = 64;          // bands (binning rows) per canvas
+constexpr int kMinBandRows = 16;       // rows of the thinnest band
 constexpr int kMaxScenes = 32;         // scenes per launch group
 constexpr int kMaxModes = 3;
 constexpr int kMaxPlanes = 32;         // half-spaces per general polyhedron
@@ -39,11 +47,14 @@ __host__ inline Geometry make_geometry(int H, int W) {
     Geometry g;
     g.H = H;
     g.W = W;
-    g.R = kSetElems / W < H ? kSetElems / W : H;
+    g.R = set_elems(W) / W < H ? set_elems(W) / W : H;
     g.nstrips = H / g.R;
-    g.B = kSetElems / H < W ? kSetElems / H : W;
+    g.B = set_elems(H) / H < W ? set_elems(H) / H : W;
     g.nblocks = W / g.B;
+    // At least kMinBandRows rows per band, so that a particle's bounding box
+    // spans few bands (and pair lists stay short) however thin the strips.
     int bh = H / kMaxBands;
+    if (bh < kMinBandRows) bh = kMinBandRows < H ? kMinBandRows : H;
     g.BH = bh > g.R ? bh : g.R;
     g.nbands = H / g.BH;
     return g;

@@ -2,14 +2,14 @@
 // optical head, inverse row FFT + intensity.
 //
 // Data flow for one H x W scene (complex64 intermediates in HBM):
-//   strip forward  (CTA per strip of R = 8192/W rows): gathers the OPD and
+//   strip forward  (CTA per strip of R = set_elems(W)/W rows): gathers the OPD and
 //                  ATT of every particle overlapping the strip in ascending
 //                  particle order (Eq. 2, Eq. 7), forms the exit wave
 //                  exp(-ATT) exp(i 2 pi OPD / lambda) (Eq. 2, Eq. 4), runs
 //                  the forward row DFTs and writes G in a column-blocked
 //                  layout [W/B][H][B] so that the column pass reads one
 //                  contiguous block.
-//   column         (CTA per block of B = 8192/H columns): forward column
+//   column         (CTA per block of B = set_elems(H)/H columns): forward column
 //                  DFTs, then for every modality the transfer function of
 //                  Eq. 3 / Eq. 5 / oblique shift times 1/(HW), inverse column
 //                  DFTs, written as Q[m] in the same blocked layout.
@@ -27,7 +27,7 @@ namespace {
 template <int N, int MODE, bool SQ = false>
 __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, int strip,
                                                    unsigned char *smem_raw) {
-    constexpr int L = kSetElems / N;
+    constexpr int L = set_elems(N) / N;
     constexpr int LS = line_stride(N);
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
     PRec *srec = reinterpret_cast<PRec *>(buf + L * LS);
@@ -36,30 +36,30 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
     const Geometry &geo = a.geo;
     const int R = SQ ? sq_rb(N) : geo.R;
     const int y0 = strip * R;
-    const int RN = R * N;  // <= kSetElems; lines R..L-1 are never read back
+    const int RN = R * N;  // <= set_elems(N); lines R..L-1 are never read back
     if constexpr (MODE == kStripFromReal) {
         const float *src = reinterpret_cast<const float *>(a.opd_att) + (size_t)y0 * N;
-        float v[kEPT];
+        float v[ept(N)];
 #pragma unroll
-        for (int i = 0; i < kEPT; ++i) {
+        for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;
             if (e < RN) v[i] = src[e];
         }
 #pragma unroll
-        for (int i = 0; i < kEPT; ++i) {
+        for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;
             if (e < RN) buf[(e / N) * LS + pad16(e % N)] = make_float2(v[i], 0.f);
         }
     } else if constexpr (MODE == kStripFromMap) {
         const float2 *src = a.opd_att + (size_t)y0 * N;
-        float2 v[kEPT];
+        float2 v[ept(N)];
 #pragma unroll
-        for (int i = 0; i < kEPT; ++i) {
+        for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;
             if (e < RN) v[i] = src[e];
         }
 #pragma unroll
-        for (int i = 0; i < kEPT; ++i) {
+        for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;
             if (e < RN) buf[(e / N) * LS + pad16(e % N)] = v[i];
         }
@@ -73,7 +73,7 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
     if constexpr (MODE == kStripOpdOnly) {
         float2 *dst = a.opd_out + (size_t)y0 * N;
 #pragma unroll
-        for (int i = 0; i < kEPT; ++i) {
+        for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;
             if (e < RN) dst[e] = buf[(e / N) * LS + pad16(e % N)];
         }
@@ -81,7 +81,7 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
     } else {
         const float tol = a.sc[s].two_over_lambda;
 #pragma unroll
-        for (int i = 0; i < kEPT; ++i) {
+        for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;
             if (MODE != kStripFromReal && e < RN) {
                 float2 *v = buf + (e / N) * LS + pad16(e % N);
@@ -101,7 +101,7 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
         float2 *G = a.w.G + (size_t)s * H * N;
         const int2 cr = a.w.colrange[s];
 #pragma unroll
-        for (int i = 0; i < kEPT; ++i) {
+        for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;
             const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
             const int kx = bk * B + c, fx = kx < N / 2 ? kx : kx - N;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_strip_forward(const __grid_cons
 template <int N, bool MULTI, bool SQ = false>
 __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
                                             unsigned char *smem_raw) {
-    constexpr int L = kSetElems / N;
+    constexpr int L = set_elems(N) / N;
     constexpr int LS = line_stride(N);
     float2 *buf0 = reinterpret_cast<float2 *>(smem_raw);
     float2 *buf1 = MULTI ? buf0 + L * LS : buf0;
@@ -138,23 +138,23 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
     const bool hi_part = u1 >= half && max(u0, half) - W <= cr.y && u1 - W >= cr.x;
     if (!lo_part && !hi_part) return;
     const float2 *G = a.w.G + ((size_t)s * geo.nblocks + bk) * N * B;
-    const int NB_ = N * B;  // <= kSetElems; lines B..L-1 are never read back
+    const int NB_ = N * B;  // <= set_elems(N); lines B..L-1 are never read back
     if (a.unit_input) {  // the spectrum of a unit impulse: 1 at every frequency
 #pragma unroll
-        for (int i = 0; i < kEPT; ++i) {
+        for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;
             if (e < NB_) buf0[(e & (B - 1)) * LS + pad16(e >> lb)] = make_float2(1.f, 0.f);
         }
     } else {
-        float2 v[kEPT];
+        float2 v[ept(N)];
 #pragma unroll
-        for (int i = 0; i < kEPT; ++i) {
+        for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;
             const int kx = u0 + (e & (B - 1)), fx = kx < half ? kx : kx - W;
             v[i] = e < NB_ && fx >= cr.x && fx <= cr.y ? G[e] : make_float2(0.f, 0.f);
         }
 #pragma unroll
-        for (int i = 0; i < kEPT; ++i) {
+        for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;
             if (e < NB_) buf0[(e & (B - 1)) * LS + pad16(e >> lb)] = v[i];
         }
@@ -170,7 +170,7 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
         if (md.op == kOpSpectrum) {  // the forward spectrum itself, to md.tab
             float2 *T = md.tab + (size_t)bk * N * B;
 #pragma unroll
-            for (int i = 0; i < kEPT; ++i) {
+            for (int i = 0; i < ept(N); ++i) {
                 const int e = threadIdx.x + i * kThreads;
                 if (e < NB_) {
                     const float2 v = buf0[(e & (B - 1)) * LS + pad16(e >> lb)];
@@ -182,7 +182,7 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
         const float2 *T = md.op == kOpTable ? md.tab + (size_t)bk * N * B : nullptr;
         const float tnorm = md.op == kOpTable ? md.scale / md.tab[0].x : 0.f;
 #pragma unroll 4
-        for (int i = 0; i < kEPT; ++i) {
+        for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;  // line-major: consecutive y
             const int c = e / N, y = e % N;
             if (c < B) {
@@ -204,7 +204,7 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
         fft_lines<N, L, true>(buf1, a.tw);
         float2 *Qm = a.w.Q + (((size_t)s * K + m) * geo.nblocks + bk) * N * B;
 #pragma unroll
-        for (int i = 0; i < kEPT; ++i) {
+        for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;
             if (e < NB_) Qm[e] = buf1[(e & (B - 1)) * LS + pad16(e >> lb)];
         }
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_column(const __grid_constant__ 
 template <int N, bool SQ = false>
 __device__ __forceinline__ void inverse_item(const InverseArgs &a, int sm, int strip,
                                              unsigned char *smem_raw) {
-    constexpr int L = kSetElems / N;
+    constexpr int L = set_elems(N) / N;
     constexpr int LS = line_stride(N);
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
     const Geometry &geo = a.geo;
@@ -233,11 +233,11 @@ __device__ __forceinline__ void inverse_item(const InverseArgs &a, int sm, int s
     const int y0 = strip * R;
     const float2 *Qm = a.w.Q + (size_t)sm * geo.nblocks * H * B;
     const int2 cr = a.w.colrange[sm / K];
-    const int RN = R * N;  // <= kSetElems; lines R..L-1 are never read back
+    const int RN = R * N;  // <= set_elems(N); lines R..L-1 are never read back
     {
-        float2 v[kEPT];
+        float2 v[ept(N)];
 #pragma unroll
-        for (int i = 0; i < kEPT; ++i) {
+        for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;
             const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
             const int kx = bk * B + c, fx = kx < N / 2 ? kx : kx - N;
@@ -245,7 +245,7 @@ __device__ __forceinline__ void inverse_item(const InverseArgs &a, int sm, int s
                                                       : make_float2(0.f, 0.f);
         }
 #pragma unroll
-        for (int i = 0; i < kEPT; ++i) {
+        for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;
             const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
             if (e < RN) buf[r * LS + pad16(bk * B + c)] = v[i];
@@ -255,7 +255,7 @@ __device__ __forceinline__ void inverse_item(const InverseArgs &a, int sm, int s
     fft_lines<N, L, true>(buf, a.tw);
     float *img = a.images + ((size_t)sm * H + y0) * N;
 #pragma unroll
-    for (int i = 0; i < kEPT; ++i) {
+    for (int i = 0; i < ept(N); ++i) {
         const int e = threadIdx.x + i * kThreads;
         if (e < RN) {
             const float2 v = buf[(e / N) * LS + pad16(e % N)];
@@ -481,19 +481,19 @@ struct Prepare {
 }  // namespace
 
 size_t strip_forward_smem(int W) {
-    const int L = kSetElems / W;
+    const int L = set_elems(W) / W;
     return (size_t)L * line_stride(W) * sizeof(float2) + kThreads * (sizeof(PRec) + sizeof(Rect)) +
            64;
 }
 
 size_t column_smem(int H, int K) {
-    const int L = kSetElems / H;
+    const int L = set_elems(H) / H;
     return (size_t)(K > 1 ? 2 : 1) * L * line_stride(H) * sizeof(float2) +
            (size_t)kMaxModes * L * sizeof(int2);
 }
 
 size_t strip_inverse_smem(int W) {
-    const int L = kSetElems / W;
+    const int L = set_elems(W) / W;
     return (size_t)L * line_stride(W) * sizeof(float2);
 }
 

@@ -20,9 +20,9 @@ __device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
 __host__ __device__ constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v >> 1); }
 
 // Rows per strip and columns per column block of a square N x N canvas
-// (both min(kSetElems / N, N)); kernels specialised for square canvases use
+// (both min(set_elems(N) / N, N)); kernels specialised for square canvases use
 // these compile-time values instead of the geometry's.
-__host__ __device__ constexpr int sq_rb(int n) { return kSetElems / n < n ? kSetElems / n : n; }
+__host__ __device__ constexpr int sq_rb(int n) { return set_elems(n) / n < n ? set_elems(n) / n : n; }
 
 // Accumulate one particle's OPD / ATT over the pixels [xa, xb] x [ya, yb]
 // of the strip buffer.  The warp's lanes cover the particle's rows (the
@@ -199,10 +199,10 @@ __device__ void raster_strip(const Geometry &geo, const Work &w, const SceneDev 
     }
 }
 
-// Elements of an 8192-sample set handled by each thread in the copy loops;
-// the loops are fully unrolled so that every thread has all of its global
-// loads in flight at once.
-constexpr int kEPT = kSetElems / kThreads;
+// Elements of an n-point transform's set handled by each thread in the copy
+// loops; the loops are fully unrolled so that every thread has all of its
+// global loads in flight at once.
+__host__ __device__ constexpr int ept(int n) { return set_elems(n) / kThreads; }
 
 // ------------------------------------------------------------ fast phases
 // sin and cos of x with the hardware approximations: x is first reduced to
@@ -262,9 +262,9 @@ __device__ __forceinline__ void load_strip_blocked(float2 *buf, const float2 *sr
     const int R = SQ ? sq_rb(N) : geo.R, B = SQ ? sq_rb(N) : geo.B;
     const int lb = SQ ? clog2(sq_rb(N)) : ilog2(B), lr = SQ ? clog2(sq_rb(N)) : ilog2(R);
     const int RN = R * N, H = SQ ? N : geo.H;
-    float2 v[kEPT];
+    float2 v[ept(N)];
 #pragma unroll
-    for (int i = 0; i < kEPT; ++i) {
+    for (int i = 0; i < ept(N); ++i) {
         const int e = threadIdx.x + i * kThreads;
         const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
         const int kx = bk * B + c, fx = kx < N / 2 ? kx : kx - N;
@@ -272,7 +272,7 @@ __device__ __forceinline__ void load_strip_blocked(float2 *buf, const float2 *sr
                                                   : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int i = 0; i < kEPT; ++i) {
+    for (int i = 0; i < ept(N); ++i) {
         const int e = threadIdx.x + i * kThreads;
         const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
         if (e < RN) buf[r * LS + pad16(bk * B + c)] = v[i];
@@ -287,7 +287,7 @@ __device__ __forceinline__ void store_strip_blocked(const float2 *buf, float2 *d
     const int lb = SQ ? clog2(sq_rb(N)) : ilog2(B), lr = SQ ? clog2(sq_rb(N)) : ilog2(R);
     const int RN = R * N, H = SQ ? N : geo.H;
 #pragma unroll
-    for (int i = 0; i < kEPT; ++i) {
+    for (int i = 0; i < ept(N); ++i) {
         const int e = threadIdx.x + i * kThreads;
         const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
         const int kx = bk * B + c, fx = kx < N / 2 ? kx : kx - N;
@@ -303,15 +303,15 @@ __device__ __forceinline__ void load_block(float2 *buf, const float2 *src, const
                                            int bk, int2 cr) {
     constexpr int LS = line_stride(N);
     const int B = geo.B, lb = ilog2(B), NB = N * B, half = geo.W / 2;
-    float2 v[kEPT];
+    float2 v[ept(N)];
 #pragma unroll
-    for (int i = 0; i < kEPT; ++i) {
+    for (int i = 0; i < ept(N); ++i) {
         const int e = threadIdx.x + i * kThreads;
         const int kx = bk * B + (e & (B - 1)), fx = kx < half ? kx : kx - geo.W;
         v[i] = e < NB && fx >= cr.x && fx <= cr.y ? src[e] : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int i = 0; i < kEPT; ++i) {
+    for (int i = 0; i < ept(N); ++i) {
         const int e = threadIdx.x + i * kThreads;
         if (e < NB) buf[(e & (B - 1)) * LS + pad16(e >> lb)] = v[i];
     }
@@ -322,7 +322,7 @@ __device__ __forceinline__ void store_block(const float2 *buf, float2 *dst, cons
     constexpr int LS = line_stride(N);
     const int B = geo.B, lb = ilog2(B), NB = N * B;
 #pragma unroll
-    for (int i = 0; i < kEPT; ++i) {
+    for (int i = 0; i < ept(N); ++i) {
         const int e = threadIdx.x + i * kThreads;
         if (e < NB) dst[e] = buf[(e & (B - 1)) * LS + pad16(e >> lb)];
     }

@@ -140,17 +140,64 @@ class Renderer:
         if grad_image.shape != (K, self.H, self.W) or grad_image.dtype != torch.float32 \
                 or not grad_image.is_contiguous() or grad_image.device.type != "cuda":
             raise ValueError("grad_image must be a contiguous cuda float32 (K, H, W) tensor")
-        gsoa = torch.zeros_like(soa)
-        gopt = torch.zeros(4, dtype=torch.float32, device=self.device)
-        nbytes = int(self._L.osog_backward_workspace_size(self.plan, n, K))
-        if nbytes == 0:
-            raise OsogError(1, "osog_backward_workspace_size")
-        ws = self.workspace(nbytes)
+        gsoa, gopt = self._grad_buffers(soa, n)
+        ws = self.workspace(self.backward_workspace_size(n, K))
         o = optics_struct(optics)
         check(self._L.osog_render_backward(self.plan, _ptr(soa), soa.shape[1], n, ctypes.byref(o),
                                            _ptr(grad_image), _ptr(gsoa), _ptr(gopt), _ptr(ws),
                                            ws.numel(), _stream(stream)),
               "osog_render_backward")
+        return gsoa, gopt
+
+    def backward_workspace_size(self, n: int, K: int) -> int:
+        nbytes = int(self._L.osog_backward_workspace_size(self.plan, int(n), int(K)))
+        if nbytes == 0:
+            raise OsogError(1, "osog_backward_workspace_size")
+        return nbytes
+
+    def _grad_buffers(self, soa: torch.Tensor, n: int):
+        # the adjoint writes every row of particles 0..n-1 and all four optics
+        # entries; only the columns n..ld-1 need zeros
+        gsoa = torch.empty_like(soa) if n == soa.shape[1] else torch.zeros_like(soa)
+        gopt = torch.empty(4, dtype=torch.float32, device=self.device)
+        return gsoa, gopt
+
+    def render_keep(self, soa: torch.Tensor, n: int | None, optics: dict, out=None, ws=None,
+                    stream=None):
+        """osog_render_keep: the (K, H, W) image of render(), with the
+        forward intermediates kept in `ws` (a uint8 device tensor, allocated
+        when None) for one backward_kept().  Returns (image, ws)."""
+        self._check_soa(soa)
+        n = soa.shape[1] if n is None else int(n)
+        K = n_modes(optics)
+        if out is None:
+            out = torch.empty((K, self.H, self.W), dtype=torch.float32, device=self.device)
+        nbytes = self.backward_workspace_size(n, K)
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        o = optics_struct(optics)
+        check(self._L.osog_render_keep(self.plan, _ptr(soa), soa.shape[1], n, ctypes.byref(o),
+                                       _ptr(out), _ptr(ws), ws.numel(), _stream(stream)),
+              "osog_render_keep")
+        return out, ws
+
+    def backward_kept(self, soa: torch.Tensor, n: int | None, optics: dict,
+                      grad_image: torch.Tensor, ws: torch.Tensor, stream=None):
+        """osog_render_backward_kept: backward() from the state that
+        render_keep() left in `ws` (same soa, n and optics); consumes it."""
+        self._check_soa(soa)
+        n = soa.shape[1] if n is None else int(n)
+        K = n_modes(optics)
+        if grad_image.shape != (K, self.H, self.W) or grad_image.dtype != torch.float32 \
+                or not grad_image.is_contiguous() or grad_image.device.type != "cuda":
+            raise ValueError("grad_image must be a contiguous cuda float32 (K, H, W) tensor")
+        gsoa, gopt = self._grad_buffers(soa, n)
+        o = optics_struct(optics)
+        check(self._L.osog_render_backward_kept(self.plan, _ptr(soa), soa.shape[1], n,
+                                                ctypes.byref(o), _ptr(grad_image), _ptr(gsoa),
+                                                _ptr(gopt), _ptr(ws), ws.numel(),
+                                                _stream(stream)),
+              "osog_render_backward_kept")
         return gsoa, gopt
 
     def render_opd(self, soa: torch.Tensor, n: int | None, optics: dict, out=None, stream=None):

@@ -161,3 +161,66 @@ def test_central_differences_of_gpu_forward_on_one_percent_of_parameters():
         b[key] -= h
         fd = (loss(soa, a) - loss(soa, b)) / (2 * h)
         assert abs(go[k] - fd) <= 2e-2 * max(abs(fd), 0.02 * np.abs(go).max()), (key, go[k], fd)
+
+
+def _inverse_scene():
+    soa, o = scenes.inverse_512()
+    x = torch.from_numpy(soa).cuda()
+    gI = torch.from_numpy(np.random.default_rng(3).standard_normal((2, 512, 512))
+                          .astype(np.float32)).cuda()
+    return x, o, gI
+
+
+def test_kept_forward_state_gives_the_same_image_and_gradients():
+    """osog_render_keep + osog_render_backward_kept reproduce osog_render and
+    osog_render_backward bit for bit (the same kernels on the same state)."""
+    r = renderer(512, 512)
+    x, o, gI = _inverse_scene()
+    img = r.render(x, None, o)
+    img_k, ws = r.render_keep(x, None, o)
+    g_k = r.backward_kept(x, None, o, gI, ws)
+    g = r.backward(x, None, o, gI)
+    assert r.sync_status() == 0
+    assert torch.equal(img, img_k)
+    assert torch.equal(g[0], g_k[0]) and torch.equal(g[1], g_k[1])
+    # and on a canvas of another size, with a ragged particle count (n < ld)
+    r2 = renderer(128, 128)
+    rng = np.random.default_rng(4)
+    soa = scenes.draw_particles(rng, 37, 128, 128, mu=(0.002, 0.03))
+    o2 = scenes.optics(128, 128, modes=7, defocus=0.8, NA=0.5, shear_px=1.2)
+    x2 = torch.from_numpy(np.ascontiguousarray(soa)).cuda()
+    gI2 = torch.randn((3, 128, 128), device="cuda")
+    img_k, ws = r2.render_keep(x2, 30, o2)
+    g_k = r2.backward_kept(x2, 30, o2, gI2, ws)
+    g = r2.backward(x2, 30, o2, gI2)
+    assert r2.sync_status() == 0
+    assert torch.equal(r2.render(x2, 30, o2), img_k)
+    assert torch.equal(g[0], g_k[0]) and torch.equal(g[1], g_k[1])
+    assert torch.all(g_k[0][:, 30:] == 0)
+
+
+def test_kept_state_is_checked_and_consumed():
+    import ctypes
+    from paper_2606_21381_gb300._lib import OsogError, optics_struct
+    r = renderer(512, 512)
+    x, o, gI = _inverse_scene()
+    _, ws = r.render_keep(x, None, o)
+    with pytest.raises(OsogError):  # other optics than the kept forward's
+        r.backward_kept(x, None, dict(o, defocus=o["defocus"] + 0.1), gI, ws)
+    with pytest.raises(OsogError):  # another particle count
+        r.backward_kept(x, x.shape[1] - 1, o, gI, ws)
+    with pytest.raises(OsogError):  # another workspace
+        r.backward_kept(x, None, o, gI, torch.empty_like(ws))
+    r.backward_kept(x, None, o, gI, ws)
+    with pytest.raises(OsogError):  # the adjoint consumed the state
+        r.backward_kept(x, None, o, gI, ws)
+    # another call writing the same workspace drops the state
+    _, ws = r.render_keep(x, None, o, ws=ws)
+    img = torch.empty((2, 512, 512), device="cuda")
+    oo = optics_struct(o)
+    assert r._L.osog_render(r.plan, ctypes.c_void_p(x.data_ptr()), x.shape[1], x.shape[1],
+                            ctypes.byref(oo), ctypes.c_void_p(img.data_ptr()),
+                            ctypes.c_void_p(ws.data_ptr()), ws.numel(), None) == 0
+    with pytest.raises(OsogError):
+        r.backward_kept(x, None, o, gI, ws)
+    assert r.sync_status() == 0
