@@ -73,7 +73,7 @@ constexpr size_t kMaxKept = 64;  // forward states remembered per plan
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t rec, rect, cnt, band_off, pairs, G, Q, chord, colrange, ctr, total;
+    size_t rec, rect, cnt, band_off, pairs, G, Q, colrange, ctr, total;
 };
 
 // Workspace regions for a launch group of up to S scenes, n records,
@@ -96,8 +96,6 @@ Layout make_layout(const Geometry &geo, int64_t n, int64_t nchunks, int S, int K
     o = align256(o + (size_t)S * geo.H * geo.W * sizeof(float2));
     l.Q = o;
     o = align256(o + (size_t)S * K * geo.H * geo.W * sizeof(float2));
-    l.chord = o;
-    o = align256(o + (size_t)S * kMaxModes * geo.W * sizeof(int2));
     l.colrange = o;
     o = align256(o + (size_t)S * sizeof(int2));
     l.ctr = o;
@@ -116,7 +114,6 @@ Work carve(void *ws, const Layout &l, int32_t *status) {
     w.pairs = reinterpret_cast<int32_t *>(b + l.pairs);
     w.G = reinterpret_cast<float2 *>(b + l.G);
     w.Q = reinterpret_cast<float2 *>(b + l.Q);
-    w.chord = reinterpret_cast<int2 *>(b + l.chord);
     w.colrange = reinterpret_cast<int2 *>(b + l.colrange);
     w.slotmap = nullptr;
     w.slotmap_ppp = 0;
@@ -283,7 +280,7 @@ int enqueue_group(osog_plan *p, const float *soa, int64_t ld, const int32_t *cou
         rc = run_kernel(p, OSOG_KERNEL_BIN_COUNT, st, [&] { return launch_bin_count(soa, ld, gd, geo, w, st); });
         if (rc) return rc;
     }
-    // The scan also tabulates the pupil chords used by the render kernels.
+    // The scan also bounds the columns that any pupil passes.
     rc = run_kernel(p, OSOG_KERNEL_BIN_SCAN, st, [&] { return launch_bin_scan(gd, geo, w, st); });
     if (rc) return rc;
     if (stage == kBinOnly) {  // autotuner dry run: the per-band pair totals only
@@ -711,8 +708,8 @@ int osog_render_dic_incoherent(osog_plan_t *p, const float *soa, int64_t ld, int
     ia.tw = p->tw_w;
     ia.S = 1;
     ia.K = 1;
-    // Each step tabulates its modality's chords (full for every op but the
-    // pupil) before the render kernels run.
+    // Each step bounds its modality's columns (all of them for every op but
+    // the pupil) before the render kernels run.
     auto use_mode = [&](const ModeDev &md) {
         gd.md[0][0] = md;
         ca.md[0][0] = md;

@@ -33,6 +33,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 template <int N>
 __global__ void __launch_bounds__(kThreads, 1) k_bwd_rows(const __grid_constant__ BwdRowsArgs a) {
+    pdl_enter();
     constexpr int L = set_elems(N) / N;
     constexpr int LS = line_stride(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_rows(const __grid_constant_
 
 template <int N>
 __global__ void __launch_bounds__(kThreads, 1) k_bwd_column(const __grid_constant__ BwdColumnArgs a) {
+    pdl_enter();
     constexpr int L = set_elems(N) / N;
     constexpr int LS = line_stride(N);
     constexpr int NW = kThreads / 32;
@@ -83,9 +85,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_column(const __grid_constan
     }
     float2 *Gb = a.w.G + ((size_t)s * geo.nblocks + bk) * N * B;
     load_block<N>(bufE, Gb, geo, bk, cr);
-    for (int j = threadIdx.x; j < K * B; j += kThreads) {
-        const int m = j >> lb, c = j & (B - 1);
-        chords[m * L + c] = a.w.chord[((size_t)s * K + m) * geo.W + bk * B + c];
+    for (int j = threadIdx.x; j < K * B; j += kThreads) {  // this block's chords
+        const int m = j >> lb, c = j & (B - 1), kx = bk * B + c;
+        chords[m * L + c] = mode_chord(a.md[s][m], kx < half ? kx : kx - geo.W, N);
     }
     __syncthreads();
     fft_lines<N, L, false>(bufE, a.tw);  // E^ of the block's columns
@@ -148,6 +150,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_column(const __grid_constan
 
 template <int N>
 __global__ void __launch_bounds__(kThreads, 1) k_bwd_strip(const __grid_constant__ BwdStripArgs a) {
+    pdl_enter();
     constexpr int L = set_elems(N) / N;
     constexpr int LS = line_stride(N);
     constexpr int NW = kThreads / 32;
@@ -248,6 +251,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_strip(const __grid_constant
 }
 
 __global__ void __launch_bounds__(kChunk) k_bwd_reduce(const __grid_constant__ BwdReduceArgs a) {
+    pdl_enter();
     const Geometry &geo = a.geo;
     if ((int)blockIdx.x >= a.nchunks) {  // optics: sum the per-block partials
         // Warp f sums component f: lane l adds blocks l, l + 32, ... in
@@ -275,17 +279,35 @@ __global__ void __launch_bounds__(kChunk) k_bwd_reduce(const __grid_constant__ B
     const Rect q = a.w.rect[p];
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (q.x0 <= q.x1 && q.y0 <= q.y1) {
+        // The particle's band slots, 8 at a time: all slot loads first, then
+        // the partials of every (slot, strip) in band and strip order.
         const int spb = geo.BH / geo.R;
-        const int b0 = q.y0 / geo.BH, b1 = q.y1 / geo.BH;
-        for (int b = b0; b <= b1 && b - b0 < a.w.slotmap_ppp; ++b) {
-            const int slot = a.w.slotmap[(size_t)p * a.w.slotmap_ppp + (b - b0)];
-            if (slot < 0) continue;
-            for (int k = 0; k < spb; ++k) {
-                const int r0 = b * geo.BH + k * geo.R;
-                if (r0 > q.y1 || r0 + geo.R - 1 < q.y0) continue;
-                const float *src = a.part + ((size_t)(sc.pair0 + slot) * spb + k) * 8;
+        const int b0 = q.y0 / geo.BH;
+        const int nb = min(q.y1 / geo.BH - b0 + 1, a.w.slotmap_ppp);
+        const int32_t *sm = a.w.slotmap + (size_t)p * a.w.slotmap_ppp;
+        for (int j0 = 0; j0 < nb; j0 += 8) {
+            int slot[8];
 #pragma unroll
-                for (int f = 0; f < 8; ++f) acc[f] += src[f];
+            for (int j = 0; j < 8; ++j) slot[j] = j0 + j < nb ? sm[j0 + j] : -1;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (slot[j] < 0) continue;
+                const int b = b0 + j0 + j;
+                const float4 *src =
+                    reinterpret_cast<const float4 *>(a.part + (size_t)(sc.pair0 + slot[j]) * spb * 8);
+                for (int k = 0; k < spb; ++k) {
+                    const int r0 = b * geo.BH + k * geo.R;
+                    if (r0 > q.y1 || r0 + geo.R - 1 < q.y0) continue;
+                    const float4 u = src[2 * k], v = src[2 * k + 1];
+                    acc[0] += u.x;
+                    acc[1] += u.y;
+                    acc[2] += u.z;
+                    acc[3] += u.w;
+                    acc[4] += v.x;
+                    acc[5] += v.y;
+                    acc[6] += v.z;
+                    acc[7] += v.w;
+                }
             }
         }
     }
@@ -297,16 +319,16 @@ __global__ void __launch_bounds__(kChunk) k_bwd_reduce(const __grid_constant__ B
 template <int N>
 struct BwdLaunch {
     static cudaError_t rows(const BwdRowsArgs &a, cudaStream_t st) {
-        k_bwd_rows<N><<<dim3(a.geo.nstrips, a.S * a.K), kThreads, strip_inverse_smem(N), st>>>(a);
-        return cudaGetLastError();
+        return launch_chain(k_bwd_rows<N>, dim3(a.geo.nstrips, a.S * a.K), kThreads,
+                            strip_inverse_smem(N), st, a);
     }
     static cudaError_t column(const BwdColumnArgs &a, cudaStream_t st) {
-        k_bwd_column<N><<<dim3(a.geo.nblocks, a.S), kThreads, bwd_column_smem(N), st>>>(a);
-        return cudaGetLastError();
+        return launch_chain(k_bwd_column<N>, dim3(a.geo.nblocks, a.S), kThreads, bwd_column_smem(N),
+                            st, a);
     }
     static cudaError_t strip(const BwdStripArgs &a, cudaStream_t st) {
-        k_bwd_strip<N><<<dim3(a.geo.nstrips, a.S), kThreads, bwd_strip_smem(N), st>>>(a);
-        return cudaGetLastError();
+        return launch_chain(k_bwd_strip<N>, dim3(a.geo.nstrips, a.S), kThreads, bwd_strip_smem(N), st,
+                            a);
     }
     static cudaError_t prepare(int which) {
         if (which == 0)
@@ -369,8 +391,7 @@ cudaError_t launch_bwd_strip(const BwdStripArgs &a, cudaStream_t st) {
     return dispatch_n<BwdStrip>(a.geo.W, a, st);
 }
 cudaError_t launch_bwd_reduce(const BwdReduceArgs &a, cudaStream_t st) {
-    k_bwd_reduce<<<a.nchunks + a.S, kChunk, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_chain(k_bwd_reduce, dim3(a.nchunks + a.S), kChunk, 0, st, a);
 }
 
 }  // namespace osog

@@ -14,8 +14,8 @@
 //   scan   (one CTA per scene): exclusive prefix of cnt over the scene's
 //          chunks for every band, then over bands, giving each band's list
 //          start in the scene's pair region.
-//          The same kernel tabulates, per scene, the pupil chord of every
-//          column (double precision) and which columns any pupil passes.
+//          The same kernel bounds, per scene, the columns that any pupil
+//          passes (the column kernels compute the exact chords).
 //   fill   (one CTA per chunk): the ballots again; a particle's slot is the
 //          band start + chunk prefix + earlier warps of the chunk + the
 //          popcount of lower lanes.  Each band list is therefore in
@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(kChunk)
 k_bin_count(const float *__restrict__ soa, int64_t ld, const __grid_constant__ GroupDev gd,
             Geometry geo, Work w) {
     __shared__ int wcnt[kChunk / 32][kMaxBands];
+    pdl_enter();
     const int chunk = blockIdx.x;
     const int s = scene_of_chunk(gd, chunk);
     const SceneDev &sc = gd.sc[s];
@@ -206,12 +207,8 @@ k_bin_count(const float *__restrict__ soa, int64_t ld, const __grid_constant__ G
 __global__ void __launch_bounds__(1024)
 k_bin_scan(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
     __shared__ int total[kMaxBands];
-    __shared__ int frange[2];
+    pdl_enter();
     const int s = blockIdx.x;
-    if (threadIdx.x == 0) {
-        frange[0] = INT32_MAX;
-        frange[1] = INT32_MIN;
-    }
     const SceneDev &sc = gd.sc[s];
     const int nch = (s + 1 < gd.S ? gd.sc[s + 1].chunk0 : gd.nchunks) - sc.chunk0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -243,31 +240,36 @@ k_bin_scan(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
         off[geo.nbands] = acc;
         if (acc > sc.pair_cap) latch(w.status, OSOG_ERR_BIN_OVERFLOW);
     }
-    // Pupil chords of every column and modality (double precision), and the
-    // hull [lo, hi] of the signed column frequencies that any modality passes
-    // (each pupil's columns form an interval, so the hull covers them all).
-    for (int kx = threadIdx.x; kx < geo.W; kx += blockDim.x) {
-        const int fx = kx < geo.W / 2 ? kx : kx - geo.W;
-        bool act = false;
+    // Hull [lo, hi] of the signed column frequencies that any modality may
+    // pass: for a pupil, the columns with (fx / (W dx) + ox)^2 <= r2, widened
+    // by one column on each side (rounding); every column for the other
+    // operations.  Columns outside the hull are never read or written; the
+    // column kernels decide the rest from the exact chords.
+    if (threadIdx.x == 0) {
+        const double wlo = -(double)(geo.W / 2), whi = (double)(geo.W / 2 - 1);
+        int lo = INT32_MAX, hi = INT32_MIN;
         for (int m = 0; m < gd.K; ++m) {
             const ModeDev &md = gd.md[s][m];
-            const int2 ch = md.op == kOpPupil ? pupil_chord(md, fx)
-                                              : make_int2(-geo.H / 2, geo.H / 2 - 1);
-            w.chord[((size_t)s * gd.K + m) * geo.W + kx] = ch;
-            act = act || ch.x <= ch.y;
+            double a = wlo, b = whi;
+            if (md.op == kOpPupil) {
+                const double r = sqrt(md.r2);
+                a = fmin(fmax(floor((-r - md.ox) / md.fx_scale) - 1.0, wlo), whi + 1.0);
+                b = fmax(fmin(ceil((r - md.ox) / md.fx_scale) + 1.0, whi), wlo - 1.0);
+            }
+            if (a <= b) {
+                lo = min(lo, (int)a);
+                hi = max(hi, (int)b);
+            }
         }
-        if (act) {
-            atomicMin(&frange[0], fx);
-            atomicMax(&frange[1], fx);
-        }
+        w.colrange[s] = make_int2(lo, hi);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) w.colrange[s] = make_int2(frange[0], frange[1]);
 }
 
 __global__ void __launch_bounds__(kChunk)
 k_bin_fill(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
     __shared__ int wpre[kChunk / 32][kMaxBands];
+    __shared__ int start[kMaxBands];  // band list start + this chunk's prefix
+    pdl_enter();
     const int chunk = blockIdx.x;
     const int s = scene_of_chunk(gd, chunk);
     const SceneDev &sc = gd.sc[s];
@@ -275,7 +277,10 @@ k_bin_fill(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
     const bool mine = local < sc.n;
     const int p = sc.p0 + local;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int32_t *off = w.band_off + (int64_t)s * (geo.nbands + 1);
+    const int32_t *pre = w.cnt + (int64_t)chunk * geo.nbands;
     for (int i = threadIdx.x; i < (kChunk / 32) * kMaxBands; i += kChunk) (&wpre[0][0])[i] = 0;
+    for (int b = threadIdx.x; b < geo.nbands; b += kChunk) start[b] = off[b] + pre[b];
     int b0 = 1, b1 = 0;
     if (mine) band_range(w.rect[p], geo.BH, b0, b1);
     __syncthreads();
@@ -297,14 +302,12 @@ k_bin_fill(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
         }
     }
     __syncthreads();
-    const int32_t *off = w.band_off + (int64_t)s * (geo.nbands + 1);
-    const int32_t *pre = w.cnt + (int64_t)chunk * geo.nbands;
     const unsigned lt = lanemask_lt();
     for (int b = lo; b <= hi; ++b) {
         const bool in = any && b0 <= b && b <= b1;
         const unsigned m = __ballot_sync(0xffffffffu, in);
         if (in) {
-            const int slot = off[b] + pre[b] + wpre[warp][b] + __popc(m & lt);
+            const int slot = start[b] + wpre[warp][b] + __popc(m & lt);
             if (slot < sc.pair_cap) w.pairs[sc.pair0 + slot] = p;
             if (w.slotmap && b - b0 < w.slotmap_ppp)
                 w.slotmap[(size_t)p * w.slotmap_ppp + (b - b0)] = slot < sc.pair_cap ? slot : -1;
@@ -317,21 +320,18 @@ k_bin_fill(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
 cudaError_t launch_bin_count(const float *soa, int64_t ld, const GroupDev &gd,
                              const Geometry &geo, const Work &w, cudaStream_t st) {
     if (gd.nchunks == 0) return cudaSuccess;
-    k_bin_count<<<gd.nchunks, kChunk, 0, st>>>(soa, ld, gd, geo, w);
-    return cudaGetLastError();
+    return launch_chain(k_bin_count, dim3(gd.nchunks), kChunk, 0, st, soa, ld, gd, geo, w);
 }
 
 cudaError_t launch_bin_scan(const GroupDev &gd, const Geometry &geo, const Work &w,
                             cudaStream_t st) {
-    k_bin_scan<<<gd.S, 1024, 0, st>>>(gd, geo, w);
-    return cudaGetLastError();
+    return launch_chain(k_bin_scan, dim3(gd.S), 1024, 0, st, gd, geo, w);
 }
 
 cudaError_t launch_bin_fill(const GroupDev &gd, const Geometry &geo, const Work &w,
                             cudaStream_t st) {
     if (gd.nchunks == 0) return cudaSuccess;
-    k_bin_fill<<<gd.nchunks, kChunk, 0, st>>>(gd, geo, w);
-    return cudaGetLastError();
+    return launch_chain(k_bin_fill, dim3(gd.nchunks), kChunk, 0, st, gd, geo, w);
 }
 
 }  // namespace osog

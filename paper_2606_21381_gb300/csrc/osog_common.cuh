@@ -136,8 +136,8 @@ struct Work {
     int32_t *pairs;     // record indices, per band, ascending
     float2 *G;          // [S][W/B][H][B] row spectra
     float2 *Q;          // [S][K][W/B][H][B] filtered columns
-    int2 *chord;        // [S][K][W] rows [lo, hi] inside the pupil per column
-    int2 *colrange;     // [S] signed column frequencies [lo, hi] any pupil passes
+    int2 *colrange;     // [S] signed column frequencies [lo, hi] outside which no
+                        // pupil passes anything (a hull, possibly wider)
     int32_t *slotmap;   // [n][pairs per particle] band-list slot of each (particle,
                         // band); written by the fill pass when not null (adjoint)
     int32_t slotmap_ppp;
@@ -164,6 +164,48 @@ __device__ __forceinline__ int2 pupil_chord(const ModeDev &md, int fx) {
     const double lo = (-root - md.oy) * md.fy_span;
     const double hi = (root - md.oy) * md.fy_span;
     return make_int2((int)ceil(lo), (int)floor(hi));
+}
+
+// Rows [lo, hi] of column fx (signed) that a modality's column operation
+// touches on an H-row canvas: the pupil chord, or the whole column for the
+// operations without a pupil circle.
+__device__ __forceinline__ int2 mode_chord(const ModeDev &md, int fx, int H) {
+    return md.op == kOpPupil ? pupil_chord(md, fx) : make_int2(-H / 2, H / 2 - 1);
+}
+
+// ---------------------------------------------------------------- launches
+// Programmatic dependent launch.  Every kernel of the render and adjoint
+// chains starts with pdl_enter(): it first lets the next kernel of the
+// stream be dispatched (once all CTAs of this grid have done the same), then
+// waits until the kernels before it in the stream have completed and their
+// writes are visible.  Nothing is read from global memory before the wait,
+// so the overlap covers launch and CTA dispatch only.  Launched without the
+// attribute (launch_chain), or after other stream work, the wait returns at
+// once.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launch of a chain kernel, with programmatic stream serialization allowed
+// for grids of at most kPdlMaxCtas CTAs: it shortens chains of small,
+// latency-bound launches (one scene), while for grids of many waves (the
+// batched path) the early dispatch measured slower.
+constexpr long kPdlMaxCtas = 1024;
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chain(void (*kernel)(KArgs...), dim3 grid, int block, size_t smem,
+                                cudaStream_t st, Args &&...args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = (long)grid.x * grid.y * grid.z <= kPdlMaxCtas ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
 }
 
 // ---------------------------------------------------------------- status

@@ -113,8 +113,6 @@ extern "C" int osog_render_noalloc(const float *soa, int64_t ld, int32_t n,
     off = up256(off + (size_t)geo.H * geo.W * sizeof(float2));
     const size_t o_Q = off;
     off = up256(off + (size_t)K * geo.H * geo.W * sizeof(float2));
-    const size_t o_chord = off;
-    off = up256(off + (size_t)kMaxModes * geo.W * sizeof(int2));
     const size_t o_colrange = off;
     off = up256(off + sizeof(int2));
     if (off > kScratchBytes) return OSOG_ERR_WORKSPACE;  // beyond the 8 MiB static scratch
@@ -133,7 +131,6 @@ extern "C" int osog_render_noalloc(const float *soa, int64_t ld, int32_t n,
     w.pairs = reinterpret_cast<int32_t *>(st->scratch + o_pairs);
     w.G = reinterpret_cast<float2 *>(st->scratch + o_G);
     w.Q = reinterpret_cast<float2 *>(st->scratch + o_Q);
-    w.chord = reinterpret_cast<int2 *>(st->scratch + o_chord);
     w.colrange = reinterpret_cast<int2 *>(st->scratch + o_colrange);
     w.slotmap = nullptr;
     w.slotmap_ppp = 0;

@@ -114,6 +114,7 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
 template <int N, int MODE, bool SQ>
 __global__ void __launch_bounds__(kThreads, 2) k_strip_forward(const __grid_constant__ StripArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_enter();
     strip_forward_item<N, MODE, SQ>(a, blockIdx.y, blockIdx.x, smem_raw);
 }
 
@@ -159,9 +160,9 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
             if (e < NB_) buf0[(e & (B - 1)) * LS + pad16(e >> lb)] = v[i];
         }
     }
-    for (int j = threadIdx.x; j < K * B; j += kThreads) {
-        const int m = j >> lb, c = j & (B - 1);
-        chords[m * L + c] = a.w.chord[((size_t)s * K + m) * W + bk * B + c];
+    for (int j = threadIdx.x; j < K * B; j += kThreads) {  // this block's chords
+        const int m = j >> lb, c = j & (B - 1), kx = u0 + c;
+        chords[m * L + c] = mode_chord(a.md[s][m], kx < half ? kx : kx - W, N);
     }
     __syncthreads();
     if (!a.unit_input) fft_lines<N, L, false>(buf0, a.tw);
@@ -215,6 +216,7 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
 template <int N, bool MULTI, bool SQ>
 __global__ void __launch_bounds__(kThreads, 2) k_column(const __grid_constant__ ColumnArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_enter();
     column_item<N, MULTI, SQ>(a, blockIdx.y, blockIdx.x, smem_raw);
 }
 
@@ -267,6 +269,7 @@ __device__ __forceinline__ void inverse_item(const InverseArgs &a, int sm, int s
 template <int N, bool SQ>
 __global__ void __launch_bounds__(kThreads, 2) k_strip_inverse(const __grid_constant__ InverseArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_enter();
     inverse_item<N, SQ>(a, blockIdx.y, blockIdx.x, smem_raw);
 }
 
@@ -389,16 +392,15 @@ struct StripFwdLaunch {
     static cudaError_t run(const StripArgs &a, StripMode mode, cudaStream_t st, size_t smem) {
         dim3 grid(a.geo.nstrips, a.S);
         if (mode == kStripRender && a.geo.H == a.geo.W)
-            k_strip_forward<N, kStripRender, true><<<grid, kThreads, smem, st>>>(a);
+            return launch_chain(k_strip_forward<N, kStripRender, true>, grid, kThreads, smem, st, a);
         else if (mode == kStripRender)
-            k_strip_forward<N, kStripRender, false><<<grid, kThreads, smem, st>>>(a);
+            return launch_chain(k_strip_forward<N, kStripRender, false>, grid, kThreads, smem, st, a);
         else if (mode == kStripOpdOnly)
-            k_strip_forward<N, kStripOpdOnly, false><<<grid, kThreads, smem, st>>>(a);
+            return launch_chain(k_strip_forward<N, kStripOpdOnly, false>, grid, kThreads, smem, st, a);
         else if (mode == kStripFromReal)
-            k_strip_forward<N, kStripFromReal, false><<<grid, kThreads, smem, st>>>(a);
+            return launch_chain(k_strip_forward<N, kStripFromReal, false>, grid, kThreads, smem, st, a);
         else
-            k_strip_forward<N, kStripFromMap, false><<<grid, kThreads, smem, st>>>(a);
-        return cudaGetLastError();
+            return launch_chain(k_strip_forward<N, kStripFromMap, false>, grid, kThreads, smem, st, a);
     }
     static cudaError_t prepare(size_t smem) {
         cudaError_t e = cudaFuncSetAttribute(k_strip_forward<N, kStripRender, true>,
@@ -425,14 +427,13 @@ struct ColumnLaunch {
         dim3 grid(a.geo.nblocks, a.S);
         const bool sq = a.geo.H == a.geo.W;
         if (a.K > 1 && sq)
-            k_column<N, true, true><<<grid, kThreads, smem, st>>>(a);
+            return launch_chain(k_column<N, true, true>, grid, kThreads, smem, st, a);
         else if (a.K > 1)
-            k_column<N, true, false><<<grid, kThreads, smem, st>>>(a);
+            return launch_chain(k_column<N, true, false>, grid, kThreads, smem, st, a);
         else if (sq)
-            k_column<N, false, true><<<grid, kThreads, smem, st>>>(a);
+            return launch_chain(k_column<N, false, true>, grid, kThreads, smem, st, a);
         else
-            k_column<N, false, false><<<grid, kThreads, smem, st>>>(a);
-        return cudaGetLastError();
+            return launch_chain(k_column<N, false, false>, grid, kThreads, smem, st, a);
     }
     static cudaError_t prepare(size_t smem1, size_t smem2) {
         cudaError_t e = cudaSuccess;
@@ -452,10 +453,9 @@ struct InverseLaunch {
     static cudaError_t run(const InverseArgs &a, cudaStream_t st, size_t smem) {
         dim3 grid(a.geo.nstrips, a.S * a.K);
         if (a.geo.H == a.geo.W)
-            k_strip_inverse<N, true><<<grid, kThreads, smem, st>>>(a);
+            return launch_chain(k_strip_inverse<N, true>, grid, kThreads, smem, st, a);
         else
-            k_strip_inverse<N, false><<<grid, kThreads, smem, st>>>(a);
-        return cudaGetLastError();
+            return launch_chain(k_strip_inverse<N, false>, grid, kThreads, smem, st, a);
     }
     static cudaError_t prepare(size_t smem) {
         cudaError_t e = cudaFuncSetAttribute(k_strip_inverse<N, true>,
