@@ -801,6 +801,35 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def fwd_bwd_only(reps: int = 5) -> None:
+    """The inverse-rendering scene's training step alone (512^2, 200
+    particles, brightfield + DIC): `reps` pairs of osog_render_keep and
+    osog_render_backward_kept, timed with CUDA events (profiling runs)."""
+    import torch
+
+    from paper_2606_21381_gb300 import scenes
+    from paper_2606_21381_gb300.render import Renderer
+    dev = torch.device("cuda")
+    soa, o = scenes.inverse_512()
+    r = Renderer(512, 512, dev)
+    x = torch.from_numpy(soa).to(dev)
+    w = torch.randn((2, 512, 512), device=dev)
+    ws, ms = None, []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record()
+        _, ws = r.render_keep(x, None, o, ws=ws)
+        r.backward_kept(x, None, o, w, ws)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    if r.sync_status() != 0:
+        raise RuntimeError("device status set in the forward + adjoint run")
+    print(json.dumps({"workload": "512x512, 200 particles, brightfield + DIC: "
+                                  "osog_render_keep + osog_render_backward_kept",
+                      "ms": [round(v, 4) for v in ms]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -812,6 +841,9 @@ def main():
     ap.add_argument("--convs-only", action="store_true",
                     help="time the warm-start network's convolution kernels on one 64-crop "
                          "batch (both tensor-core engines) and exit")
+    ap.add_argument("--fwd-bwd-only", action="store_true",
+                    help="run five forward + adjoint pairs of the 512x512 inverse-rendering "
+                         "scene and exit (profiling runs)")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the learned warm-start benchmark (training + inverse solves)")
     ap.add_argument("--quick", action="store_true",
@@ -824,6 +856,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.convs_only:
         convs_only()
+        return
+    if args.fwd_bwd_only:
+        fwd_bwd_only()
         return
     if args.impl == "reference":
         res = run_reference(args, rank, world)
