@@ -116,8 +116,10 @@ def test_empty_scene_background_every_size(N):
         assert np.abs(got[k] - bg[k]).max() <= I_TOL * bg[k]
 
 
-@pytest.mark.parametrize("N", [32, 128, 1024])
+@pytest.mark.parametrize("N", [32, 64, 128, 256, 512, 1024])
 def test_random_scene_every_fft_plan(N):
+    """Every transform length below 2048 (each has its own radix plan, and
+    the strip height and column-block width follow from its set size)."""
     rng = np.random.default_rng(N)
     n = max(4, N * N // 300)
     soa = scenes.draw_particles(rng, n, N, N, mu=(0.0, 0.02))
