@@ -306,6 +306,23 @@ int osog_render_backward_kept(osog_plan_t *plan, const float *soa, int64_t ld, i
                               osog_stream_t stream);
 
 /*
+ * Bind a device array of the four differentiable optics scalars to the plan:
+ *   params_dev  device float32 [4]: defocus_um, shear_px, shear_angle,
+ *               bias_phase (the order of grad_optics)
+ * While bound, every render and adjoint of this plan (all entry points that
+ * take a plan) reads these four values on the device when its kernels run,
+ * and ignores the optics struct's own four fields; the struct's other fields
+ * apply as before.  A CUDA graph captured from such calls therefore sees the
+ * values a device-side update writes between replays (an inverse-rendering
+ * step without a device-to-host read of the optics).  The array stays the
+ * caller's and must outlive the binding and any graph that uses it; its
+ * values are not checked (non-finite values give non-finite images).  NULL
+ * unbinds.  OSOG_ERR_INVALID_ARG for a NULL plan or a pointer that is not
+ * 4-byte aligned.
+ */
+int osog_plan_bind_optics_params(osog_plan_t *plan, const float *params_dev);
+
+/*
  * Batched forward render of S scenes that share the plan's H x W and the
  * same modality bits (per-scene optics may otherwise differ).
  *   soa_all  device float32 [9][ld]; scene s owns columns

@@ -28,7 +28,7 @@ EXPORTS = ("osog_plan_create", "osog_plan_destroy", "osog_workspace_size", "osog
            "osog_render_backward_kept", "osog_autotune",
            "osog_polyhedra_workspace_size", "osog_render_polyhedra",
            "osog_dic_incoherent_workspace_size", "osog_render_dic_incoherent",
-           "osog_sensor_noise")
+           "osog_sensor_noise", "osog_plan_bind_optics_params")
 
 
 class OsogError(RuntimeError):
@@ -126,6 +126,8 @@ def lib(build_if_missing: bool = True):
     L.osog_backward_workspace_size.restype = sz
     L.osog_render_backward.argtypes = [vp, vp, i64, i32, P(Optics), vp, vp, vp, vp, sz, vp]
     L.osog_render_backward.restype = ctypes.c_int
+    L.osog_plan_bind_optics_params.argtypes = [vp, vp]
+    L.osog_plan_bind_optics_params.restype = ctypes.c_int
     L.osog_render_keep.argtypes = [vp, vp, i64, i32, P(Optics), vp, vp, sz, vp]
     L.osog_render_keep.restype = ctypes.c_int
     L.osog_render_backward_kept.argtypes = [vp, vp, i64, i32, P(Optics), vp, vp, vp, vp, sz, vp]

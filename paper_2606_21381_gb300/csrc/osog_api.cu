@@ -47,6 +47,8 @@ struct osog_plan {
         osog_optics_t optics;
     };
     std::vector<Kept> kept;
+    // device array of the four differentiable optics scalars, or null
+    const float *optics_dyn = nullptr;
 };
 
 namespace {
@@ -149,7 +151,7 @@ SceneDev scene_dev(const osog_optics_t &o) {
     return s;
 }
 
-ModeDev mode_dev(const osog_optics_t &o, uint32_t mode) {
+ModeDev mode_dev(const osog_optics_t &o, uint32_t mode, const float *dyn) {
     const double two_pi = 6.283185307179586476925286766559;
     ModeDev m{};
     const double r = o.NA / o.lambda_um;
@@ -174,6 +176,8 @@ ModeDev mode_dev(const osog_optics_t &o, uint32_t mode) {
     m.dic = mode == OSOG_MODE_DIC ? 1 : 0;
     m.dsx1 = (float)(0.5 * o.dx_um * cos(o.shear_angle));
     m.dsy1 = (float)(0.5 * o.dx_um * sin(o.shear_angle));
+    m.dyn = dyn;
+    m.half_dx = (float)(0.5 * o.dx_um);
     return m;
 }
 
@@ -259,7 +263,7 @@ int enqueue_group(osog_plan *p, const float *soa, int64_t ld, const int32_t *cou
         pairs += (int64_t)counts[s] * pairs_per_particle;
         int k = 0;
         for (int bit = 0; bit < 3; ++bit)
-            if (optics[s].modes & (1u << bit)) gd.md[s][k++] = mode_dev(optics[s], 1u << bit);
+            if (optics[s].modes & (1u << bit)) gd.md[s][k++] = mode_dev(optics[s], 1u << bit, p->optics_dyn);
     }
     if (pairs > INT32_MAX || n > INT32_MAX) return fail(OSOG_ERR_INVALID_ARG, "too many particles");
     gd.nchunks = (int32_t)chunks;
@@ -410,7 +414,7 @@ int bwd_setup(osog_plan *p, const float *soa, int64_t ld, int32_t n, const osog_
     b.sc.pair_cap = (int32_t)((int64_t)n * ppp);
     b.gd.sc[0] = b.sc;
     for (int bit = 0, k = 0; bit < 3; ++bit)
-        if (optics->modes & (1u << bit)) b.gd.md[0][k++] = mode_dev(*optics, 1u << bit);
+        if (optics->modes & (1u << bit)) b.gd.md[0][k++] = mode_dev(*optics, 1u << bit, p->optics_dyn);
     b.w = carve(ws, b.bl.fwd, p->status);
     b.w.slotmap = reinterpret_cast<int32_t *>(static_cast<char *>(ws) + b.bl.slotmap);
     b.w.slotmap_ppp = ppp;
@@ -726,7 +730,7 @@ int osog_render_dic_incoherent(osog_plan_t *p, const float *soa, int64_t ld, int
 
     // 1. |h|^2: unit spectrum times the brightfield pupil (NA, defocus),
     //    inverse transform, squared modulus (h = IDFT2(P) / (H W)).
-    const ModeDev bf = mode_dev(*optics, OSOG_MODE_BRIGHTFIELD);
+    const ModeDev bf = mode_dev(*optics, OSOG_MODE_BRIGHTFIELD, p->optics_dyn);
     ca.unit_input = 1;
     ia.images = J;
     ia.real_out = 0;
@@ -741,7 +745,7 @@ int osog_render_dic_incoherent(osog_plan_t *p, const float *soa, int64_t ld, int
     if ((rc = use_mode(sp)) || (rc = strip(kStripFromReal)) || (rc = column())) return rc;
     // 3. J = |D|^2, D = IDFT2(DFT2(U) 2i sin(k . ds + theta)) / (H W): the
     //    exit wave sheared and interfered on every frequency (Eq. 5).
-    ModeDev dic = mode_dev(*optics, OSOG_MODE_DIC);
+    ModeDev dic = mode_dev(*optics, OSOG_MODE_DIC, p->optics_dyn);
     dic.op = kOpAllPass;
     dic.dz = 0.f;
     const int64_t chunks = (n + kChunk - 1) / kChunk;
@@ -876,6 +880,7 @@ int osog_batch_submit(osog_plan_t *p, const float *soa_all, int64_t ld, const in
     put(&opt.ppp, sizeof opt.ppp);
     put(&opt.persistent, sizeof opt.persistent);
     put(&opt.band_rows, sizeof opt.band_rows);
+    put(&p->optics_dyn, sizeof p->optics_dyn);
     if (!(p->gexec && key == p->gkey)) {
         const int64_t before = p->launches;
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
@@ -1048,6 +1053,14 @@ int osog_autotune(osog_plan_t *p, const float *soa_all, int64_t ld, const int32_
         out->persistent = chosen.persistent ? 1 : -1;
         out->band_rows = chosen.band_rows;
     }
+    return OSOG_OK;
+}
+
+int osog_plan_bind_optics_params(osog_plan_t *p, const float *params_dev) {
+    if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    if (reinterpret_cast<uintptr_t>(params_dev) & 3)
+        return fail(OSOG_ERR_INVALID_ARG, "optics parameters not 4-byte aligned");
+    p->optics_dyn = params_dev;
     return OSOG_OK;
 }
 

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_column(const __grid_constan
     for (int i = 0; i < ept(N); ++i) acc[i] = make_float2(0.f, 0.f);
     float po[4] = {0.f, 0.f, 0.f, 0.f};
     for (int m = 0; m < K; ++m) {
-        const ModeDev &md = a.md[s][m];
+        const ModeDev md = live_mode(a.md[s][m]);
         const float2 *Qb = a.w.Q + (((size_t)s * K + m) * geo.nblocks + bk) * N * B;
         load_block<N>(bufZ, Qb, geo, bk, cr);
         __syncthreads();

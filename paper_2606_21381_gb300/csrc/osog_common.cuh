@@ -107,7 +107,30 @@ struct ModeDev {
     int32_t op;           // kOpPupil, kOpAllPass, kOpTable or kOpSpectrum
     float2 *tab;          // kOpTable: multiplier table; kOpSpectrum: output
                           // (both column-blocked [W/B][H][B] like Q)
+    const float *dyn;     // bound optics scalars (defocus_um, shear_px, shear_angle,
+                          // bias_phase) read when the kernel runs; null: dz .. bias above
+    float half_dx;        // dx / 2 (um): dsx, dsy of the bound shear
 };
+
+// The modality with the plan's bound optics scalars applied (see
+// osog_plan_bind_optics_params): defocus, DIC shear and bias are read from
+// device memory when the kernel runs, so a replayed CUDA graph sees values
+// updated on the device between replays.
+__device__ __forceinline__ ModeDev live_mode(const ModeDev &m) {
+    ModeDev r = m;
+    if (m.dyn) {
+        const float sp = m.dyn[1];
+        float sa, ca;
+        sincosf(m.dyn[2], &sa, &ca);
+        r.dz = m.dyn[0];
+        r.dsx = m.half_dx * sp * ca;
+        r.dsy = m.half_dx * sp * sa;
+        r.dsx1 = m.half_dx * ca;
+        r.dsy1 = m.half_dx * sa;
+        r.bias = m.dyn[3];
+    }
+    return r;
+}
 
 // What the column pass does with one (scene, modality):
 //   kOpPupil     multiply by the transfer function inside the pupil chord
@@ -216,11 +239,14 @@ __device__ __forceinline__ void latch(int32_t *status, int code) {
 // ---------------------------------------------------------------- complex
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// The products are written as one rounded product and one fused
+// multiply-add, so that every kernel that inlines them rounds alike
+// (the compiler cannot contract them differently in different kernels).
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return make_float2(fmaf(a.x, b.x, -__fmul_rn(a.y, b.y)), fmaf(a.x, b.y, __fmul_rn(a.y, b.x)));
 }
 __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
-    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+    return make_float2(fmaf(a.x, b.x, __fmul_rn(a.y, b.y)), fmaf(a.y, b.x, -__fmul_rn(a.x, b.y)));
 }
 
 // ---------------------------------------------------------------- float-float

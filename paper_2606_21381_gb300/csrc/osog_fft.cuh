@@ -61,7 +61,7 @@ __device__ __forceinline__ float2 twc(float2 x) {
     } else {
         constexpr float c = cos16(m);
         constexpr float s = INV ? sin16(m) : -sin16(m);
-        return make_float2(x.x * c - x.y * s, x.x * s + x.y * c);
+        return make_float2(fmaf(x.x, c, -__fmul_rn(x.y, s)), fmaf(x.x, s, __fmul_rn(x.y, c)));
     }
 }
 

@@ -167,7 +167,7 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
     __syncthreads();
     if (!a.unit_input) fft_lines<N, L, false>(buf0, a.tw);
     for (int m = 0; m < K; ++m) {
-        const ModeDev &md = a.md[s][m];
+        const ModeDev md = live_mode(a.md[s][m]);
         if (md.op == kOpSpectrum) {  // the forward spectrum itself, to md.tab
             float2 *T = md.tab + (size_t)bk * N * B;
 #pragma unroll
@@ -261,7 +261,7 @@ __device__ __forceinline__ void inverse_item(const InverseArgs &a, int sm, int s
         const int e = threadIdx.x + i * kThreads;
         if (e < RN) {
             const float2 v = buf[(e / N) * LS + pad16(e % N)];
-            img[e] = a.real_out ? v.x : fmaf(v.x, v.x, v.y * v.y);
+            img[e] = a.real_out ? v.x : fmaf(v.x, v.x, __fmul_rn(v.y, v.y));
         }
     }
 }

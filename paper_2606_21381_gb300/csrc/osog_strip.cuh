@@ -233,21 +233,24 @@ __device__ __forceinline__ float2 exit_wave(float opd, float att, float two_over
 // oblique shift), times 2i sin(k . ds + theta) for DIC (Eq. 5).  The defocus
 // phase is evaluated as -dz |q|^2 / (sqrt(k0^2 - |q|^2) + k0), which has no
 // cancellation for small |q|.
+// Every product that could be contracted into a fused multiply-add is
+// written out (rounded product or fmaf), so that all kernels round alike.
 __device__ __forceinline__ float2 transfer(const ModeDev &md, int fx, int fy) {
-    const float kx = (float)fx * md.kstep_x, ky = (float)fy * md.kstep_y;
-    const float qx = kx + md.qoff_x, qy = ky + md.qoff_y;
-    const float q2 = fmaf(qx, qx, qy * qy);
-    const float chi = __fdividef(-md.dz * q2, sqrtf(fmaxf(fmaf(md.k0, md.k0, -q2), 0.f)) + md.k0);
+    const float kx = __fmul_rn((float)fx, md.kstep_x), ky = __fmul_rn((float)fy, md.kstep_y);
+    const float qx = __fadd_rn(kx, md.qoff_x), qy = __fadd_rn(ky, md.qoff_y);
+    const float q2 = fmaf(qx, qx, __fmul_rn(qy, qy));
+    const float chi = __fdividef(__fmul_rn(-md.dz, q2),
+                                 __fadd_rn(sqrtf(fmaxf(fmaf(md.k0, md.k0, -q2), 0.f)), md.k0));
     float sn, cs;
     phase_sincos(chi, &sn, &cs);
     float2 h = make_float2(cs, sn);
     if (md.dic) {
         float sa, ca;
         phase_sincos(fmaf(kx, md.dsx, fmaf(ky, md.dsy, md.bias)), &sa, &ca);
-        const float g = 2.f * sa;
-        h = make_float2(-sn * g, cs * g);
+        const float g = __fmul_rn(2.f, sa);
+        h = make_float2(__fmul_rn(-sn, g), __fmul_rn(cs, g));
     }
-    return make_float2(h.x * md.scale, h.y * md.scale);
+    return make_float2(__fmul_rn(h.x, md.scale), __fmul_rn(h.y, md.scale));
 }
 
 // ---------------------------------------------------------------- layouts

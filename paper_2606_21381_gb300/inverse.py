@@ -43,6 +43,12 @@ class SolveConfig:
     log_every: int = 0
     spectral_weight: float = 0.0     # weight of the log-amplitude spectral loss (Eq. 8)
     record_every: int = 0            # with a ground truth: error history every n steps
+    # "graph": every step on the device, replayed as one CUDA graph after a
+    # few eager warm-up steps; "device": the same step launched eagerly;
+    # "autograd": torch autograd through autograd.render with the optics
+    # scalars on the host (one device-to-host read per step)
+    mode: str = "graph"
+    warmup_steps: int = 3            # eager steps before the graph is captured
 
 
 @dataclass
@@ -137,14 +143,127 @@ def _device_errors(x: torch.Tensor, truth: torch.Tensor) -> torch.Tensor:
     return torch.stack([rel_dn.median(), rel_T.median(), within])
 
 
+class _DeviceStep:
+    """One solve step with all of its state on the device: the render with
+    the forward intermediates kept (osog_render_keep), the curriculum misfit
+    and its gradient with respect to the image (torch autograd on the
+    misfit alone), the adjoint (osog_render_backward_kept), and Adam on the
+    free particle rows and on defocus and shear.  The four optics scalars
+    are a device tensor bound to the plan, so the step reads no value back
+    to the host and can be captured as a CUDA graph.  The step counter, the
+    curriculum cut-off and the Adam bias corrections are device scalars
+    too."""
+
+    def __init__(self, target, soa0, optics0, renderer, cfg, fixed_optics):
+        dev = renderer.device
+        self.r, self.cfg, self.target = renderer, cfg, target
+        self.o = dict(optics0)
+        self.x = torch.from_numpy(np.ascontiguousarray(soa0, dtype=np.float32)).to(dev)
+        self.free = torch.zeros_like(self.x, dtype=torch.bool)
+        self.free[list(FREE_ROWS)] = True
+        self.lr = torch.zeros_like(self.x)
+        self.lr[0] = self.lr[1] = cfg.lr_pos
+        self.lr[2] = cfg.lr_theta
+        self.lr[5] = cfg.lr_T
+        self.lr[6] = cfg.lr_dn
+        self.params = torch.tensor([float(optics0[k]) for k in OPTICS_PARAMS],
+                                   dtype=torch.float32, device=dev)
+        self.plr = torch.tensor([0.0 if fixed_optics else cfg.lr_defocus,
+                                 0.0 if fixed_optics else cfg.lr_shear, 0.0, 0.0],
+                                dtype=torch.float32, device=dev)
+        self.m1, self.m2 = torch.zeros_like(self.x), torch.zeros_like(self.x)
+        self.p1, self.p2 = torch.zeros_like(self.params), torch.zeros_like(self.params)
+        self.t = torch.zeros((), dtype=torch.float32, device=dev)
+        self.losses = torch.zeros(max(cfg.steps, 1), dtype=torch.float32, device=dev)
+        K, H, W = target.shape
+        self.misfit = SpectralMisfit(target, optics0["dx"], float(target.numel()))
+        self.ramp = float(max(1, int(cfg.steps * cfg.curriculum_frac)))
+        self.img = torch.empty((K, H, W), dtype=torch.float32, device=dev)
+        self.ws = torch.empty(renderer.backward_workspace_size(self.x.shape[1], K),
+                              dtype=torch.uint8, device=dev)
+
+    def __call__(self) -> None:
+        cfg, o = self.cfg, self.o
+        b1, b2 = cfg.betas
+        na = cfg.na_start + (o["NA"] - cfg.na_start) * torch.clamp(self.t / self.ramp, max=1.0)
+        cutoff = 2.0 * na / o["lambda_um"]
+        self.r.render_keep(self.x, None, o, out=self.img, ws=self.ws)
+        img = self.img.detach().requires_grad_(True)
+        with torch.enable_grad():
+            loss = self.misfit(img, cutoff)
+            if cfg.spectral_weight:
+                loss = loss + cfg.spectral_weight * spectral_loss(img, self.target)
+            (g_img,) = torch.autograd.grad(loss, img)
+        gx, gp = self.r.backward_kept(self.x, None, o, g_img.contiguous(), self.ws)
+        t1 = self.t + 1.0
+        c1, c2 = 1.0 - torch.pow(b1, t1), 1.0 - torch.pow(b2, t1)
+        self.m1.mul_(b1).add_(gx, alpha=1 - b1)
+        self.m2.mul_(b2).addcmul_(gx, gx, value=1 - b2)
+        step = self.lr * (self.m1 / c1) / (torch.sqrt(self.m2 / c2) + 1e-30)
+        self.x.sub_(torch.where(self.free, step, torch.zeros_like(step)))
+        self.x[5].clamp_(min=1e-3)
+        self.p1.mul_(b1).add_(gp, alpha=1 - b1)
+        self.p2.mul_(b2).addcmul_(gp, gp, value=1 - b2)
+        self.params.sub_(self.plr * (self.p1 / c1) / (torch.sqrt(self.p2 / c2) + 1e-30))
+        self.losses.index_copy_(0, self.t.long().view(1), loss.detach().view(1))
+        self.t.copy_(t1)
+
+
+def _solve_device(target, soa0, optics0, renderer, cfg, fixed_optics, truth) -> SolveResult:
+    dev = renderer.device
+    st = _DeviceStep(target, soa0, optics0, renderer, cfg, fixed_optics)
+    res = SolveResult(soa=None, optics_params=None)
+    truth_d = None
+    if truth is not None and cfg.record_every:
+        truth_d = torch.from_numpy(np.ascontiguousarray(truth, dtype=np.float32)).to(dev)
+    stream = torch.cuda.Stream(dev)
+    stream.wait_stream(torch.cuda.current_stream(dev))
+    renderer.bind_optics_params(st.params)
+    try:
+        with torch.cuda.stream(stream):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            if truth_d is not None:
+                res.history.append((0, 0.0, *_device_errors(st.x, truth_d).tolist()))
+            eager = cfg.steps if cfg.mode == "device" else min(cfg.warmup_steps, cfg.steps)
+            graph = None
+            for it in range(cfg.steps):
+                if it < eager:
+                    st()
+                else:
+                    if graph is None:
+                        graph = torch.cuda.CUDAGraph()
+                        with torch.cuda.graph(graph, stream=stream):
+                            st()
+                    graph.replay()
+                if truth_d is not None and (it + 1) % cfg.record_every == 0:
+                    e = _device_errors(st.x, truth_d).tolist()
+                    res.history.append((it + 1, time.perf_counter() - t0, *e))
+            torch.cuda.synchronize(dev)
+            res.seconds = time.perf_counter() - t0
+    finally:
+        renderer.bind_optics_params(None)
+    torch.cuda.current_stream(dev).wait_stream(stream)
+    res.steps = cfg.steps
+    res.losses = st.losses[:cfg.steps].cpu().tolist()
+    res.soa = st.x.cpu().numpy()
+    res.optics_params = st.params.cpu().double().numpy()
+    return res
+
+
 def solve(target: torch.Tensor, soa0: np.ndarray, optics0: dict, renderer: Renderer,
           cfg: SolveConfig | None = None, fixed_optics: bool = False,
           truth: np.ndarray | None = None) -> SolveResult:
     """Adam on the curriculum-filtered squared image misfit.  target is the
     (K, H, W) measured image; soa0 / optics0 the initial guess.  With the
     true particle tensor and cfg.record_every > 0 the error history is
-    recorded (the clock keeps running across the records)."""
+    recorded (the clock keeps running across the records).  cfg.mode picks
+    the device-resident step (CUDA graph or eager) or the autograd loop."""
     cfg = cfg or SolveConfig()
+    if cfg.mode in ("graph", "device"):
+        return _solve_device(target, soa0, optics0, renderer, cfg, fixed_optics, truth)
+    if cfg.mode != "autograd":
+        raise ValueError("SolveConfig.mode must be 'graph', 'device' or 'autograd'")
     dev = renderer.device
     soa = torch.from_numpy(np.ascontiguousarray(soa0, dtype=np.float32)).to(dev)
     free = torch.zeros_like(soa, dtype=torch.bool)

@@ -288,6 +288,18 @@ class Renderer:
         image_host.copy_(img, non_blocking=True)
         return image_host
 
+    def bind_optics_params(self, params: torch.Tensor | None) -> None:
+        """osog_plan_bind_optics_params: every later call of this plan reads
+        (defocus, shear_px, shear_angle, bias_phase) from `params` (a float32
+        device tensor of 4) when its kernels run, instead of from the optics
+        dict; None unbinds.  The renderer keeps a reference while bound."""
+        if params is not None and (params.device.type != "cuda" or params.dtype != torch.float32
+                                   or params.shape != (4,) or not params.is_contiguous()):
+            raise ValueError("params must be a contiguous float32 CUDA tensor of shape (4,)")
+        check(self._L.osog_plan_bind_optics_params(self.plan, _ptr(params)),
+              "osog_plan_bind_optics_params")
+        self._bound_params = params
+
     # ------------------------------------------------------------ status / timing
     def sync_status(self, stream=None) -> int:
         return int(self._L.osog_sync_status(self.plan, _stream(stream)))

@@ -51,3 +51,81 @@ def test_solve_with_the_spectral_loss_term():
     x1 = torch.from_numpy(res.soa).cuda()
     assert float(inverse.spectral_loss(r.render(x1, None, o), target)) < \
         0.1 * float(inverse.spectral_loss(r.render(x0, None, o0), target))
+
+
+def _scene_and_guess(seed):
+    from paper_2606_21381_gb300 import inverse
+    from paper_2606_21381_gb300.render import Renderer
+    soa, o = scenes.inverse_512()
+    o = dict(o, defocus=0.8, shear_px=1.0)
+    r = Renderer(512, 512)
+    target = r.render(torch.from_numpy(soa).cuda(), None, o)
+    s0, o0 = inverse.perturb(soa, o, np.random.default_rng(seed))
+    return soa, o, r, target, s0, o0
+
+
+def test_graph_replays_equal_the_eager_device_steps():
+    """The captured solve step replayed as a CUDA graph gives bit for bit
+    what the same step launched eagerly gives."""
+    from paper_2606_21381_gb300 import inverse
+    soa, o, r, target, s0, o0 = _scene_and_guess(9)
+    out = {}
+    for mode in ("graph", "device"):
+        res = inverse.solve(target, s0, o0, r, inverse.SolveConfig(steps=12, mode=mode))
+        assert r.sync_status() == 0
+        out[mode] = res
+    assert np.array_equal(out["graph"].soa, out["device"].soa)
+    assert np.array_equal(out["graph"].optics_params, out["device"].optics_params)
+    assert out["graph"].losses == out["device"].losses
+    assert out["graph"].losses[-1] < out["graph"].losses[0]
+
+
+def test_autograd_loop_agrees_with_the_device_step():
+    """The autograd loop (optics on the host, float64 Adam on them) and the
+    device-resident step take the same path within float rounding."""
+    from paper_2606_21381_gb300 import inverse
+    soa, o, r, target, s0, o0 = _scene_and_guess(10)
+    a = inverse.solve(target, s0, o0, r, inverse.SolveConfig(steps=30, mode="autograd"))
+    d = inverse.solve(target, s0, o0, r, inverse.SolveConfig(steps=30, mode="graph"))
+    assert r.sync_status() == 0
+    # Adam moves a parameter whose gradient is near zero by about +-lr per
+    # step whatever its size, so rounding can flip single particles' early
+    # steps: compare medians over the particles and the losses
+    for row in (0, 1, 2, 5, 6):
+        moved = np.median(np.abs(a.soa[row] - s0[row]))
+        diff = np.median(np.abs(a.soa[row] - d.soa[row]))
+        assert diff <= 0.05 * moved + 1e-7, (row, diff, moved)
+    assert np.allclose(a.optics_params, d.optics_params, rtol=1e-2, atol=1e-4)
+    assert abs(a.losses[-1] - d.losses[-1]) <= 0.05 * a.losses[-1]
+    assert abs(a.losses[0] - d.losses[0]) <= 1e-4 * a.losses[0]
+
+
+def test_bound_optics_scalars_match_the_struct():
+    """Defocus, shear and bias read from a bound device array give the images
+    and gradients of the same values given in the optics struct."""
+    from paper_2606_21381_gb300.autograd import OPTICS_PARAMS
+    soa, o, r, target, s0, o0 = _scene_and_guess(11)
+    x = torch.from_numpy(soa).cuda()
+    want = dict(o, defocus=0.6, shear_px=1.3, shear_angle=0.5, bias_phase=0.9)
+    gI = torch.randn((2, 512, 512), device="cuda")
+    img_s = r.render(x, None, want)
+    g_s = r.backward(x, None, want, gI)
+    params = torch.tensor([want[k] for k in OPTICS_PARAMS], dtype=torch.float32, device="cuda")
+    r.bind_optics_params(params)
+    try:
+        img_b = r.render(x, None, o)          # the struct's four scalars are ignored
+        g_b = r.backward(x, None, o, gI)
+        params[0] = 0.0                       # read when the kernels run
+        img_0 = r.render(x, None, o)
+    finally:
+        r.bind_optics_params(None)
+    img_0s = r.render(x, None, dict(want, defocus=0.0))
+    assert r.sync_status() == 0
+    scale = float(img_s.abs().max())
+    assert float((img_b - img_s).abs().max()) <= 1e-5 * scale
+    assert float((img_0 - img_0s).abs().max()) <= 1e-5 * scale
+    assert float((img_0 - img_s).abs().max()) > 1e-3 * scale
+    for a, b in zip(g_b, g_s):
+        assert float((a - b).abs().max()) <= 1e-3 * float(b.abs().max())
+    # unbound again: the struct's values apply
+    assert torch.equal(r.render(x, None, want), img_s)
