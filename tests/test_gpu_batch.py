@@ -100,3 +100,30 @@ def test_host_pipeline_matches_batch():
     for (soa_all, offs, optics), h in zip(batches, outs):
         want = r.batch(torch.from_numpy(soa_all).cuda(), offs, optics).cpu()
         assert torch.equal(h, want)
+
+
+def test_bound_optics_scalars_in_the_batched_path():
+    """With a bound device array every scene of a batch takes its defocus,
+    shear and bias from it, also through the cached CUDA graph (whose key
+    includes the binding), and unbinding restores the per-scene values."""
+    from paper_2606_21381_gb300.autograd import OPTICS_PARAMS
+    soas, optics, dev, offs = batch(77, 4, 256, 7)
+    r = renderer(256, 256)
+    vals = {"defocus": 0.7, "shear_px": 1.4, "shear_angle": 0.3, "bias_phase": 1.1}
+    same = [dict(o, **vals) for o in optics]
+    want = r.batch(dev, offs, same, tuning={"use_graph": 1}).clone()
+    own = r.batch(dev, offs, optics, tuning={"use_graph": 1}).clone()
+    params = torch.tensor([vals[k] for k in OPTICS_PARAMS], dtype=torch.float32, device="cuda")
+    r.bind_optics_params(params)
+    try:
+        got = [r.batch(dev, offs, optics, tuning={"use_graph": g}).clone() for g in (0, 1, 1)]
+    finally:
+        r.bind_optics_params(None)
+    back = r.batch(dev, offs, optics, tuning={"use_graph": 1}).clone()
+    assert r.sync_status() == 0
+    scale = float(want.abs().max())
+    for g in got:
+        assert float((g - want).abs().max()) <= 1e-5 * scale
+    assert torch.equal(got[1], got[2]) and torch.equal(got[0], got[1])
+    assert torch.equal(back, own)
+    assert float((own - want).abs().max()) > 1e-3 * scale
