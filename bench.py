@@ -175,13 +175,20 @@ def issue_peak_ginst():
 
 
 def source_digest() -> str:
-    """Hash of the sources the render kernels and their launches are built
-    from (the convolution and noise kernels do not enter)."""
+    """Hash of the code the render kernels and their launches are built
+    from (the convolution and noise kernels do not enter): comments and
+    blank lines are removed first, so that editing a comment keeps the
+    recorded counters valid while any change to the code voids them."""
     import hashlib
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2606_21381_gb300", "csrc")
     for f in RENDER_SOURCES:
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        text = open(os.path.join(csrc, f), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        lines = [ln.rstrip() for ln in text.splitlines() if ln.strip()]
+        h.update("\n".join(lines).encode())
     return h.hexdigest()[:12]
 
 

@@ -265,7 +265,8 @@ size_t osog_backward_workspace_size(const osog_plan_t *plan, int32_t n_max, int3
  *   grad_optics  device float32 [4]: dL/d(defocus_um, shear_px, shear_angle,
  *                bias_phase); the shear and bias entries are zero unless the
  *                DIC modality is selected
- * The forward intermediates are recomputed, not read from an earlier render;
+ * The forward intermediates are recomputed, not read from an earlier render
+ * (osog_render_keep + osog_render_backward_kept below keep them instead);
  * every sum runs in a fixed order (bitwise reproducible).  The pupil circle
  * is a hard cut-off, so NA has no gradient.  Workspace:
  * osog_backward_workspace_size(plan, n, K).  Errors as for osog_render.

@@ -138,7 +138,7 @@ __device__ __forceinline__ void raster_particle(float2 *buf, int LS, int y0, con
 // order, into shared memory together with their records (one parallel
 // global load per round instead of one dependent load per particle).  Each
 // warp then rasterises, in order, the staged particles that overlap its own
-// N/8 columns.
+// N/16 columns (16 warps of the 512-thread CTA).
 template <int N>
 __device__ void raster_strip(const Geometry &geo, const Work &w, const SceneDev &sc, int s,
                              int y0, float2 *buf, PRec *srec, Rect *srect, int *wsum) {
