@@ -219,14 +219,23 @@ class Adam:
 
     @torch.no_grad()
     def step(self, grads, lr=None) -> None:
+        """p -= lr (m / c1) / (sqrt(v / c2) + eps) on all parameters at once
+        (multi-tensor operations: a few launches instead of a few per
+        tensor)."""
         self.t += 1
         b1, b2 = self.betas
         lr = self.lr if lr is None else lr
         c1, c2 = 1 - b1 ** self.t, 1 - b2 ** self.t
-        for p, g, m, v in zip(self.p, grads, self.m, self.v):
-            m.mul_(b1).add_(g, alpha=1 - b1)
-            v.mul_(b2).addcmul_(g, g, value=1 - b2)
-            p.sub_(lr * (m / c1) / (torch.sqrt(v / c2) + self.eps))
+        torch._foreach_mul_(self.m, b1)
+        torch._foreach_add_(self.m, grads, alpha=1 - b1)
+        torch._foreach_mul_(self.v, b2)
+        torch._foreach_addcmul_(self.v, grads, grads, value=1 - b2)
+        den = torch._foreach_div(self.v, c2)
+        torch._foreach_sqrt_(den)
+        torch._foreach_add_(den, self.eps)
+        upd = torch._foreach_div(self.m, den)
+        torch._foreach_mul_(upd, lr / c1)
+        torch._foreach_sub_(self.p, upd)
 
 
 # ------------------------------------------------------------------ data
