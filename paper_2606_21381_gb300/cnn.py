@@ -169,8 +169,16 @@ class WarmStartNet:
         self.refresh()
 
     def refresh(self) -> None:
-        """Round the master weights to the bf16 copies the kernels read."""
-        self.wb = [w.to(torch.bfloat16).contiguous() for w in self.w]
+        """Round the master weights to the bf16 copies the kernels read (in
+        place once they exist, so that a captured CUDA graph keeps reading
+        the current values)."""
+        wb = getattr(self, "wb", None)
+        if wb is not None and len(wb) == len(self.w) and all(
+                a.shape == b.shape and a.device == b.device for a, b in zip(wb, self.w)):
+            for a, b in zip(wb, self.w):
+                a.copy_(b)
+        else:
+            self.wb = [w.to(torch.bfloat16).contiguous() for w in self.w]
 
     def parameters(self) -> list[torch.Tensor]:
         return self.w + self.b
@@ -373,7 +381,10 @@ class RenderStream:
         dev = self.r.device
         st = self.staging
         st.next_turn()
-        imgs = self.r.batch(st.to_device("soa", soa_all, dev), offsets, optics_list)
+        # direct launches: the counts change every batch, so a cached graph
+        # would be captured anew each time
+        imgs = self.r.batch(st.to_device("soa", soa_all, dev), offsets, optics_list,
+                            tuning={"use_graph": 0})
         x = pack_input(imgs, self.crop)
         tgt, mask = cell_targets(soas, optics_list, self.size, self.crop)
         return x, st.to_device("tgt", tgt, dev), st.to_device("mask", mask, dev)
@@ -384,14 +395,17 @@ def loss_and_grad(out: torch.Tensor, tgt: torch.Tensor, mask: torch.Tensor):
     """Loss of the head output and its gradient: logistic loss of the centre
     heat map over all cells, squared error of (T, dn, dn T) at cells holding
     a centre, squared error of the cell-averaged global channels."""
+    # channels by slices only (no index tensors to copy from the host, so
+    # the step can be captured as a CUDA graph): T and dn are adjacent, the
+    # four global channels too
     o = out.detach().requires_grad_(True)
     heat = torch.nn.functional.binary_cross_entropy_with_logits(o[..., CH_HEAT], tgt[..., CH_HEAT])
     m = mask.float()
-    reg_ch = [CH_T, CH_DN, CH_OPD]
-    reg = (((o[..., reg_ch] - tgt[..., reg_ch]) ** 2).sum(-1) * m).sum() / m.sum().clamp(min=1.0)
-    glob_ch = [CH_DEFOCUS, CH_NA, CH_SHEAR, CH_MEAN_DN]
-    g = o[..., glob_ch].mean(dim=(1, 2))
-    glob = ((g - tgt[:, 0, 0, glob_ch]) ** 2).sum(-1).mean()
+    d = o - tgt
+    sq = (d[..., CH_T:CH_DN + 1] ** 2).sum(-1) + d[..., CH_OPD] ** 2
+    reg = (sq * m).sum() / m.sum().clamp(min=1.0)
+    g = o[..., CH_DEFOCUS:CH_MEAN_DN + 1].mean(dim=(1, 2))
+    glob = ((g - tgt[:, 0, 0, CH_DEFOCUS:CH_MEAN_DN + 1]) ** 2).sum(-1).mean()
     loss = heat + reg + glob
     loss.backward()
     return loss.detach(), o.grad, torch.stack([heat.detach(), reg.detach(), glob.detach()])
@@ -407,6 +421,10 @@ class TrainConfig:
     lr_final: float = 1e-4          # cosine decay to this
     seed: int = 0
     log_every: int = 0
+    # replay the network's step (forward, loss, backward, Adam) as one CUDA
+    # graph after a few eager steps; the render of each batch stays eager
+    graph: bool = True
+    warmup_steps: int = 3
 
 
 @dataclass
@@ -417,8 +435,51 @@ class TrainResult:
     losses: np.ndarray              # (steps, 4): total, heat, regression, global
 
 
+class _GraphedStep:
+    """The network's training step on static input buffers with every
+    per-step scalar on the device (step count, cosine learning rate, Adam
+    bias corrections), so that it can be captured once as a CUDA graph and
+    replayed: forward, loss and its gradient, backward, Adam (per tensor,
+    with device scalars) and the bf16 weight copies."""
+
+    def __init__(self, net, opt, cfg, steps, x, tgt, mask):
+        self.net, self.opt, self.cfg, self.steps = net, opt, cfg, float(steps)
+        self.x, self.tgt, self.mask = x.clone(), tgt.clone(), mask.clone()
+        self.t = torch.zeros((), dtype=torch.float32, device=net.device)
+        self.out = torch.zeros(4, dtype=torch.float32, device=net.device)
+
+    def load(self, x, tgt, mask) -> None:
+        self.x.copy_(x)
+        self.tgt.copy_(tgt)
+        self.mask.copy_(mask)
+
+    def __call__(self) -> None:
+        net, opt, cfg = self.net, self.opt, self.cfg
+        b1, b2 = opt.betas
+        lr = cfg.lr_final + 0.5 * (cfg.lr - cfg.lr_final) * (
+            1.0 + torch.cos(math.pi * self.t / self.steps))
+        t1 = self.t + 1.0
+        c1, c2 = 1.0 - torch.pow(b1, t1), 1.0 - torch.pow(b2, t1)
+        out, acts = net.forward(self.x)
+        loss, dout, parts = loss_and_grad(out, self.tgt, self.mask)
+        grads = net.backward(dout, acts)
+        with torch.no_grad():
+            for p, g, m, v in zip(opt.p, [g[0] for g in grads] + [g[1] for g in grads],
+                                  opt.m, opt.v):
+                m.mul_(b1).add_(g, alpha=1 - b1)
+                v.mul_(b2).addcmul_(g, g, value=1 - b2)
+                p.sub_(lr * (m / c1) / (torch.sqrt(v / c2) + opt.eps))
+            net.refresh()
+            self.out[0] = loss
+            self.out[1:] = parts
+            self.t.copy_(t1)
+
+
 def train(net: WarmStartNet, cfg: TrainConfig | None = None, renderer=None) -> TrainResult:
-    """Adam on crops rendered on the fly, one batched render per step."""
+    """Adam on crops rendered on the fly, one batched render per step.  With
+    cfg.graph the network's step runs eagerly for cfg.warmup_steps steps
+    and is then replayed as one CUDA graph (the render stays eager: its
+    particle counts change every batch)."""
     from .render import Renderer
     cfg = cfg or TrainConfig()
     r = renderer or Renderer(cfg.canvas, cfg.canvas, net.device)
@@ -426,6 +487,8 @@ def train(net: WarmStartNet, cfg: TrainConfig | None = None, renderer=None) -> T
     steps = max(1, math.ceil(cfg.samples / data.crops_per_batch))
     opt = Adam(net.parameters(), cfg.lr)
     hist = torch.zeros((steps, 4), device=net.device)
+    if cfg.graph:
+        return _train_graphed(net, cfg, data, steps, opt, hist)
     torch.cuda.synchronize(net.device)
     t0 = time.perf_counter()
     for it in range(steps):
@@ -443,6 +506,37 @@ def train(net: WarmStartNet, cfg: TrainConfig | None = None, renderer=None) -> T
     torch.cuda.synchronize(net.device)
     return TrainResult(steps, steps * data.crops_per_batch, time.perf_counter() - t0,
                        hist.cpu().numpy())
+
+
+def _train_graphed(net, cfg, data, steps, opt, hist) -> TrainResult:
+    dev = net.device
+    stream = torch.cuda.Stream(dev)
+    stream.wait_stream(torch.cuda.current_stream(dev))
+    step, graph = None, None
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for it in range(steps):
+            x, tgt, mask = data.next()
+            if step is None:
+                step = _GraphedStep(net, opt, cfg, steps, x, tgt, mask)
+            else:
+                step.load(x, tgt, mask)
+            if it < cfg.warmup_steps:
+                step()
+            else:
+                if graph is None:
+                    graph = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(graph, stream=stream):
+                        step()
+                graph.replay()
+            hist[it] = step.out
+            if cfg.log_every and it % cfg.log_every == 0:
+                print(f"step {it:5d} loss {float(step.out[0]):.4f}")
+        torch.cuda.synchronize(dev)
+        seconds = time.perf_counter() - t0
+    torch.cuda.current_stream(dev).wait_stream(stream)
+    return TrainResult(steps, steps * data.crops_per_batch, seconds, hist.cpu().numpy())
 
 
 @torch.no_grad()

@@ -57,3 +57,25 @@ def test_warm_start_reaches_one_percent_in_fewer_steps(trained):
         plain.append(a[0])
         warm.append(b[0])
     assert sum(warm) < 0.85 * sum(plain), (plain, warm)
+
+
+def test_graphed_training_follows_the_eager_loop():
+    """The training step replayed as a CUDA graph (device-side step count,
+    learning rate and bias corrections) takes the path of the eager loop:
+    same renders, same losses up to float rounding, same weights."""
+    from paper_2606_21381_gb300 import cnn
+    from paper_2606_21381_gb300.render import Renderer
+    r = Renderer(512, 512)
+    out = {}
+    for graph in (False, True):
+        net = cnn.WarmStartNet(torch.device("cuda"), seed=3)
+        res = cnn.train(net, cnn.TrainConfig(samples=64 * 12, graph=graph, seed=4), r)
+        out[graph] = (res.losses, [w.clone() for w in net.w])
+    assert r.sync_status() == 0 and cnn.sync_status() == 0
+    la, lb = out[False][0], out[True][0]
+    assert la.shape == lb.shape == (12, 4)
+    assert np.allclose(la, lb, rtol=1e-2, atol=1e-5)
+    # Adam steps a weight by about lr whatever its gradient's size, so a
+    # rounding-level gradient can flip single entries: compare norms
+    for wa, wb in zip(out[False][1], out[True][1]):
+        assert float(torch.linalg.norm(wa - wb)) <= 2e-3 * float(torch.linalg.norm(wa)) + 1e-6
