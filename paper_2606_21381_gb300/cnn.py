@@ -522,7 +522,7 @@ def _train_graphed(net, cfg, data, steps, opt, hist) -> TrainResult:
                 step = _GraphedStep(net, opt, cfg, steps, x, tgt, mask)
             else:
                 step.load(x, tgt, mask)
-            if it < cfg.warmup_steps:
+            if it < max(cfg.warmup_steps, 1):  # eager before the capture
                 step()
             else:
                 if graph is None:

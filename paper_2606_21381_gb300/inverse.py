@@ -225,7 +225,9 @@ def _solve_device(target, soa0, optics0, renderer, cfg, fixed_optics, truth) -> 
             t0 = time.perf_counter()
             if truth_d is not None:
                 res.history.append((0, 0.0, *_device_errors(st.x, truth_d).tolist()))
-            eager = cfg.steps if cfg.mode == "device" else min(cfg.warmup_steps, cfg.steps)
+            # at least one eager step before the capture (plans and kernels
+            # must exist before a graph can record them)
+            eager = cfg.steps if cfg.mode == "device" else min(max(cfg.warmup_steps, 1), cfg.steps)
             graph = None
             for it in range(cfg.steps):
                 if it < eager:
