@@ -228,7 +228,9 @@ inline cudaError_t launch_chain(void (*kernel)(KArgs...), dim3 grid, int block, 
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = (long)grid.x * grid.y * grid.z <= kPdlMaxCtas ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+    if (e != cudaSuccess) (void)cudaGetLastError();  // reported once, by the return value
+    return e;
 }
 
 // ---------------------------------------------------------------- status
