@@ -174,7 +174,7 @@ def issue_peak_ginst():
     return 4 * 152 * mhz / 1e3
 
 
-def source_digest() -> str:
+def source_digest(csrc: str | None = None) -> str:
     """Hash of the code the render kernels and their launches are built
     from (the convolution and noise kernels do not enter): comments and
     blank lines are removed first, so that editing a comment keeps the
@@ -182,7 +182,7 @@ def source_digest() -> str:
     import hashlib
     import re
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2606_21381_gb300", "csrc")
+    csrc = csrc or os.path.join(ROOT, "paper_2606_21381_gb300", "csrc")
     for f in RENDER_SOURCES:
         text = open(os.path.join(csrc, f), encoding="utf-8").read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
