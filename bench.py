@@ -451,6 +451,16 @@ def run_gpu(args, rank, world, local_rank):
     pipe.synchronize()
     pipe_s = time.perf_counter() - t0
     del pipe
+    # the device-to-host rate of the image batch alone (the pipeline's bound
+    # once its copies overlap the renders)
+    d2h_ms = []
+    for i in range(3):
+        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record(stream)
+        img_host[0].copy_(out, non_blocking=True)
+        b.record(stream)
+        stream.synchronize()
+        d2h_ms.append(a.elapsed_time(b))
     with torch.cuda.stream(stream):
         status = r.sync_status(stream)
         if status != 0:
@@ -466,7 +476,8 @@ def run_gpu(args, rank, world, local_rank):
                                            "numa_node": numa_node, "fwd_bwd_dic1024_ms": fb1_ms,
                                            "fwd_bwd_recompute_ms": fb_re_ms,
                                            "deterministic": deterministic,
-                                           "e2e_pipelined": (n_pipe, pipe_s)})
+                                           "e2e_pipelined": (n_pipe, pipe_s),
+                                           "d2h_ms": min(d2h_ms)})
 
 
 def conv_profile(net, x, reps: int = 10):
@@ -714,7 +725,11 @@ def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms
                        "every step; copies of one step overlap the render of the next; "
                        "host wall clock over %d steps" % extra["e2e_pipelined"][0],
                 "serial_value": round(SCENES / (statistics.median(e2e_ms) / 1e3), 2),
-                "host_numa_node": extra.get("numa_node")},
+                "host_numa_node": extra.get("numa_node"),
+                "d2h_gbs": round(SCENES * K * SIZE * SIZE * 4 / extra["d2h_ms"] / 1e6, 1),
+                "copy_bound_value": round(SCENES / (max(extra["d2h_ms"], ms_step) / 1e3), 2),
+                "bound": "the image batch's device-to-host copy (d2h_gbs) or the render, "
+                         "whichever is longer, with copies and renders fully overlapped"},
         "fwd_bwd": None if not fwd_bwd_ms else {
             "ms": round(statistics.median(fwd_bwd_ms), 4),
             "workload": "512x512, 200 particles, brightfield + DIC: osog_render_keep + "
