@@ -748,6 +748,7 @@ int osog_render_dic_incoherent(osog_plan_t *p, const float *soa, int64_t ld, int
     ModeDev dic = mode_dev(*optics, OSOG_MODE_DIC, p->optics_dyn);
     dic.op = kOpAllPass;
     dic.dz = 0.f;
+    dic.fixed_dz = 1;  // the defocus is in |h|^2 (step 1), also when bound
     const int64_t chunks = (n + kChunk - 1) / kChunk;
     gd.nchunks = (int32_t)chunks;
     gd.sc[0].n = n;

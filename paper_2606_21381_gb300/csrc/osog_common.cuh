@@ -110,6 +110,8 @@ struct ModeDev {
     const float *dyn;     // bound optics scalars (defocus_um, shear_px, shear_angle,
                           // bias_phase) read when the kernel runs; null: dz .. bias above
     float half_dx;        // dx / 2 (um): dsx, dsy of the bound shear
+    int32_t fixed_dz;     // 1: dz stays as set here whatever is bound (an operation
+                          // that applies no defocus)
 };
 
 // The modality with the plan's bound optics scalars applied (see
@@ -122,7 +124,7 @@ __device__ __forceinline__ ModeDev live_mode(const ModeDev &m) {
         const float sp = m.dyn[1];
         float sa, ca;
         sincosf(m.dyn[2], &sa, &ca);
-        r.dz = m.dyn[0];
+        if (!m.fixed_dz) r.dz = m.dyn[0];
         r.dsx = m.half_dx * sp * ca;
         r.dsy = m.half_dx * sp * sa;
         r.dsx1 = m.half_dx * ca;

@@ -224,3 +224,18 @@ def test_kept_state_is_checked_and_consumed():
     with pytest.raises(OsogError):
         r.backward_kept(x, None, o, gI, ws)
     assert r.sync_status() == 0
+
+
+def test_kept_state_on_a_non_square_canvas_with_three_modalities():
+    r = renderer(64, 256)
+    rng = np.random.default_rng(12)
+    soa = scenes.draw_particles(rng, 25, 64, 256, mu=(0.002, 0.03))
+    o = scenes.optics(64, 256, modes=7, defocus=-0.6, NA=0.5, shear_px=0.8, bias_phase=0.4)
+    x = torch.from_numpy(np.ascontiguousarray(soa)).cuda()
+    gI = torch.randn((3, 64, 256), device="cuda")
+    img_k, ws = r.render_keep(x, None, o)
+    g_k = r.backward_kept(x, None, o, gI, ws)
+    g = r.backward(x, None, o, gI)
+    assert r.sync_status() == 0
+    assert torch.equal(r.render(x, None, o), img_k)
+    assert torch.equal(g[0], g_k[0]) and torch.equal(g[1], g_k[1])

@@ -46,3 +46,26 @@ def test_empty_field_is_the_bias_background():
     img = r.render_dic_incoherent(torch.zeros((9, 1), device="cuda"), 0, o).cpu().numpy()
     assert r.sync_status() == 0
     np.testing.assert_allclose(img, 4 * math.sin(o["bias_phase"]) ** 2, rtol=0, atol=1e-5)
+
+
+def test_bound_optics_scalars_in_the_incoherent_dic():
+    """The incoherent DIC reads defocus, shear and bias from a bound device
+    array like every other entry point of the plan."""
+    from paper_2606_21381_gb300.autograd import OPTICS_PARAMS
+    from paper_2606_21381_gb300.render import Renderer
+    r = Renderer(128, 128)
+    rng = np.random.default_rng(21)
+    soa = scenes.draw_particles(rng, 20, 128, 128, mu=(0.0, 0.02))
+    x = torch.from_numpy(np.ascontiguousarray(soa)).cuda()
+    base = scenes.optics(128, 128, modes=4, NA=0.5)
+    want = dict(base, defocus=0.4, shear_px=1.2, shear_angle=0.7, bias_phase=0.6)
+    ref = r.render_dic_incoherent(x, None, want)
+    params = torch.tensor([want[k] for k in OPTICS_PARAMS], dtype=torch.float32, device="cuda")
+    r.bind_optics_params(params)
+    try:
+        got = r.render_dic_incoherent(x, None, base)
+    finally:
+        r.bind_optics_params(None)
+    assert r.sync_status() == 0
+    scale = float(ref.abs().max())
+    assert float((got - ref).abs().max()) <= 1e-5 * scale

@@ -129,3 +129,17 @@ def test_bound_optics_scalars_match_the_struct():
         assert float((a - b).abs().max()) <= 1e-3 * float(b.abs().max())
     # unbound again: the struct's values apply
     assert torch.equal(r.render(x, None, want), img_s)
+
+
+def test_graphed_solve_with_fixed_optics():
+    """With the optics fixed the bound scalars never move, and the particles
+    still converge (the guess's optics are the true ones here)."""
+    from paper_2606_21381_gb300 import inverse
+    soa, o, r, target, s0, _ = _scene_and_guess(12)
+    res = inverse.solve(target, s0, o, r, inverse.SolveConfig(steps=200), fixed_optics=True)
+    assert r.sync_status() == 0
+    want = np.array([o[k] for k in ("defocus", "shear_px", "shear_angle", "bias_phase")])
+    assert np.allclose(res.optics_params, want, rtol=0, atol=1e-6)
+    assert res.losses[-1] < 1e-2 * res.losses[0]
+    e = inverse.errors(res.soa, soa)
+    assert e["dn_rel_median"] < 0.01
