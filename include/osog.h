@@ -375,7 +375,9 @@ int64_t osog_plan_launch_count(const osog_plan_t *plan);
  * and writes, per kernel class (OSOG_KERNEL_*), the summed device time in
  * milliseconds and the launch count.  Arrays have OSOG_KERNEL_CLASS_COUNT
  * entries.  At most 8192 launches are timed per session; later ones are
- * counted but not timed.
+ * counted but not timed.  A single scene of at most 256 particles is binned
+ * by one launch (count, scan and fill together), counted as
+ * OSOG_KERNEL_BIN_COUNT.
  */
 int osog_profile_begin(osog_plan_t *plan);
 int osog_profile_end(osog_plan_t *plan, osog_stream_t stream, float *ms,

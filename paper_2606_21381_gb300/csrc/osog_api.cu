@@ -280,24 +280,32 @@ int enqueue_group(osog_plan *p, const float *soa, int64_t ld, const int32_t *cou
         w.plane_coef = reinterpret_cast<float4 *>(static_cast<char *>(ws) + coef);
     }
     int rc;
-    if (stage != kFromMap) {
-        rc = run_kernel(p, OSOG_KERNEL_BIN_COUNT, st, [&] { return launch_bin_count(soa, ld, gd, geo, w, st); });
+    if (stage != kFromMap && stage != kBinOnly && S == 1 && gd.nchunks == 1) {
+        // one scene of one chunk: the three binning passes in one launch
+        rc = run_kernel(p, OSOG_KERNEL_BIN_COUNT, st,
+                        [&] { return launch_bin_single(soa, ld, gd, geo, w, st); });
         if (rc) return rc;
-    }
-    // The scan also bounds the columns that any pupil passes.
-    rc = run_kernel(p, OSOG_KERNEL_BIN_SCAN, st, [&] { return launch_bin_scan(gd, geo, w, st); });
-    if (rc) return rc;
-    if (stage == kBinOnly) {  // autotuner dry run: the per-band pair totals only
-        opt.band_off_out->resize((size_t)S * (geo.nbands + 1));
-        cudaError_t e = cudaMemcpyAsync(opt.band_off_out->data(), w.band_off,
-                                        sizeof(int32_t) * opt.band_off_out->size(),
-                                        cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        return e == cudaSuccess ? OSOG_OK : cuda_fail(e, "autotune dry run");
-    }
-    if (stage != kFromMap) {
-        rc = run_kernel(p, OSOG_KERNEL_BIN_FILL, st, [&] { return launch_bin_fill(gd, geo, w, st); });
+    } else {
+        if (stage != kFromMap) {
+            rc = run_kernel(p, OSOG_KERNEL_BIN_COUNT, st,
+                            [&] { return launch_bin_count(soa, ld, gd, geo, w, st); });
+            if (rc) return rc;
+        }
+        // The scan also bounds the columns that any pupil passes.
+        rc = run_kernel(p, OSOG_KERNEL_BIN_SCAN, st, [&] { return launch_bin_scan(gd, geo, w, st); });
         if (rc) return rc;
+        if (stage == kBinOnly) {  // autotuner dry run: the per-band pair totals only
+            opt.band_off_out->resize((size_t)S * (geo.nbands + 1));
+            cudaError_t e = cudaMemcpyAsync(opt.band_off_out->data(), w.band_off,
+                                            sizeof(int32_t) * opt.band_off_out->size(),
+                                            cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            return e == cudaSuccess ? OSOG_OK : cuda_fail(e, "autotune dry run");
+        }
+        if (stage != kFromMap) {
+            rc = run_kernel(p, OSOG_KERNEL_BIN_FILL, st, [&] { return launch_bin_fill(gd, geo, w, st); });
+            if (rc) return rc;
+        }
     }
     StripArgs sa{};
     sa.geo = geo;
@@ -436,13 +444,20 @@ int bwd_check_grads(const float *grad_image, const float *grad_soa, const float 
 int bwd_forward(osog_plan *p, const float *soa, int64_t ld, const BwdState &b, float *image,
                 cudaStream_t st) {
     const Geometry &geo = p->geo;
-    int rc = run_kernel(p, OSOG_KERNEL_BIN_COUNT, st,
+    int rc;
+    if (b.gd.nchunks == 1) {  // one chunk: the three binning passes in one launch
+        rc = run_kernel(p, OSOG_KERNEL_BIN_COUNT, st,
+                        [&] { return launch_bin_single(soa, ld, b.gd, geo, b.w, st); });
+        if (rc) return rc;
+    } else {
+        rc = run_kernel(p, OSOG_KERNEL_BIN_COUNT, st,
                         [&] { return launch_bin_count(soa, ld, b.gd, geo, b.w, st); });
-    if (rc) return rc;
-    rc = run_kernel(p, OSOG_KERNEL_BIN_SCAN, st, [&] { return launch_bin_scan(b.gd, geo, b.w, st); });
-    if (rc) return rc;
-    rc = run_kernel(p, OSOG_KERNEL_BIN_FILL, st, [&] { return launch_bin_fill(b.gd, geo, b.w, st); });
-    if (rc) return rc;
+        if (rc) return rc;
+        rc = run_kernel(p, OSOG_KERNEL_BIN_SCAN, st, [&] { return launch_bin_scan(b.gd, geo, b.w, st); });
+        if (rc) return rc;
+        rc = run_kernel(p, OSOG_KERNEL_BIN_FILL, st, [&] { return launch_bin_fill(b.gd, geo, b.w, st); });
+        if (rc) return rc;
+    }
     StripArgs sa{};
     sa.geo = geo;
     sa.w = b.w;

@@ -168,6 +168,30 @@ __device__ Rect setup_particle(const float *soa, int64_t ld, int p, const SceneD
     return q;
 }
 
+// Hull [lo, hi] of the signed column frequencies that any modality of scene
+// s may pass: for a pupil, the columns with (fx / (W dx) + ox)^2 <= r2,
+// widened by one column on each side (rounding); every column for the other
+// operations.  Columns outside the hull are never read or written; the
+// column kernels decide the rest from the exact chords.
+__device__ int2 column_hull(const GroupDev &gd, int s, const Geometry &geo) {
+    const double wlo = -(double)(geo.W / 2), whi = (double)(geo.W / 2 - 1);
+    int lo = INT32_MAX, hi = INT32_MIN;
+    for (int m = 0; m < gd.K; ++m) {
+        const ModeDev &md = gd.md[s][m];
+        double a = wlo, b = whi;
+        if (md.op == kOpPupil) {
+            const double r = sqrt(md.r2);
+            a = fmin(fmax(floor((-r - md.ox) / md.fx_scale) - 1.0, wlo), whi + 1.0);
+            b = fmax(fmin(ceil((r - md.ox) / md.fx_scale) + 1.0, whi), wlo - 1.0);
+        }
+        if (a <= b) {
+            lo = min(lo, (int)a);
+            hi = max(hi, (int)b);
+        }
+    }
+    return make_int2(lo, hi);
+}
+
 __global__ void __launch_bounds__(kChunk)
 k_bin_count(const float *__restrict__ soa, int64_t ld, const __grid_constant__ GroupDev gd,
             Geometry geo, Work w) {
@@ -240,29 +264,7 @@ k_bin_scan(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
         off[geo.nbands] = acc;
         if (acc > sc.pair_cap) latch(w.status, OSOG_ERR_BIN_OVERFLOW);
     }
-    // Hull [lo, hi] of the signed column frequencies that any modality may
-    // pass: for a pupil, the columns with (fx / (W dx) + ox)^2 <= r2, widened
-    // by one column on each side (rounding); every column for the other
-    // operations.  Columns outside the hull are never read or written; the
-    // column kernels decide the rest from the exact chords.
-    if (threadIdx.x == 0) {
-        const double wlo = -(double)(geo.W / 2), whi = (double)(geo.W / 2 - 1);
-        int lo = INT32_MAX, hi = INT32_MIN;
-        for (int m = 0; m < gd.K; ++m) {
-            const ModeDev &md = gd.md[s][m];
-            double a = wlo, b = whi;
-            if (md.op == kOpPupil) {
-                const double r = sqrt(md.r2);
-                a = fmin(fmax(floor((-r - md.ox) / md.fx_scale) - 1.0, wlo), whi + 1.0);
-                b = fmax(fmin(ceil((r - md.ox) / md.fx_scale) + 1.0, whi), wlo - 1.0);
-            }
-            if (a <= b) {
-                lo = min(lo, (int)a);
-                hi = max(hi, (int)b);
-            }
-        }
-        w.colrange[s] = make_int2(lo, hi);
-    }
+    if (threadIdx.x == 0) w.colrange[s] = column_hull(gd, s, geo);
 }
 
 __global__ void __launch_bounds__(kChunk)
@@ -315,6 +317,89 @@ k_bin_fill(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
     }
 }
 
+// One scene of at most kChunk particles: count, scan and fill in one CTA.
+// The slots are those of the three kernels (band start, then the earlier
+// warps, then the lower lanes: ascending particle order in every band list),
+// and the scene's column hull is bounded as in the scan.
+__global__ void __launch_bounds__(kChunk)
+k_bin_single(const float *__restrict__ soa, int64_t ld, const __grid_constant__ GroupDev gd,
+             Geometry geo, Work w) {
+    __shared__ int wpre[kChunk / 32][kMaxBands];
+    __shared__ int start[kMaxBands];
+    pdl_enter();
+    const SceneDev &sc = gd.sc[0];
+    const int local = threadIdx.x;
+    const bool mine = local < sc.n;
+    const int p = sc.p0 + local;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < (kChunk / 32) * kMaxBands; i += kChunk) (&wpre[0][0])[i] = 0;
+    int b0 = 1, b1 = 0;
+    if (mine) {
+        const Rect r = setup_particle(soa, ld, p, sc, geo, w);
+        w.rect[p] = r;
+        band_range(r, geo.BH, b0, b1);
+    }
+    __syncthreads();
+    const bool any = b0 <= b1;
+    const int lo = __reduce_min_sync(0xffffffffu, any ? b0 : kMaxBands);
+    const int hi = __reduce_max_sync(0xffffffffu, any ? b1 : -1);
+    for (int b = lo; b <= hi; ++b) {
+        const unsigned m = __ballot_sync(0xffffffffu, any && b0 <= b && b <= b1);
+        if (lane == 0) wpre[warp][b] = __popc(m);
+    }
+    __syncthreads();
+    int total = 0;
+    if (threadIdx.x < geo.nbands) {  // exclusive over the warps, in place
+        const int b = threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < kChunk / 32; ++k) {
+            const int t = wpre[k][b];
+            wpre[k][b] = total;
+            total += t;
+        }
+        start[b] = total;
+    }
+    __syncthreads();
+    if (warp == 0) {  // exclusive over the bands, two per lane (nbands <= 64)
+        const int ba = 2 * lane, bb = ba + 1;
+        const int ta = ba < geo.nbands ? start[ba] : 0, tb = bb < geo.nbands ? start[bb] : 0;
+        int inc = ta + tb;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += t;
+        }
+        const int all = __shfl_sync(0xffffffffu, inc, 31);
+        __syncwarp();
+        int32_t *off = w.band_off;  // scene 0
+        if (ba < geo.nbands) {
+            start[ba] = inc - ta - tb;
+            off[ba] = inc - ta - tb;
+        }
+        if (bb < geo.nbands) {
+            start[bb] = inc - tb;
+            off[bb] = inc - tb;
+        }
+        if (lane == 0) {
+            off[geo.nbands] = all;
+            if (all > sc.pair_cap) latch(w.status, OSOG_ERR_BIN_OVERFLOW);
+            w.colrange[0] = column_hull(gd, 0, geo);
+        }
+    }
+    __syncthreads();
+    const unsigned lt = lanemask_lt();
+    for (int b = lo; b <= hi; ++b) {
+        const bool in = any && b0 <= b && b <= b1;
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (in) {
+            const int slot = start[b] + wpre[warp][b] + __popc(m & lt);
+            if (slot < sc.pair_cap) w.pairs[sc.pair0 + slot] = p;
+            if (w.slotmap && b - b0 < w.slotmap_ppp)
+                w.slotmap[(size_t)p * w.slotmap_ppp + (b - b0)] = slot < sc.pair_cap ? slot : -1;
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_bin_count(const float *soa, int64_t ld, const GroupDev &gd,
@@ -326,6 +411,11 @@ cudaError_t launch_bin_count(const float *soa, int64_t ld, const GroupDev &gd,
 cudaError_t launch_bin_scan(const GroupDev &gd, const Geometry &geo, const Work &w,
                             cudaStream_t st) {
     return launch_chain(k_bin_scan, dim3(gd.S), 1024, 0, st, gd, geo, w);
+}
+
+cudaError_t launch_bin_single(const float *soa, int64_t ld, const GroupDev &gd,
+                              const Geometry &geo, const Work &w, cudaStream_t st) {
+    return launch_chain(k_bin_single, dim3(1), kChunk, 0, st, soa, ld, gd, geo, w);
 }
 
 cudaError_t launch_bin_fill(const GroupDev &gd, const Geometry &geo, const Work &w,

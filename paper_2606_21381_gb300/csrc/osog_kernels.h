@@ -94,6 +94,10 @@ cudaError_t launch_bin_scan(const GroupDev &gd, const Geometry &geo, const Work 
                             cudaStream_t st);
 cudaError_t launch_bin_fill(const GroupDev &gd, const Geometry &geo, const Work &w,
                             cudaStream_t st);
+// count + scan + fill in one launch for a single scene of one chunk
+// (1..kChunk particles); same results as the three launches
+cudaError_t launch_bin_single(const float *soa, int64_t ld, const GroupDev &gd,
+                              const Geometry &geo, const Work &w, cudaStream_t st);
 
 size_t strip_forward_smem(int W);
 size_t column_smem(int H, int K);

@@ -253,8 +253,12 @@ def test_host_side_errors():
 
 
 def test_launch_count_and_profile():
-    soa, o = scenes.plain_256()
+    # more than one binning chunk (256 particles): count, scan, fill, strip,
+    # column, inverse
     r = renderer(256, 256)
+    rng = np.random.default_rng(31)
+    soa = scenes.draw_particles(rng, 300, 256, 256)
+    o = scenes.optics(256, 256, modes=3)
     before = r.launch_count()
     r.profile_begin()
     r.render(torch.from_numpy(soa).cuda(), None, o)
@@ -263,3 +267,30 @@ def test_launch_count_and_profile():
     fwd = ("bin_count", "bin_scan", "bin_fill", "strip_forward", "column", "strip_inverse")
     assert all(prof[k][1] == 1 and prof[k][0] > 0 for k in fwd)
     assert all(v[1] == 0 for k, v in prof.items() if k not in fwd)
+    # one chunk (64 particles): the three binning passes in one launch,
+    # counted as bin_count
+    soa, o = scenes.plain_256()
+    before = r.launch_count()
+    r.profile_begin()
+    r.render(torch.from_numpy(soa).cuda(), None, o)
+    prof = r.profile_end()
+    assert r.launch_count() - before == 4
+    assert prof["bin_count"][1] == 1 and prof["bin_scan"][1] == 0 and prof["bin_fill"][1] == 0
+    assert r.sync_status() == 0
+
+
+def test_single_chunk_binning_equals_the_three_passes():
+    # the same 256 particles rendered alone (one chunk, one launch) and as
+    # the first scene of a batch whose other scene makes the group span
+    # several chunks (count, scan and fill): bitwise the same image
+    r = renderer(256, 256)
+    rng = np.random.default_rng(32)
+    a = scenes.draw_particles(rng, 256, 256, 256, mu=(0.0, 0.02))
+    b = scenes.draw_particles(rng, 700, 256, 256, mu=(0.0, 0.02))
+    o = scenes.optics(256, 256, modes=7, defocus=0.4)
+    alone = r.render(torch.from_numpy(np.ascontiguousarray(a)).cuda(), None, o).clone()
+    soa_all, offs = scenes.concat([a, b])
+    both = r.batch(torch.from_numpy(soa_all).cuda(), offs, [o, o],
+                   tuning={"use_graph": 0}).clone()
+    assert r.sync_status() == 0
+    assert torch.equal(alone, both[0])
