@@ -571,6 +571,9 @@ def warm_start_bench(dev, samples: int = 200_000, seeds=(7, 9, 10)):
     from paper_2606_21381_gb300 import cnn, inverse
     from paper_2606_21381_gb300.render import Renderer
     r = Renderer(512, 512, dev)
+    # warm-up of every code path the timed training takes (kernel modules,
+    # the captured step), on a network of its own
+    cnn.train(cnn.WarmStartNet(dev, seed=1), cnn.TrainConfig(samples=64 * 8, seed=99), r)
     net = cnn.WarmStartNet(dev, seed=0)
     tr = cnn.train(net, cnn.TrainConfig(samples=samples), r)
     ev = cnn.calibrate(net, r)
