@@ -40,6 +40,53 @@ def test_sphere_opd_closed_form():
     assert opd.max() > 0.2
 
 
+def sphere_chord_um(H, W, cx, cy, R_um, dx):
+    """Closed-form chord 2 sqrt(R^2 - r^2) (um) of a sphere through every
+    pixel centre; centre coordinates are the fp32 values the oracle reads."""
+    y, x = np.mgrid[0:H, 0:W] + 0.5
+    r2 = ((x - np.float32(cx)) ** 2 + (y - np.float32(cy)) ** 2) * dx * dx
+    return 2 * np.sqrt(np.maximum(0.0, R_um ** 2 - r2))
+
+
+def test_sphere_absorption_closed_form():
+    """Eq. 4 (Beer-Lambert amplitude) composed like Eq. 2's integral: an
+    absorbing sphere of radius R has absorption exponent ATT = mu * 2
+    sqrt(R^2 - r^2), independent of its dn and orientation."""
+    dx, R_um = 0.5, 2.5
+    H, W = 48, 56
+    for mu, dn, th in ((0.013, 0.02, 0.0), (0.2, 0.0, 1.9), (-0.05, 0.04, 0.4)):
+        soa = one_particle(cx=27.4, cy=22.9, a=R_um / dx, b=R_um / dx, T=2 * R_um, dn=dn,
+                           mu=mu, theta=th)
+        opd, att = oracle.opd_att(soa, 1, H, W, dx=dx)
+        want = np.float64(np.float32(mu)) * sphere_chord_um(H, W, 27.4, 22.9, R_um, dx)
+        assert np.abs(att - want).max() < 1e-12
+        assert np.abs(att).max() > 0.5 * abs(mu) * 2 * R_um
+        # the same chord carries the OPD: ATT / OPD = mu / dn wherever dn != 0
+        if dn:
+            want_opd = np.float64(np.float32(dn)) * sphere_chord_um(H, W, 27.4, 22.9, R_um, dx)
+            assert np.abs(opd - want_opd).max() < 1e-12
+
+
+def test_beer_lambert_intensity_through_an_all_pass_pupil():
+    """Eq. 2 with the amplitude of Eq. 4 imaged through a pupil that passes
+    every grid frequency with unit modulus (NA beyond the grid's corner
+    frequency, dz = 0): I = |E|^2 = exp(-2 ATT) at every pixel, whatever the
+    phase.  ATT is taken from the closed form of two disjoint absorbing
+    spheres, not from the oracle's own map."""
+    dx, H, W = 0.5, 64, 64
+    spheres = ((20.3, 18.6, 3.0, 0.03, 0.011), (41.8, 44.2, 2.25, 0.05, 0.07))  # fp32-exact radii
+    soa = np.concatenate([one_particle(cx=cx, cy=cy, a=R / dx, b=R / dx, T=2 * R, dn=dn, mu=mu)
+                          for cx, cy, R, dn, mu in spheres], axis=1)
+    att = sum(np.float64(np.float32(mu)) * sphere_chord_um(H, W, cx, cy, R, dx)
+              for cx, cy, R, dn, mu in spheres)
+    # corner frequency sqrt(2) / (2 dx) = 1.41 cycles/um < NA / lambda = 1.82
+    o = oracle.make_optics(H, W, dx=dx, lambda_um=0.55, NA=1.0, n_medium=1.5, defocus=0.0,
+                           modes=1)
+    I = oracle.render(soa, 2, o)["images"][0]
+    assert np.abs(I - np.exp(-2 * att)).max() < 1e-12
+    assert I.min() < 0.7  # the absorption did act
+
+
 def test_ellipse_orientation_convention():
     """theta turns the first semi-axis from +x toward +y."""
     th = math.pi / 6
