@@ -162,16 +162,22 @@ def ncu_instructions(kernel: str):
     return None
 
 
-def issue_peak_ginst():
+def sm_count(device=None) -> int:
+    """Streaming multiprocessors of the device (152 on a GB300)."""
+    import torch
+    return int(torch.cuda.get_device_properties(device or 0).multi_processor_count)
+
+
+def issue_peak_ginst(sms: int):
     """Warp-instruction issue peak (G/s): one warp instruction per clock
-    on each of the 4 sub-partitions of the 152 SMs at the measured maximum
-    SM clock."""
+    on each of the 4 sub-partitions of every SM at the measured maximum SM
+    clock."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             mhz = float(json.load(f)["sm_max_mhz"])
     except Exception:
         mhz = 2070.0
-    return 4 * 152 * mhz / 1e3
+    return 4 * sms * mhz / 1e3
 
 
 def source_digest(csrc: str | None = None) -> str:
@@ -209,9 +215,15 @@ def active_fraction(optics: dict) -> float:
 
 def algorithmic_bytes(kernel: str, counts, H: int, W: int, K: int, pairs: int,
                       active: float = 1.0):
-    """Minimum HBM bytes of one launch of each kernel over the batch: row
-    spectra G and filtered columns Q only for the pupil-passed columns
-    (fraction `active`), the image in full."""
+    """Minimum HBM bytes of one launch of each kernel over the batch, per
+    pixel of every scene: 8 B for the row spectra G written by the strip
+    pass, 8 + 8K B for the column pass's read of G and write of the K
+    filtered spectra Q, 8K + 4K B for the inverse pass's read of Q and write
+    of the float32 images (16 + 20K B/px in all), plus 36 B of particle
+    tensor, 64 + 8 B of record and rectangle per particle and 4 B per
+    particle-band pair.  With active < 1 the G and Q terms count only the
+    columns some pupil passes (the pruned figure: the render never writes
+    or reads the others)."""
     px = len(counts) * H * W
     n = int(sum(counts))
     return int({
@@ -364,6 +376,9 @@ def run_gpu(args, rank, world, local_rank):
             stream.synchronize()
             single40k.append(a.elapsed_time(b))
 
+        # ---- the 16 x 1024^2 DIC batch
+        dic_batch = dic_1024_batch(dev, stream, args.steps, *measured_peaks())
+
         # ---- forward + adjoint of the inverse-rendering scene (512^2, 200
         #      particles, brightfield + DIC), one loss gradient per iteration
         fb_soa, fb_o = scenes.inverse_512()
@@ -476,6 +491,7 @@ def run_gpu(args, rank, world, local_rank):
                                            "numa_node": numa_node, "fwd_bwd_dic1024_ms": fb1_ms,
                                            "fwd_bwd_recompute_ms": fb_re_ms,
                                            "deterministic": deterministic,
+                                           "dic_1024_batch": dic_batch,
                                            "e2e_pipelined": (n_pipe, pipe_s),
                                            "d2h_ms": min(d2h_ms)})
 
@@ -631,11 +647,11 @@ def warm_start_bench(dev, samples: int = 200_000, seeds=(7, 9, 10)):
     }
 
 
-def issue_roofline(kernels: dict):
+def issue_roofline(kernels: dict, sms: int):
     """The bound the render kernels actually meet: warp instructions per
     launch (committed ncu counts) over the live launch time, against the
     issue peak."""
-    peak = issue_peak_ginst()
+    peak = issue_peak_ginst(sms)
     out = {}
     for k in ("strip_forward", "column", "strip_inverse"):
         inst = ncu_instructions(k)
@@ -646,6 +662,64 @@ def issue_roofline(kernels: dict):
                   "frac": round(rate / peak, 4)}
     return {"bound": "issue", "unit": "G warp-instructions/s", "peak": round(peak, 1),
             "kernels": out} if out else None
+
+
+def single_scene_entry(ms_list, n: int, K: int, peak: float, peak_src: str) -> dict:
+    """The 40,000-particle 2048^2 scene rendered alone (osog_render): frames/s
+    and its whole-frame roofline (16 + 20K B/px plus particle and bin bytes
+    over the event-timed frame)."""
+    ms = statistics.median(ms_list)
+    b = sum(algorithmic_bytes(k, [n], SIZE, SIZE, K, 2 * n)
+            for k in ("bin_count", "bin_fill", "strip_forward", "column", "strip_inverse"))
+    gbs = b / (ms / 1e3) / 1e9
+    return {"ms": round(ms, 4), "frames_per_s": round(1e3 / ms, 2),
+            "particles_per_s": round(n / (ms / 1e3), 1),
+            "roofline": {"bound": "hbm", "algorithmic_bytes": b, "achieved": round(gbs, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+                         "peak_source": peak_src},
+            "context": PAPER_CONTEXT}
+
+
+def dic_1024_batch(dev, stream, steps: int, peak: float, peak_src: str) -> dict:
+    """16 DIC images of 1024^2 with 4,000 particles each (shear 1 px at 45
+    degrees, bias pi/4, NA 0.5, defocus U(-2, 2) um per image), rendered as
+    one batch replayed as a CUDA graph: frames/s and the step's roofline."""
+    import torch
+
+    from paper_2606_21381_gb300.render import Renderer
+    soas, optics = zip(*[scenes.dic_1024(i) for i in range(16)])
+    soa_all, offs = scenes.concat(list(soas))
+    r = Renderer(1024, 1024, dev)
+    x = torch.from_numpy(soa_all).to(dev)
+    out = torch.empty((16, 1, 1024, 1024), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        r.autotune(x, offs, list(optics), out=out, stream=stream)
+        for _ in range(3):
+            r.batch(x, offs, list(optics), out=out, stream=stream)
+        t = []
+        for i in range(max(5, min(steps, 50))):
+            flush.fill_(i & 0xff)
+            a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+            a.record(stream)
+            r.batch(x, offs, list(optics), out=out, stream=stream)
+            b.record(stream)
+            stream.synchronize()
+            t.append(a.elapsed_time(b))
+        if r.sync_status(stream) != 0:
+            raise RuntimeError("device status set in the DIC 1024 batch")
+    counts = [s.shape[1] for s in soas]
+    ms = statistics.median(t)
+    b = sum(algorithmic_bytes(k, counts, 1024, 1024, 1, 2 * sum(counts))
+            for k in ("bin_count", "bin_fill", "strip_forward", "column", "strip_inverse"))
+    gbs = b / (ms / 1e3) / 1e9
+    return {"workload": "16 x 1024^2 DIC, 4,000 particles per image, NA 0.5, shear 1 px at 45 "
+                        "deg, bias pi/4, defocus U(-2, 2) um; one batch as a CUDA graph",
+            "ms_per_batch": round(ms, 4), "frames_per_s": round(16 / (ms / 1e3), 1),
+            "particles_per_s": round(sum(counts) / (ms / 1e3), 1),
+            "roofline": {"bound": "hbm", "algorithmic_bytes": b, "achieved": round(gbs, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+                         "peak_source": peak_src}}
 
 
 def max_over_ranks(value: float, world: int, device) -> float:
@@ -683,11 +757,14 @@ def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms
     pairs_est = int(sum(counts) * 2)
     peak, peak_src = measured_peaks()
     act = active_fraction(scenes.batch_2048_scene(0, 1, SIZE)[1])
-    bytes_dom = algorithmic_bytes(dom, counts, SIZE, SIZE, K, pairs_est, act)
+    bytes_dom = algorithmic_bytes(dom, counts, SIZE, SIZE, K, pairs_est)
+    bytes_dom_pruned = algorithmic_bytes(dom, counts, SIZE, SIZE, K, pairs_est, act)
     dur_s = kernels[dom]["ms_per_launch"] / 1e3
     achieved = bytes_dom / dur_s / 1e9
     traffic = ncu_traffic(dom)
-    step_bytes = sum(algorithmic_bytes(k, counts, SIZE, SIZE, K, pairs_est, act) for k in kernels)
+    step_bytes = sum(algorithmic_bytes(k, counts, SIZE, SIZE, K, pairs_est) for k in kernels)
+    step_bytes_pruned = sum(algorithmic_bytes(k, counts, SIZE, SIZE, K, pairs_est, act)
+                            for k in kernels)
     ms_step = timed_max / args.steps
     return {
         "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": world,
@@ -701,11 +778,17 @@ def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": bytes_dom,
-                     "pupil_active_columns": round(act, 4)},
-        "issue_roofline": issue_roofline(kernels),
+                     "pruned": {"what": "G and Q counted only on the pupil-passed columns "
+                                        "(the bytes the kernel does move)",
+                                "pupil_active_columns": round(act, 4),
+                                "algorithmic_bytes_per_launch": bytes_dom_pruned,
+                                "achieved": round(bytes_dom_pruned / dur_s / 1e9, 1),
+                                "frac": round(bytes_dom_pruned / dur_s / 1e9 / peak, 4)}},
+        "issue_roofline": issue_roofline(kernels, sm_count(dev)),
         "step_roofline": {"algorithmic_bytes": step_bytes,
                           "achieved_gbs": round(step_bytes / (ms_step / 1e3) / 1e9, 1),
-                          "frac": round(step_bytes / (ms_step / 1e3) / 1e9 / peak, 4)},
+                          "frac": round(step_bytes / (ms_step / 1e3) / 1e9 / peak, 4),
+                          "pruned_frac": round(step_bytes_pruned / (ms_step / 1e3) / 1e9 / peak, 4)},
         "kernels": kernels,
         "kernels_three_launch": {k: {"ms_per_launch": v[0] / v[1], "share": v[0] / max(
             sum(x[0] for x in (extra or {}).get("kernels_three_launch", {}).values()), 1e-30)}
@@ -715,10 +798,9 @@ def finish(args, rank, world, dev, counts, soa_all, timed_ms, prof, per_scene_ms
                                "ms_per_batch": round(statistics.median(per_scene_ms), 4),
                                "frames_per_s": round(SCENES / (statistics.median(per_scene_ms) / 1e3), 2),
                                "batched_speedup": round(statistics.median(per_scene_ms) / ms_step, 3)},
-        "single_scene_40k": None if args.quick else {
-                             "ms": round(statistics.median(single40k), 4),
-                             "frames_per_s": round(1e3 / statistics.median(single40k), 2),
-                             "context": PAPER_CONTEXT},
+        "single_scene_40k": None if args.quick else single_scene_entry(
+            single40k, max(counts), K, peak, peak_src),
+        "dic_1024_batch": (extra or {}).get("dic_1024_batch"),
         "e2e": None if args.quick else {
                 "value": round(SCENES * extra["e2e_pipelined"][0] / extra["e2e_pipelined"][1], 2),
                 "unit": "frames/s",

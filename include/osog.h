@@ -127,13 +127,24 @@ typedef struct {
  *                       gives at most 64 bands (R = 8192 / W rows for
  *                       W >= 1024, 4 for 128 <= W <= 512, 512 / W below);
  *                       0 = the default max(H / 64, 16, R)
+ *   wait_polls          persistent launch: polls (about 0.1 us apart) before a
+ *                       wait for another stage's work gives up and latches
+ *                       OSOG_ERR_TIMEOUT (0 = 2^24); after one wait has given
+ *                       up the launch's later waits return at once, so it
+ *                       always ends
+ *   test_wait_extra     failure-detection test: raises the number of finished
+ *                       strips each column item of the persistent launch waits
+ *                       for by this many, so its waits run out (0 = off); the
+ *                       images of such a launch are invalid
  */
 typedef struct {
     int32_t pairs_per_particle;
     int32_t use_graph;
     int32_t persistent;
     int32_t band_rows;
-    int32_t reserved[4];
+    int32_t wait_polls;
+    int32_t test_wait_extra;
+    int32_t reserved[2];
 } osog_tuning_t;
 
 /*
@@ -357,6 +368,54 @@ int osog_autotune(osog_plan_t *plan, const float *soa_all, int64_t ld,
                   float *images, void *ws, size_t ws_bytes, osog_stream_t stream,
                   osog_tuning_t *out);
 
+/*
+ * Image losses of inverse rendering (Sec. IV.B), evaluated with the
+ * library's FFT passes: K float32 images of the plan's H x W against K
+ * target images, with A_k and B_k their unnormalised forward 2-D DFTs.
+ *   misfit     the coarse-to-fine curriculum's low-pass misfit,
+ *              misfit_scale sum_k sum_px (lp(I_k) - lp(T_k))^2 with lp the
+ *              ideal low-pass filter |f| <= cutoff (cycles/um, on the grid
+ *              fftfreq(W, dx_um) x fftfreq(H, dx_um)), computed by Parseval
+ *              as misfit_scale / (H W) sum_{|f| <= cutoff} |A - B|^2;
+ *   spectral   Eq. 8, the squared difference of the log-amplitude spectra,
+ *              1 / (K H W) sum_k sum_f (log(|A_k| + e_k) - log(|B_k| + e_k))^2
+ *              with the guard e_k = eps_rel max_f |B_k(f)| (the paper writes
+ *              log|F(.)|; the guard keeps frequencies where both spectra are
+ *              rounding noise from dominating; float32 spectra carry noise of
+ *              ~1e-7 of their largest amplitude, so eps_rel >= 1e-5).
+ *
+ * osog_loss_target stores the targets' spectra and largest amplitudes in a
+ * caller-owned device table of osog_loss_table_size(plan, K) bytes (256-byte
+ * aligned); one table serves any number of osog_image_loss calls.
+ *   target  device float32 [K][H][W], 1 <= K <= 32
+ *
+ * osog_image_loss writes, on the device,
+ *   loss[0] = misfit (0 when misfit_scale is 0), loss[1] = spectral loss
+ *   (0 when spectral_weight is 0), and, when grad_image is not NULL,
+ *   grad_image = d(misfit + spectral_weight spectral)/dI (float32 [K][H][W]).
+ * The cutoff is read from device memory when the kernels run, so a CUDA
+ * graph captured from this call follows a cutoff updated on the device.
+ * Every sum runs in a fixed order (bitwise reproducible).  Both calls take a
+ * workspace of osog_loss_workspace_size(plan, K) bytes.  Host-side errors:
+ * OSOG_ERR_INVALID_ARG (bad K, pointer or parameter), OSOG_ERR_WORKSPACE.
+ */
+typedef struct {
+    double dx_um;            /* pixel pitch (the misfit's frequency grid) */
+    const float *cutoff;     /* device float: low-pass radius (cycles/um); needed when
+                                misfit_scale != 0 */
+    double misfit_scale;     /* 0: no misfit */
+    double spectral_weight;  /* weight of Eq. 8 in the gradient; 0: not evaluated */
+    double eps_rel;          /* > 0: guard of the logarithms */
+} osog_loss_t;
+
+size_t osog_loss_table_size(const osog_plan_t *plan, int32_t K);
+size_t osog_loss_workspace_size(const osog_plan_t *plan, int32_t K);
+int osog_loss_target(osog_plan_t *plan, const float *target, int32_t K, void *table,
+                     size_t table_bytes, void *ws, size_t ws_bytes, osog_stream_t stream);
+int osog_image_loss(osog_plan_t *plan, const float *image, int32_t K, const void *table,
+                    size_t table_bytes, const osog_loss_t *params, float *loss,
+                    float *grad_image, void *ws, size_t ws_bytes, osog_stream_t stream);
+
 /* Synchronise `stream`, return the first device-latched status since the
  * last call (OSOG_OK if none) and clear it. */
 int osog_sync_status(osog_plan_t *plan, osog_stream_t stream);
@@ -393,21 +452,34 @@ int osog_profile_end(osog_plan_t *plan, osog_stream_t stream, float *ms,
  * static device arrays of the library (8 MiB of scratch plus 33 KB of
  * tables) that each GPU loading the library keeps until the process exits.
  *   Limit: the render's scratch must fit in 8 MiB, e.g. a 256 x 256 canvas
- *   with 3 modalities and up to ~55,000 particles, or 512 x 512 with one
- *   modality and up to ~35,000; larger renders return OSOG_ERR_WORKSPACE
- *   before any device work.  Other host-side errors: OSOG_ERR_INVALID_ARG,
- *   OSOG_ERR_UNSUPPORTED_SIZE, OSOG_ERR_CUDA; osog_last_error is not set.
+ *   with 3 modalities and up to ~50,000 particles, or 512 x 512 with one
+ *   modality and up to ~33,000; larger renders return OSOG_ERR_WORKSPACE
+ *   before any device work.  The particle-band lists get the scratch that the
+ *   other regions leave (at least one slot per particle); a scene whose
+ *   particles span more bands than that latches OSOG_ERR_BIN_OVERFLOW and
+ *   renders without the pairs that did not fit.  Other host-side errors:
+ *   OSOG_ERR_INVALID_ARG, OSOG_ERR_UNSUPPORTED_SIZE, OSOG_ERR_CUDA;
+ *   osog_last_error is not set.
  *   The first call on a device sets that device up (resolves the static
  *   arrays' addresses, uploads the tables, sets kernel attributes); make it
  *   before any stream capture.
  *   All calls share the static scratch: calls that overlap on the GPU (on
  *   different streams, or from different threads) race and must be ordered
- *   by the caller.  Invalid particles are skipped as in osog_render, but no
- *   device status is reported by this entry point.
+ *   by the caller.  Device-side errors (invalid or non-finite particles,
+ *   bin overflow) latch in one status word per device, shared by every call
+ *   of this entry point and kept until osog_noalloc_sync_status reads it.
  */
 int osog_render_noalloc(const float *soa, int64_t ld, int32_t n,
                         const osog_optics_t *optics, float *image,
                         osog_stream_t stream);
+
+/*
+ * Status of osog_render_noalloc on the current device (allocates nothing):
+ * synchronises `stream`, returns the first code latched by any
+ * osog_render_noalloc call on this device since the last read (OSOG_OK if
+ * none) and clears it.  OSOG_ERR_CUDA if a runtime call fails.
+ */
+int osog_noalloc_sync_status(osog_stream_t stream);
 
 #ifdef __cplusplus
 }

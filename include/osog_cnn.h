@@ -83,6 +83,15 @@ void osog_conv_use_tcgen05(int32_t enable);
  * cores gave up; results of that call are invalid), clearing it. */
 int osog_conv_sync_status(osog_stream_t stream);
 
+/* Failure-detection test hook.  With polls > 0, every later tcgen05
+ * convolution CTA also waits, for at most `polls` polls, on a barrier that
+ * nothing arrives on: the wait runs out, the kernel latches the status that
+ * osog_conv_sync_status reports as OSOG_ERR_TIMEOUT, still waits for its own
+ * tensor-core work, releases its tensor memory and finishes (its results stay
+ * valid).  polls <= 0 turns the hook off (the default).  Returns OSOG_OK or
+ * OSOG_ERR_CUDA. */
+int osog_conv_test_wait_limit(int32_t polls);
+
 /* Derivative of a ReLU: dy_out[i] = dy[i] where act[i] > 0, else 0 (bf16). */
 int osog_relu_backward(const uint16_t *dy, const uint16_t *act, uint16_t *dy_out, int64_t count,
                        osog_stream_t stream);

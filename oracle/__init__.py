@@ -99,6 +99,11 @@ def _load():
         lib.orc_render_poly.argtypes = [d, i64, i32, d, d, ctypes.POINTER(_Optics), d, d, d,
                                         d, d]
         lib.orc_render_grad.argtypes = [d, i64, i32, ctypes.POINTER(_Optics), d, d, d]
+        lib.orc_spectral_loss.argtypes = [d, d, i32, i32, i32, ctypes.c_double, d]
+        lib.orc_spectral_loss.restype = ctypes.c_double
+        lib.orc_lowpass_misfit.argtypes = [d, d, i32, i32, i32, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, d]
+        lib.orc_lowpass_misfit.restype = ctypes.c_double
         _lib = lib
     return _lib
 
@@ -334,3 +339,35 @@ def render_grad(soa: np.ndarray, n: int, o: dict, gI: np.ndarray):
     gopt = np.zeros(4)
     _load().orc_render_grad(_p(soa), ld, int(n), ctypes.byref(s), _p(gI), _p(gsoa), _p(gopt))
     return gsoa[:, :int(n)], gopt
+
+
+# ---------------------------------------------------------------- losses
+def _images(img: np.ndarray, tgt: np.ndarray):
+    img = np.ascontiguousarray(img, dtype=np.float64)
+    tgt = np.ascontiguousarray(tgt, dtype=np.float64)
+    if img.shape != tgt.shape or img.ndim != 3:
+        raise ValueError("image and target must be (K, H, W) arrays of one shape")
+    return img, tgt
+
+
+def spectral_loss(img: np.ndarray, tgt: np.ndarray, eps_rel: float = 1e-6):
+    """Eq. 8: (loss, dloss/dimg) of the log-amplitude spectral loss of
+    (K, H, W) images (see orc_spectral_loss)."""
+    img, tgt = _images(img, tgt)
+    K, H, W = img.shape
+    g = np.empty_like(img)
+    v = _load().orc_spectral_loss(_p(img), _p(tgt), K, H, W, float(eps_rel), _p(g))
+    return float(v), g
+
+
+def lowpass_misfit(img: np.ndarray, tgt: np.ndarray, dx: float, cutoff: float,
+                   scale: float = 1.0):
+    """(loss, dloss/dimg) of the curriculum misfit: scale times the sum of
+    squared differences of the images low-passed at `cutoff` cycles/um
+    (see orc_lowpass_misfit)."""
+    img, tgt = _images(img, tgt)
+    K, H, W = img.shape
+    g = np.empty_like(img)
+    v = _load().orc_lowpass_misfit(_p(img), _p(tgt), K, H, W, float(dx), float(cutoff),
+                                   float(scale), _p(g))
+    return float(v), g

@@ -24,6 +24,10 @@
  *     Eq. 5 taken coherently through the pupil, and in the literal
  *     incoherent reading of Eq. 5 (orc_dic_incoherent);
  *   - an own radix-2 FFT and a brute-force DFT (used to pin the FFT);
+ *   - the losses of inverse rendering: the log-amplitude spectral loss of
+ *     Eq. 8 (orc_spectral_loss) and the low-pass image misfit of the
+ *     coarse-to-fine solve (orc_lowpass_misfit), each with its gradient
+ *     with respect to the image;
  *   - the gradient of a linear functional of the images with respect to
  *     every particle field and to the optics scalars, by the analytic
  *     adjoint of the chain above (orc_render_grad), pinned by central
@@ -863,6 +867,102 @@ void orc_sensor_noise(const float *img, int64_t count, double g, double sigma,
         double lam = g * (img[i] > 0.0f ? (double)img[i] : 0.0);
         out[i] = ((double)orc_poisson(lam, seed, i) + sigma * orc_normal(seed, i)) / g;
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* Image losses of inverse rendering                                   */
+/* ------------------------------------------------------------------ */
+
+/* Spectral loss of Eq. 8 (Sec. IV.B): the squared difference of the log
+ * amplitude spectra of an image and a target, K images of H x W each,
+ *   L = 1 / (K H W) sum_k sum_f (log(|A_k(f)| + e_k) - log(|B_k(f)| + e_k))^2,
+ * A_k = F I_k and B_k = F T_k the unnormalised forward 2-D DFTs, and e_k =
+ * eps_rel max_f |B_k(f)| the guard inside the logarithms (a reading: the
+ * paper writes log|F(.)| with no guard; without one every frequency where
+ * both spectra are only rounding noise would count as much as the band).
+ * With d_f = log(|A_f| + e) - log(|B_f| + e) and A_f = a_f + i b_f,
+ * dL/da_f + i dL/db_f = 2 d_f A_f / (K H W |A_f| (|A_f| + e)) (zero where
+ * A_f = 0), and since A is the DFT of a real image, dL/dI = Re(G) with G the
+ * unnormalised inverse DFT of that complex gradient.  grad (K H W values)
+ * receives dL/dI when it is not NULL.  Returns L. */
+double orc_spectral_loss(const double *img, const double *tgt, int K, int H, int W,
+                         double eps_rel, double *grad)
+{
+    const size_t n = (size_t)H * W;
+    double *ar = malloc(sizeof(double) * n), *ai = malloc(sizeof(double) * n);
+    double *br = malloc(sizeof(double) * n), *bi = malloc(sizeof(double) * n);
+    double total = 0.0;
+    const double norm = (double)K * (double)n;
+    for (int k = 0; k < K; ++k) {
+        for (size_t i = 0; i < n; ++i) {
+            ar[i] = img[k * n + i]; ai[i] = 0.0;
+            br[i] = tgt[k * n + i]; bi[i] = 0.0;
+        }
+        orc_fft2(ar, ai, H, W, -1);
+        orc_fft2(br, bi, H, W, -1);
+        double bmax = 0.0;
+        for (size_t i = 0; i < n; ++i) {
+            const double m = hypot(br[i], bi[i]);
+            if (m > bmax) bmax = m;
+        }
+        const double e = eps_rel * bmax;
+        for (size_t i = 0; i < n; ++i) {
+            const double ma = hypot(ar[i], ai[i]);
+            const double d = log(ma + e) - log(hypot(br[i], bi[i]) + e);
+            total += d * d;
+            /* complex gradient, kept in (ar, ai) for the inverse transform */
+            const double c = ma > 0.0 ? 2.0 * d / (norm * ma * (ma + e)) : 0.0;
+            ar[i] *= c;
+            ai[i] *= c;
+        }
+        if (grad) {
+            orc_fft2(ar, ai, H, W, +1);
+            for (size_t i = 0; i < n; ++i) grad[k * n + i] = ar[i];
+        }
+    }
+    free(ar); free(ai); free(br); free(bi);
+    return total / norm;
+}
+
+/* Misfit of the inverse solve's coarse-to-fine curriculum (Sec. IV.B): the
+ * squared difference of the image and the target after both pass an ideal
+ * low-pass filter of radius `cutoff` (cycles/um) on the frequency grid
+ * f = (fftfreq(W, dx), fftfreq(H, dx)), summed over the K H W pixels and
+ * multiplied by `scale`.  By Parseval this is
+ *   L = scale / (H W) sum_k sum_{|f| <= cutoff} |A_k(f) - B_k(f)|^2,
+ * and dL/dI = 2 scale / (H W) Re(F^-1 [m (A - B)]) with F^-1 the
+ * unnormalised inverse DFT and m the filter's indicator.  grad as above. */
+double orc_lowpass_misfit(const double *img, const double *tgt, int K, int H, int W,
+                          double dx, double cutoff, double scale, double *grad)
+{
+    const size_t n = (size_t)H * W;
+    double *ar = malloc(sizeof(double) * n), *ai = malloc(sizeof(double) * n);
+    double total = 0.0;
+    for (int k = 0; k < K; ++k) {
+        for (size_t i = 0; i < n; ++i) {
+            ar[i] = img[k * n + i] - tgt[k * n + i];
+            ai[i] = 0.0;
+        }
+        orc_fft2(ar, ai, H, W, -1);  /* A - B by linearity */
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const size_t i = (size_t)y * W + x;
+                const double fx = (double)(x < W / 2 ? x : x - W) / ((double)W * dx);
+                const double fy = (double)(y < H / 2 ? y : y - H) / ((double)H * dx);
+                if (fx * fx + fy * fy <= cutoff * cutoff) {
+                    total += ar[i] * ar[i] + ai[i] * ai[i];
+                } else {
+                    ar[i] = 0.0;
+                    ai[i] = 0.0;
+                }
+            }
+        if (grad) {
+            orc_fft2(ar, ai, H, W, +1);
+            for (size_t i = 0; i < n; ++i) grad[k * n + i] = 2.0 * scale / (double)n * ar[i];
+        }
+    }
+    free(ar); free(ai);
+    return total * scale / (double)n;
 }
 
 /* Threads of the OpenMP loops above (timing on one core or all). */

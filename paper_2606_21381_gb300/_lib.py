@@ -24,11 +24,14 @@ EXPORTS = ("osog_plan_create", "osog_plan_destroy", "osog_workspace_size", "osog
            "osog_render_opd", "osog_optics_from_opd", "osog_batch_submit",
            "osog_sync_status", "osog_last_error", "osog_plan_launch_count",
            "osog_profile_begin", "osog_profile_end", "osog_render_noalloc",
+           "osog_noalloc_sync_status",
            "osog_backward_workspace_size", "osog_render_backward", "osog_render_keep",
            "osog_render_backward_kept", "osog_autotune",
            "osog_polyhedra_workspace_size", "osog_render_polyhedra",
            "osog_dic_incoherent_workspace_size", "osog_render_dic_incoherent",
-           "osog_sensor_noise", "osog_plan_bind_optics_params")
+           "osog_sensor_noise", "osog_plan_bind_optics_params",
+           "osog_loss_table_size", "osog_loss_workspace_size", "osog_loss_target",
+           "osog_image_loss")
 
 
 class OsogError(RuntimeError):
@@ -56,14 +59,22 @@ class ConvShape(ctypes.Structure):
 CNN_EXPORTS = ("osog_conv_out_h", "osog_conv_out_w", "osog_conv2d_forward",
                "osog_conv2d_backward_data", "osog_conv2d_backward_filter_workspace",
                "osog_conv2d_backward_filter", "osog_relu_backward", "osog_conv_use_tcgen05",
-               "osog_conv_sync_status")
+               "osog_conv_sync_status", "osog_conv_test_wait_limit")
+
+
+class LossParams(ctypes.Structure):
+    """Mirror of osog_loss_t."""
+    _fields_ = [("dx_um", ctypes.c_double), ("cutoff", ctypes.c_void_p),
+                ("misfit_scale", ctypes.c_double), ("spectral_weight", ctypes.c_double),
+                ("eps_rel", ctypes.c_double)]
 
 
 class Tuning(ctypes.Structure):
     """Mirror of osog_tuning_t."""
     _fields_ = [("pairs_per_particle", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("persistent", ctypes.c_int32), ("band_rows", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("wait_polls", ctypes.c_int32), ("test_wait_extra", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 def optics_struct(o: dict) -> Optics:
@@ -135,6 +146,7 @@ def lib(build_if_missing: bool = True):
     L.osog_autotune.argtypes = [vp, vp, i64, P(i32), i32, P(Optics), vp, vp, sz, vp, P(Tuning)]
     L.osog_autotune.restype = ctypes.c_int
     L.osog_render_noalloc.argtypes = [vp, i64, i32, P(Optics), vp, vp]
+    L.osog_noalloc_sync_status.argtypes = [vp]
     L.osog_polyhedra_workspace_size.argtypes = [vp, i32, i32, i32]
     L.osog_polyhedra_workspace_size.restype = sz
     L.osog_render_polyhedra.argtypes = [vp, vp, i64, i32, vp, vp, i32, P(Optics), vp, vp, sz, vp]
@@ -162,9 +174,20 @@ def lib(build_if_missing: bool = True):
     L.osog_conv_use_tcgen05.restype = None
     L.osog_conv_sync_status.argtypes = [vp]
     L.osog_conv_sync_status.restype = ctypes.c_int
+    L.osog_conv_test_wait_limit.argtypes = [i32]
+    L.osog_conv_test_wait_limit.restype = ctypes.c_int
     L.osog_relu_backward.argtypes = [vp, vp, vp, i64, vp]
     L.osog_relu_backward.restype = ctypes.c_int
     L.osog_render_noalloc.restype = ctypes.c_int
+    L.osog_noalloc_sync_status.restype = ctypes.c_int
+    L.osog_loss_table_size.argtypes = [vp, i32]
+    L.osog_loss_table_size.restype = sz
+    L.osog_loss_workspace_size.argtypes = [vp, i32]
+    L.osog_loss_workspace_size.restype = sz
+    L.osog_loss_target.argtypes = [vp, vp, i32, vp, sz, vp, sz, vp]
+    L.osog_loss_target.restype = ctypes.c_int
+    L.osog_image_loss.argtypes = [vp, vp, i32, vp, sz, P(LossParams), vp, vp, vp, sz, vp]
+    L.osog_image_loss.restype = ctypes.c_int
     _lib = L
     return L
 

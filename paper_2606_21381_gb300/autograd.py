@@ -12,7 +12,10 @@ from __future__ import annotations
 
 import torch
 
+from ._lib import OsogError
 from .render import Renderer
+
+INVALID_ARG = 1  # osog_render_backward_kept: no kept forward state matches
 
 OPTICS_PARAMS = ("defocus", "shear_px", "shear_angle", "bias_phase")
 
@@ -46,10 +49,17 @@ class RenderFunction(torch.autograd.Function):
     def backward(ctx, grad_image):
         (soa,) = ctx.saved_tensors
         g = grad_image.contiguous().float()
+        gsoa = gopt = None
         if ctx.ws is not None:
-            gsoa, gopt = ctx.renderer.backward_kept(soa, None, ctx.optics, g, ctx.ws)
+            try:
+                gsoa, gopt = ctx.renderer.backward_kept(soa, None, ctx.optics, g, ctx.ws)
+            except OsogError as e:
+                # the plan remembers the states of its last 64 workspaces; an
+                # older one was dropped, so the adjoint recomputes the forward
+                if e.code != INVALID_ARG:
+                    raise
             ctx.ws = None  # consumed: a second backward recomputes the forward
-        else:
+        if gsoa is None:
             gsoa, gopt = ctx.renderer.backward(soa, None, ctx.optics, g)
         dtype, device = ctx.params_meta
         return gsoa, gopt.to(device=device, dtype=dtype), None, None

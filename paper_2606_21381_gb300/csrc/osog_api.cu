@@ -3,6 +3,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -47,6 +48,7 @@ struct osog_plan {
         osog_optics_t optics;
     };
     std::vector<Kept> kept;
+    std::mutex kept_lock;  // autograd may run the adjoint on a thread of its own
     // device array of the four differentiable optics scalars, or null
     const float *optics_dyn = nullptr;
 };
@@ -75,7 +77,7 @@ constexpr size_t kMaxKept = 64;  // forward states remembered per plan
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t rec, rect, cnt, band_off, pairs, G, Q, colrange, ctr, total;
+    size_t rec, rrec, rect, cnt, band_off, pairs, G, Q, colrange, ctr, total;
 };
 
 // Workspace regions for a launch group of up to S scenes, n records,
@@ -86,6 +88,8 @@ Layout make_layout(const Geometry &geo, int64_t n, int64_t nchunks, int S, int K
     size_t o = 0;
     l.rec = o;
     o = align256(o + (size_t)n * sizeof(PRec));
+    l.rrec = o;
+    o = align256(o + (size_t)n * sizeof(RRec));
     l.rect = o;
     o = align256(o + (size_t)n * sizeof(Rect));
     l.cnt = o;
@@ -101,7 +105,7 @@ Layout make_layout(const Geometry &geo, int64_t n, int64_t nchunks, int S, int K
     l.colrange = o;
     o = align256(o + (size_t)S * sizeof(int2));
     l.ctr = o;
-    o = align256(o + (size_t)(1 + 2 * S) * sizeof(int32_t));
+    o = align256(o + (size_t)(2 + 2 * S) * sizeof(int32_t));
     l.total = o;
     return l;
 }
@@ -110,6 +114,7 @@ Work carve(void *ws, const Layout &l, int32_t *status) {
     char *b = static_cast<char *>(ws);
     Work w;
     w.rec = reinterpret_cast<PRec *>(b + l.rec);
+    w.rrec = reinterpret_cast<RRec *>(b + l.rrec);
     w.rect = reinterpret_cast<Rect *>(b + l.rect);
     w.cnt = reinterpret_cast<int32_t *>(b + l.cnt);
     w.band_off = reinterpret_cast<int32_t *>(b + l.band_off);
@@ -141,44 +146,6 @@ int check_optics(const osog_plan *p, const osog_optics_t *o) {
     if (!(o->bevel_slope > 0)) return fail(OSOG_ERR_INVALID_ARG, "bevel_slope must be > 0");
     if (o->modes == 0 || (o->modes & ~7u)) return fail(OSOG_ERR_INVALID_ARG, "modes must be in 1..7");
     return OSOG_OK;
-}
-
-SceneDev scene_dev(const osog_optics_t &o) {
-    SceneDev s{};
-    s.two_over_lambda = (float)(2.0 / o.lambda_um);
-    s.prism_g = (float)(2.0 * o.bevel_slope * o.dx_um);
-    s.dx_um = (float)o.dx_um;
-    return s;
-}
-
-ModeDev mode_dev(const osog_optics_t &o, uint32_t mode, const float *dyn) {
-    const double two_pi = 6.283185307179586476925286766559;
-    ModeDev m{};
-    const double r = o.NA / o.lambda_um;
-    m.r2 = r * r;
-    m.ox = m.oy = 0.0;
-    if (mode == OSOG_MODE_OBLIQUE) {
-        m.ox = o.oblique_frac * r * cos(o.oblique_angle);
-        m.oy = o.oblique_frac * r * sin(o.oblique_angle);
-    }
-    m.fx_scale = 1.0 / ((double)o.W * o.dx_um);
-    m.fy_span = (double)o.H * o.dx_um;
-    m.kstep_x = (float)(two_pi / ((double)o.W * o.dx_um));
-    m.kstep_y = (float)(two_pi / ((double)o.H * o.dx_um));
-    m.qoff_x = (float)(two_pi * m.ox);
-    m.qoff_y = (float)(two_pi * m.oy);
-    m.k0 = (float)(two_pi * o.n_medium / o.lambda_um);
-    m.dz = (float)o.defocus_um;
-    m.dsx = (float)(0.5 * o.shear_px * o.dx_um * cos(o.shear_angle));
-    m.dsy = (float)(0.5 * o.shear_px * o.dx_um * sin(o.shear_angle));
-    m.bias = (float)o.bias_phase;
-    m.scale = (float)(1.0 / ((double)o.H * o.W));
-    m.dic = mode == OSOG_MODE_DIC ? 1 : 0;
-    m.dsx1 = (float)(0.5 * o.dx_um * cos(o.shear_angle));
-    m.dsy1 = (float)(0.5 * o.dx_um * sin(o.shear_angle));
-    m.dyn = dyn;
-    m.half_dx = (float)(0.5 * o.dx_um);
-    return m;
 }
 
 // Launch helper: optional event bracketing and the launch counter.
@@ -218,6 +185,8 @@ struct GroupOpts {
     int ppp = kDefaultPairs;
     bool persistent = false;
     int band_rows = 0;
+    int wait_polls = 0;       // persistent launch: 0 = the default limit
+    int wait_extra = 0;       // failure-detection test (osog_tuning_t.test_wait_extra)
     std::vector<int32_t> *band_off_out = nullptr;  // kBinOnly: host copy of band_off
     const float4 *planes = nullptr;                 // kind-2 particles (single scene)
     const int32_t *plane_off = nullptr;
@@ -337,7 +306,9 @@ int enqueue_group(osog_plan *p, const float *soa, int64_t ld, const int32_t *cou
         pa.ia = ia;
         pa.ctr = reinterpret_cast<int32_t *>(static_cast<char *>(ws) + l.ctr);
         pa.total = S * (geo.nstrips + geo.nblocks + K * geo.nstrips);
-        cudaError_t e = cudaMemsetAsync(pa.ctr, 0, sizeof(int32_t) * (1 + 2 * S), st);
+        pa.wait_polls = opt.wait_polls > 0 ? opt.wait_polls : (1 << 24);
+        pa.wait_extra = opt.wait_extra > 0 ? opt.wait_extra : 0;
+        cudaError_t e = cudaMemsetAsync(pa.ctr, 0, sizeof(int32_t) * (2 + 2 * S), st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
         return run_kernel(p, OSOG_KERNEL_PERSISTENT, st, [&] { return launch_persistent(pa, st); });
     }
@@ -547,6 +518,7 @@ bool same_optics(const osog_optics_t &a, const osog_optics_t &b) {
 // Drop the forward states that osog_render_keep left in workspace ws (any
 // other call that writes ws invalidates them).
 void forget_kept(osog_plan *p, const void *ws) {
+    std::lock_guard<std::mutex> guard(p->kept_lock);
     for (size_t i = p->kept.size(); i-- > 0;)
         if (p->kept[i].ws == ws) p->kept.erase(p->kept.begin() + i);
 }
@@ -867,6 +839,8 @@ int osog_batch_submit(osog_plan_t *p, const float *soa_all, int64_t ld, const in
         if (tuning->pairs_per_particle > 0) opt.ppp = tuning->pairs_per_particle;
         if (tuning->persistent != 0) opt.persistent = tuning->persistent > 0;
         if (tuning->band_rows > 0) opt.band_rows = tuning->band_rows;
+        opt.wait_polls = tuning->wait_polls;
+        opt.wait_extra = tuning->test_wait_extra;
         use_graph = tuning->use_graph > 0;
     }
     const int ppp = opt.ppp;
@@ -896,6 +870,8 @@ int osog_batch_submit(osog_plan_t *p, const float *soa_all, int64_t ld, const in
     put(&opt.ppp, sizeof opt.ppp);
     put(&opt.persistent, sizeof opt.persistent);
     put(&opt.band_rows, sizeof opt.band_rows);
+    put(&opt.wait_polls, sizeof opt.wait_polls);
+    put(&opt.wait_extra, sizeof opt.wait_extra);
     put(&p->optics_dyn, sizeof p->optics_dyn);
     if (!(p->gexec && key == p->gkey)) {
         const int64_t before = p->launches;
@@ -973,6 +949,7 @@ int osog_render_keep(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
     k.ld = ld;
     k.n = n;
     k.optics = *optics;
+    std::lock_guard<std::mutex> guard(p->kept_lock);
     if (p->kept.size() >= kMaxKept) p->kept.erase(p->kept.begin());  // the oldest goes
     p->kept.push_back(k);
     return OSOG_OK;
@@ -988,9 +965,12 @@ int osog_render_backward_kept(osog_plan_t *p, const float *soa, int64_t ld, int3
     rc = bwd_check_grads(grad_image, grad_soa, grad_optics, n);
     if (rc) return rc;
     bool found = false;
-    for (const osog_plan::Kept &k : p->kept)
-        found = found || (k.ws == ws && k.ws_bytes == ws_bytes && k.soa == soa && k.ld == ld &&
-                          k.n == n && same_optics(k.optics, *optics));
+    {
+        std::lock_guard<std::mutex> guard(p->kept_lock);
+        for (const osog_plan::Kept &k : p->kept)
+            found = found || (k.ws == ws && k.ws_bytes == ws_bytes && k.soa == soa &&
+                              k.ld == ld && k.n == n && same_optics(k.optics, *optics));
+    }
     if (!found)
         return fail(OSOG_ERR_INVALID_ARG, "no forward state kept in this workspace for these "
                                           "arguments (osog_render_keep)");
@@ -1070,6 +1050,136 @@ int osog_autotune(osog_plan_t *p, const float *soa_all, int64_t ld, const int32_
         out->band_rows = chosen.band_rows;
     }
     return OSOG_OK;
+}
+
+// ------------------------------------------------------------ image losses
+// The target table: K complex spectra [K][W/B][H][B] (column-blocked like
+// Q), then the K largest amplitudes.
+static size_t loss_table_spectra(const osog_plan *p, int K) {
+    return align256((size_t)K * p->H * p->W * sizeof(float2));
+}
+
+size_t osog_loss_table_size(const osog_plan_t *p, int32_t K) {
+    if (!p || K < 1 || K > kMaxScenes) return 0;
+    return loss_table_spectra(p, K) + align256((size_t)K * sizeof(float));
+}
+
+// Workspace of the loss passes: G and Q of K single-modality images, the
+// column ranges, then the per-block partial sums.
+static size_t loss_ws_part(const osog_plan *p, int K) {
+    return make_layout(p->geo, 0, 0, K, 1, 0).total;
+}
+
+size_t osog_loss_workspace_size(const osog_plan_t *p, int32_t K) {
+    if (!p || K < 1 || K > kMaxScenes) return 0;
+    return loss_ws_part(p, K) + align256((size_t)K * p->geo.nblocks * 2 * sizeof(float));
+}
+
+// The spectra of K real images through the strip and column passes, with
+// modality md (kOpSpectrum or kOpLoss) per image; the column ranges are
+// set by the scan kernel (every column for these operations).
+static int loss_passes(osog_plan *p, const float *images, int K, ModeDev md, float2 *tab,
+                       const LossDev *loss, float *grad, void *ws, cudaStream_t st) {
+    const Geometry &geo = p->geo;
+    const Layout l = make_layout(geo, 0, 0, K, 1, 0);
+    const Work w = carve(ws, l, p->status);
+    GroupDev gd{};
+    gd.S = K;
+    gd.K = 1;
+    StripArgs sa{};
+    sa.geo = geo;
+    sa.w = w;
+    sa.tw = p->tw_w;
+    sa.opd_att = reinterpret_cast<const float2 *>(images);
+    sa.S = K;
+    ColumnArgs ca{};
+    ca.geo = geo;
+    ca.w = w;
+    ca.tw = p->tw_h;
+    ca.S = K;
+    ca.K = 1;
+    if (loss) ca.loss = *loss;
+    for (int s = 0; s < K; ++s) {
+        md.tab = tab + (size_t)s * geo.H * geo.W;
+        gd.md[s][0] = md;
+        ca.md[s][0] = md;
+    }
+    int rc = run_kernel(p, OSOG_KERNEL_BIN_SCAN, st, [&] { return launch_bin_scan(gd, geo, w, st); });
+    if (rc) return rc;
+    rc = run_kernel(p, OSOG_KERNEL_STRIP_FORWARD, st,
+                    [&] { return launch_strip_forward(sa, kStripFromReal, st); });
+    if (rc) return rc;
+    rc = run_kernel(p, OSOG_KERNEL_COLUMN, st, [&] { return launch_column(ca, st); });
+    if (rc || !grad) return rc;
+    InverseArgs ia{};
+    ia.geo = geo;
+    ia.w = w;
+    ia.tw = p->tw_w;
+    ia.images = grad;
+    ia.S = K;
+    ia.K = 1;
+    ia.real_out = 1;
+    return run_kernel(p, OSOG_KERNEL_STRIP_INVERSE, st, [&] { return launch_strip_inverse(ia, st); });
+}
+
+int osog_loss_target(osog_plan_t *p, const float *target, int32_t K, void *table,
+                     size_t table_bytes, void *ws, size_t ws_bytes, osog_stream_t stream) {
+    if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    if (K < 1 || K > kMaxScenes || !target || !table)
+        return fail(OSOG_ERR_INVALID_ARG, "need 1 <= K <= 32 and non-NULL target, table");
+    if (reinterpret_cast<uintptr_t>(table) & 255 || table_bytes < osog_loss_table_size(p, K))
+        return fail(OSOG_ERR_WORKSPACE, "loss table too small or not 256-byte aligned");
+    int rc = check_ws(ws, osog_loss_workspace_size(p, K), ws_bytes);
+    if (rc) return rc;
+    forget_kept(p, ws);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    ModeDev md{};
+    md.op = kOpSpectrum;
+    md.scale = 1.f;
+    float2 *spec = static_cast<float2 *>(table);
+    rc = loss_passes(p, target, K, md, spec, nullptr, nullptr, ws, st);
+    if (rc) return rc;
+    float *maxamp = reinterpret_cast<float *>(static_cast<char *>(table) + loss_table_spectra(p, K));
+    cudaError_t e = launch_max_amplitude(spec, K, (int64_t)p->H * p->W, maxamp, st);
+    return e == cudaSuccess ? OSOG_OK : cuda_fail(e, "osog_loss_target");
+}
+
+int osog_image_loss(osog_plan_t *p, const float *image, int32_t K, const void *table,
+                    size_t table_bytes, const osog_loss_t *params, float *loss,
+                    float *grad_image, void *ws, size_t ws_bytes, osog_stream_t stream) {
+    if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    if (K < 1 || K > kMaxScenes || !image || !table || !params || !loss)
+        return fail(OSOG_ERR_INVALID_ARG, "need 1 <= K <= 32 and non-NULL image, table, params, loss");
+    if (reinterpret_cast<uintptr_t>(table) & 255 || table_bytes < osog_loss_table_size(p, K))
+        return fail(OSOG_ERR_WORKSPACE, "loss table too small or not 256-byte aligned");
+    if (!finite_all({params->dx_um, params->misfit_scale, params->spectral_weight, params->eps_rel}) ||
+        !(params->dx_um > 0) || !(params->eps_rel > 0))
+        return fail(OSOG_ERR_INVALID_ARG, "loss parameters need finite values, dx_um > 0, eps_rel > 0");
+    if ((params->misfit_scale != 0.0 && !params->cutoff) ||
+        (reinterpret_cast<uintptr_t>(params->cutoff) & 3))
+        return fail(OSOG_ERR_INVALID_ARG, "the misfit needs a 4-byte aligned device cutoff");
+    int rc = check_ws(ws, osog_loss_workspace_size(p, K), ws_bytes);
+    if (rc) return rc;
+    forget_kept(p, ws);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    LossDev L{};
+    L.cutoff = params->misfit_scale != 0.0 ? params->cutoff : nullptr;
+    L.misfit_scale = (float)params->misfit_scale;
+    L.spectral_weight = (float)params->spectral_weight;
+    L.eps_rel = (float)params->eps_rel;
+    L.inv_ntot = (float)(1.0 / ((double)K * p->H * p->W));
+    L.fx_scale = (float)(1.0 / ((double)p->W * params->dx_um));
+    L.fy_scale = (float)(1.0 / ((double)p->H * params->dx_um));
+    L.maxamp = reinterpret_cast<const float *>(static_cast<const char *>(table) +
+                                               loss_table_spectra(p, K));
+    L.part = reinterpret_cast<float *>(static_cast<char *>(ws) + loss_ws_part(p, K));
+    ModeDev md{};
+    md.op = kOpLoss;
+    rc = loss_passes(p, image, K, md, const_cast<float2 *>(static_cast<const float2 *>(table)),
+                     &L, grad_image, ws, st);
+    if (rc) return rc;
+    cudaError_t e = launch_loss_reduce(L.part, (int64_t)K * p->geo.nblocks, loss, st);
+    return e == cudaSuccess ? OSOG_OK : cuda_fail(e, "osog_image_loss");
 }
 
 int osog_plan_bind_optics_params(osog_plan_t *p, const float *params_dev) {

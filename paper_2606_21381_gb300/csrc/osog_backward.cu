@@ -173,16 +173,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_strip(const __grid_constant
     for (int i = threadIdx.x; i < geo.R * LS / 2; i += kThreads) o4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     fft_lines<N, L, true>(bufG, a.tw);                                    // dL/dE
-    raster_strip<N>(geo, a.w, sc, s, y0, bufO, srec, srect, wsum);      // OPD, ATT
-    const float tol = sc.two_over_lambda;
-    const float k2pi = 3.14159265358979323846f * tol;                   // 2 pi / lambda
+    // OPD and ATT as fixed-point accumulators in bufO (its staging shares
+    // the gather's staging area below, used only after the raster)
+    raster_strip<N, kAccPhase>(geo, a.w, sc, s, y0, geo.R, bufO,
+                               reinterpret_cast<unsigned char *>(srec));
+    __syncthreads();
+    const float k2pi = 3.14159265358979323846f * sc.two_over_lambda;   // 2 pi / lambda
 #pragma unroll
     for (int i = 0; i < ept(N); ++i) {
         const int e = threadIdx.x + i * kThreads;
         if (e < RN) {
             const int idx = (e / N) * LS + pad16(e % N);
-            const float2 oa = bufO[idx], g = bufG[idx];
-            const float2 E = exit_wave(oa.x, oa.y, tol);
+            const float2 g = bufG[idx];
+            const float2 E = exit_wave_fixed(reinterpret_cast<const uint2 *>(bufO)[idx]);
             const float ex = E.x, ey = E.y;
             bufO[idx] = make_float2(k2pi * fmaf(g.y, ex, -g.x * ey), -fmaf(g.x, ex, g.y * ey));
         }
@@ -370,8 +373,9 @@ size_t bwd_column_smem(int H) {
 
 size_t bwd_strip_smem(int W) {
     const int L = set_elems(W) / W;
+    const size_t gather = kThreads * (sizeof(PRec) + sizeof(Rect) + sizeof(int)) + 64;
     return (size_t)2 * L * line_stride(W) * sizeof(float2) +
-           kThreads * (sizeof(PRec) + sizeof(Rect) + sizeof(int)) + 64;
+           (gather > raster_smem() ? gather : raster_smem());
 }
 
 cudaError_t prepare_backward(int H, int W) {

@@ -124,6 +124,12 @@ __device__ Rect setup_particle(const float *soa, int64_t ld, int p, const SceneD
     r.mu = f[7];
     float ex, ey;
     const float c = fabsf(r.ch), s = fabsf(r.sh);
+    RRec rr;
+    rr.cx = cx;
+    rr.cy = cy;
+    rr.tsa = 0.f;
+    rr.dn = f[6];
+    rr.mu = f[7];
     if (kind == 2.f) {
         if (!setup_planes(w, poff, pcnt, cd, sd, (double)sc.dx_um)) {
             latch(status, OSOG_ERR_NONFINITE_INPUT);
@@ -135,6 +141,10 @@ __device__ Rect setup_particle(const float *soa, int64_t ld, int p, const SceneD
         r.p1l = 0.f;
         r.g = -1.f;  // marks a general polyhedron
         ex = ey = a;  // circumscribed radius of the footprint (px)
+        rr.p[0] = __int_as_float(poff);
+        rr.p[1] = __int_as_float(pcnt);
+        rr.p[2] = rr.p[3] = rr.p[4] = rr.p[5] = 0.f;
+        rr.kind = 2;
     } else if (kind == 1.f) {
         r.p0h = a;
         r.p0l = 0.f;
@@ -143,6 +153,13 @@ __device__ Rect setup_particle(const float *soa, int64_t ld, int p, const SceneD
         r.g = sc.prism_g;
         ex = a * c + b * s;
         ey = a * s + b * c;
+        rr.p[0] = r.ch;
+        rr.p[1] = r.sh;
+        rr.p[2] = a;
+        rr.p[3] = b;
+        rr.p[4] = sc.prism_g;
+        rr.p[5] = T;
+        rr.kind = 1;
     } else {
         const double ia = 1.0 / (double)a, ib = 1.0 / (double)b;
         r.p0h = (float)ia;
@@ -152,8 +169,23 @@ __device__ Rect setup_particle(const float *soa, int64_t ld, int p, const SceneD
         r.g = 0.f;
         ex = sqrtf(a * a * c * c + b * b * s * s);
         ey = sqrtf(a * a * s * s + b * b * c * c);
+        // the row quadric of (u/a)^2 + (v/b)^2 (see RRec), in double precision
+        const double ia2 = ia * ia, ib2 = ib * ib;
+        const double alpha = cd * cd * ia2 + sd * sd * ib2;
+        const double m = -cd * sd * (ia2 - ib2) / alpha;
+        const double inv_alpha = 1.0 / alpha;
+        const double kappa = ia2 * ib2 * inv_alpha * inv_alpha;
+        const double v3[3] = {m, inv_alpha, kappa};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            rr.p[2 * k] = (float)v3[k];
+            rr.p[2 * k + 1] = (float)(v3[k] - (double)rr.p[2 * k]);
+        }
+        rr.tsa = (float)((double)T * sqrt(alpha));
+        rr.kind = 0;
     }
     rec[p] = r;
+    w.rrec[p] = rr;
     // Pixel centres j + 0.5 inside [cx - ex, cx + ex], widened by one pixel
     // on each side; the thickness is exactly zero on the extra pixels.
     const float xl = floorf(cx - ex - 1.5f), xh = ceilf(cx + ex + 0.5f);

@@ -394,6 +394,10 @@ constexpr int kUStage = UM * UBK * 2;   // bytes of one operand stage (B <= 128 
 constexpr int kSpinLimit = 1 << 22;
 
 __device__ int g_cnn_status;
+// Failure-detection test (osog_conv_test_wait_limit): when positive, every
+// tcgen05 convolution CTA also waits, for this many polls, on a barrier that
+// nothing arrives on, so the bounded wait runs out and latches g_cnn_status.
+__device__ int g_cnn_probe_polls;
 
 __device__ __forceinline__ int canon(int row, int k) {  // byte offset in a stage
     return (row >> 3) * (UKC * 128) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
@@ -420,8 +424,8 @@ __device__ __forceinline__ int canon_mn(int mn, int k) {
     return (mn >> 3) * (UKC * 128) + (k >> 3) * 128 + (k & 7) * 16 + (mn & 7) * 2;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < kSpinLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit = kSpinLimit) {
+    for (int it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      "selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
@@ -554,6 +558,8 @@ __global__ void __launch_bounds__(UNT) k_conv_umma(const __grid_constant__ Args 
     if (tid == 0) {
         for (int st = 0; st < UST; ++st)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(smem_u32(mbar + st)), "r"(1));
+        // the failure-detection probe's barrier (after tslot): nothing arrives on it
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(smem_u32(mbar + UST + 1)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     const int nk = (a.Kred + UBK - 1) / UBK;
@@ -611,6 +617,8 @@ __global__ void __launch_bounds__(UNT) k_conv_umma(const __grid_constant__ Args 
         const int last = nk - 1;
         ok = mbar_wait(smem_u32(mbar + last % UST), (uint32_t)((last / UST) & 1)) && ok;
     }
+    if (tid == 0 && g_cnn_probe_polls > 0)  // a wait made to run out (test hook)
+        ok = mbar_wait(smem_u32(mbar + UST + 1), 0u, g_cnn_probe_polls) && ok;
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (!ok && lane == 0) atomicExch(&g_cnn_status, 1);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -682,6 +690,8 @@ __global__ void __launch_bounds__(UNT) k_wgrad_umma(const __grid_constant__ Args
     if (tid == 0) {
         for (int st = 0; st < UST; ++st)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(smem_u32(mbar + st)), "r"(1));
+        // the failure-detection probe's barrier (after tslot): nothing arrives on it
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(smem_u32(mbar + UST + 1)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     const int nk = (pend - pbeg + UBK - 1) / UBK;
@@ -780,6 +790,8 @@ __global__ void __launch_bounds__(UNT) k_wgrad_umma(const __grid_constant__ Args
         const int last = nk - 1;
         ok = mbar_wait(smem_u32(mbar + last % UST), (uint32_t)((last / UST) & 1)) && ok;
     }
+    if (tid == 0 && g_cnn_probe_polls > 0)  // a wait made to run out (test hook)
+        ok = mbar_wait(smem_u32(mbar + UST + 1), 0u, g_cnn_probe_polls) && ok;
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (!ok && lane == 0) atomicExch(&g_cnn_status, 1);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -1104,6 +1116,11 @@ int osog_relu_backward(const uint16_t *dy, const uint16_t *act, uint16_t *dy_out
 }
 
 void osog_conv_use_tcgen05(int32_t enable) { g_use_tcgen05 = enable ? 1 : 0; }
+
+int osog_conv_test_wait_limit(int32_t polls) {
+    const int v = polls > 0 ? polls : 0;
+    return cudaMemcpyToSymbol(g_cnn_probe_polls, &v, sizeof v) == cudaSuccess ? OSOG_OK : OSOG_ERR_CUDA;
+}
 
 int osog_conv_sync_status(osog_stream_t stream) {
     if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return OSOG_ERR_CUDA;

@@ -73,6 +73,27 @@ struct __align__(16) PRec {
 };
 static_assert(sizeof(PRec) == 64, "PRec is 64 bytes");
 
+// Per-particle constants of the row-span raster (48 bytes), written by the
+// setup pass beside PRec.  For an ellipsoid the chord through pixel centre
+// (X, Y) is t = T sqrt(1 - rho^2), and along the row Y
+//   1 - rho^2 = alpha ((x0 + w - X)(X - (x0 - w))),  x0 = cx + m ey,
+//   w^2 = 1/alpha - kappa ey^2,  ey = Y - cy,
+// with alpha = c^2/a^2 + s^2/b^2, m = -c s (1/a^2 - 1/b^2) / alpha and
+// kappa = 1 / (a^2 b^2 alpha^2) (the quadric of (u/a)^2 + (v/b)^2 in ex for
+// fixed ey).  These constants are rounded from double precision to
+// float-float pairs so that the row's chord ends x0 -+ w are known to
+// ~1e-13 px, which the square root near the rim needs.
+struct __align__(16) RRec {
+    float cx, cy;
+    float p[6];   // ellipsoid: m, 1/alpha, kappa (hi, lo each)
+                  // prism: cos, sin, hx, hy (px), g = 2 s_b dx, T
+                  // polyhedron: plane offset, plane count (int bits)
+    float tsa;    // ellipsoid: T sqrt(alpha)
+    float dn, mu;
+    int32_t kind;
+};
+static_assert(sizeof(RRec) == 48, "RRec is 48 bytes");
+
 // Bounding rectangle of the pixels a particle may touch (inclusive), or an
 // empty rectangle (x0 > x1) for a skipped particle.
 struct __align__(8) Rect {
@@ -141,7 +162,29 @@ __device__ __forceinline__ ModeDev live_mode(const ModeDev &m) {
 //   kOpTable     multiply every frequency by tab / tab[0] (real DC term)
 //   kOpSpectrum  write the forward column spectrum times scale to tab (no
 //                inverse transform, Q untouched)
-enum { kOpPupil = 0, kOpAllPass = 1, kOpTable = 2, kOpSpectrum = 3 };
+//   kOpLoss      the image losses of inverse rendering (see LossDev): per
+//                frequency their terms, summed per column block, and the
+//                complex gradient of their weighted sum, inverse-transformed
+//                to Q (tab holds the target's spectrum)
+enum { kOpPupil = 0, kOpAllPass = 1, kOpTable = 2, kOpSpectrum = 3, kOpLoss = 4 };
+
+// Parameters of kOpLoss, the same for every image of a launch.  With A the
+// image's unnormalised spectrum and B the target's:
+//   misfit    scale / (H W) sum_{|f| <= cutoff} |A - B|^2 (the low-pass
+//             image misfit by Parseval), gradient term 2 scale / (H W) (A - B);
+//   spectral  1 / ntot sum_f (log(|A| + e) - log(|B| + e))^2 (Eq. 8), e =
+//             eps_rel max|B| of that image, gradient term weight 2 d A /
+//             (ntot |A| (|A| + e)).
+struct LossDev {
+    const float *cutoff;    // device scalar: low-pass radius (cycles / um); null: misfit off
+    float misfit_scale;
+    float spectral_weight;  // 0: spectral loss off
+    float eps_rel;
+    float inv_ntot;         // 1 / (K H W)
+    float fx_scale, fy_scale;  // 1 / (W dx), 1 / (H dx): cycles / um per index
+    const float *maxamp;    // [images] largest target amplitude
+    float *part;            // [images][blocks][2] per-block sums (misfit, spectral)
+};
 
 struct GroupDev {
     int32_t S;
@@ -155,6 +198,7 @@ struct GroupDev {
 // Pointers into the workspace for one launch group.
 struct Work {
     PRec *rec;
+    RRec *rrec;         // row-span raster constants, one per record
     Rect *rect;
     int32_t *cnt;       // [nchunks][nbands]: counts, then exclusive prefix
     int32_t *band_off;  // [S][nbands + 1]

@@ -1,6 +1,8 @@
 // Host-side launchers of the libosog kernels (one definition per .cu file).
 #pragma once
 
+#include <math.h>
+
 #include "osog_common.cuh"
 
 namespace osog {
@@ -26,6 +28,7 @@ struct ColumnArgs {
     const float2 *tw;        // H-point twiddles
     int32_t S, K;
     int32_t unit_input;      // 1: the column spectrum is 1 everywhere (no G read, no DFT)
+    LossDev loss;            // kOpLoss parameters
     ModeDev md[kMaxScenes][kMaxModes];
 };
 
@@ -40,13 +43,16 @@ struct InverseArgs {
 
 // The three render stages of a launch group in one persistent launch
 // (square canvases).  ctr[0] hands out work items; ctr[1 + s] counts the
-// finished strips of scene s, ctr[1 + S + s] its finished column blocks.
+// finished strips of scene s, ctr[1 + S + s] its finished column blocks;
+// ctr[1 + 2 S] is raised when a wait of the launch gives up.
 struct PersistArgs {
     StripArgs sa;
     ColumnArgs ca;
     InverseArgs ia;
-    int32_t *ctr;      // [1 + 2 S], zero at launch
+    int32_t *ctr;      // [2 + 2 S], zero at launch
     int32_t total;     // work items
+    int32_t wait_polls;   // polls before a wait gives up (latching OSOG_ERR_TIMEOUT)
+    int32_t wait_extra;   // failure-detection test: added to the column items' target
 };
 
 // Adjoint passes (osog_render_backward).
@@ -88,6 +94,48 @@ struct BwdReduceArgs {  // fixed-order sums into the particle and optics gradien
     SceneDev sc[kMaxScenes];
 };
 
+// Host: the scene constants of one optics struct (the caller fills in the
+// launch fields p0, n, chunk0, pair0 and pair_cap), and the transfer-
+// function constants of one modality bit, in double precision rounded
+// once.  dyn is the plan's bound optics array (or null).
+inline SceneDev scene_dev(const osog_optics_t &o) {
+    SceneDev s{};
+    s.two_over_lambda = (float)(2.0 / o.lambda_um);
+    s.prism_g = (float)(2.0 * o.bevel_slope * o.dx_um);
+    s.dx_um = (float)o.dx_um;
+    return s;
+}
+
+inline ModeDev mode_dev(const osog_optics_t &o, uint32_t mode, const float *dyn) {
+    const double two_pi = 6.283185307179586476925286766559;
+    ModeDev m{};
+    const double r = o.NA / o.lambda_um;
+    m.r2 = r * r;
+    m.ox = m.oy = 0.0;
+    if (mode == OSOG_MODE_OBLIQUE) {
+        m.ox = o.oblique_frac * r * cos(o.oblique_angle);
+        m.oy = o.oblique_frac * r * sin(o.oblique_angle);
+    }
+    m.fx_scale = 1.0 / ((double)o.W * o.dx_um);
+    m.fy_span = (double)o.H * o.dx_um;
+    m.kstep_x = (float)(two_pi / ((double)o.W * o.dx_um));
+    m.kstep_y = (float)(two_pi / ((double)o.H * o.dx_um));
+    m.qoff_x = (float)(two_pi * m.ox);
+    m.qoff_y = (float)(two_pi * m.oy);
+    m.k0 = (float)(two_pi * o.n_medium / o.lambda_um);
+    m.dz = (float)o.defocus_um;
+    m.dsx = (float)(0.5 * o.shear_px * o.dx_um * cos(o.shear_angle));
+    m.dsy = (float)(0.5 * o.shear_px * o.dx_um * sin(o.shear_angle));
+    m.bias = (float)o.bias_phase;
+    m.scale = (float)(1.0 / ((double)o.H * o.W));
+    m.dic = mode == OSOG_MODE_DIC ? 1 : 0;
+    m.dsx1 = (float)(0.5 * o.dx_um * cos(o.shear_angle));
+    m.dsy1 = (float)(0.5 * o.dx_um * sin(o.shear_angle));
+    m.dyn = dyn;
+    m.half_dx = (float)(0.5 * o.dx_um);
+    return m;
+}
+
 cudaError_t launch_bin_count(const float *soa, int64_t ld, const GroupDev &gd,
                              const Geometry &geo, const Work &w, cudaStream_t st);
 cudaError_t launch_bin_scan(const GroupDev &gd, const Geometry &geo, const Work &w,
@@ -99,13 +147,19 @@ cudaError_t launch_bin_fill(const GroupDev &gd, const Geometry &geo, const Work 
 cudaError_t launch_bin_single(const float *soa, int64_t ld, const GroupDev &gd,
                               const Geometry &geo, const Work &w, cudaStream_t st);
 
-size_t strip_forward_smem(int W);
+size_t strip_forward_smem(int W, bool opd_mode = false);  // opd_mode: kStripOpdOnly
 size_t column_smem(int H, int K);
 size_t strip_inverse_smem(int W);
 cudaError_t prepare_kernels(int H, int W);  // opt-in shared memory sizes
 cudaError_t launch_strip_forward(const StripArgs &a, StripMode mode, cudaStream_t st);
 cudaError_t launch_column(const ColumnArgs &a, cudaStream_t st);
 cudaError_t launch_strip_inverse(const InverseArgs &a, cudaStream_t st);
+// largest |spectrum| of each of S column-blocked H x W spectra (one CTA each)
+cudaError_t launch_max_amplitude(const float2 *spec, int S, int64_t count, float *maxamp,
+                                 cudaStream_t st);
+// fixed-order sums of kOpLoss's per-block partials into loss[0] (misfit)
+// and loss[1] (spectral loss)
+cudaError_t launch_loss_reduce(const float *part, int64_t nparts, float *loss, cudaStream_t st);
 
 size_t persistent_smem(int N, int K);
 cudaError_t launch_persistent(const PersistArgs &a, cudaStream_t st);

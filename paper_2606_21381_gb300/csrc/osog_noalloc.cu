@@ -24,7 +24,6 @@ namespace {
 constexpr size_t kScratchBytes = (size_t)8 << 20;  // 8 MiB of intermediate buffers
 constexpr int kTwiddleCount = 32 + 64 + 128 + 256 + 512 + 1024 + 2048;
 constexpr int kMaxDevices = 64;
-constexpr int kPairsPerParticle = 8;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 static __device__ __align__(256) float2 g_twiddles[kTwiddleCount];  // tables of sizes 32..2048
@@ -95,27 +94,33 @@ extern "C" int osog_render_noalloc(const float *soa, int64_t ld, int32_t n,
     const int K = (int)(o->modes & 1u) + (int)((o->modes >> 1) & 1u) + (int)((o->modes >> 2) & 1u);
     const Geometry geo = make_geometry(o->H, o->W);
 
-    // Scratch layout (same regions as a workspace of osog_render).
+    // Scratch layout (the regions of an osog_render workspace).  The band
+    // lists come last and take whatever the other regions leave, up to the
+    // most a scene can need (every particle in every band).
     const int64_t chunks = ((int64_t)n + kChunk - 1) / kChunk;
-    const int64_t pairs = (int64_t)n * kPairsPerParticle;
     size_t off = 0;
     const size_t o_rec = off;
     off = up256(off + (size_t)n * sizeof(PRec));
+    const size_t o_rrec = off;
+    off = up256(off + (size_t)n * sizeof(RRec));
     const size_t o_rect = off;
     off = up256(off + (size_t)n * sizeof(Rect));
     const size_t o_cnt = off;
     off = up256(off + (size_t)chunks * geo.nbands * sizeof(int32_t));
     const size_t o_band = off;
     off = up256(off + (size_t)(geo.nbands + 1) * sizeof(int32_t));
-    const size_t o_pairs = off;
-    off = up256(off + (size_t)pairs * sizeof(int32_t));
     const size_t o_G = off;
     off = up256(off + (size_t)geo.H * geo.W * sizeof(float2));
     const size_t o_Q = off;
     off = up256(off + (size_t)K * geo.H * geo.W * sizeof(float2));
     const size_t o_colrange = off;
     off = up256(off + sizeof(int2));
-    if (off > kScratchBytes) return OSOG_ERR_WORKSPACE;  // beyond the 8 MiB static scratch
+    const size_t o_pairs = off;
+    if (off > kScratchBytes || (n > 0 && kScratchBytes - off < (size_t)n * sizeof(int32_t)))
+        return OSOG_ERR_WORKSPACE;  // beyond the 8 MiB static scratch
+    const int64_t pair_room = (int64_t)((kScratchBytes - off) / sizeof(int32_t));
+    const int64_t pair_most = (int64_t)n * geo.nbands;
+    const int64_t pairs = pair_room < pair_most ? pair_room : pair_most;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return OSOG_ERR_CUDA;
@@ -125,6 +130,7 @@ extern "C" int osog_render_noalloc(const float *soa, int64_t ld, int32_t n,
 
     Work w;
     w.rec = reinterpret_cast<PRec *>(st->scratch + o_rec);
+    w.rrec = reinterpret_cast<RRec *>(st->scratch + o_rrec);
     w.rect = reinterpret_cast<Rect *>(st->scratch + o_rect);
     w.cnt = reinterpret_cast<int32_t *>(st->scratch + o_cnt);
     w.band_off = reinterpret_cast<int32_t *>(st->scratch + o_band);
@@ -137,47 +143,23 @@ extern "C" int osog_render_noalloc(const float *soa, int64_t ld, int32_t n,
     w.status = st->status;
 
     // Scene and transfer-function constants (double precision on the host).
-    const double two_pi = 6.283185307179586476925286766559;
     GroupDev gd{};
     gd.S = 1;
     gd.K = K;
     gd.nchunks = (int32_t)chunks;
     SceneDev &sc = gd.sc[0];
+    sc = scene_dev(*o);
     sc.p0 = 0;
     sc.n = n;
     sc.chunk0 = 0;
     sc.pair0 = 0;
     sc.pair_cap = (int32_t)pairs;
-    sc.two_over_lambda = (float)(2.0 / o->lambda_um);
-    sc.prism_g = (float)(2.0 * o->bevel_slope * o->dx_um);
-    int k = 0;
-    for (int bit = 0; bit < 3; ++bit) {
-        const uint32_t mode = 1u << bit;
-        if (!(o->modes & mode)) continue;
-        ModeDev &m = gd.md[0][k++];
-        const double r = o->NA / o->lambda_um;
-        m.r2 = r * r;
-        m.ox = mode == OSOG_MODE_OBLIQUE ? o->oblique_frac * r * cos(o->oblique_angle) : 0.0;
-        m.oy = mode == OSOG_MODE_OBLIQUE ? o->oblique_frac * r * sin(o->oblique_angle) : 0.0;
-        m.fx_scale = 1.0 / ((double)o->W * o->dx_um);
-        m.fy_span = (double)o->H * o->dx_um;
-        m.kstep_x = (float)(two_pi / ((double)o->W * o->dx_um));
-        m.kstep_y = (float)(two_pi / ((double)o->H * o->dx_um));
-        m.qoff_x = (float)(two_pi * m.ox);
-        m.qoff_y = (float)(two_pi * m.oy);
-        m.k0 = (float)(two_pi * o->n_medium / o->lambda_um);
-        m.dz = (float)o->defocus_um;
-        m.dsx = (float)(0.5 * o->shear_px * o->dx_um * cos(o->shear_angle));
-        m.dsy = (float)(0.5 * o->shear_px * o->dx_um * sin(o->shear_angle));
-        m.bias = (float)o->bias_phase;
-        m.scale = (float)(1.0 / ((double)o->H * o->W));
-        m.dic = mode == OSOG_MODE_DIC ? 1 : 0;
-    }
+    for (int bit = 0, k = 0; bit < 3; ++bit)
+        if (o->modes & (1u << bit)) gd.md[0][k++] = mode_dev(*o, 1u << bit, nullptr);
 
+    // Every scratch region is written in full before it is read; the status
+    // word keeps what earlier calls latched until osog_noalloc_sync_status.
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    // The status word is the only scratch that must start at zero; every
-    // other region is written in full before it is read.
-    if (cudaMemsetAsync(st->status, 0, sizeof(int32_t), s) != cudaSuccess) return OSOG_ERR_CUDA;
     const float2 *tw_w = st->twiddles + twiddle_offset(o->W);
     const float2 *tw_h = st->twiddles + twiddle_offset(o->H);
     if (launch_bin_count(soa, ld, gd, geo, w, s) != cudaSuccess) return OSOG_ERR_CUDA;
@@ -207,4 +189,19 @@ extern "C" int osog_render_noalloc(const float *soa, int64_t ld, int32_t n,
     ia.K = K;
     if (launch_strip_inverse(ia, s) != cudaSuccess) return OSOG_ERR_CUDA;
     return OSOG_OK;
+}
+
+extern "C" int osog_noalloc_sync_status(osog_stream_t stream) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return OSOG_ERR_CUDA;
+    DeviceState *st = nullptr;
+    int rc = setup_device(dev, &st);
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int32_t code = 0;  // pageable: the copy below completes before it returns
+    if (cudaStreamSynchronize(s) != cudaSuccess) return OSOG_ERR_CUDA;
+    if (cudaMemcpy(&code, st->status, sizeof code, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return OSOG_ERR_CUDA;
+    if (cudaMemset(st->status, 0, sizeof(int32_t)) != cudaSuccess) return OSOG_ERR_CUDA;
+    return code;
 }

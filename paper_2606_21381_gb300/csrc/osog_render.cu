@@ -29,16 +29,16 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
                                                    unsigned char *smem_raw) {
     constexpr int L = set_elems(N) / N;
     constexpr int LS = line_stride(N);
+    constexpr int ACC = MODE == kStripOpdOnly ? kAccOpd : kAccPhase;
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
-    PRec *srec = reinterpret_cast<PRec *>(buf + L * LS);
-    Rect *srect = reinterpret_cast<Rect *>(srec + kThreads);
-    int *wsum = reinterpret_cast<int *>(srect + kThreads);
+    // accumulators: one uint2 per padded slot (phase mode) or two int64 (OPD mode)
+    unsigned char *scratch = smem_raw + (ACC == kAccOpd ? 2 : 1) * L * LS * sizeof(float2);
     const Geometry &geo = a.geo;
     const int R = SQ ? sq_rb(N) : geo.R;
     const int y0 = strip * R;
     const int RN = R * N;  // <= set_elems(N); lines R..L-1 are never read back
     if constexpr (MODE == kStripFromReal) {
-        const float *src = reinterpret_cast<const float *>(a.opd_att) + (size_t)y0 * N;
+        const float *src = reinterpret_cast<const float *>(a.opd_att) + ((size_t)s * geo.H + y0) * N;
         float v[ept(N)];
 #pragma unroll
         for (int i = 0; i < ept(N); ++i) {
@@ -65,31 +65,45 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
         }
     } else {
         float4 *b4 = reinterpret_cast<float4 *>(buf);
-        for (int i = threadIdx.x; i < R * LS / 2; i += kThreads) b4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int n4 = (ACC == kAccOpd ? 2 : 1) * R * LS / 2;
+        for (int i = threadIdx.x; i < n4; i += kThreads) b4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
-        raster_strip<N>(a.geo, a.w, a.sc[s], s, y0, buf, srec, srect, wsum);
+        raster_strip<N, ACC>(a.geo, a.w, a.sc[s], s, y0, R, smem_raw, scratch);
     }
     __syncthreads();
     if constexpr (MODE == kStripOpdOnly) {
+        const longlong2 *acc = reinterpret_cast<const longlong2 *>(smem_raw);
         float2 *dst = a.opd_out + (size_t)y0 * N;
 #pragma unroll
         for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;
-            if (e < RN) dst[e] = buf[(e / N) * LS + pad16(e % N)];
+            if (e < RN) {
+                const longlong2 v = acc[(e / N) * LS + pad16(e % N)];
+                dst[e] = make_float2(__ll2float_rn(v.x) * 2.3283064365386963e-10f,
+                                     __ll2float_rn(v.y) * 2.3283064365386963e-10f);  // 2^-32
+            }
         }
         return;
     } else {
-        const float tol = a.sc[s].two_over_lambda;
+        if constexpr (MODE == kStripRender) {
 #pragma unroll
-        for (int i = 0; i < ept(N); ++i) {
-            const int e = threadIdx.x + i * kThreads;
-            if (MODE != kStripFromReal && e < RN) {
-                float2 *v = buf + (e / N) * LS + pad16(e % N);
-                const float2 oa = *v;
-                if (oa.x != 0.f || oa.y != 0.f) {  // empty pixels keep E = 1
-                    *v = exit_wave(oa.x, oa.y, tol);
-                } else {
-                    *v = make_float2(1.f, 0.f);
+            for (int i = 0; i < ept(N); ++i) {
+                const int e = threadIdx.x + i * kThreads;
+                if (e < RN) {
+                    float2 *v = buf + (e / N) * LS + pad16(e % N);
+                    *v = exit_wave_fixed(*reinterpret_cast<const uint2 *>(v));
+                }
+            }
+        } else if constexpr (MODE == kStripFromMap) {
+            const float tol = a.sc[s].two_over_lambda;
+#pragma unroll
+            for (int i = 0; i < ept(N); ++i) {
+                const int e = threadIdx.x + i * kThreads;
+                if (e < RN) {
+                    float2 *v = buf + (e / N) * LS + pad16(e % N);
+                    const float2 oa = *v;
+                    *v = oa.x != 0.f || oa.y != 0.f ? exit_wave(oa.x, oa.y, tol)
+                                                    : make_float2(1.f, 0.f);
                 }
             }
         }
@@ -116,6 +130,75 @@ __global__ void __launch_bounds__(kThreads, 2) k_strip_forward(const __grid_cons
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_enter();
     strip_forward_item<N, MODE, SQ>(a, blockIdx.y, blockIdx.x, smem_raw);
+}
+
+// The image losses of inverse rendering on one column block of image s
+// (kOpLoss, see LossDev): buf0 holds the image's unnormalised spectrum A,
+// md.tab the target's B.  Writes the complex gradient of the weighted loss
+// to buf1 (the caller inverse-transforms it) and the block's two sums,
+// reduced in a fixed order, to part[s][bk].
+template <int N>
+__device__ __forceinline__ void loss_columns(const ColumnArgs &a, int s, int bk, int B, int W,
+                                             const float2 *buf0, float2 *buf1) {
+    constexpr int LS = line_stride(N);
+    __shared__ float red[2 * (kThreads / 32)];
+    const LossDev &L = a.loss;
+    const float2 *Tb = a.md[s][0].tab + (size_t)bk * N * B;
+    const bool mis = L.cutoff != nullptr;
+    const float cut = mis ? *L.cutoff : 0.f;
+    const float cut2 = cut * cut;
+    const float gm = 2.f * L.misfit_scale / ((float)N * (float)W);  // 2 scale / (H W)
+    const bool spec = L.spectral_weight != 0.f;
+    const float e = L.eps_rel * L.maxamp[s];
+    const float gs = 2.f * L.spectral_weight * L.inv_ntot;
+    const int half = W / 2;
+    float pm = 0.f, ps = 0.f;
+#pragma unroll 4
+    for (int i = 0; i < ept(N); ++i) {
+        const int el = threadIdx.x + i * kThreads;  // line-major: consecutive y
+        const int c = el / N, y = el % N;
+        if (c < B) {
+            const int kx = bk * B + c;
+            const float fx = (float)(kx < half ? kx : kx - W) * L.fx_scale;
+            const float fy = (float)(y < N / 2 ? y : y - N) * L.fy_scale;
+            const float2 A = buf0[c * LS + pad16(y)];
+            const float2 T = Tb[y * B + c];
+            float2 g = make_float2(0.f, 0.f);
+            if (mis && fmaf(fx, fx, fy * fy) <= cut2) {
+                const float2 D = csub(A, T);
+                pm = fmaf(D.x, D.x, fmaf(D.y, D.y, pm));
+                g = make_float2(gm * D.x, gm * D.y);
+            }
+            if (spec) {
+                const float ma = sqrtf(fmaf(A.x, A.x, A.y * A.y));
+                const float mb = sqrtf(fmaf(T.x, T.x, T.y * T.y));
+                const float d = __logf(ma + e) - __logf(mb + e);
+                ps = fmaf(d, d, ps);
+                if (ma > 0.f) {
+                    const float q = __fdividef(gs * d, ma * (ma + e));
+                    g = make_float2(fmaf(q, A.x, g.x), fmaf(q, A.y, g.y));
+                }
+            }
+            buf1[c * LS + pad16(y)] = g;
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        pm += __shfl_xor_sync(0xffffffffu, pm, d);
+        ps += __shfl_xor_sync(0xffffffffu, ps, d);
+    }
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[2 * warp] = pm;
+        red[2 * warp + 1] = ps;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        float v = 0.f;
+        for (int w = 0; w < kThreads / 32; ++w) v += red[2 * w + threadIdx.x];
+        const float k = threadIdx.x == 0 ? L.misfit_scale / ((float)N * (float)W) : L.inv_ntot;
+        L.part[((size_t)s * (W / B) + bk) * 2 + threadIdx.x] = v * k;
+    }
 }
 
 // One column block bk of scene s.
@@ -180,6 +263,9 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
             }
             continue;  // buf0 is only read: the next modality may still use it
         }
+        if (md.op == kOpLoss) {
+            loss_columns<N>(a, s, bk, B, W, buf0, buf1);
+        } else {
         const float2 *T = md.op == kOpTable ? md.tab + (size_t)bk * N * B : nullptr;
         const float tnorm = md.op == kOpTable ? md.scale / md.tab[0].x : 0.f;
 #pragma unroll 4
@@ -200,6 +286,7 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
                 }
                 buf1[c * LS + pad16(y)] = v;
             }
+        }
         }
         __syncthreads();
         fft_lines<N, L, true>(buf1, a.tw);
@@ -275,17 +362,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_strip_inverse(const __grid_cons
 
 // ------------------------------------------------------------ persistent
 // Bounded wait on a completion counter: thread 0 polls until it reaches
-// target or the iteration limit runs out (then the status word records a
-// timeout and the item proceeds on whatever is there, so the launch always
-// ends); the fence orders the producer's writes before this CTA's reads.
+// target or `polls` polls run out; then it raises the launch's gave-up flag,
+// latches OSOG_ERR_TIMEOUT in the status word and the item proceeds on
+// whatever is there, so the launch always ends.  Once the flag is up, later
+// waits of the launch return at once.  The fence orders the producer's
+// writes before this CTA's reads.
 constexpr int kSpinLimit = 1 << 24;
 
-__device__ __forceinline__ void wait_count(const int32_t *cnt, int target, int32_t *status) {
+__device__ __forceinline__ void wait_count(const int32_t *cnt, int target, int32_t *gave_up,
+                                           int32_t *status, int polls) {
     if (threadIdx.x == 0) {
+        const volatile int32_t *flag = gave_up;
         int spins = 0;
-        while (*reinterpret_cast<const volatile int32_t *>(cnt) < target) {
+        while (*reinterpret_cast<const volatile int32_t *>(cnt) < target && !*flag) {
             __nanosleep(100);
-            if (++spins >= kSpinLimit) {
+            if (++spins >= polls) {
+                atomicExch(gave_up, 1);
                 latch(status, OSOG_ERR_TIMEOUT);
                 break;
             }
@@ -324,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, MULTI ? 1 : 2) k_persistent(const __
     const Geometry &geo = a.sa.geo;
     const int S = a.sa.S, K = a.ca.K;
     const int na = geo.nstrips, nb = geo.nblocks, nc = K * geo.nstrips;
-    int32_t *doneA = a.ctr + 1, *doneB = a.ctr + 1 + S;
+    int32_t *doneA = a.ctr + 1, *doneB = a.ctr + 1 + S, *gave_up = a.ctr + 1 + 2 * S;
     for (;;) {
         if (threadIdx.x == 0) {
             const int it = atomicAdd(a.ctr, 1);
@@ -341,10 +433,10 @@ __global__ void __launch_bounds__(kThreads, MULTI ? 1 : 2) k_persistent(const __
         if (stage == 0) {
             strip_forward_item<N, kStripRender, true>(a.sa, s, idx, smem_raw);
         } else if (stage == 1) {
-            wait_count(doneA + s, na, a.sa.w.status);
+            wait_count(doneA + s, na + a.wait_extra, gave_up, a.sa.w.status, a.wait_polls);
             column_item<N, MULTI, true>(a.ca, s, idx, smem_raw);
         } else {
-            wait_count(doneB + s, nb, a.sa.w.status);
+            wait_count(doneB + s, nb, gave_up, a.sa.w.status, a.wait_polls);
             inverse_item<N, true>(a.ia, s * K + idx / na, idx % na, smem_raw);
         }
         __syncthreads();
@@ -389,34 +481,36 @@ struct PersistLaunch {
 
 template <int N>
 struct StripFwdLaunch {
-    static cudaError_t run(const StripArgs &a, StripMode mode, cudaStream_t st, size_t smem) {
+    static cudaError_t run(const StripArgs &a, StripMode mode, cudaStream_t st) {
         dim3 grid(a.geo.nstrips, a.S);
+        const size_t smem = strip_forward_smem(N), smem_opd = strip_forward_smem(N, true);
         if (mode == kStripRender && a.geo.H == a.geo.W)
             return launch_chain(k_strip_forward<N, kStripRender, true>, grid, kThreads, smem, st, a);
         else if (mode == kStripRender)
             return launch_chain(k_strip_forward<N, kStripRender, false>, grid, kThreads, smem, st, a);
         else if (mode == kStripOpdOnly)
-            return launch_chain(k_strip_forward<N, kStripOpdOnly, false>, grid, kThreads, smem, st, a);
+            return launch_chain(k_strip_forward<N, kStripOpdOnly, false>, grid, kThreads, smem_opd, st, a);
         else if (mode == kStripFromReal)
             return launch_chain(k_strip_forward<N, kStripFromReal, false>, grid, kThreads, smem, st, a);
         else
             return launch_chain(k_strip_forward<N, kStripFromMap, false>, grid, kThreads, smem, st, a);
     }
-    static cudaError_t prepare(size_t smem) {
+    static cudaError_t prepare() {
+        const int smem = (int)strip_forward_smem(N), smem_opd = (int)strip_forward_smem(N, true);
         cudaError_t e = cudaFuncSetAttribute(k_strip_forward<N, kStripRender, true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_strip_forward<N, kStripRender, false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_strip_forward<N, kStripOpdOnly, false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_opd);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_strip_forward<N, kStripFromMap, false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_strip_forward<N, kStripFromReal, false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         return e;
     }
 };
@@ -471,19 +565,87 @@ template <int N>
 struct Prepare {
     static cudaError_t run(int which, int other) {
         (void)other;
-        if (which == 0) return StripFwdLaunch<N>::prepare(strip_forward_smem(N));
+        if (which == 0) return StripFwdLaunch<N>::prepare();
         if (which == 1) return ColumnLaunch<N>::prepare(column_smem(N, 1), column_smem(N, 3));
         if (which == 3) return PersistLaunch<N>::prepare();
         return InverseLaunch<N>::prepare(strip_inverse_smem(N));
     }
 };
 
+// Largest |z| of spectrum blockIdx.y (count samples), as the maximum of
+// |z|^2 over grid-strided CTAs merged by an integer atomicMax on the
+// float's bits (non-negative floats order like their bits; the maximum does
+// not depend on the order).  out must start at zero; the square root is
+// taken by the reader.
+__global__ void __launch_bounds__(256) k_max_amplitude(const float2 *spec, int64_t count,
+                                                       float *out) {
+    __shared__ float red[8];
+    const float2 *p = spec + (size_t)blockIdx.y * count;
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * 256 + threadIdx.x; i < count; i += (int64_t)gridDim.x * 256) {
+        const float2 v = p[i];
+        m = fmaxf(m, fmaf(v.x, v.x, v.y * v.y));
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+        atomicMax(reinterpret_cast<int *>(out) + blockIdx.y, __float_as_int(m));
+    }
+}
+
+__global__ void k_sqrt_inplace(float *v, int n) {
+    if ((int)threadIdx.x < n) v[threadIdx.x] = sqrtf(v[threadIdx.x]);
+}
+
+// loss[c] = sum over i of part[2 i + c] (c = 0, 1): lanes stride over the
+// partials in double, then a fixed butterfly and the warps in order.
+__global__ void __launch_bounds__(256) k_loss_reduce(const float *part, int64_t nparts,
+                                                     float *loss) {
+    __shared__ double red[2][8];
+    double v0 = 0.0, v1 = 0.0;
+    for (int64_t i = threadIdx.x; i < nparts; i += 256) {
+        v0 += (double)part[2 * i];
+        v1 += (double)part[2 * i + 1];
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, d);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = v0;
+        red[1][threadIdx.x >> 5] = v1;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[threadIdx.x][w];
+        loss[threadIdx.x] = (float)t;
+    }
+}
+
 }  // namespace
 
-size_t strip_forward_smem(int W) {
+cudaError_t launch_max_amplitude(const float2 *spec, int S, int64_t count, float *maxamp,
+                                 cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(maxamp, 0, sizeof(float) * S, st);
+    if (e != cudaSuccess) return e;
+    k_max_amplitude<<<dim3(256, S), 256, 0, st>>>(spec, count, maxamp);
+    k_sqrt_inplace<<<1, 32, 0, st>>>(maxamp, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss_reduce(const float *part, int64_t nparts, float *loss, cudaStream_t st) {
+    k_loss_reduce<<<1, 256, 0, st>>>(part, nparts, loss);
+    return cudaGetLastError();
+}
+
+size_t strip_forward_smem(int W, bool opd_mode) {
     const int L = set_elems(W) / W;
-    return (size_t)L * line_stride(W) * sizeof(float2) + kThreads * (sizeof(PRec) + sizeof(Rect)) +
-           64;
+    return (size_t)(opd_mode ? 2 : 1) * L * line_stride(W) * sizeof(float2) + raster_smem();
 }
 
 size_t column_smem(int H, int K) {
@@ -516,7 +678,7 @@ cudaError_t launch_persistent(const PersistArgs &a, cudaStream_t st) {
 }
 
 cudaError_t launch_strip_forward(const StripArgs &a, StripMode mode, cudaStream_t st) {
-    return dispatch_n<StripFwdLaunch>(a.geo.W, a, mode, st, strip_forward_smem(a.geo.W));
+    return dispatch_n<StripFwdLaunch>(a.geo.W, a, mode, st);
 }
 
 cudaError_t launch_column(const ColumnArgs &a, cudaStream_t st) {

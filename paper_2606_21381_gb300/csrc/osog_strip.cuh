@@ -1,6 +1,6 @@
 // Device pieces shared by the forward and adjoint render kernels: the
-// ordered strip raster, the transfer functions of the optical head, and a
-// dispatcher over the power-of-two transform sizes.
+// fixed-point strip raster, the transfer functions of the optical head, and
+// a dispatcher over the power-of-two transform sizes.
 #pragma once
 
 #include "osog_fft.cuh"
@@ -24,137 +24,229 @@ __host__ __device__ constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v
 // these compile-time values instead of the geometry's.
 __host__ __device__ constexpr int sq_rb(int n) { return set_elems(n) / n < n ? set_elems(n) / n : n; }
 
-// Accumulate one particle's OPD / ATT over the pixels [xa, xb] x [ya, yb]
-// of the strip buffer.  The warp's lanes cover the particle's rows (the
-// next power of two of their count, at most 32) times 32 / that many
-// consecutive columns, stepping across the columns.
-//   ellipsoid: t = T sqrt(1 - rho^2), rho^2 = u'^2 + v'^2 with
-//              u' = (c ex + s ey) / a, v' = (-s ex + c ey) / b, evaluated
-//              in float32 and redone in float-float inside the rim band;
-//   prism:     t = clamp(g min(hx - |u|, hy - |v|), 0, T), g = 2 s_b dx;
-//   polyhedron (g < 0): t = z_hi - z_lo over the particle's pixel-affine
-//              plane bounds coef[off .. off + m) (Eq. 1), 0 outside a wall.
-__device__ __forceinline__ void raster_particle(float2 *buf, int LS, int y0, const PRec &r,
-                                                const float4 *__restrict__ coef, int xa, int xb,
-                                                int ya, int yb, int lane) {
-    const int bh = yb - ya + 1;
-    const int lyn = bh >= 32 ? 32 : (bh <= 1 ? 1 : 1 << (32 - __clz(bh - 1)));
-    const int lxn = 32 / lyn;
-    const int shx = ilog2(lxn);
-    const int lx = lane & (lxn - 1), ly = lane >> shx;
-    // Two pixels per lane and step (x and x + lxn): both chords first, then
-    // both shared-memory updates, so that the loads of the pair overlap.
-    // A pixel outside the footprint is skipped (t < 0).
-    if (r.g < 0.f) {
-        const float4 *pc = coef + __float_as_int(r.p0h);
-        const int m = __float_as_int(r.p1h);
-        for (int yy = ya + ly; yy <= yb; yy += lyn) {
-            const float ey = ((float)yy + 0.5f) - r.cy;
-            float2 *row = buf + (yy - y0) * LS;
-            for (int xx = xa + lx; xx <= xb; xx += lxn) {
-                const float ex = ((float)xx + 0.5f) - r.cx;
-                float zlo = -INFINITY, zhi = INFINITY;
-                bool inside = true;
-                for (int i = 0; i < m; ++i) {
-                    const float4 q = __ldg(pc + i);  // same address in every lane
-                    const float z = fmaf(-q.y, ex, fmaf(-q.z, ey, q.x));
-                    if (q.w > 0.f)
-                        zhi = fminf(zhi, z);
-                    else if (q.w < 0.f)
-                        zlo = fmaxf(zlo, z);
-                    else
-                        inside = inside && z >= 0.f;
-                }
-                if (!inside || !(zhi > zlo)) continue;
-                const float t = zhi - zlo;
-                float2 acc = row[pad16(xx)];
-                acc.x = fmaf(r.dn, t, acc.x);
-                acc.y = fmaf(r.mu, t, acc.y);
-                row[pad16(xx)] = acc;
-            }
+// ------------------------------------------------------------ raster
+// Composition of a strip's OPD and ATT (Eq. 2's integral over z, Eq. 7's
+// accumulate) by integer addition in shared memory.  Every (particle, pixel)
+// contribution is rounded once to a fixed-point integer and added with a
+// shared-memory atomic; integer sums do not depend on their order, so the
+// strip is bitwise the same whichever lane, warp or strip adds what (the
+// batched and per-scene paths and every band height agree bit for bit).
+//   kAccPhase (render, adjoint): per pixel a uint32 phase in units of 2^-23
+//     cycles of dn t / lambda, summed modulo 2^32 (only the phase modulo one
+//     cycle enters exp(i 2 pi OPD / lambda)), and an int32 absorption
+//     exponent in units of 2^-20 with each particle's mu t clamped to
+//     [-16, 16] (past e^-16 of amplitude a particle is opaque; the sum stays
+//     in range while fewer than 128 such particles overlap a pixel).
+//   kAccOpd (osog_render_opd): int64 OPD and ATT in units of 2^-32 um.
+// Work proceeds per (particle, row) item: the row's span of pixel centres
+// inside the footprint is found analytically (the ellipse's chord ends, the
+// rotated rectangle's slab crossings), and the CTA's lanes are packed over
+// the items' pixels, up to four per lane.
+enum { kAccPhase = 0, kAccOpd = 1 };
+
+struct __align__(16) RowItem {
+    uint32_t hdr;   // first column j0 (bits 0-11), pixel count (12-23),
+                    // row in the strip (24-28), kind (29-30)
+    float f[9];     // ellipsoid: left and right chord ends (hi, lo each), T sqrt(alpha)
+                    // prism: cx, s ey, c ey, cos, sin, hx, hy, g, T
+                    // polyhedron: cx, ey, plane offset, plane count (int bits)
+    float dn;       // kAccPhase: dn / lambda (cycles per um); kAccOpd: dn
+    float mu;
+};
+static_assert(sizeof(RowItem) == 48, "RowItem is 48 bytes");
+
+__device__ __forceinline__ ff ff_sqrt(ff a) {  // a.h > 0
+    const float s = sqrtf(a.h);
+    const float e = __fadd_rn(__fmaf_rn(-s, s, a.h), a.l);
+    return fast_two_sum(s, e * __fdividef(0.5f, s));
+}
+
+// The item of particle r on canvas row y (strip row `row`): false when the
+// footprint has no pixel centre on that row.  Columns are clipped to the
+// particle's bounding rectangle q, itself inside the canvas.
+template <int ACC>
+__device__ __forceinline__ bool make_row_item(const RRec &r, const Rect &q, int y, int row,
+                                              float inv_lambda, RowItem &it) {
+    if (y < q.y0 || y > q.y1 || q.x0 > q.x1) return false;
+    const float yc = (float)y + 0.5f;
+    float lo, hi;  // span of pixel-centre x, widened below
+    if (r.kind == 0) {
+        const ff ey = two_sum(yc, -r.cy);
+        const ff x0 = ff_add(ff{r.cx, 0.f}, ff_mul(ff{r.p[0], r.p[1]}, ey));
+        const ff w2 = ff_add(ff{r.p[2], r.p[3]}, ff_neg(ff_mul(ff{r.p[4], r.p[5]}, ff_mul(ey, ey))));
+        if (!(w2.h > 0.f)) return false;
+        const ff w = ff_sqrt(w2);
+        const ff xl = ff_add(x0, ff_neg(w)), xr = ff_add(x0, w);
+        it.f[0] = xl.h;
+        it.f[1] = xl.l;
+        it.f[2] = xr.h;
+        it.f[3] = xr.l;
+        it.f[4] = r.tsa;
+        lo = xl.h;
+        hi = xr.h;
+    } else if (r.kind == 1) {
+        // |c ex + s ey| < hx and |-s ex + c ey| < hy, ex = X - cx
+        const float c = r.p[0], sn = r.p[1], hx = r.p[2], hy = r.p[3];
+        const float ey = yc - r.cy;
+        const float s_ey = sn * ey, c_ey = c * ey;
+        lo = -3.0e38f;
+        hi = 3.0e38f;
+        if (fabsf(c) > 1e-6f) {
+            const float a0 = __fdividef(-hx - s_ey, c), a1 = __fdividef(hx - s_ey, c);
+            lo = fmaxf(lo, fminf(a0, a1));
+            hi = fminf(hi, fmaxf(a0, a1));
+        } else if (!(fabsf(s_ey) < hx + 1.f)) {
+            return false;
         }
-    } else if (r.g > 0.f) {
-        for (int yy = ya + ly; yy <= yb; yy += lyn) {
-            const float ey = ((float)yy + 0.5f) - r.cy;
-            const float s_ey = r.sh * ey, c_ey = r.ch * ey;
-            float2 *row = buf + (yy - y0) * LS;
-            auto chord = [&](int xx) {
-                const float ex = ((float)xx + 0.5f) - r.cx;
-                const float u = fmaf(r.ch, ex, s_ey);
-                const float v = fmaf(-r.sh, ex, c_ey);
-                const float d = fminf(r.p0h - fabsf(u), r.p1h - fabsf(v));
-                return fminf(fmaxf(r.g * d, 0.f), r.T);
-            };
-            for (int xx = xa + lx; xx <= xb; xx += 2 * lxn) {
-                const int x2 = xx + lxn;
-                const float t1 = chord(xx);
-                const float t2 = x2 <= xb ? chord(x2) : -1.f;
-                float2 *p1 = row + pad16(xx), *p2 = row + pad16(x2);
-                float2 a1 = *p1, a2;
-                if (t2 >= 0.f) a2 = *p2;
-                *p1 = make_float2(fmaf(r.dn, t1, a1.x), fmaf(r.mu, t1, a1.y));
-                if (t2 >= 0.f) *p2 = make_float2(fmaf(r.dn, t2, a2.x), fmaf(r.mu, t2, a2.y));
-            }
+        if (fabsf(sn) > 1e-6f) {
+            const float a0 = __fdividef(c_ey - hy, sn), a1 = __fdividef(c_ey + hy, sn);
+            lo = fmaxf(lo, fminf(a0, a1));
+            hi = fminf(hi, fmaxf(a0, a1));
+        } else if (!(fabsf(c_ey) < hy + 1.f)) {
+            return false;
+        }
+        if (!(lo <= hi)) return false;
+        lo += r.cx;
+        hi += r.cx;
+        it.f[0] = r.cx;
+        it.f[1] = s_ey;
+        it.f[2] = c_ey;
+        it.f[3] = c;
+        it.f[4] = sn;
+        it.f[5] = hx;
+        it.f[6] = hy;
+        it.f[7] = r.p[4];
+        it.f[8] = r.p[5];
+    } else {
+        it.f[0] = r.cx;
+        it.f[1] = yc - r.cy;
+        it.f[2] = r.p[0];
+        it.f[3] = r.p[1];
+        lo = (float)q.x0;
+        hi = (float)q.x1 + 1.f;
+    }
+    // pixel centres j + 0.5 in [lo, hi], one more column on each side for
+    // the rounding of the ends (their thickness evaluates to zero)
+    const int j0 = max((int)q.x0, (int)floorf(fmaxf(lo - 0.5f, -2.f)) - 1);
+    const int j1 = min((int)q.x1, (int)ceilf(fminf(hi - 0.5f, 4096.f)) + 1);
+    if (j1 < j0) return false;
+    it.hdr = (uint32_t)j0 | ((uint32_t)(j1 - j0 + 1) << 12) | ((uint32_t)row << 24) |
+             ((uint32_t)r.kind << 29);
+    it.dn = ACC == kAccPhase ? r.dn * inv_lambda : r.dn;
+    it.mu = r.mu;
+    return true;
+}
+
+// Chord t (um) of an item's particle at pixel centre X of its row; t <= 0
+// outside the footprint.
+//   ellipsoid: t = T sqrt(alpha) sqrt((xr - X)(X - xl)); both factors are
+//              taken from the float-float chord ends, so each has a relative
+//              error of one rounding even at the rim;
+//   prism:     t = clamp(g min(hx - |u|, hy - |v|), 0, T), g = 2 s_b dx;
+//   polyhedron: t = z_hi - z_lo over the pixel-affine plane bounds, 0
+//              outside a wall (Eq. 1).
+__device__ __forceinline__ float item_chord(const RowItem &it, int kind, float X,
+                                            const float4 *__restrict__ coef) {
+    if (kind == 0) {
+        const float ep = __fadd_rn(__fsub_rn(it.f[2], X), it.f[3]);
+        const float en = __fsub_rn(__fsub_rn(X, it.f[0]), it.f[1]);
+        const float qq = __fmul_rn(ep, en);
+        return qq > 1e-30f ? it.f[4] * qq * rsqrtf(qq) : -1.f;
+    }
+    const float ex = X - it.f[0];
+    if (kind == 1) {
+        const float u = fmaf(it.f[3], ex, it.f[1]);
+        const float v = fmaf(-it.f[4], ex, it.f[2]);
+        const float d = fminf(it.f[5] - fabsf(u), it.f[6] - fabsf(v));
+        return fminf(it.f[7] * d, it.f[8]);
+    }
+    const float4 *pc = coef + __float_as_int(it.f[2]);
+    const int m = __float_as_int(it.f[3]);
+    const float ey = it.f[1];
+    float zlo = -INFINITY, zhi = INFINITY;
+    bool inside = true;
+    for (int i = 0; i < m; ++i) {
+        const float4 pl = __ldg(pc + i);
+        const float z = fmaf(-pl.y, ex, fmaf(-pl.z, ey, pl.x));
+        if (pl.w > 0.f)
+            zhi = fminf(zhi, z);
+        else if (pl.w < 0.f)
+            zlo = fmaxf(zlo, z);
+        else
+            inside = inside && z >= 0.f;
+    }
+    return inside && zhi > zlo ? zhi - zlo : -1.f;
+}
+
+// Adds one particle's contribution at chord t > 0 to the pixel's accumulators.
+template <int ACC>
+__device__ __forceinline__ void deposit(void *acc, float t, float dn, float mu) {
+    if constexpr (ACC == kAccPhase) {
+        uint32_t *a = static_cast<uint32_t *>(acc);
+        const float c = t * dn;                   // cycles
+        const float r = c - rintf(c);             // in [-1/2, 1/2]
+        // round(r 2^23) from the mantissa of r 2^23 + 1.5 2^23
+        const int q = __float_as_int(fmaf(r, 8388608.f, 12582912.f)) - 0x4B400000;
+        atomicAdd(a, (uint32_t)q);
+        if (mu != 0.f) {
+            const float x = fminf(fmaxf(t * mu, -16.f), 16.f) * 1048576.f;
+            atomicAdd(reinterpret_cast<int *>(a + 1), __float2int_rn(x));
         }
     } else {
-        const float cia = r.ch * r.p0h, sia = r.sh * r.p0h;
-        const float cib = r.ch * r.p1h, sib = r.sh * r.p1h;
-        for (int yy = ya + ly; yy <= yb; yy += lyn) {
-            const float yc = (float)yy + 0.5f;
-            const float ey = yc - r.cy;
-            const float u0 = sia * ey, v0 = cib * ey;
-            float2 *row = buf + (yy - y0) * LS;
-            auto chord = [&](int xx) {
-                const float xc = (float)xx + 0.5f;
-                const float ex = xc - r.cx;
-                const float ua = fmaf(cia, ex, u0);
-                const float vb = fmaf(-sib, ex, v0);
-                float delta = 1.f - fmaf(ua, ua, vb * vb);
-                if (delta < kRimBand) {
-                    if (delta <= -kRimBand) return -1.f;
-                    delta = ellipse_delta_ff(r, xc, yc);
-                    if (!(delta > 0.f)) return -1.f;
-                }
-                return r.T * delta * rsqrtf(delta);
-            };
-            for (int xx = xa + lx; xx <= xb; xx += 2 * lxn) {
-                const int x2 = xx + lxn;
-                const float t1 = chord(xx);
-                const float t2 = x2 <= xb ? chord(x2) : -1.f;
-                float2 *p1 = row + pad16(xx), *p2 = row + pad16(x2);
-                float2 a1, a2;
-                if (t1 >= 0.f) a1 = *p1;
-                if (t2 >= 0.f) a2 = *p2;
-                if (t1 >= 0.f) *p1 = make_float2(fmaf(r.dn, t1, a1.x), fmaf(r.mu, t1, a1.y));
-                if (t2 >= 0.f) *p2 = make_float2(fmaf(r.dn, t2, a2.x), fmaf(r.mu, t2, a2.y));
-            }
-        }
+        unsigned long long *a = static_cast<unsigned long long *>(acc);
+        atomicAdd(a, (unsigned long long)__float2ll_rn(t * dn * 4294967296.f));
+        if (mu != 0.f) atomicAdd(a + 1, (unsigned long long)__float2ll_rn(t * mu * 4294967296.f));
     }
 }
 
-// OPD/ATT of the strip [y0, y0 + R) into buf, particles in list order.
-// The band list is consumed kThreads entries at a time: every thread tests
-// one entry against the strip's rows and the kept entries are compacted, in
-// order, into shared memory together with their records (one parallel
-// global load per round instead of one dependent load per particle).  Each
-// warp then rasterises, in order, the staged particles that overlap its own
-// N/16 columns (16 warps of the 512-thread CTA).
-template <int N>
+// Exit wave of a pixel's phase-mode accumulators (Eq. 2 with the
+// Beer-Lambert amplitude of Eq. 4): the phase, taken modulo one cycle into
+// [-1/2, 1/2) cycles, feeds the hardware sin / cos directly.
+__device__ __forceinline__ float2 exit_wave_fixed(uint2 acc) {
+    if (acc.x == 0u && acc.y == 0u) return make_float2(1.f, 0.f);
+    const int p = (int)(acc.x << 9) >> 9;  // units of 2^-23 cycles
+    float s, c;
+    __sincosf((float)p * 7.4901405658471572e-07f, &s, &c);        // 2 pi 2^-23
+    const float a = __expf((float)(int)acc.y * -9.5367431640625e-07f);  // -2^-20
+    return make_float2(a * c, a * s);
+}
+
+// Shared memory of raster_strip beyond the accumulators: the staged band
+// entries, one round of row items and the per-warp counts.
+constexpr size_t raster_smem() {
+    return (size_t)kThreads * (sizeof(int) + sizeof(Rect)) + (size_t)kThreads * sizeof(RowItem) +
+           2 * (kThreads / 32) * sizeof(int);
+}
+
+// OPD and ATT of the strip [y0, y0 + R) into the accumulators acc (zeroed
+// by the caller; kAccPhase: uint2 per padded pixel slot, line stride LS;
+// kAccOpd: two int64 per slot).  The band list is consumed kThreads
+// entries at a time: entries whose rectangle meets the strip's rows are
+// compacted into shared memory; then groups of kThreads / R staged
+// particles become one item per (particle, row) each, compacted ellipsoids
+// first and the other kinds after them (so that most warps run one chord
+// formula), and every warp packs its lanes over the pixels of 32 items.
+template <int N, int ACC>
 __device__ void raster_strip(const Geometry &geo, const Work &w, const SceneDev &sc, int s,
-                             int y0, float2 *buf, PRec *srec, Rect *srect, int *wsum) {
+                             int y0, int R, void *acc, unsigned char *scratch) {
     constexpr int LS = line_stride(N);
     constexpr int NW = kThreads / 32;
+    int *sid = reinterpret_cast<int *>(scratch);
+    Rect *srect = reinterpret_cast<Rect *>(sid + kThreads);
+    RowItem *items = reinterpret_cast<RowItem *>(srect + kThreads);
+    int *wsum = reinterpret_cast<int *>(items + kThreads);
     const int band = y0 / geo.BH;
     const int32_t *off = w.band_off + (size_t)s * (geo.nbands + 1);
     const int hi = min(off[band + 1], sc.pair_cap);
     const int lo = min(off[band], hi);
     const int32_t *ids = w.pairs + sc.pair0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cw = N / NW;
-    const int c0 = warp * cw, c1 = c0 + cw - 1;
-    const int ylast = y0 + geo.R - 1;
+    const int ylast = y0 + R - 1;
     const unsigned lt = lanemask_lt();
+    const float inv_lambda = 0.5f * sc.two_over_lambda;
+    const int lr = ilog2(R), np = kThreads >> lr;  // particles per item round
     for (int base = lo; base < hi; base += kThreads) {
+        // 1. the entries of this band that meet the strip's rows
         const int i = base + threadIdx.x;
         int id = 0;
         Rect q = {1, 0, 1, 0};
@@ -175,27 +267,87 @@ __device__ void raster_strip(const Geometry &geo, const Work &w, const SceneDev 
         }
         if (keep) {
             const int slot = before + __popc(m & lt);
+            sid[slot] = id;
             srect[slot] = q;
-            srec[slot] = w.rec[id];
         }
         __syncthreads();
-        for (int i0 = 0; i0 < nl; i0 += 32) {
-            const int k = i0 + lane;
-            Rect r = {1, 0, 1, 0};
-            if (k < nl) r = srect[k];
-            unsigned mm = __ballot_sync(kFull, k < nl && r.x0 <= c1 && r.x1 >= c0);
-            while (mm) {
-                const int src = __ffs(mm) - 1;
-                mm &= mm - 1;
-                const Rect rq = srect[i0 + src];
-                const PRec rec = srec[i0 + src];
-                raster_particle(buf, LS, y0, rec, w.plane_coef, max((int)rq.x0, c0),
-                                min((int)rq.x1, c1),
-                                max((int)rq.y0, y0), min((int)rq.y1, ylast), lane);
-                __syncwarp();
+        // 2. rounds of np staged particles x R rows
+        for (int p0 = 0; p0 < nl; p0 += np) {
+            const int lp = p0 + (threadIdx.x >> lr), row = threadIdx.x & (R - 1);
+            RowItem it;
+            bool valid = false, ell = false;
+            if (lp < nl) {
+                const int pid = sid[lp];
+                const RRec r = w.rrec[pid];
+                valid = make_row_item<ACC>(r, srect[lp], y0 + row, row, inv_lambda, it);
+                ell = r.kind == 0;
             }
+            const unsigned me = __ballot_sync(kFull, valid && ell);
+            const unsigned mo = __ballot_sync(kFull, valid && !ell);
+            if (lane == 0) {
+                wsum[warp] = __popc(me);
+                wsum[NW + warp] = __popc(mo);
+            }
+            __syncthreads();
+            int be = 0, ne = 0, bo = 0, no = 0;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const int ce = wsum[k], co = wsum[NW + k];
+                be += k < warp ? ce : 0;
+                bo += k < warp ? co : 0;
+                ne += ce;
+                no += co;
+            }
+            if (valid) items[ell ? be + __popc(me & lt) : ne + bo + __popc(mo & lt)] = it;
+            __syncthreads();
+            // 3. pixels: warp c takes items [32 c, 32 c + 32), lanes over
+            //    their quads (four consecutive pixels of one item)
+            const int nitems = ne + no;
+            for (int c0 = warp * 32; c0 < nitems; c0 += NW * 32) {
+                const int my = c0 + lane;
+                const int nq = my < nitems ? (int)((((items[my].hdr >> 12) & 0xFFFu) + 3u) >> 2) : 0;
+                int inc = nq;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int t = __shfl_up_sync(kFull, inc, d);
+                    if (lane >= d) inc += t;
+                }
+                const int exc = inc - nq;
+                const int total = __shfl_sync(kFull, inc, 31);
+                for (int qb = 0; qb < total; qb += 32) {
+                    const int qi = qb + lane;
+                    int k = 0;  // the first item whose inclusive quad count exceeds qi
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int v = __shfl_sync(kFull, inc, k + step - 1);
+                        if (v <= qi) k += step;
+                    }
+                    const int e0 = __shfl_sync(kFull, exc, k & 31);
+                    if (qi >= total) continue;
+                    const RowItem &rit = items[c0 + k];
+                    const uint32_t h = rit.hdr;
+                    const int j0 = (int)(h & 0xFFFu), cnt = (int)((h >> 12) & 0xFFFu);
+                    const int rrow = (int)((h >> 24) & 31u), kind = (int)(h >> 29);
+                    // quad q of an item of nq quads takes its pixels q, q + nq,
+                    // q + 2 nq, q + 3 nq: the lanes on one item then touch
+                    // consecutive pixels at each step (distinct banks)
+                    const int q = qi - e0, nqi = (cnt + 3) >> 2;
+                    for (int kk = q; kk < cnt; kk += nqi) {
+                        const int x = j0 + kk;
+                        const float t = item_chord(rit, kind, (float)x + 0.5f, w.plane_coef);
+                        if (t > 0.f) {
+                            const int slot = rrow * LS + pad16(x);
+                            if constexpr (ACC == kAccPhase)
+                                deposit<ACC>(reinterpret_cast<uint2 *>(acc) + slot, t, rit.dn, rit.mu);
+                            else
+                                deposit<ACC>(reinterpret_cast<ulonglong2 *>(acc) + slot, t, rit.dn,
+                                             rit.mu);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 

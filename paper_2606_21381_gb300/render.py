@@ -13,7 +13,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import OsogError, Optics, Tuning, check, optics_struct
+from ._lib import LossParams, OsogError, Optics, Tuning, check, optics_struct
 
 
 def n_modes(optics: dict) -> int:
@@ -247,6 +247,8 @@ class Renderer:
             t.use_graph = int(tuning.get("use_graph", 1))
             t.persistent = int(tuning.get("persistent", 0))
             t.band_rows = int(tuning.get("band_rows", 0))
+            t.wait_polls = int(tuning.get("wait_polls", 0))
+            t.test_wait_extra = int(tuning.get("test_wait_extra", 0))
         need = self.workspace_size(n_total, K, S)
         if t.pairs_per_particle > 8:
             need = int(need * t.pairs_per_particle / 8) + (1 << 20)
@@ -299,6 +301,60 @@ class Renderer:
         check(self._L.osog_plan_bind_optics_params(self.plan, _ptr(params)),
               "osog_plan_bind_optics_params")
         self._bound_params = params
+
+    # ------------------------------------------------------------ image losses
+    def loss_target(self, target: torch.Tensor, stream=None) -> torch.Tensor:
+        """osog_loss_target: the device table of the (K, H, W) target images'
+        spectra and largest amplitudes that image_loss() compares with."""
+        K = self._check_images(target, "target")
+        table = torch.empty(self._L.osog_loss_table_size(self.plan, K), dtype=torch.uint8,
+                            device=self.device)
+        ws = self._loss_ws(K)
+        check(self._L.osog_loss_target(self.plan, _ptr(target), K, _ptr(table), table.numel(),
+                                       _ptr(ws), ws.numel(), _stream(stream)), "osog_loss_target")
+        return table
+
+    def image_loss(self, image: torch.Tensor, table: torch.Tensor, dx_um: float,
+                   cutoff: torch.Tensor | None = None, misfit_scale: float = 0.0,
+                   spectral_weight: float = 0.0, eps_rel: float = 1e-4, loss=None, grad=None,
+                   want_grad: bool = True, stream=None):
+        """osog_image_loss: (loss (2,) = [misfit, spectral], dL/dimage or
+        None) for (K, H, W) images against the table of loss_target().
+        `cutoff` is a float32 device scalar (cycles/um) read when the
+        kernels run; the gradient is that of misfit + spectral_weight *
+        spectral."""
+        K = self._check_images(image, "image")
+        if cutoff is not None and (cutoff.device.type != "cuda" or cutoff.dtype != torch.float32
+                                   or cutoff.numel() != 1):
+            raise ValueError("cutoff must be a float32 CUDA scalar tensor")
+        if loss is None:
+            loss = torch.empty(2, dtype=torch.float32, device=self.device)
+        if want_grad and grad is None:
+            grad = torch.empty_like(image)
+        p = LossParams()
+        p.dx_um, p.misfit_scale = float(dx_um), float(misfit_scale)
+        p.spectral_weight, p.eps_rel = float(spectral_weight), float(eps_rel)
+        p.cutoff = None if cutoff is None else cutoff.data_ptr()
+        ws = self._loss_ws(K)
+        check(self._L.osog_image_loss(self.plan, _ptr(image), K, _ptr(table), table.numel(),
+                                      ctypes.byref(p), _ptr(loss),
+                                      _ptr(grad) if want_grad else None, _ptr(ws), ws.numel(),
+                                      _stream(stream)), "osog_image_loss")
+        return loss, (grad if want_grad else None)
+
+    def _check_images(self, t: torch.Tensor, what: str) -> int:
+        if t.device.type != "cuda" or t.dtype != torch.float32 or t.dim() != 3 \
+                or tuple(t.shape[1:]) != (self.H, self.W) or not t.is_contiguous():
+            raise ValueError(f"{what} must be a contiguous cuda float32 (K, H, W) tensor")
+        return int(t.shape[0])
+
+    def _loss_ws(self, K: int) -> torch.Tensor:
+        # a workspace of its own: the loss may run between a render_keep and
+        # its backward_kept, whose state lives in the shared one
+        need = int(self._L.osog_loss_workspace_size(self.plan, K))
+        if getattr(self, "_lws", None) is None or self._lws.numel() < need:
+            self._lws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        return self._lws
 
     # ------------------------------------------------------------ status / timing
     def sync_status(self, stream=None) -> int:

@@ -239,3 +239,25 @@ def test_kept_state_on_a_non_square_canvas_with_three_modalities():
     assert r.sync_status() == 0
     assert torch.equal(r.render(x, None, o), img_k)
     assert torch.equal(g[0], g_k[0]) and torch.equal(g[1], g_k[1])
+
+
+def test_more_live_differentiable_renders_than_the_plan_remembers():
+    """A loss over 65 differentiable renders of one renderer: the plan keeps
+    the forward states of its last 64 workspaces, so the oldest render's
+    adjoint finds its state dropped and recomputes the forward.  Every
+    gradient equals the one osog_render_backward gives for that render."""
+    from paper_2606_21381_gb300.autograd import render
+    r = renderer(128, 128)
+    rng = np.random.default_rng(31)
+    soa = scenes.draw_particles(rng, 20, 128, 128, mu=(0.002, 0.02))
+    o = scenes.optics(128, 128, modes=1, defocus=0.4)
+    base = torch.from_numpy(np.ascontiguousarray(soa)).cuda()
+    xs = [(base + 0.01 * i * (torch.arange(9, device="cuda") < 2).float()[:, None])
+          .requires_grad_(True) for i in range(65)]
+    ws = [torch.randn((1, 128, 128), device="cuda") for _ in range(65)]
+    loss = sum((render(x, o, r) * w).sum() for x, w in zip(xs, ws))
+    loss.backward()
+    assert r.sync_status() == 0
+    for x, w in zip(xs, ws):
+        gs, _ = r.backward(x.detach(), None, o, w)
+        assert torch.equal(x.grad, gs)
