@@ -220,21 +220,26 @@ def algorithmic_bytes(kernel: str, counts, H: int, W: int, K: int, pairs: int,
     pass, 8 + 8K B for the column pass's read of G and write of the K
     filtered spectra Q, 8K + 4K B for the inverse pass's read of Q and write
     of the float32 images (16 + 20K B/px in all), plus 36 B of particle
-    tensor, 64 + 8 B of record and rectangle per particle and 4 B per
-    particle-band pair.  With active < 1 the G and Q terms count only the
+    tensor, 64 + 48 + 8 B of records and rectangle per particle written at
+    setup, read again by the raster (48 + 8 B), and 4 B per particle-band
+    pair.  With active < 1 the G and Q terms count only the
     columns some pupil passes (the pruned figure: the render never writes
     or reads the others)."""
     px = len(counts) * H * W
     n = int(sum(counts))
     return int({
-        "bin_count": n * (36 + 64 + 8),
+        "bin_count": n * (36 + 64 + 48 + 8),
         "bin_scan": 0,
         "bin_fill": n * 8 + pairs * 4,
-        "strip_forward": px * 8 * active + n * (64 + 8) + pairs * 4,
+        # the tile raster: records and rectangles in, pair ids; the per-pixel
+        # phase words it hands to the strip pass are not algorithmic bytes
+        # (a fused pass keeps them on chip), so the strip pass counts G only
+        "raster": n * (48 + 8) + pairs * 4,
+        "strip_forward": px * 8 * active,
         "column": px * (8 + 8 * K) * active,
         "strip_inverse": px * 8 * K * active + px * 4 * K,
         # the three render stages in one launch: their bytes together
-        "persistent": px * 8 * active + n * (64 + 8) + pairs * 4 + px * (8 + 8 * K) * active
+        "persistent": px * 8 * active + n * (48 + 8) + pairs * 4 + px * (8 + 8 * K) * active
         + px * 8 * K * active + px * 4 * K,
     }[kernel])
 
@@ -670,7 +675,8 @@ def single_scene_entry(ms_list, n: int, K: int, peak: float, peak_src: str) -> d
     over the event-timed frame)."""
     ms = statistics.median(ms_list)
     b = sum(algorithmic_bytes(k, [n], SIZE, SIZE, K, 2 * n)
-            for k in ("bin_count", "bin_fill", "strip_forward", "column", "strip_inverse"))
+            for k in ("bin_count", "bin_fill", "raster", "strip_forward", "column",
+                      "strip_inverse"))
     gbs = b / (ms / 1e3) / 1e9
     return {"ms": round(ms, 4), "frames_per_s": round(1e3 / ms, 2),
             "particles_per_s": round(n / (ms / 1e3), 1),
@@ -711,7 +717,8 @@ def dic_1024_batch(dev, stream, steps: int, peak: float, peak_src: str) -> dict:
     counts = [s.shape[1] for s in soas]
     ms = statistics.median(t)
     b = sum(algorithmic_bytes(k, counts, 1024, 1024, 1, 2 * sum(counts))
-            for k in ("bin_count", "bin_fill", "strip_forward", "column", "strip_inverse"))
+            for k in ("bin_count", "bin_fill", "raster", "strip_forward", "column",
+                      "strip_inverse"))
     gbs = b / (ms / 1e3) / 1e9
     return {"workload": "16 x 1024^2 DIC, 4,000 particles per image, NA 0.5, shear 1 px at 45 "
                         "deg, bias pi/4, defocus U(-2, 2) um; one batch as a CUDA graph",

@@ -79,7 +79,8 @@ extern "C" {
 #define OSOG_KERNEL_BWD_STRIP 8
 #define OSOG_KERNEL_BWD_REDUCE 9
 #define OSOG_KERNEL_PERSISTENT 10
-#define OSOG_KERNEL_CLASS_COUNT 11
+#define OSOG_KERNEL_RASTER 11
+#define OSOG_KERNEL_CLASS_COUNT 12
 
 typedef struct osog_plan osog_plan_t;
 /* Binary-compatible with cudaStream_t; NULL is the legacy default stream. */
@@ -136,6 +137,11 @@ typedef struct {
  *                       strips each column item of the persistent launch waits
  *                       for by this many, so its waits run out (0 = off); the
  *                       images of such a launch are invalid
+ *   raster              1: rasterise in a kernel of its own over tiles of one
+ *                       band by a few hundred columns, handing the per-pixel
+ *                       phase and absorption words to the strip pass through
+ *                       the filtered-spectrum region; -1: inside the strip
+ *                       pass (default).  Both give bitwise the same images.
  */
 typedef struct {
     int32_t pairs_per_particle;
@@ -144,7 +150,8 @@ typedef struct {
     int32_t band_rows;
     int32_t wait_polls;
     int32_t test_wait_extra;
-    int32_t reserved[2];
+    int32_t raster;
+    int32_t reserved;
 } osog_tuning_t;
 
 /*
@@ -356,8 +363,9 @@ int osog_batch_submit(osog_plan_t *plan, const float *soa_all, int64_t ld,
  * each candidate band height (the smallest valid one and up to three
  * doublings), the exact particle-band pairs per particle the batch needs (a
  * binning dry run), then times the batch three times with three launches
- * per group and, on square canvases, with the persistent launch, and keeps
- * the fastest.  The choice is stored in the plan for (S, total particles,
+ * per group (the raster inside the strip pass, and in a tile kernel of its
+ * own) and, on square canvases, with the persistent launch, and keeps the
+ * fastest.  The choice is stored in the plan for (S, total particles,
  * K) and used by later osog_batch_submit calls of that shape whose tuning
  * leaves the fields at 0; it is also written to *out when out is not NULL.
  * Arguments as for osog_batch_submit; images receive a valid render.  This

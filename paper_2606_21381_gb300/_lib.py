@@ -15,7 +15,7 @@ from . import build as _build
 MODE_BF, MODE_OBLIQUE, MODE_DIC = 1, 2, 4
 KERNEL_CLASSES = ("bin_count", "bin_scan", "bin_fill", "strip_forward", "column",
                   "strip_inverse", "bwd_rows", "bwd_column", "bwd_strip", "bwd_reduce",
-                  "persistent")
+                  "persistent", "raster")
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_SIZE", 3: "WORKSPACE",
           4: "BIN_OVERFLOW", 5: "NONFINITE_INPUT", 6: "TIMEOUT", 7: "CUDA",
           8: "INVALID_PARTICLE"}
@@ -74,7 +74,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("pairs_per_particle", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("persistent", ctypes.c_int32), ("band_rows", ctypes.c_int32),
                 ("wait_polls", ctypes.c_int32), ("test_wait_extra", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("raster", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def optics_struct(o: dict) -> Optics:

@@ -31,7 +31,7 @@ struct osog_plan {
         int S;
         int64_t n;
         int K;
-        int ppp, persistent, band_rows;
+        int ppp, persistent, band_rows, raster;
     };
     std::vector<Tuned> tuned;
     // cached graph of the last batched launch sequence
@@ -180,6 +180,29 @@ int run_kernel(osog_plan *p, int cls, cudaStream_t st, F &&launch) {
 
 enum Stage { kFull, kOpdOnly, kFromMap, kBinOnly };
 
+// The forward raster and row pass of a launch group: either the strip pass
+// rasterises its own rows (the default), or (tiles) the tile raster writes
+// every pixel's fixed-point phase and absorption words into the region of Q
+// (the filtered spectra, unused until the column pass) and the strip pass
+// forms the exit wave from them.  The words are the same either way.
+int raster_and_strip(osog_plan *p, StripArgs &sa, cudaStream_t st, bool tiles = false) {
+    if (!tiles)
+        return run_kernel(p, OSOG_KERNEL_STRIP_FORWARD, st,
+                          [&] { return launch_strip_forward(sa, kStripRender, st); });
+    RasterArgs ra{};
+    ra.geo = sa.geo;
+    ra.w = sa.w;
+    ra.P = reinterpret_cast<uint2 *>(sa.w.Q);
+    ra.S = sa.S;
+    ra.TW = raster_tile_cols(sa.geo);
+    for (int s = 0; s < sa.S; ++s) ra.sc[s] = sa.sc[s];
+    int rc = run_kernel(p, OSOG_KERNEL_RASTER, st, [&] { return launch_raster_tiles(ra, st); });
+    if (rc) return rc;
+    sa.phase = ra.P;
+    return run_kernel(p, OSOG_KERNEL_STRIP_FORWARD, st,
+                      [&] { return launch_strip_forward(sa, kStripFromPhase, st); });
+}
+
 // Per-call choices of the batched path (see osog_tuning_t).
 struct GroupOpts {
     int ppp = kDefaultPairs;
@@ -187,6 +210,7 @@ struct GroupOpts {
     int band_rows = 0;
     int wait_polls = 0;       // persistent launch: 0 = the default limit
     int wait_extra = 0;       // failure-detection test (osog_tuning_t.test_wait_extra)
+    bool raster_tiles = false;  // the raster in a kernel of its own
     std::vector<int32_t> *band_off_out = nullptr;  // kBinOnly: host copy of band_off
     const float4 *planes = nullptr;                 // kind-2 particles (single scene)
     const int32_t *plane_off = nullptr;
@@ -312,8 +336,12 @@ int enqueue_group(osog_plan *p, const float *soa, int64_t ld, const int32_t *cou
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
         return run_kernel(p, OSOG_KERNEL_PERSISTENT, st, [&] { return launch_persistent(pa, st); });
     }
-    const StripMode sm = stage == kOpdOnly ? kStripOpdOnly : stage == kFromMap ? kStripFromMap : kStripRender;
-    rc = run_kernel(p, OSOG_KERNEL_STRIP_FORWARD, st, [&] { return launch_strip_forward(sa, sm, st); });
+    if (stage == kFull) {
+        rc = raster_and_strip(p, sa, st, opt.raster_tiles);
+    } else {
+        const StripMode sm = stage == kOpdOnly ? kStripOpdOnly : kStripFromMap;
+        rc = run_kernel(p, OSOG_KERNEL_STRIP_FORWARD, st, [&] { return launch_strip_forward(sa, sm, st); });
+    }
     if (rc || stage == kOpdOnly) return rc;
     rc = run_kernel(p, OSOG_KERNEL_COLUMN, st, [&] { return launch_column(ca, st); });
     if (rc) return rc;
@@ -435,7 +463,7 @@ int bwd_forward(osog_plan *p, const float *soa, int64_t ld, const BwdState &b, f
     sa.tw = p->tw_w;
     sa.S = 1;
     sa.sc[0] = b.sc;
-    rc = run_kernel(p, OSOG_KERNEL_STRIP_FORWARD, st, [&] { return launch_strip_forward(sa, kStripRender, st); });
+    rc = raster_and_strip(p, sa, st);
     if (rc) return rc;
     ColumnArgs ca{};
     ca.geo = geo;
@@ -712,6 +740,7 @@ int osog_render_dic_incoherent(osog_plan_t *p, const float *soa, int64_t ld, int
         return run_kernel(p, OSOG_KERNEL_STRIP_INVERSE, st, [&] { return launch_strip_inverse(ia, st); });
     };
     auto strip = [&](StripMode m) {
+        if (m == kStripRender) return raster_and_strip(p, sa, st);
         return run_kernel(p, OSOG_KERNEL_STRIP_FORWARD, st, [&] { return launch_strip_forward(sa, m, st); });
     };
 
@@ -833,6 +862,7 @@ int osog_batch_submit(osog_plan_t *p, const float *soa_all, int64_t ld, const in
             opt.ppp = t.ppp;
             opt.persistent = t.persistent > 0;
             opt.band_rows = t.band_rows;
+            opt.raster_tiles = t.raster > 0;
         }
     bool use_graph = true;
     if (tuning) {
@@ -841,6 +871,7 @@ int osog_batch_submit(osog_plan_t *p, const float *soa_all, int64_t ld, const in
         if (tuning->band_rows > 0) opt.band_rows = tuning->band_rows;
         opt.wait_polls = tuning->wait_polls;
         opt.wait_extra = tuning->test_wait_extra;
+        if (tuning->raster != 0) opt.raster_tiles = tuning->raster > 0;
         use_graph = tuning->use_graph > 0;
     }
     const int ppp = opt.ppp;
@@ -872,6 +903,7 @@ int osog_batch_submit(osog_plan_t *p, const float *soa_all, int64_t ld, const in
     put(&opt.band_rows, sizeof opt.band_rows);
     put(&opt.wait_polls, sizeof opt.wait_polls);
     put(&opt.wait_extra, sizeof opt.wait_extra);
+    put(&opt.raster_tiles, sizeof opt.raster_tiles);
     put(&p->optics_dyn, sizeof p->optics_dyn);
     if (!(p->gexec && key == p->gkey)) {
         const int64_t before = p->launches;
@@ -1007,8 +1039,9 @@ int osog_autotune(osog_plan_t *p, const float *soa_all, int64_t ld, const int32_
         if (rc) break;
         o.ppp = need;
         if (ws_need(p, n_total, K, S, o.ppp) > ws_bytes) continue;
-        for (int pers = 0; pers < (p->H == p->W ? 2 : 1); ++pers) {
-            o.persistent = pers == 1;
+        for (int mode = 0; mode < (p->H == p->W ? 3 : 2); ++mode) {
+            o.persistent = mode == 2;       // one persistent launch
+            o.raster_tiles = mode == 1;     // the raster in a kernel of its own
             float t[3];
             for (int r = 0; r < 3 && rc == OSOG_OK; ++r) {
                 cudaEventRecord(e0, st);
@@ -1037,17 +1070,20 @@ int osog_autotune(osog_plan_t *p, const float *soa_all, int64_t ld, const int32_
     bool found = false;
     for (auto &t : p->tuned)
         if (t.S == S && t.n == n_total && t.K == K) {
-            t = {S, n_total, K, chosen.ppp, chosen.persistent ? 1 : -1, chosen.band_rows};
+            t = {S, n_total, K, chosen.ppp, chosen.persistent ? 1 : -1, chosen.band_rows,
+                 chosen.raster_tiles ? 1 : -1};
             found = true;
         }
     if (!found)
-        p->tuned.push_back({S, n_total, K, chosen.ppp, chosen.persistent ? 1 : -1, chosen.band_rows});
+        p->tuned.push_back({S, n_total, K, chosen.ppp, chosen.persistent ? 1 : -1, chosen.band_rows,
+                            chosen.raster_tiles ? 1 : -1});
     if (out) {
         *out = osog_tuning_t{};
         out->pairs_per_particle = chosen.ppp;
         out->use_graph = 1;
         out->persistent = chosen.persistent ? 1 : -1;
         out->band_rows = chosen.band_rows;
+        out->raster = chosen.raster_tiles ? 1 : -1;
     }
     return OSOG_OK;
 }

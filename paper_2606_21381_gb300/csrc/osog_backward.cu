@@ -375,7 +375,7 @@ size_t bwd_strip_smem(int W) {
     const int L = set_elems(W) / W;
     const size_t gather = kThreads * (sizeof(PRec) + sizeof(Rect) + sizeof(int)) + 64;
     return (size_t)2 * L * line_stride(W) * sizeof(float2) +
-           (gather > raster_smem() ? gather : raster_smem());
+           (gather > raster_smem<kThreads>() ? gather : raster_smem<kThreads>());
 }
 
 cudaError_t prepare_backward(int H, int W) {

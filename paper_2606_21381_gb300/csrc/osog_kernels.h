@@ -10,7 +10,10 @@ namespace osog {
 // Stage selector of the forward strip kernel.
 // kStripFromReal: the strip's field is a real image [H][W] (float, read
 // from opd_att), used as (value, 0) without an exit-wave step.
-enum StripMode { kStripRender = 0, kStripOpdOnly = 1, kStripFromMap = 2, kStripFromReal = 3 };
+// kStripFromPhase: the strip's exit wave from the fixed-point phase and
+// absorption words that the tile raster wrote (StripArgs.phase).
+enum StripMode { kStripRender = 0, kStripOpdOnly = 1, kStripFromMap = 2, kStripFromReal = 3,
+                 kStripFromPhase = 4 };
 
 struct StripArgs {
     Geometry geo;
@@ -18,7 +21,20 @@ struct StripArgs {
     const float2 *tw;        // W-point twiddles
     const float2 *opd_att;   // kStripFromMap input [H][W] (opd, att)
     float2 *opd_out;         // kStripOpdOnly output [H][W]
+    const uint2 *phase;      // kStripFromPhase input [S][H][W]
     int32_t S;
+    SceneDev sc[kMaxScenes];
+};
+
+// The tile raster: one CTA per tile of BH rows (one binning band) by TW
+// columns of one scene; writes the tile's fixed-point phase and absorption
+// words (see raster_region) to P [S][H][W].
+struct RasterArgs {
+    Geometry geo;
+    Work w;
+    uint2 *P;
+    int32_t S;
+    int32_t TW;
     SceneDev sc[kMaxScenes];
 };
 
@@ -154,6 +170,8 @@ cudaError_t prepare_kernels(int H, int W);  // opt-in shared memory sizes
 cudaError_t launch_strip_forward(const StripArgs &a, StripMode mode, cudaStream_t st);
 cudaError_t launch_column(const ColumnArgs &a, cudaStream_t st);
 cudaError_t launch_strip_inverse(const InverseArgs &a, cudaStream_t st);
+int raster_tile_cols(const Geometry &geo);  // TW of the tile raster
+cudaError_t launch_raster_tiles(const RasterArgs &a, cudaStream_t st);
 // largest |spectrum| of each of S column-blocked H x W spectra (one CTA each)
 cudaError_t launch_max_amplitude(const float2 *spec, int S, int64_t count, float *maxamp,
                                  cudaStream_t st);

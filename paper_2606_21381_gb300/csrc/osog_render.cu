@@ -50,6 +50,19 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
             const int e = threadIdx.x + i * kThreads;
             if (e < RN) buf[(e / N) * LS + pad16(e % N)] = make_float2(v[i], 0.f);
         }
+    } else if constexpr (MODE == kStripFromPhase) {
+        const uint2 *src = a.phase + ((size_t)s * geo.H + y0) * N;
+        uint2 v[ept(N)];
+#pragma unroll
+        for (int i = 0; i < ept(N); ++i) {
+            const int e = threadIdx.x + i * kThreads;
+            if (e < RN) v[i] = src[e];
+        }
+#pragma unroll
+        for (int i = 0; i < ept(N); ++i) {
+            const int e = threadIdx.x + i * kThreads;
+            if (e < RN) buf[(e / N) * LS + pad16(e % N)] = exit_wave_fixed(v[i]);
+        }
     } else if constexpr (MODE == kStripFromMap) {
         const float2 *src = a.opd_att + (size_t)y0 * N;
         float2 v[ept(N)];
@@ -123,6 +136,36 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
                 G[((size_t)bk * H + y0 + r) * B + c] = buf[r * LS + pad16(kx)];
         }
     }
+}
+
+// ------------------------------------------------------------ tile raster
+constexpr int kRThreads = 256;
+
+__global__ void __launch_bounds__(kRThreads, 4) k_raster_tiles(const __grid_constant__ RasterArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_enter();
+    const Geometry &geo = a.geo;
+    const int s = blockIdx.z, band = blockIdx.y;
+    const int TW = a.TW, TH = geo.BH;
+    const int tx0 = blockIdx.x * TW, ty0 = band * TH;
+    uint2 *acc = reinterpret_cast<uint2 *>(smem_raw);
+    unsigned char *scratch = smem_raw + (size_t)TH * TW * sizeof(uint2);
+    uint4 *a4 = reinterpret_cast<uint4 *>(acc);
+    for (int i = threadIdx.x; i < TH * TW / 2; i += kRThreads) a4[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    const SceneDev &sc = a.sc[s];
+    const int32_t *off = a.w.band_off + (size_t)s * (geo.nbands + 1);
+    const int hi = min(off[band + 1], sc.pair_cap);
+    const int lo = min(off[band], hi);
+    auto slot = [acc, TW, tx0](int row, int x) -> void * { return acc + row * TW + (x - tx0); };
+    raster_region<kRThreads, kAccPhase>(a.w, a.w.pairs + sc.pair0, lo, hi, ty0, TH, tx0,
+                                        tx0 + TW - 1, 0.5f * sc.two_over_lambda, slot, scratch);
+    __syncthreads();
+    // the tile's rows, two pixels per 16-byte store
+    const int lw = ilog2(TW / 2);
+    uint4 *dst = reinterpret_cast<uint4 *>(a.P + ((size_t)s * geo.H + ty0) * geo.W + tx0);
+    for (int i = threadIdx.x; i < TH * TW / 2; i += kRThreads)
+        dst[(size_t)(i >> lw) * (geo.W / 2) + (i & (TW / 2 - 1))] = a4[i];
 }
 
 template <int N, int MODE, bool SQ>
@@ -367,7 +410,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_strip_inverse(const __grid_cons
 // whatever is there, so the launch always ends.  Once the flag is up, later
 // waits of the launch return at once.  The fence orders the producer's
 // writes before this CTA's reads.
-constexpr int kSpinLimit = 1 << 24;
 
 __device__ __forceinline__ void wait_count(const int32_t *cnt, int target, int32_t *gave_up,
                                            int32_t *status, int polls) {
@@ -484,6 +526,7 @@ struct StripFwdLaunch {
     static cudaError_t run(const StripArgs &a, StripMode mode, cudaStream_t st) {
         dim3 grid(a.geo.nstrips, a.S);
         const size_t smem = strip_forward_smem(N), smem_opd = strip_forward_smem(N, true);
+        const size_t smem_fft = strip_inverse_smem(N);  // the set alone: no raster
         if (mode == kStripRender && a.geo.H == a.geo.W)
             return launch_chain(k_strip_forward<N, kStripRender, true>, grid, kThreads, smem, st, a);
         else if (mode == kStripRender)
@@ -492,6 +535,10 @@ struct StripFwdLaunch {
             return launch_chain(k_strip_forward<N, kStripOpdOnly, false>, grid, kThreads, smem_opd, st, a);
         else if (mode == kStripFromReal)
             return launch_chain(k_strip_forward<N, kStripFromReal, false>, grid, kThreads, smem, st, a);
+        else if (mode == kStripFromPhase && a.geo.H == a.geo.W)
+            return launch_chain(k_strip_forward<N, kStripFromPhase, true>, grid, kThreads, smem_fft, st, a);
+        else if (mode == kStripFromPhase)
+            return launch_chain(k_strip_forward<N, kStripFromPhase, false>, grid, kThreads, smem_fft, st, a);
         else
             return launch_chain(k_strip_forward<N, kStripFromMap, false>, grid, kThreads, smem, st, a);
     }
@@ -511,6 +558,11 @@ struct StripFwdLaunch {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_strip_forward<N, kStripFromReal, false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        for (int sq = 0; sq < 2 && e == cudaSuccess; ++sq)
+            e = cudaFuncSetAttribute(sq ? k_strip_forward<N, kStripFromPhase, true>
+                                        : k_strip_forward<N, kStripFromPhase, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)strip_inverse_smem(N));
         return e;
     }
 };
@@ -645,7 +697,7 @@ cudaError_t launch_loss_reduce(const float *part, int64_t nparts, float *loss, c
 
 size_t strip_forward_smem(int W, bool opd_mode) {
     const int L = set_elems(W) / W;
-    return (size_t)(opd_mode ? 2 : 1) * L * line_stride(W) * sizeof(float2) + raster_smem();
+    return (size_t)(opd_mode ? 2 : 1) * L * line_stride(W) * sizeof(float2) + raster_smem<kThreads>();
 }
 
 size_t column_smem(int H, int K) {
@@ -662,6 +714,27 @@ size_t strip_inverse_smem(int W) {
 size_t persistent_smem(int N, int K) {
     const size_t a = strip_forward_smem(N), b = column_smem(N, K), c = strip_inverse_smem(N);
     return a > b ? (a > c ? a : c) : (b > c ? b : c);
+}
+
+int raster_tile_cols(const Geometry &geo) {
+    int tw = 4096 / geo.BH;
+    if (tw < 32) tw = 32;
+    return tw > geo.W ? geo.W : tw;
+}
+
+static size_t raster_tiles_smem(int BH, int TW) {
+    return (size_t)BH * TW * sizeof(uint2) + raster_smem<kRThreads>();
+}
+
+cudaError_t launch_raster_tiles(const RasterArgs &a, cudaStream_t st) {
+    const dim3 grid(a.geo.W / a.TW, a.geo.nbands, a.S);
+    const size_t smem = raster_tiles_smem(a.geo.BH, a.TW);
+    if (smem > 48 * 1024) {  // tall bands: opt in to the size (host-side, cached by the driver)
+        const cudaError_t e = cudaFuncSetAttribute(k_raster_tiles,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_chain(k_raster_tiles, grid, kRThreads, smem, st, a);
 }
 
 cudaError_t prepare_kernels(int H, int W) {

@@ -45,31 +45,35 @@ __host__ __device__ constexpr int sq_rb(int n) { return set_elems(n) / n < n ? s
 enum { kAccPhase = 0, kAccOpd = 1 };
 
 struct __align__(16) RowItem {
-    uint32_t hdr;   // first column j0 (bits 0-11), pixel count (12-23),
-                    // row in the strip (24-28), kind (29-30)
-    float f[9];     // ellipsoid: left and right chord ends (hi, lo each), T sqrt(alpha)
-                    // prism: cx, s ey, c ey, cos, sin, hx, hy, g, T
+    uint32_t hdr;   // first column j0 (bits 0-11), pixel count (12-23), kind (24-25)
+    float f[8];     // ellipsoid: left and right chord ends (hi, lo each), T sqrt(alpha)
+                    // prism: cx, g s ey, g c ey, g cos, g sin, g hx, g hy, T
                     // polyhedron: cx, ey, plane offset, plane count (int bits)
+    int32_t row;    // row in the rasterised region
     float dn;       // kAccPhase: dn / lambda (cycles per um); kAccOpd: dn
     float mu;
 };
 static_assert(sizeof(RowItem) == 48, "RowItem is 48 bytes");
 
-__device__ __forceinline__ ff ff_sqrt(ff a) {  // a.h > 0
-    const float s = sqrtf(a.h);
+// Square root of a float-float a (a.h > 0): a float estimate s, then one
+// correction step (a - s^2) / (2 s) with the residual taken exactly by a
+// fused multiply-add, which also absorbs the estimate's own rounding.
+__device__ __forceinline__ ff ff_sqrt(ff a) {
+    const float r = rsqrtf(a.h);
+    const float s = a.h * r;
     const float e = __fadd_rn(__fmaf_rn(-s, s, a.h), a.l);
-    return fast_two_sum(s, e * __fdividef(0.5f, s));
+    return fast_two_sum(s, e * (0.5f * r));
 }
 
-// The item of particle r on canvas row y (strip row `row`): false when the
-// footprint has no pixel centre on that row.  Columns are clipped to the
-// particle's bounding rectangle q, itself inside the canvas.
+// The item of particle r on canvas row y (region row `row`), its columns
+// clipped to [c0, c1] (inside the particle's bounding rectangle and the
+// canvas): false when no pixel centre of the footprint is left.
 template <int ACC>
-__device__ __forceinline__ bool make_row_item(const RRec &r, const Rect &q, int y, int row,
+__device__ __forceinline__ bool make_row_item(const RRec &r, int c0, int c1, int y, int row,
                                               float inv_lambda, RowItem &it) {
-    if (y < q.y0 || y > q.y1 || q.x0 > q.x1) return false;
     const float yc = (float)y + 0.5f;
     float lo, hi;  // span of pixel-centre x, widened below
+    float c = 0.f, sn = 0.f, s_ey = 0.f, c_ey = 0.f;
     if (r.kind == 0) {
         const ff ey = two_sum(yc, -r.cy);
         const ff x0 = ff_add(ff{r.cx, 0.f}, ff_mul(ff{r.p[0], r.p[1]}, ey));
@@ -86,9 +90,12 @@ __device__ __forceinline__ bool make_row_item(const RRec &r, const Rect &q, int 
         hi = xr.h;
     } else if (r.kind == 1) {
         // |c ex + s ey| < hx and |-s ex + c ey| < hy, ex = X - cx
-        const float c = r.p[0], sn = r.p[1], hx = r.p[2], hy = r.p[3];
+        c = r.p[0];
+        sn = r.p[1];
+        const float hx = r.p[2], hy = r.p[3];
         const float ey = yc - r.cy;
-        const float s_ey = sn * ey, c_ey = c * ey;
+        s_ey = sn * ey;
+        c_ey = c * ey;
         lo = -3.0e38f;
         hi = 3.0e38f;
         if (fabsf(c) > 1e-6f) {
@@ -108,41 +115,45 @@ __device__ __forceinline__ bool make_row_item(const RRec &r, const Rect &q, int 
         if (!(lo <= hi)) return false;
         lo += r.cx;
         hi += r.cx;
-        it.f[0] = r.cx;
-        it.f[1] = s_ey;
-        it.f[2] = c_ey;
-        it.f[3] = c;
-        it.f[4] = sn;
-        it.f[5] = hx;
-        it.f[6] = hy;
-        it.f[7] = r.p[4];
-        it.f[8] = r.p[5];
     } else {
         it.f[0] = r.cx;
         it.f[1] = yc - r.cy;
         it.f[2] = r.p[0];
         it.f[3] = r.p[1];
-        lo = (float)q.x0;
-        hi = (float)q.x1 + 1.f;
+        lo = (float)c0;
+        hi = (float)c1 + 1.f;
     }
     // pixel centres j + 0.5 in [lo, hi], one more column on each side for
     // the rounding of the ends (their thickness evaluates to zero)
-    const int j0 = max((int)q.x0, (int)floorf(fmaxf(lo - 0.5f, -2.f)) - 1);
-    const int j1 = min((int)q.x1, (int)ceilf(fminf(hi - 0.5f, 4096.f)) + 1);
+    const int j0 = max(c0, (int)floorf(fmaxf(lo - 0.5f, -2.f)) - 1);
+    const int j1 = min(c1, (int)ceilf(fminf(hi - 0.5f, 4096.f)) + 1);
     if (j1 < j0) return false;
-    it.hdr = (uint32_t)j0 | ((uint32_t)(j1 - j0 + 1) << 12) | ((uint32_t)row << 24) |
-             ((uint32_t)r.kind << 29);
+    if (r.kind == 1) {  // everything in um: g u = g c ex + g s ey, g = 2 s_b dx
+        const float g = r.p[4];
+        it.f[0] = r.cx;
+        it.f[1] = g * s_ey;
+        it.f[2] = g * c_ey;
+        it.f[3] = g * c;
+        it.f[4] = g * sn;
+        it.f[5] = g * r.p[2];
+        it.f[6] = g * r.p[3];
+        it.f[7] = r.p[5];
+    }
+    it.hdr = (uint32_t)j0 | ((uint32_t)(j1 - j0 + 1) << 12) | ((uint32_t)r.kind << 24);
+    it.row = row;
     it.dn = ACC == kAccPhase ? r.dn * inv_lambda : r.dn;
     it.mu = r.mu;
     return true;
 }
 
-// Chord t (um) of an item's particle at pixel centre X of its row; t <= 0
-// outside the footprint.
+// Chord t (um) of an item's particle at the pixel centre X of its row, a
+// function of the pixel alone (not of where the item's span starts, which
+// depends on the tiling); t <= 0 outside the footprint.
 //   ellipsoid: t = T sqrt(alpha) sqrt((xr - X)(X - xl)); both factors are
 //              taken from the float-float chord ends, so each has a relative
 //              error of one rounding even at the rim;
-//   prism:     t = clamp(g min(hx - |u|, hy - |v|), 0, T), g = 2 s_b dx;
+//   prism:     t = clamp(g min(hx - |u|, hy - |v|), 0, T), g = 2 s_b dx,
+//              taken as min(g hx - |g u|, g hy - |g v|) capped at T;
 //   polyhedron: t = z_hi - z_lo over the pixel-affine plane bounds, 0
 //              outside a wall (Eq. 1).
 __device__ __forceinline__ float item_chord(const RowItem &it, int kind, float X,
@@ -155,10 +166,9 @@ __device__ __forceinline__ float item_chord(const RowItem &it, int kind, float X
     }
     const float ex = X - it.f[0];
     if (kind == 1) {
-        const float u = fmaf(it.f[3], ex, it.f[1]);
-        const float v = fmaf(-it.f[4], ex, it.f[2]);
-        const float d = fminf(it.f[5] - fabsf(u), it.f[6] - fabsf(v));
-        return fminf(it.f[7] * d, it.f[8]);
+        const float gu = fmaf(it.f[3], ex, it.f[1]);
+        const float gv = fmaf(-it.f[4], ex, it.f[2]);
+        return fminf(fminf(it.f[5] - fabsf(gu), it.f[6] - fabsf(gv)), it.f[7]);
     }
     const float4 *pc = coef + __float_as_int(it.f[2]);
     const int m = __float_as_int(it.f[3]);
@@ -178,7 +188,8 @@ __device__ __forceinline__ float item_chord(const RowItem &it, int kind, float X
     return inside && zhi > zlo ? zhi - zlo : -1.f;
 }
 
-// Adds one particle's contribution at chord t > 0 to the pixel's accumulators.
+// Adds one particle's contribution at chord t > 0 to the pixel's accumulators
+// (phase mode: a uint2 slot, x the phase, y the absorption exponent).
 template <int ACC>
 __device__ __forceinline__ void deposit(void *acc, float t, float dn, float mu) {
     if constexpr (ACC == kAccPhase) {
@@ -206,47 +217,77 @@ __device__ __forceinline__ float2 exit_wave_fixed(uint2 acc) {
     if (acc.x == 0u && acc.y == 0u) return make_float2(1.f, 0.f);
     const int p = (int)(acc.x << 9) >> 9;  // units of 2^-23 cycles
     float s, c;
-    __sincosf((float)p * 7.4901405658471572e-07f, &s, &c);        // 2 pi 2^-23
+    __sincosf((float)p * 7.4901405658471572e-07f, &s, &c);              // 2 pi 2^-23
     const float a = __expf((float)(int)acc.y * -9.5367431640625e-07f);  // -2^-20
     return make_float2(a * c, a * s);
 }
 
-// Shared memory of raster_strip beyond the accumulators: the staged band
-// entries, one round of row items and the per-warp counts.
-constexpr size_t raster_smem() {
-    return (size_t)kThreads * (sizeof(int) + sizeof(Rect)) + (size_t)kThreads * sizeof(RowItem) +
-           2 * (kThreads / 32) * sizeof(int);
+// Exclusive prefix sum of one value per thread over the NT threads of the
+// CTA (warp scans, then the warp totals in order); total receives the sum.
+// Begins and ends with a barrier-separated use of wsum[0 .. NT/32).
+template <int NT>
+__device__ __forceinline__ int block_excl_scan(int v, int *wsum, int &total) {
+    constexpr int NW = NT / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(kFull, inc, d);
+        if (lane >= d) inc += t;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    int before = 0;
+    total = 0;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+        const int c = wsum[k];
+        before += k < warp ? c : 0;
+        total += c;
+    }
+    return before + inc - v;
 }
 
-// OPD and ATT of the strip [y0, y0 + R) into the accumulators acc (zeroed
-// by the caller; kAccPhase: uint2 per padded pixel slot, line stride LS;
-// kAccOpd: two int64 per slot).  The band list is consumed kThreads
-// entries at a time: entries whose rectangle meets the strip's rows are
-// compacted into shared memory; then groups of kThreads / R staged
-// particles become one item per (particle, row) each, compacted ellipsoids
-// first and the other kinds after them (so that most warps run one chord
-// formula), and every warp packs its lanes over the pixels of 32 items.
-template <int N, int ACC>
-__device__ void raster_strip(const Geometry &geo, const Work &w, const SceneDev &sc, int s,
-                             int y0, int R, void *acc, unsigned char *scratch) {
-    constexpr int LS = line_stride(N);
-    constexpr int NW = kThreads / 32;
+// Pixels of one chunk of a row item, and chunks per pass of the pixel phase.
+constexpr int kChunkPx = 8;
+constexpr int kChunkCap = 1024;
+
+// Shared memory of raster_region beyond the accumulators: the staged band
+// entries, their row offsets, one round of row items, the items' chunk
+// offsets, one pass of chunks and the per-warp counts.
+template <int NT>
+__host__ __device__ constexpr size_t raster_smem() {
+    return (size_t)NT * (sizeof(int) + sizeof(Rect)) + (size_t)(NT + 4) * sizeof(int) +
+           (size_t)NT * sizeof(RowItem) + (size_t)kChunkCap * sizeof(uint32_t) +
+           2 * (NT / 32) * sizeof(int);
+}
+
+// OPD and ATT of the region rows [ty0, ty0 + nrows) x columns [tx0, tx1]
+// of scene s from the band list entries [lo, hi) (ids of the scene's
+// records), added into the accumulators that slot(row, x) addresses (zeroed
+// by the caller; kAccPhase: uint2, kAccOpd: two int64).  The list is
+// consumed NT entries at a time: entries whose rectangle meets the region
+// are compacted into shared memory; each staged particle gives one item per
+// region row it covers, built NT at a time and compacted ellipsoids first
+// and the other kinds after them (so that most warps run one chord
+// formula); the items' pixels are then shared out evenly over the warps in
+// chunks of up to kChunkPx.  Every thread of the CTA must call it.
+template <int NT, int ACC, typename Slot>
+__device__ void raster_region(const Work &w, const int32_t *ids, int lo, int hi, int ty0,
+                              int nrows, int tx0, int tx1, float inv_lambda, Slot slot,
+                              unsigned char *scratch) {
+    constexpr int NW = NT / 32;
     int *sid = reinterpret_cast<int *>(scratch);
-    Rect *srect = reinterpret_cast<Rect *>(sid + kThreads);
-    RowItem *items = reinterpret_cast<RowItem *>(srect + kThreads);
-    int *wsum = reinterpret_cast<int *>(items + kThreads);
-    const int band = y0 / geo.BH;
-    const int32_t *off = w.band_off + (size_t)s * (geo.nbands + 1);
-    const int hi = min(off[band + 1], sc.pair_cap);
-    const int lo = min(off[band], hi);
-    const int32_t *ids = w.pairs + sc.pair0;
+    Rect *srect = reinterpret_cast<Rect *>(sid + NT);
+    int *rowpre = reinterpret_cast<int *>(srect + NT);          // [NT + 1]
+    RowItem *items = reinterpret_cast<RowItem *>(rowpre + NT + 4);
+    uint32_t *chunk = reinterpret_cast<uint32_t *>(items + NT);           // [kChunkCap]
+    int *wsum = reinterpret_cast<int *>(chunk + kChunkCap);               // [2 NW]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ylast = y0 + R - 1;
+    const int tyl = ty0 + nrows - 1;
     const unsigned lt = lanemask_lt();
-    const float inv_lambda = 0.5f * sc.two_over_lambda;
-    const int lr = ilog2(R), np = kThreads >> lr;  // particles per item round
-    for (int base = lo; base < hi; base += kThreads) {
-        // 1. the entries of this band that meet the strip's rows
+    for (int base = lo; base < hi; base += NT) {
+        // 1. the entries that meet the region
         const int i = base + threadIdx.x;
         int id = 0;
         Rect q = {1, 0, 1, 0};
@@ -254,33 +295,43 @@ __device__ void raster_strip(const Geometry &geo, const Work &w, const SceneDev 
             id = ids[i];
             q = w.rect[id];
         }
-        const bool keep = i < hi && q.y0 <= ylast && q.y1 >= y0;
-        const unsigned m = __ballot_sync(kFull, keep);
-        if (lane == 0) wsum[warp] = __popc(m);
-        __syncthreads();
-        int before = 0, nl = 0;
-#pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            const int c = wsum[k];
-            before += k < warp ? c : 0;
-            nl += c;
-        }
+        const bool keep = i < hi && q.y0 <= tyl && q.y1 >= ty0 && q.x0 <= tx1 && q.x1 >= tx0;
+        int nl;
+        const int kslot = block_excl_scan<NT>(keep ? 1 : 0, wsum, nl);
         if (keep) {
-            const int slot = before + __popc(m & lt);
-            sid[slot] = id;
-            srect[slot] = q;
+            sid[kslot] = id;
+            srect[kslot] = q;
         }
         __syncthreads();
-        // 2. rounds of np staged particles x R rows
-        for (int p0 = 0; p0 < nl; p0 += np) {
-            const int lp = p0 + (threadIdx.x >> lr), row = threadIdx.x & (R - 1);
+        // 2. rows of the region each staged particle covers, as offsets
+        int npairs;
+        {
+            int nr = 0;
+            if ((int)threadIdx.x < nl) {
+                const Rect r = srect[threadIdx.x];
+                nr = min((int)r.y1, tyl) - max((int)r.y0, ty0) + 1;
+            }
+            const int pre = block_excl_scan<NT>(nr, wsum, npairs);
+            rowpre[threadIdx.x] = pre;
+        }
+        __syncthreads();
+        // 3. rounds of NT (particle, row) items
+        for (int pb = 0; pb < npairs; pb += NT) {
+            const int j = pb + threadIdx.x;
             RowItem it;
             bool valid = false, ell = false;
-            if (lp < nl) {
-                const int pid = sid[lp];
-                const RRec r = w.rrec[pid];
-                valid = make_row_item<ACC>(r, srect[lp], y0 + row, row, inv_lambda, it);
-                ell = r.kind == 0;
+            if (j < npairs) {
+                int p = 0, ph = nl;  // the last staged particle whose rows start at or before j
+                while (ph - p > 1) {
+                    const int mid = (p + ph) >> 1;
+                    if (rowpre[mid] <= j) p = mid; else ph = mid;
+                }
+                const Rect r = srect[p];
+                const int y = max((int)r.y0, ty0) + (j - rowpre[p]);
+                const RRec rr = w.rrec[sid[p]];
+                valid = make_row_item<ACC>(rr, max((int)r.x0, tx0), min((int)r.x1, tx1), y, y - ty0,
+                                           inv_lambda, it);
+                ell = rr.kind == 0;
             }
             const unsigned me = __ballot_sync(kFull, valid && ell);
             const unsigned mo = __ballot_sync(kFull, valid && !ell);
@@ -300,55 +351,79 @@ __device__ void raster_strip(const Geometry &geo, const Work &w, const SceneDev 
             }
             if (valid) items[ell ? be + __popc(me & lt) : ne + bo + __popc(mo & lt)] = it;
             __syncthreads();
-            // 3. pixels: warp c takes items [32 c, 32 c + 32), lanes over
-            //    their quads (four consecutive pixels of one item)
+            // 4. pixels: every item is cut into chunks of up to kChunkPx
+            //    consecutive pixels, numbered through the items by a prefix
+            //    sum (kind order kept); each lane takes one chunk at a time
+            //    and evaluates its pixels as independent unrolled chains; a
+            //    pass hands kChunkCap chunks out evenly over the warps.
             const int nitems = ne + no;
-            for (int c0 = warp * 32; c0 < nitems; c0 += NW * 32) {
-                const int my = c0 + lane;
-                const int nq = my < nitems ? (int)((((items[my].hdr >> 12) & 0xFFFu) + 3u) >> 2) : 0;
-                int inc = nq;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const int t = __shfl_up_sync(kFull, inc, d);
-                    if (lane >= d) inc += t;
-                }
-                const int exc = inc - nq;
-                const int total = __shfl_sync(kFull, inc, 31);
-                for (int qb = 0; qb < total; qb += 32) {
-                    const int qi = qb + lane;
-                    int k = 0;  // the first item whose inclusive quad count exceeds qi
-#pragma unroll
-                    for (int step = 16; step > 0; step >>= 1) {
-                        const int v = __shfl_sync(kFull, inc, k + step - 1);
-                        if (v <= qi) k += step;
-                    }
-                    const int e0 = __shfl_sync(kFull, exc, k & 31);
-                    if (qi >= total) continue;
-                    const RowItem &rit = items[c0 + k];
+            int TC;
+            const int mych = (int)threadIdx.x < nitems
+                                 ? (int)((((items[threadIdx.x].hdr >> 12) & 0xFFFu) + kChunkPx - 1) /
+                                         kChunkPx)
+                                 : 0;
+            const int cfirst = block_excl_scan<NT>(mych, wsum, TC);
+            for (int cb = 0; cb < TC; cb += kChunkCap) {
+                __syncthreads();  // the previous pass has read the chunk table
+                // chunk entry: item index (bits 0-15), first pixel of the chunk (16-31)
+                for (int c = max(cfirst, cb); c < min(cfirst + mych, cb + kChunkCap); ++c)
+                    chunk[c - cb] = (uint32_t)threadIdx.x | ((uint32_t)((c - cfirst) * kChunkPx) << 16);
+                __syncthreads();
+                const int nc = min(TC - cb, kChunkCap);
+                const int ca = (int)((long)nc * warp / NW), cz = (int)((long)nc * (warp + 1) / NW);
+                for (int c = ca + lane; c < cz; c += 32) {
+                    const uint32_t ce = chunk[c];
+                    const RowItem rit = items[ce & 0xFFFFu];  // registers: the atomics below
+                                                              // may not alias it
                     const uint32_t h = rit.hdr;
                     const int j0 = (int)(h & 0xFFFu), cnt = (int)((h >> 12) & 0xFFFu);
-                    const int rrow = (int)((h >> 24) & 31u), kind = (int)(h >> 29);
-                    // quad q of an item of nq quads takes its pixels q, q + nq,
-                    // q + 2 nq, q + 3 nq: the lanes on one item then touch
-                    // consecutive pixels at each step (distinct banks)
-                    const int q = qi - e0, nqi = (cnt + 3) >> 2;
-                    for (int kk = q; kk < cnt; kk += nqi) {
-                        const int x = j0 + kk;
-                        const float t = item_chord(rit, kind, (float)x + 0.5f, w.plane_coef);
-                        if (t > 0.f) {
-                            const int slot = rrow * LS + pad16(x);
-                            if constexpr (ACC == kAccPhase)
-                                deposit<ACC>(reinterpret_cast<uint2 *>(acc) + slot, t, rit.dn, rit.mu);
-                            else
-                                deposit<ACC>(reinterpret_cast<ulonglong2 *>(acc) + slot, t, rit.dn,
-                                             rit.mu);
-                        }
+                    const int kind = (int)((h >> 24) & 3u);
+                    const int k0 = (int)(ce >> 16);
+                    const int len = min(kChunkPx, cnt - k0);
+                    const int x0 = j0 + k0;
+                    float t[kChunkPx];
+                    if (kind == 0) {
+#pragma unroll
+                        for (int u = 0; u < kChunkPx; ++u)
+                            t[u] = item_chord(rit, 0, (float)(x0 + u) + 0.5f, nullptr);
+                    } else if (kind == 1) {
+#pragma unroll
+                        for (int u = 0; u < kChunkPx; ++u)
+                            t[u] = item_chord(rit, 1, (float)(x0 + u) + 0.5f, nullptr);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < kChunkPx; ++u)
+                            t[u] = u < len ? item_chord(rit, 2, (float)(x0 + u) + 0.5f, w.plane_coef)
+                                           : -1.f;
                     }
+#pragma unroll
+                    for (int u = 0; u < kChunkPx; ++u)
+                        if (u < len && t[u] > 0.f) deposit<ACC>(slot(rit.row, x0 + u), t[u], rit.dn, rit.mu);
                 }
             }
             __syncthreads();
         }
     }
+}
+
+// The strip [y0, y0 + R) of scene s rasterised into the padded FFT lines of
+// an N-point set (the adjoint's re-raster; osog_render_opd in OPD mode).
+template <int N, int ACC>
+__device__ void raster_strip(const Geometry &geo, const Work &w, const SceneDev &sc, int s,
+                             int y0, int R, void *acc, unsigned char *scratch) {
+    constexpr int LS = line_stride(N);
+    const int band = y0 / geo.BH;
+    const int32_t *off = w.band_off + (size_t)s * (geo.nbands + 1);
+    const int hi = min(off[band + 1], sc.pair_cap);
+    const int lo = min(off[band], hi);
+    auto slot = [acc](int row, int x) -> void * {
+        if constexpr (ACC == kAccPhase)
+            return reinterpret_cast<uint2 *>(acc) + row * LS + pad16(x);
+        else
+            return reinterpret_cast<ulonglong2 *>(acc) + row * LS + pad16(x);
+    };
+    raster_region<kThreads, ACC>(w, w.pairs + sc.pair0, lo, hi, y0, R, 0, geo.W - 1,
+                                 0.5f * sc.two_over_lambda, slot, scratch);
 }
 
 // Elements of an n-point transform's set handled by each thread in the copy

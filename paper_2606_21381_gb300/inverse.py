@@ -9,8 +9,9 @@ taken through a low-pass filter whose cut-off rises from a small numerical
 aperture to the objective's over the first part of the run; both the model
 and the target images pass through the same filter.
 
-The render and its gradient run in libosog; the loss, the filter and Adam
-are plain torch on the device.
+The render, its gradient and the image losses with their gradients run in
+libosog's kernels; Adam and the curriculum schedule are plain torch on the
+device.
 """
 from __future__ import annotations
 
@@ -63,58 +64,65 @@ class SolveResult:
     history: list = field(default_factory=list)
 
 
-def lowpass_mask(H: int, W: int, dx: float, lam: float, na: float, device) -> torch.Tensor:
-    """rfft2 mask keeping spatial frequencies below 2 NA / lambda (the
-    intensity band of a coherent image through a pupil of that NA)."""
-    fy = torch.fft.fftfreq(H, dx, device=device)[:, None]
-    fx = torch.fft.rfftfreq(W, dx, device=device)[None, :]
-    return ((fx * fx + fy * fy) <= (2.0 * na / lam) ** 2).float()
+class ImageLoss:
+    """The solve's loss of images against the target, on the GPU
+    (osog_image_loss): the squared misfit of the images low-passed at the
+    curriculum's cut-off, summed over pixels and divided by the target's
+    pixel count, plus spectral_weight times the log-amplitude spectral loss
+    of Eq. 8.  The target's spectra are computed once; the cut-off
+    (cycles/um) is a device scalar that the step updates in place, so the
+    step stays capturable as a CUDA graph.  __call__ returns the device
+    loss (2,) = [misfit, spectral] and dL/dimage, both in buffers of this
+    object (overwritten by the next call)."""
+
+    def __init__(self, renderer: Renderer, target: torch.Tensor, dx: float,
+                 spectral_weight: float = 0.0, eps_rel: float = 1e-4):
+        self.r = renderer
+        self.target = target.contiguous()
+        self.dx = float(dx)
+        self.spectral_weight = float(spectral_weight)
+        self.eps_rel = float(eps_rel)
+        self.scale = 1.0 / float(target.numel())
+        self.table = renderer.loss_target(self.target)
+        dev = renderer.device
+        self.cutoff = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.loss = torch.empty(2, dtype=torch.float32, device=dev)
+        self.grad = torch.empty_like(self.target)
+
+    def __call__(self, img: torch.Tensor):
+        return self.r.image_loss(img.contiguous(), self.table, self.dx, self.cutoff,
+                                 misfit_scale=self.scale, spectral_weight=self.spectral_weight,
+                                 eps_rel=self.eps_rel, loss=self.loss, grad=self.grad)
+
+    def total(self) -> torch.Tensor:
+        """misfit + spectral_weight * spectral of the last call (device scalar)."""
+        return self.loss[0] + self.spectral_weight * self.loss[1]
 
 
-def filtered(img: torch.Tensor, mask: torch.Tensor) -> torch.Tensor:
-    return torch.fft.irfft2(torch.fft.rfft2(img) * mask, s=img.shape[-2:])
+class _ImageLossFunction(torch.autograd.Function):
+    """ImageLoss as a differentiable function of the image (autograd mode)."""
+
+    @staticmethod
+    def forward(ctx, img, loss_fn: ImageLoss):
+        loss, grad = loss_fn(img)
+        ctx.save_for_backward(grad.clone())
+        return loss_fn.total().clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return grad * g, None
 
 
-class SpectralMisfit:
-    """sum((filtered(img) - filtered(target))^2) / norm for the low-pass
-    masks of the curriculum, evaluated in the frequency domain (Parseval):
-    (1 / (H W norm)) sum over the rfft half-plane of w_k m_k |F(img)_k -
-    F(target)_k|^2, with w = 1 on the columns 0 and W/2 (their own
-    conjugates) and 2 elsewhere.  The target's spectrum and the squared
-    radii of the grid are computed once."""
-
-    def __init__(self, target: torch.Tensor, dx: float, norm: float):
-        H, W = target.shape[-2:]
-        dev = target.device
-        fy = torch.fft.fftfreq(H, dx, device=dev, dtype=torch.float64)[:, None]
-        fx = torch.fft.rfftfreq(W, dx, device=dev, dtype=torch.float64)[None, :]
-        self.r2 = fx * fx + fy * fy
-        w = torch.full((W // 2 + 1,), 2.0, device=dev, dtype=torch.float64)
-        w[0] = 1.0
-        if W % 2 == 0:
-            w[-1] = 1.0
-        self.w = w[None, :]
-        self.ft = torch.fft.rfft2(target)
-        self.scale = 1.0 / (H * W * norm)
-
-    def __call__(self, img: torch.Tensor, cutoff: float) -> torch.Tensor:
-        m = torch.where(self.r2 <= cutoff * cutoff, self.w, torch.zeros_like(self.w)).float()
-        d = torch.fft.rfft2(img) - self.ft
-        return (m * (d.real * d.real + d.imag * d.imag)).sum() * self.scale
-
-
-def spectral_loss(img: torch.Tensor, target: torch.Tensor, eps_rel: float = 1e-6) -> torch.Tensor:
-    """Eq. 8: squared difference of the log amplitude spectra of the images
-    (mean over the (K, H, W) frequencies).  The guard eps added inside the
-    logarithms is eps_rel times the largest target amplitude of each
-    modality, so frequencies where both spectra are only rounding noise
-    (beyond the band the pupil passes) do not dominate.  Invariant to
-    circular shifts of either image."""
-    fb = torch.abs(torch.fft.fft2(target)).detach()
-    eps = eps_rel * fb.amax(dim=(-2, -1), keepdim=True)
-    a = torch.log(torch.abs(torch.fft.fft2(img)) + eps)
-    b = torch.log(fb + eps)
-    return ((a - b) ** 2).mean()
+def spectral_loss(img: torch.Tensor, target: torch.Tensor, renderer: Renderer,
+                  eps_rel: float = 1e-4) -> torch.Tensor:
+    """Eq. 8 of (K, H, W) images against a target on the GPU: the mean over
+    frequencies of (log(|F(img)| + e) - log(|F(target)| + e))^2 with e =
+    eps_rel times the target's largest amplitude per image (device scalar)."""
+    fn = ImageLoss(renderer, target, 1.0, spectral_weight=1.0, eps_rel=eps_rel)
+    loss, _ = renderer.image_loss(img.contiguous(), fn.table, 1.0, None, spectral_weight=1.0,
+                                  eps_rel=eps_rel, want_grad=False)
+    return loss[1]
 
 
 def perturb(soa: np.ndarray, optics: dict, rng: np.random.Generator, frac: float = 0.2):
@@ -176,7 +184,7 @@ class _DeviceStep:
         self.t = torch.zeros((), dtype=torch.float32, device=dev)
         self.losses = torch.zeros(max(cfg.steps, 1), dtype=torch.float32, device=dev)
         K, H, W = target.shape
-        self.misfit = SpectralMisfit(target, optics0["dx"], float(target.numel()))
+        self.loss_fn = ImageLoss(renderer, target, optics0["dx"], cfg.spectral_weight)
         self.ramp = float(max(1, int(cfg.steps * cfg.curriculum_frac)))
         self.img = torch.empty((K, H, W), dtype=torch.float32, device=dev)
         self.ws = torch.empty(renderer.backward_workspace_size(self.x.shape[1], K),
@@ -186,15 +194,11 @@ class _DeviceStep:
         cfg, o = self.cfg, self.o
         b1, b2 = cfg.betas
         na = cfg.na_start + (o["NA"] - cfg.na_start) * torch.clamp(self.t / self.ramp, max=1.0)
-        cutoff = 2.0 * na / o["lambda_um"]
+        self.loss_fn.cutoff.copy_((2.0 / o["lambda_um"]) * na)
         self.r.render_keep(self.x, None, o, out=self.img, ws=self.ws)
-        img = self.img.detach().requires_grad_(True)
-        with torch.enable_grad():
-            loss = self.misfit(img, cutoff)
-            if cfg.spectral_weight:
-                loss = loss + cfg.spectral_weight * spectral_loss(img, self.target)
-            (g_img,) = torch.autograd.grad(loss, img)
-        gx, gp = self.r.backward_kept(self.x, None, o, g_img.contiguous(), self.ws)
+        _, g_img = self.loss_fn(self.img)
+        loss = self.loss_fn.total()
+        gx, gp = self.r.backward_kept(self.x, None, o, g_img, self.ws)
         t1 = self.t + 1.0
         c1, c2 = 1.0 - torch.pow(b1, t1), 1.0 - torch.pow(b2, t1)
         self.m1.mul_(b1).add_(gx, alpha=1 - b1)
@@ -282,8 +286,6 @@ def solve(target: torch.Tensor, soa0: np.ndarray, optics0: dict, renderer: Rende
     m1, m2 = torch.zeros_like(soa), torch.zeros_like(soa)
     p1, p2 = torch.zeros_like(params), torch.zeros_like(params)
     b1, b2 = cfg.betas
-    H, W = target.shape[-2:]
-    norm = float(target.numel())
     res = SolveResult(soa=None, optics_params=None)
     truth_d = None
     if truth is not None and cfg.record_every:
@@ -293,13 +295,12 @@ def solve(target: torch.Tensor, soa0: np.ndarray, optics0: dict, renderer: Rende
     if truth_d is not None:
         res.history.append((0, 0.0, *_device_errors(x.detach(), truth_d).tolist()))
     ramp = max(1, int(cfg.steps * cfg.curriculum_frac))
-    misfit = SpectralMisfit(target, optics0["dx"], norm)
+    loss_fn = ImageLoss(renderer, target, optics0["dx"], cfg.spectral_weight)
     for it in range(cfg.steps):
         na = cfg.na_start + (optics0["NA"] - cfg.na_start) * min(1.0, it / ramp)
         img = render(x, optics0, renderer, params)
-        loss = misfit(img, 2.0 * na / optics0["lambda_um"])
-        if cfg.spectral_weight:
-            loss = loss + cfg.spectral_weight * spectral_loss(img, target)
+        loss_fn.cutoff.fill_(2.0 * na / optics0["lambda_um"])
+        loss = _ImageLossFunction.apply(img, loss_fn)
         gx, gp = torch.autograd.grad(loss, (x, params), allow_unused=True)
         with torch.no_grad():
             t = it + 1

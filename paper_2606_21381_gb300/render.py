@@ -249,6 +249,7 @@ class Renderer:
             t.band_rows = int(tuning.get("band_rows", 0))
             t.wait_polls = int(tuning.get("wait_polls", 0))
             t.test_wait_extra = int(tuning.get("test_wait_extra", 0))
+            t.raster = int(tuning.get("raster", 0))
         need = self.workspace_size(n_total, K, S)
         if t.pairs_per_particle > 8:
             need = int(need * t.pairs_per_particle / 8) + (1 << 20)
@@ -279,7 +280,7 @@ class Renderer:
             offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), S, arr, _ptr(out),
             _ptr(ws), ws.numel(), _stream(stream), ctypes.byref(t)), "osog_autotune")
         return {"pairs_per_particle": t.pairs_per_particle, "use_graph": t.use_graph,
-                "persistent": t.persistent, "band_rows": t.band_rows}
+                "persistent": t.persistent, "band_rows": t.band_rows, "raster": t.raster}
 
     def render_host(self, soa_host: torch.Tensor, n: int, optics: dict,
                     image_host: torch.Tensor, stream=None):

@@ -127,3 +127,19 @@ def test_bound_optics_scalars_in_the_batched_path():
     assert torch.equal(got[1], got[2]) and torch.equal(got[0], got[1])
     assert torch.equal(back, own)
     assert float((own - want).abs().max()) > 1e-3 * scale
+
+
+def test_tile_raster_and_strip_raster_agree_bitwise():
+    # the raster's phase and absorption words are integer sums, so the tile
+    # kernel and the strip pass compose bitwise the same exit waves
+    for size, modes, S in ((512, 1, 3), (256, 3, 5)):
+        soas, optics, dev, offs = batch(40 + size, S, size, modes, 200, 3000)
+        r = renderer(size, size)
+        fused = r.batch(dev, offs, optics, tuning={"use_graph": 0, "raster": -1}).clone()
+        tiles = r.batch(dev, offs, optics, tuning={"use_graph": 0, "raster": 1}).clone()
+        graph = r.batch(dev, offs, optics, tuning={"raster": 1}).clone()
+        assert r.sync_status() == 0
+        assert torch.equal(fused, tiles) and torch.equal(fused, graph)
+        s = S - 1
+        ref = oracle.render(soas[s], soas[s].shape[1], oracle.make_optics(**optics[s]))["images"]
+        assert np.abs(tiles[s].cpu().numpy().astype(np.float64) - ref).max() <= 2e-4

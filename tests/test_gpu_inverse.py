@@ -49,8 +49,8 @@ def test_solve_with_the_spectral_loss_term():
     assert res.losses[-1] < 1e-2 * res.losses[0]
     x0 = torch.from_numpy(s0).cuda()
     x1 = torch.from_numpy(res.soa).cuda()
-    assert float(inverse.spectral_loss(r.render(x1, None, o), target)) < \
-        0.1 * float(inverse.spectral_loss(r.render(x0, None, o0), target))
+    assert float(inverse.spectral_loss(r.render(x1, None, o), target, r)) < \
+        0.1 * float(inverse.spectral_loss(r.render(x0, None, o0), target, r))
 
 
 def _scene_and_guess(seed):
