@@ -116,7 +116,8 @@ typedef struct {
  * Tuning of the batched path (osog_batch_submit).  Zero fields take the
  * value osog_autotune stored in the plan for this batch shape, else the
  * default.
- *   pairs_per_particle  particle-band pairs reserved per particle (default 8)
+ *   pairs_per_particle  particle-band pairs reserved per particle (default: the
+ *                       plan's, see osog_plan_set_pairs_per_particle)
  *   use_graph           1: replay the launch sequence as a CUDA graph that the
  *                       plan caches per batch shape; 0 (or -1): launch directly
  *   persistent          1: the three render stages of each group of up to 32
@@ -342,6 +343,28 @@ int osog_render_backward_kept(osog_plan_t *plan, const float *soa, int64_t ld, i
 int osog_plan_bind_optics_params(osog_plan_t *plan, const float *params_dev);
 
 /*
+ * Particle-band pairs reserved per particle (default 8) by this plan's
+ * single-scene calls (osog_render, osog_render_opd, osog_render_keep, the
+ * adjoint, the polyhedra and incoherent-DIC renders), by the batched path
+ * when its tuning leaves pairs_per_particle at 0, and by every workspace-size
+ * query of the plan; query the workspace size after setting it.  A particle
+ * whose bounding rectangle meets more bands than reserved latches
+ * OSOG_ERR_BIN_OVERFLOW.  Drops the plan's kept forward states.
+ * OSOG_ERR_INVALID_ARG unless 1 <= pairs_per_particle <= 64.
+ */
+int osog_plan_set_pairs_per_particle(osog_plan_t *plan, int32_t pairs_per_particle);
+
+/*
+ * The reservation that a scene needs when no particle's bounding rectangle
+ * reaches further than max_half_extent_px from its centre along y (a + b is
+ * a bound for every kind: the half-height of an ellipse or of a rotated
+ * rectangle with half-lengths a, b, and the radius a of a polyhedron),
+ * given the plan's band height; 0 for a negative or non-finite extent.
+ */
+int32_t osog_pairs_for_extent(const osog_plan_t *plan, double max_half_extent_px);
+
+/*
+ * Batched forward render of S scenes that share the plan's H x W and the/*
  * Batched forward render of S scenes that share the plan's H x W and the
  * same modality bits (per-scene optics may otherwise differ).
  *   soa_all  device float32 [9][ld]; scene s owns columns

@@ -31,7 +31,7 @@ EXPORTS = ("osog_plan_create", "osog_plan_destroy", "osog_workspace_size", "osog
            "osog_dic_incoherent_workspace_size", "osog_render_dic_incoherent",
            "osog_sensor_noise", "osog_plan_bind_optics_params",
            "osog_loss_table_size", "osog_loss_workspace_size", "osog_loss_target",
-           "osog_image_loss")
+           "osog_image_loss", "osog_plan_set_pairs_per_particle", "osog_pairs_for_extent")
 
 
 class OsogError(RuntimeError):
@@ -188,6 +188,10 @@ def lib(build_if_missing: bool = True):
     L.osog_loss_target.restype = ctypes.c_int
     L.osog_image_loss.argtypes = [vp, vp, i32, vp, sz, P(LossParams), vp, vp, vp, sz, vp]
     L.osog_image_loss.restype = ctypes.c_int
+    L.osog_plan_set_pairs_per_particle.argtypes = [vp, i32]
+    L.osog_plan_set_pairs_per_particle.restype = ctypes.c_int
+    L.osog_pairs_for_extent.argtypes = [vp, ctypes.c_double]
+    L.osog_pairs_for_extent.restype = i32
     _lib = L
     return L
 

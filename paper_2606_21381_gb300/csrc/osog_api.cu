@@ -51,6 +51,9 @@ struct osog_plan {
     std::mutex kept_lock;  // autograd may run the adjoint on a thread of its own
     // device array of the four differentiable optics scalars, or null
     const float *optics_dyn = nullptr;
+    // particle-band pairs reserved per particle by single-scene calls and by
+    // the workspace queries (osog_plan_set_pairs_per_particle)
+    int ppp = 8;
 };
 
 namespace {
@@ -205,7 +208,7 @@ int raster_and_strip(osog_plan *p, StripArgs &sa, cudaStream_t st, bool tiles = 
 
 // Per-call choices of the batched path (see osog_tuning_t).
 struct GroupOpts {
-    int ppp = kDefaultPairs;
+    int ppp = kDefaultPairs;  // replaced by the plan's reservation
     bool persistent = false;
     int band_rows = 0;
     int wait_polls = 0;       // persistent launch: 0 = the default limit
@@ -405,7 +408,7 @@ int bwd_setup(osog_plan *p, const float *soa, int64_t ld, int32_t n, const osog_
     if (n > 0 && !soa) return fail(OSOG_ERR_INVALID_ARG, "soa is NULL");
     b.K = popcount3(optics->modes);
     b.chunks = (n + kChunk - 1) / kChunk;
-    const int ppp = kDefaultPairs;
+    const int ppp = p->ppp;
     b.bl = make_bwd_layout(p->geo, n, b.chunks, b.K, ppp);
     rc = check_ws(ws, b.bl.total, ws_bytes);
     if (rc) return rc;
@@ -543,6 +546,12 @@ bool same_optics(const osog_optics_t &a, const osog_optics_t &b) {
            a.bevel_slope == b.bevel_slope;
 }
 
+// Drop every kept forward state of the plan.
+void forget_all_kept(osog_plan *p) {
+    std::lock_guard<std::mutex> guard(p->kept_lock);
+    p->kept.clear();
+}
+
 // Drop the forward states that osog_render_keep left in workspace ws (any
 // other call that writes ws invalidates them).
 void forget_kept(osog_plan *p, const void *ws) {
@@ -600,7 +609,7 @@ void osog_plan_destroy(osog_plan_t *p) {
 
 size_t osog_workspace_size(const osog_plan_t *p, int32_t n_max, int32_t K, int32_t batch) {
     if (!p || n_max < 0 || K < 0 || K > 3 || batch < 1) return 0;
-    return ws_need(p, n_max, K, batch, kDefaultPairs);
+    return ws_need(p, n_max, K, batch, p->ppp);
 }
 
 static int render_stage(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
@@ -618,9 +627,11 @@ static int render_stage(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
     if (stage != kOpdOnly && !image) return fail(OSOG_ERR_INVALID_ARG, "image is NULL");
     const int K = popcount3(optics->modes);
     const int nn = stage == kFromMap ? 0 : n;
-    rc = check_ws(ws, ws_need(p, nn, stage == kOpdOnly ? 0 : K, 1, kDefaultPairs), ws_bytes);
+    rc = check_ws(ws, ws_need(p, nn, stage == kOpdOnly ? 0 : K, 1, p->ppp), ws_bytes);
     if (rc) return rc;
-    return enqueue_group(p, soa, ld, &nn, 1, optics, K, GroupOpts{}, ws, ws_bytes, image,
+    GroupOpts o;
+    o.ppp = p->ppp;
+    return enqueue_group(p, soa, ld, &nn, 1, optics, K, o, ws, ws_bytes, image,
                          opd_att, opd_out, stage, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -633,7 +644,7 @@ int osog_render(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
 size_t osog_polyhedra_workspace_size(const osog_plan_t *p, int32_t n_max, int32_t K,
                                      int32_t n_planes) {
     if (!p || n_max < 0 || K < 1 || K > 3 || n_planes < 0) return 0;
-    return align256(ws_need(p, n_max, K, 1, kDefaultPairs)) + (size_t)n_planes * sizeof(float4);
+    return align256(ws_need(p, n_max, K, 1, p->ppp)) + (size_t)n_planes * sizeof(float4);
 }
 
 int osog_render_polyhedra(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
@@ -655,6 +666,7 @@ int osog_render_polyhedra(osog_plan_t *p, const float *soa, int64_t ld, int32_t 
     rc = check_ws(ws, osog_polyhedra_workspace_size(p, n, K, n_planes), ws_bytes);
     if (rc) return rc;
     GroupOpts o;
+    o.ppp = p->ppp;
     o.planes = reinterpret_cast<const float4 *>(planes);
     o.plane_off = plane_offsets;
     o.n_planes = n_planes;
@@ -670,9 +682,9 @@ struct DicLayout {
     size_t img, otf, total;
 };
 
-DicLayout dic_layout(const Geometry &geo, int64_t n) {
+DicLayout dic_layout(const Geometry &geo, int64_t n, int ppp) {
     DicLayout d;
-    d.l = make_layout(geo, n, (n + kChunk - 1) / kChunk + 1, 1, 1, n * kDefaultPairs);
+    d.l = make_layout(geo, n, (n + kChunk - 1) / kChunk + 1, 1, 1, n * ppp);
     size_t o = d.l.total;
     d.img = o;
     o = align256(o + (size_t)geo.H * geo.W * sizeof(float));
@@ -684,7 +696,7 @@ DicLayout dic_layout(const Geometry &geo, int64_t n) {
 
 size_t osog_dic_incoherent_workspace_size(const osog_plan_t *p, int32_t n_max) {
     if (!p || n_max < 0) return 0;
-    return dic_layout(p->geo, n_max).total;
+    return dic_layout(p->geo, n_max, p->ppp).total;
 }
 
 int osog_render_dic_incoherent(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
@@ -698,7 +710,7 @@ int osog_render_dic_incoherent(osog_plan_t *p, const float *soa, int64_t ld, int
     if (n > 0 && !soa) return fail(OSOG_ERR_INVALID_ARG, "soa is NULL");
     if (!image) return fail(OSOG_ERR_INVALID_ARG, "image is NULL");
     const Geometry &geo = p->geo;
-    const DicLayout dl = dic_layout(geo, n);
+    const DicLayout dl = dic_layout(geo, n, p->ppp);
     rc = check_ws(ws, dl.total, ws_bytes);
     if (rc) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -768,7 +780,7 @@ int osog_render_dic_incoherent(osog_plan_t *p, const float *soa, int64_t ld, int
     const int64_t chunks = (n + kChunk - 1) / kChunk;
     gd.nchunks = (int32_t)chunks;
     gd.sc[0].n = n;
-    gd.sc[0].pair_cap = (int32_t)((int64_t)n * kDefaultPairs);
+    gd.sc[0].pair_cap = (int32_t)((int64_t)n * p->ppp);
     if ((rc = run_kernel(p, OSOG_KERNEL_BIN_COUNT, st,
                          [&] { return launch_bin_count(soa, ld, gd, geo, w, st); })))
         return rc;
@@ -857,6 +869,7 @@ int osog_batch_submit(osog_plan_t *p, const float *soa_all, int64_t ld, const in
     // Options: explicit tuning fields first, then the autotuned values for
     // this batch shape, then the defaults.
     GroupOpts opt;
+    opt.ppp = p->ppp;
     for (const auto &t : p->tuned)
         if (t.S == S && t.n == n_total && t.K == K) {
             opt.ppp = t.ppp;
@@ -946,7 +959,7 @@ int osog_batch_submit(osog_plan_t *p, const float *soa_all, int64_t ld, const in
 
 size_t osog_backward_workspace_size(const osog_plan_t *p, int32_t n_max, int32_t K) {
     if (!p || n_max < 0 || K < 1 || K > 3) return 0;
-    return make_bwd_layout(p->geo, n_max, (n_max + kChunk - 1) / kChunk + 1, K, kDefaultPairs).total;
+    return make_bwd_layout(p->geo, n_max, (n_max + kChunk - 1) / kChunk + 1, K, p->ppp).total;
 }
 
 int osog_render_backward(osog_plan_t *p, const float *soa, int64_t ld, int32_t n,
@@ -1216,6 +1229,23 @@ int osog_image_loss(osog_plan_t *p, const float *image, int32_t K, const void *t
     if (rc) return rc;
     cudaError_t e = launch_loss_reduce(L.part, (int64_t)K * p->geo.nblocks, loss, st);
     return e == cudaSuccess ? OSOG_OK : cuda_fail(e, "osog_image_loss");
+}
+
+int osog_plan_set_pairs_per_particle(osog_plan_t *p, int32_t pairs_per_particle) {
+    if (!p) return fail(OSOG_ERR_INVALID_ARG, "plan is NULL");
+    if (pairs_per_particle < 1 || pairs_per_particle > kMaxBands)
+        return fail(OSOG_ERR_INVALID_ARG, "pairs_per_particle must be in 1..64");
+    forget_all_kept(p);  // a kept state's layout depends on the reservation
+    p->ppp = pairs_per_particle;
+    return OSOG_OK;
+}
+
+int32_t osog_pairs_for_extent(const osog_plan_t *p, double max_half_extent_px) {
+    if (!p || !(max_half_extent_px >= 0.0) || !isfinite(max_half_extent_px)) return 0;
+    // a bounding rectangle spans at most 2 h + 4 rows (widened for rounding),
+    // which meet at most floor((2 h + 3) / BH) + 2 bands of BH rows
+    const double bands = floor((2.0 * max_half_extent_px + 3.0) / p->geo.BH) + 2.0;
+    return (int32_t)(bands < p->geo.nbands ? bands : p->geo.nbands);
 }
 
 int osog_plan_bind_optics_params(osog_plan_t *p, const float *params_dev) {

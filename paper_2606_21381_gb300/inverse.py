@@ -50,6 +50,29 @@ class SolveConfig:
     # scalars on the host (one device-to-host read per step)
     mode: str = "graph"
     warmup_steps: int = 3            # eager steps before the graph is captured
+    # device modes: every checkpoint_every steps the solve state is handed to
+    # on_checkpoint(state) (see SolveState; 0 = never)
+    checkpoint_every: int = 0
+
+
+@dataclass
+class SolveState:
+    """Everything the device-resident solve carries from one step to the
+    next, as host tensors: the particle tensor, the four optics scalars,
+    Adam's moments of both, the step counter (which also sets the
+    curriculum's cut-off) and the losses so far.  solve(..., resume=state)
+    continues from it bit for bit (same configuration, target and renderer
+    size)."""
+    step: int
+    tensors: dict
+
+    def save(self, path: str) -> None:
+        torch.save({"step": self.step, "tensors": self.tensors}, path)
+
+    @staticmethod
+    def load(path: str) -> "SolveState":
+        d = torch.load(path, map_location="cpu")
+        return SolveState(step=int(d["step"]), tensors=d["tensors"])
 
 
 @dataclass
@@ -190,6 +213,21 @@ class _DeviceStep:
         self.ws = torch.empty(renderer.backward_workspace_size(self.x.shape[1], K),
                               dtype=torch.uint8, device=dev)
 
+    _STATE = ("x", "params", "m1", "m2", "p1", "p2", "t", "losses")
+
+    def state(self) -> SolveState:
+        """A copy of the step's state on the host (synchronises)."""
+        return SolveState(step=int(self.t.item()),
+                          tensors={k: getattr(self, k).detach().cpu().clone() for k in self._STATE})
+
+    def load_state(self, st: SolveState) -> None:
+        """Restore a state in place (the buffers a captured graph refers to)."""
+        for k in self._STATE:
+            dst, src = getattr(self, k), st.tensors[k]
+            if dst.shape != src.shape or dst.dtype != src.dtype:
+                raise ValueError(f"solve state field {k} does not match this solve")
+            dst.copy_(src.to(dst.device))
+
     def __call__(self) -> None:
         cfg, o = self.cfg, self.o
         b1, b2 = cfg.betas
@@ -213,9 +251,16 @@ class _DeviceStep:
         self.t.copy_(t1)
 
 
-def _solve_device(target, soa0, optics0, renderer, cfg, fixed_optics, truth) -> SolveResult:
+def _solve_device(target, soa0, optics0, renderer, cfg, fixed_optics, truth, resume,
+                  on_checkpoint) -> SolveResult:
     dev = renderer.device
     st = _DeviceStep(target, soa0, optics0, renderer, cfg, fixed_optics)
+    first = 0
+    if resume is not None:
+        st.load_state(resume)
+        first = resume.step
+        if not 0 <= first <= cfg.steps:
+            raise ValueError("the resumed state's step lies outside this configuration's steps")
     res = SolveResult(soa=None, optics_params=None)
     truth_d = None
     if truth is not None and cfg.record_every:
@@ -233,8 +278,8 @@ def _solve_device(target, soa0, optics0, renderer, cfg, fixed_optics, truth) -> 
             # must exist before a graph can record them)
             eager = cfg.steps if cfg.mode == "device" else min(max(cfg.warmup_steps, 1), cfg.steps)
             graph = None
-            for it in range(cfg.steps):
-                if it < eager:
+            for it in range(first, cfg.steps):
+                if it < first + eager:
                     st()
                 else:
                     if graph is None:
@@ -245,6 +290,9 @@ def _solve_device(target, soa0, optics0, renderer, cfg, fixed_optics, truth) -> 
                 if truth_d is not None and (it + 1) % cfg.record_every == 0:
                     e = _device_errors(st.x, truth_d).tolist()
                     res.history.append((it + 1, time.perf_counter() - t0, *e))
+                if on_checkpoint is not None and cfg.checkpoint_every and \
+                        (it + 1) % cfg.checkpoint_every == 0:
+                    on_checkpoint(st.state())
             torch.cuda.synchronize(dev)
             res.seconds = time.perf_counter() - t0
     finally:
@@ -259,15 +307,22 @@ def _solve_device(target, soa0, optics0, renderer, cfg, fixed_optics, truth) -> 
 
 def solve(target: torch.Tensor, soa0: np.ndarray, optics0: dict, renderer: Renderer,
           cfg: SolveConfig | None = None, fixed_optics: bool = False,
-          truth: np.ndarray | None = None) -> SolveResult:
+          truth: np.ndarray | None = None, resume: SolveState | None = None,
+          on_checkpoint=None) -> SolveResult:
     """Adam on the curriculum-filtered squared image misfit.  target is the
     (K, H, W) measured image; soa0 / optics0 the initial guess.  With the
     true particle tensor and cfg.record_every > 0 the error history is
     recorded (the clock keeps running across the records).  cfg.mode picks
-    the device-resident step (CUDA graph or eager) or the autograd loop."""
+    the device-resident step (CUDA graph or eager) or the autograd loop.
+    In the device modes, on_checkpoint(state) receives a SolveState every
+    cfg.checkpoint_every steps, and resume=state continues a solve from one
+    (the same cfg, target, guess and renderer size)."""
     cfg = cfg or SolveConfig()
     if cfg.mode in ("graph", "device"):
-        return _solve_device(target, soa0, optics0, renderer, cfg, fixed_optics, truth)
+        return _solve_device(target, soa0, optics0, renderer, cfg, fixed_optics, truth, resume,
+                             on_checkpoint)
+    if resume is not None or on_checkpoint is not None:
+        raise ValueError("checkpoints are taken in the device modes ('graph', 'device')")
     if cfg.mode != "autograd":
         raise ValueError("SolveConfig.mode must be 'graph', 'device' or 'autograd'")
     dev = renderer.device

@@ -303,6 +303,23 @@ class Renderer:
               "osog_plan_bind_optics_params")
         self._bound_params = params
 
+    # ------------------------------------------------------------ bin reservation
+    def set_pairs_per_particle(self, k: int) -> None:
+        """osog_plan_set_pairs_per_particle: particle-band pairs reserved per
+        particle by this renderer's calls (default 8)."""
+        check(self._L.osog_plan_set_pairs_per_particle(self.plan, int(k)),
+              "osog_plan_set_pairs_per_particle")
+
+    def fit_pairs(self, soa: torch.Tensor, n: int | None = None) -> int:
+        """Size the reservation for a particle tensor from its largest
+        half-extent a + b (one device-to-host read); returns it."""
+        self._check_soa(soa)
+        n = soa.shape[1] if n is None else int(n)
+        hh = float((soa[3, :n] + soa[4, :n]).max()) if n > 0 else 0.0
+        k = max(1, int(self._L.osog_pairs_for_extent(self.plan, hh)))
+        self.set_pairs_per_particle(k)
+        return k
+
     # ------------------------------------------------------------ image losses
     def loss_target(self, target: torch.Tensor, stream=None) -> torch.Tensor:
         """osog_loss_target: the device table of the (K, H, W) target images'

@@ -143,3 +143,30 @@ def test_graphed_solve_with_fixed_optics():
     assert res.losses[-1] < 1e-2 * res.losses[0]
     e = inverse.errors(res.soa, soa)
     assert e["dn_rel_median"] < 0.01
+
+
+def test_resumed_solve_equals_an_uninterrupted_one(tmp_path):
+    """A solve checkpointed halfway (saved to disk and loaded back) and
+    resumed ends bitwise where the uninterrupted solve ends: the state holds
+    everything the step carries (particles, optics scalars, Adam moments,
+    the step counter that drives the curriculum, the losses)."""
+    from paper_2606_21381_gb300 import inverse
+    from paper_2606_21381_gb300.render import Renderer
+    rng = np.random.default_rng(17)
+    soa = scenes.draw_particles(rng, 40, 256, 256, mu=(0.005, 0.02))
+    o = scenes.optics(256, 256, modes=5, defocus=0.6, NA=0.45)
+    r = Renderer(256, 256)
+    target = r.render(torch.from_numpy(soa).cuda(), None, o)
+    s0, o0 = inverse.perturb(soa, o, rng)
+    cfg = inverse.SolveConfig(steps=40, checkpoint_every=20)
+    saved = []
+    full = inverse.solve(target, s0, o0, r, cfg, on_checkpoint=saved.append)
+    assert [s.step for s in saved] == [20, 40]
+    path = str(tmp_path / "solve_state.pt")
+    saved[0].save(path)
+    resumed = inverse.solve(target, s0, o0, r, cfg, resume=inverse.SolveState.load(path))
+    assert r.sync_status() == 0
+    assert np.array_equal(full.soa, resumed.soa)
+    assert np.array_equal(full.optics_params, resumed.optics_params)
+    assert full.losses == resumed.losses
+    assert not np.array_equal(full.soa, s0)  # the solve did move

@@ -205,7 +205,8 @@ def test_particles_off_canvas_and_single_pixel():
 def test_large_particle_spanning_the_canvas():
     """A particle spanning all 64 bands of a 1024^2 canvas overflows the
     default reservation of 8 pairs per particle (reported, not a fault); a
-    larger reservation renders it exactly."""
+    larger reservation, set for the batch or sized for the plan from the
+    particles' extent, renders it exactly."""
     soa = np.zeros((9, 2), np.float32)
     soa[:, 0] = [512, 512, 0.2, 600, 350, 1.0, 0.02, 0.001, 0]
     soa[:, 1] = [400, 560, 0.7, 60, 20, 2.0, 0.03, 0.0, 1]
@@ -219,6 +220,15 @@ def test_large_particle_spanning_the_canvas():
     assert r.sync_status() == 0
     ref = oracle.render(soa, 2, oracle.make_optics(**o))["images"]
     assert_images_close(got.astype(np.float64), ref, o)
+    # the single-scene call sized from the particles' extent renders it too
+    try:
+        k = r.fit_pairs(torch.from_numpy(soa).cuda())
+        assert 8 < k <= 64
+        got = r.render(torch.from_numpy(soa).cuda(), None, o).cpu().numpy()
+        assert r.sync_status() == 0
+        assert_images_close(got.astype(np.float64), ref, o)
+    finally:
+        r.set_pairs_per_particle(8)
 
 
 def test_invalid_particles_are_reported_and_skipped():
