@@ -129,15 +129,20 @@ typedef struct {
  *                       gives at most 64 bands (R = 8192 / W rows for
  *                       W >= 1024, 4 for 128 <= W <= 512, 512 / W below);
  *                       0 = the default max(H / 64, 16, R)
- *   wait_polls          persistent launch: polls (about 0.1 us apart) before a
- *                       wait for another stage's work gives up and latches
- *                       OSOG_ERR_TIMEOUT (0 = 2^24); after one wait has given
- *                       up the launch's later waits return at once, so it
- *                       always ends
- *   test_wait_extra     failure-detection test: raises the number of finished
- *                       strips each column item of the persistent launch waits
- *                       for by this many, so its waits run out (0 = off); the
- *                       images of such a launch are invalid
+ *   wait_polls          polls before a bounded device wait gives up and
+ *                       latches OSOG_ERR_TIMEOUT: in the persistent launch the
+ *                       wait for another stage's work (about 0.1 us apart,
+ *                       0 = 2^24; after one wait has given up the launch's
+ *                       later waits return at once), in the column pass of a
+ *                       square canvas of 1024 or more the wait for the bulk
+ *                       copy of its column block (0 = 2^20); the launch always
+ *                       ends
+ *   test_wait_extra     failure-detection test (0 = off): raises the number of
+ *                       finished strips each column item of the persistent
+ *                       launch waits for by this many, and makes the column
+ *                       pass's bulk-copy barrier expect 16 bytes more than its
+ *                       copy delivers, so those waits run out; the images of
+ *                       such a launch are invalid
  *   raster              1: rasterise in a kernel of its own over tiles of one
  *                       band by a few hundred columns, handing the per-pixel
  *                       phase and absorption words to the strip pass through

@@ -319,6 +319,8 @@ int enqueue_group(osog_plan *p, const float *soa, int64_t ld, const int32_t *cou
     ca.K = K;
     for (int s = 0; s < S; ++s)
         for (int k = 0; k < K; ++k) ca.md[s][k] = gd.md[s][k];
+    ca.wait_polls = opt.wait_polls;
+    ca.wait_extra = opt.wait_extra;
     InverseArgs ia{};
     ia.geo = geo;
     ia.w = w;

@@ -44,6 +44,9 @@ struct ColumnArgs {
     const float2 *tw;        // H-point twiddles
     int32_t S, K;
     int32_t unit_input;      // 1: the column spectrum is 1 everywhere (no G read, no DFT)
+    int32_t wait_polls;      // bulk-copy wait: polls before it gives up (0: the default)
+    int32_t wait_extra;      // failure-detection test: the bulk-copy barrier expects 16
+                             // bytes more than arrive, so its wait runs out
     LossDev loss;            // kOpLoss parameters
     ModeDev md[kMaxScenes][kMaxModes];
 };

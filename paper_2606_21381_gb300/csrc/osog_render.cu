@@ -244,8 +244,81 @@ __device__ __forceinline__ void loss_columns(const ColumnArgs &a, int s, int bk,
     }
 }
 
+// ------------------------------------------------------------ bulk copies
+// A contiguous global -> shared copy made by the TMA unit (cp.async.bulk),
+// completing on an mbarrier of the CTA: both addresses 16-byte aligned, the
+// size a multiple of 16.  The CTA's threads wait on the barrier with a
+// bounded number of polls; a wait that runs out latches OSOG_ERR_TIMEOUT,
+// waits once more (again bounded) for the copy in flight and lets the item
+// go on with whatever has arrived, so the launch always ends.
+__device__ __forceinline__ uint32_t shared_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// `missing` bytes more than the copy delivers are expected on the barrier
+// (a failure-detection test: the wait then runs out; 0 in normal use).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar, uint32_t missing = 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(shared_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                 ::"r"(shared_addr(bar)), "r"(bytes + missing) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 ::"r"(shared_addr(dst)), "l"(src), "r"(bytes), "r"(shared_addr(bar)) : "memory");
+}
+
+constexpr int kBulkPolls = 1 << 20;
+
+__device__ __forceinline__ bool bulk_try(uint64_t *bar, int polls) {
+    const uint32_t b = shared_addr(bar);
+    for (int it = 0; it < polls; ++it) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+                     "selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(b) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_wait(uint64_t *bar, int32_t *status, int polls) {
+    if (polls <= 0) polls = kBulkPolls;
+    if (!bulk_try(bar, polls)) {
+        latch(status, OSOG_ERR_TIMEOUT);
+        (void)bulk_try(bar, polls);
+    }
+}
+
+// The first Stockham pass (radix P0, stride 1) of the L columns of a column
+// block whose samples are still in the block's global layout, (y, c) at
+// raw[y L + c], where the bulk copy put them (raw aliases buf).  A warp's
+// lanes take (c = lane mod L, consecutive j), so its loads cover 32
+// consecutive samples and its stores spread over the banks like those of
+// the regular pass; columns whose bit in `live` is clear read as zero.
+template <int N, bool INV>
+__device__ __forceinline__ void first_pass_from_block(float2 *buf, unsigned live) {
+    constexpr int L = set_elems(N) / N;
+    constexpr int P = fft_radix(N, 0);
+    constexpr int NB = N / P;
+    constexpr int LS = line_stride(N);
+    static_assert(L * NB == kThreads && 32 % L == 0, "one butterfly per thread");
+    const int lane = threadIdx.x & 31;
+    const int c = lane % L, j = (threadIdx.x >> 5) * (32 / L) + lane / L;
+    const bool on = (live >> c) & 1u;
+    float2 v[P];
+#pragma unroll
+    for (int r = 0; r < P; ++r) v[r] = on ? buf[(j + r * NB) * L + c] : make_float2(0.f, 0.f);
+    __syncthreads();
+    dft<P, INV>(v);
+    float2 *dst = buf + c * LS + pad16(j * P);
+#pragma unroll
+    for (int r = 0; r < P; ++r) dst[r] = v[r];
+    __syncthreads();
+}
+
 // One column block bk of scene s.
-template <int N, bool MULTI, bool SQ = false>
+// BULK: a square canvas of N >= 1024 (L = B full columns per block) whose
+// G block arrives by one bulk copy.
+template <int N, bool MULTI, bool SQ = false, bool BULK = false>
 __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
                                             unsigned char *smem_raw) {
     constexpr int L = set_elems(N) / N;
@@ -266,7 +339,14 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
     if (!lo_part && !hi_part) return;
     const float2 *G = a.w.G + ((size_t)s * geo.nblocks + bk) * N * B;
     const int NB_ = N * B;  // <= set_elems(N); lines B..L-1 are never read back
-    if (a.unit_input) {  // the spectrum of a unit impulse: 1 at every frequency
+    static_assert(!BULK || (SQ && N >= 1024), "bulk staging needs full column blocks");
+    __shared__ uint64_t bar;  // completes the bulk copy (BULK)
+    const bool bulk = BULK && !a.unit_input;
+    if (bulk) {
+        if constexpr (BULK)
+            if (threadIdx.x == 0)
+                bulk_load(buf0, G, (uint32_t)(N * L * sizeof(float2)), &bar, a.wait_extra ? 16u : 0u);
+    } else if (a.unit_input) {  // the spectrum of a unit impulse: 1 at every frequency
 #pragma unroll
         for (int i = 0; i < ept(N); ++i) {
             const int e = threadIdx.x + i * kThreads;
@@ -290,8 +370,22 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
         const int m = j >> lb, c = j & (B - 1), kx = u0 + c;
         chords[m * L + c] = mode_chord(a.md[s][m], kx < half ? kx : kx - W, N);
     }
-    __syncthreads();
-    if (!a.unit_input) fft_lines<N, L, false>(buf0, a.tw);
+    __syncthreads();  // (bulk) the barrier's initialisation precedes every wait
+    if constexpr (BULK) {
+        if (bulk) {
+            unsigned live = 0;  // columns inside the pupils' hull; the others read as zero
+#pragma unroll
+            for (int c = 0; c < L; ++c) {
+                const int kx = u0 + c, fx = kx < half ? kx : kx - W;
+                live |= (fx >= cr.x && fx <= cr.y ? 1u : 0u) << c;
+            }
+            bulk_wait(&bar, a.w.status, a.wait_polls);
+            first_pass_from_block<N, false>(buf0, live);
+            fft_lines<N, L, false, 1>(buf0, a.tw);
+        }
+    } else if (!a.unit_input) {
+        fft_lines<N, L, false>(buf0, a.tw);
+    }
     for (int m = 0; m < K; ++m) {
         const ModeDev md = live_mode(a.md[s][m]);
         if (md.op == kOpSpectrum) {  // the forward spectrum itself, to md.tab
@@ -347,7 +441,7 @@ template <int N, bool MULTI, bool SQ>
 __global__ void __launch_bounds__(kThreads, 2) k_column(const __grid_constant__ ColumnArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_enter();
-    column_item<N, MULTI, SQ>(a, blockIdx.y, blockIdx.x, smem_raw);
+    column_item<N, MULTI, SQ, SQ && N >= 1024>(a, blockIdx.y, blockIdx.x, smem_raw);
 }
 
 // One strip of the image sm = s K + m.

@@ -30,6 +30,16 @@ def test_inverse_solve_recovers_parameters():
     assert res.losses[-1] < 1e-2 * res.losses[0]
     # fixed particles (a, b, mu, kind) are untouched
     assert np.array_equal(res.soa[[3, 4, 7, 8]], s0[[3, 4, 7, 8]])
+    # the particles outside the 1% set trade dn against T: the phase fixes the
+    # product dn T, T alone is seen only through the absorption contrast mu T,
+    # which is weakest for the smallest particles
+    rel = lambda row: np.abs(res.soa[row] - soa[row]) / np.abs(soa[row])
+    dnT = np.abs(res.soa[5] * res.soa[6] - soa[5] * soa[6]) / np.abs(soa[5] * soa[6])
+    miss = (rel(6) > 0.01) | (rel(5) > 0.01)
+    assert miss.any()
+    assert np.median(dnT[miss]) < 0.5 * np.median(rel(6)[miss])
+    size = soa[3] * soa[4]
+    assert np.median(size[miss]) < np.median(size[~miss])
 
 
 def test_solve_with_the_spectral_loss_term():

@@ -6,6 +6,9 @@ failure-detection form that neither faults nor hangs the GPU):
 - the persistent batched launch: each column item waits for one more
   finished strip than its scene has (osog_tuning_t.test_wait_extra) with a
   short poll limit (osog_tuning_t.wait_polls);
+- the column pass's wait for the bulk copy of its column block (square
+  canvases of 1024 or more): the barrier expects 16 bytes more than the
+  copy delivers (the same test_wait_extra), with a short poll limit;
 - the tcgen05 convolutions: every CTA also waits, for a few polls, on a
   barrier that nothing arrives on (osog_conv_test_wait_limit); the kernel
   still waits for its own tensor-core work and releases its tensor memory,
@@ -38,6 +41,26 @@ def test_persistent_launch_wait_runs_out_and_the_next_launch_is_correct():
     assert r.sync_status() == TIMEOUT
     assert r.sync_status() == 0  # read and cleared
     again = r.batch(dev, offs, optics, tuning={"use_graph": 0, "persistent": 1}).clone()
+    assert r.sync_status() == 0
+    assert torch.equal(again, base)
+
+
+def test_column_bulk_copy_wait_runs_out_and_the_next_launch_is_correct():
+    from paper_2606_21381_gb300.render import Renderer
+    rng = np.random.default_rng(10)
+    soas = [scenes.draw_particles(rng, int(c), 1024, 1024, mu=(0, 0.02)) for c in (900, 400)]
+    optics = [scenes.optics(1024, 1024, modes=1, defocus=d) for d in (0.4, -0.8)]
+    soa_all, offs = scenes.concat(soas)
+    dev = torch.from_numpy(soa_all).cuda()
+    r = Renderer(1024, 1024)
+    three = {"use_graph": 0, "persistent": -1}
+    base = r.batch(dev, offs, optics, tuning=three).clone()
+    assert r.sync_status() == 0
+    r.batch(dev, offs, optics, tuning=dict(three, wait_polls=2000, test_wait_extra=1))
+    torch.cuda.synchronize()   # the launch ended
+    assert r.sync_status() == TIMEOUT
+    assert r.sync_status() == 0
+    again = r.batch(dev, offs, optics, tuning=three).clone()
     assert r.sync_status() == 0
     assert torch.equal(again, base)
 
