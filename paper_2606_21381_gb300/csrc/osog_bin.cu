@@ -75,7 +75,7 @@ __device__ bool setup_planes(const Work &w, int off, int m, double c, double s, 
     return true;
 }
 
-// Setup of one particle: validation, FP64-rounded record, bounding rect.
+// Setup of one particle: validation, float-float record, bounding rect.
 __device__ Rect setup_particle(const float *soa, int64_t ld, int p, const SceneDev &sc,
                                const Geometry &geo, const Work &w) {
     PRec *rec = w.rec;
@@ -110,15 +110,26 @@ __device__ Rect setup_particle(const float *soa, int64_t ld, int p, const SceneD
             return empty;
         }
     }
-    double sd, cd;
-    sincos((double)th, &sd, &cd);
+    // cos and sin of the angle in float-float on the FP32 pipes (angles
+    // beyond 2^20 rad, a case of no physical use, in double)
+    ff cf, sf;
+    if (fabsf(th) <= kMaxReducedAngle) {
+        ff_sincos(th, &cf, &sf);
+    } else {
+        double sd, cd;
+        sincos((double)th, &sd, &cd);
+        cf.h = (float)cd;
+        cf.l = (float)(cd - (double)cf.h);
+        sf.h = (float)sd;
+        sf.l = (float)(sd - (double)sf.h);
+    }
     PRec r;
     r.cx = cx;
     r.cy = cy;
-    r.ch = (float)cd;
-    r.cl = (float)(cd - (double)r.ch);
-    r.sh = (float)sd;
-    r.sl = (float)(sd - (double)r.sh);
+    r.ch = cf.h;
+    r.cl = cf.l;
+    r.sh = sf.h;
+    r.sl = sf.l;
     r.T = T;
     r.dn = f[6];
     r.mu = f[7];
@@ -131,6 +142,7 @@ __device__ Rect setup_particle(const float *soa, int64_t ld, int p, const SceneD
     rr.dn = f[6];
     rr.mu = f[7];
     if (kind == 2.f) {
+        const double cd = (double)cf.h + (double)cf.l, sd = (double)sf.h + (double)sf.l;
         if (!setup_planes(w, poff, pcnt, cd, sd, (double)sc.dx_um)) {
             latch(status, OSOG_ERR_NONFINITE_INPUT);
             return empty;
@@ -161,27 +173,23 @@ __device__ Rect setup_particle(const float *soa, int64_t ld, int p, const SceneD
         rr.p[5] = T;
         rr.kind = 1;
     } else {
-        const double ia = 1.0 / (double)a, ib = 1.0 / (double)b;
-        r.p0h = (float)ia;
-        r.p0l = (float)(ia - (double)r.p0h);
-        r.p1h = (float)ib;
-        r.p1l = (float)(ib - (double)r.p1h);
+        const ff ia = ff_recip(a), ib = ff_recip(b);
+        r.p0h = ia.h;
+        r.p0l = ia.l;
+        r.p1h = ib.h;
+        r.p1l = ib.l;
         r.g = 0.f;
         ex = sqrtf(a * a * c * c + b * b * s * s);
         ey = sqrtf(a * a * s * s + b * b * c * c);
-        // the row quadric of (u/a)^2 + (v/b)^2 (see RRec), in double precision
-        const double ia2 = ia * ia, ib2 = ib * ib;
-        const double alpha = cd * cd * ia2 + sd * sd * ib2;
-        const double m = -cd * sd * (ia2 - ib2) / alpha;
-        const double inv_alpha = 1.0 / alpha;
-        const double kappa = ia2 * ib2 * inv_alpha * inv_alpha;
-        const double v3[3] = {m, inv_alpha, kappa};
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            rr.p[2 * k] = (float)v3[k];
-            rr.p[2 * k + 1] = (float)(v3[k] - (double)rr.p[2 * k]);
-        }
-        rr.tsa = (float)((double)T * sqrt(alpha));
+        // the row quadric of (u/a)^2 + (v/b)^2 (see RRec), in float-float
+        const Quadric q = ellipse_quadric(a, b, cf, sf);
+        rr.p[0] = q.m.h;
+        rr.p[1] = q.m.l;
+        rr.p[2] = q.inv_alpha.h;
+        rr.p[3] = q.inv_alpha.l;
+        rr.p[4] = q.kappa.h;
+        rr.p[5] = q.kappa.l;
+        rr.tsa = f_fma(T, q.sqrt_alpha.l, f_mul(T, q.sqrt_alpha.h));
         rr.kind = 0;
     }
     rec[p] = r;

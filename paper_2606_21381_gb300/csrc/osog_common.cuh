@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "osog.h"
+#include "osog_ff.h"
 
 namespace osog {
 
@@ -61,9 +62,10 @@ __host__ inline Geometry make_geometry(int H, int W) {
 }
 
 // Per-particle record written by the setup pass (64 bytes).  Angles and
-// inverse semi-axes are stored as float-float pairs (hi + lo) rounded from
-// double precision so that the ellipsoid rim can be evaluated with ~2^-44
-// relative error (see ellipse_delta_ff()).
+// inverse semi-axes are stored as float-float pairs (hi + lo), computed in
+// float-float arithmetic (cos, sin to 2^-47, reciprocals to 2^-47) so that
+// the ellipsoid rim can be evaluated with ~2^-44 relative error (see
+// ellipse_delta_ff()).
 struct __align__(16) PRec {
     float cx, cy;
     float ch, cl, sh, sl;     // cos(theta), sin(theta) hi/lo
@@ -80,9 +82,11 @@ static_assert(sizeof(PRec) == 64, "PRec is 64 bytes");
 //   w^2 = 1/alpha - kappa ey^2,  ey = Y - cy,
 // with alpha = c^2/a^2 + s^2/b^2, m = -c s (1/a^2 - 1/b^2) / alpha and
 // kappa = 1 / (a^2 b^2 alpha^2) (the quadric of (u/a)^2 + (v/b)^2 in ex for
-// fixed ey).  These constants are rounded from double precision to
-// float-float pairs so that the row's chord ends x0 -+ w are known to
-// ~1e-13 px, which the square root near the rim needs.
+// fixed ey).  The setup pass computes them as float-float pairs, to about
+// 2^-44 relative (ellipse_quadric(), in the cancellation-free form
+// m = -c s (b^2 - a^2) / D, D = b^2 c^2 + a^2 s^2), so that the row's chord
+// ends x0 -+ w are known to ~1e-11 px at a 100 px semi-axis, which the square
+// root near the rim needs.
 struct __align__(16) RRec {
     float cx, cy;
     float p[6];   // ellipsoid: m, 1/alpha, kappa (hi, lo each)
@@ -298,40 +302,11 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
 }
 
 // ---------------------------------------------------------------- float-float
-// Error-free transformations (Knuth TwoSum, FMA-based TwoProd; Dekker 1971,
-// Ogita-Rump-Oishi 2005).  The _rn intrinsics keep the compiler from
-// contracting or reordering the compensated steps.
-struct ff {
-    float h, l;
-};
-
-__device__ __forceinline__ ff two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, e};
-}
-__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // |a| >= |b|
-    float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-    ff s = two_sum(a.h, b.h);
-    float e = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
-    return fast_two_sum(s.h, e);
-}
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-    float p = __fmul_rn(a.h, b.h);
-    float e = __fmaf_rn(a.h, b.h, -p);
-    e = __fmaf_rn(a.h, b.l, e);
-    e = __fmaf_rn(a.l, b.h, e);
-    return fast_two_sum(p, e);
-}
-__device__ __forceinline__ ff ff_neg(ff a) { return {-a.h, -a.l}; }
+// struct ff and its error-free transformations: osog_ff.h.
 
 // ---------------------------------------------------------------- geometry
 // 1 - rho^2 of an ellipsoid at pixel centre (x, y) in float-float, from the
-// FP64-rounded record: u = c ex + s ey, v = -s ex + c ey, rho^2 = (u/a)^2 +
+// float-float record: u = c ex + s ey, v = -s ex + c ey, rho^2 = (u/a)^2 +
 // (v/b)^2 with ex = x - cx taken exactly (TwoSum).  Used where the float32
 // value of 1 - rho^2 is small: there the float32 rounding of rho^2 (~2e-7)
 // would put an error of order T sqrt(2e-7) on the thickness T sqrt(1 - rho^2).
