@@ -190,6 +190,106 @@ __device__ __forceinline__ void fft_lines(float2 *buf, const float2 *__restrict_
     }
 }
 
+// Passes [PASS, END) of the radix plan, each an in-place Stockham pass.
+template <int N, int L, bool INV, int PASS, int END>
+__device__ __forceinline__ void fft_pass_range(float2 *buf, const float2 *__restrict__ tw) {
+    if constexpr (PASS < END) {
+        stockham_pass<N, L, fft_radix(N, PASS), fft_ns(N, PASS), INV>(buf,
+                                                                      tw + fft_twoff(N, PASS));
+        fft_pass_range<N, L, INV, PASS + 1, END>(buf, tw);
+    }
+}
+
+// The first pass of the plan (stride 1, no twiddles) with its inputs taken
+// from ld(l, i), sample i of line l, instead of from buf: the kernels fold
+// the step that produces a line (a global load, the exit wave, a transfer
+// function) into the pass.  The butterflies and the order of every
+// operation are those of stockham_pass, so the results are bitwise the same.
+// IN_PLACE: ld reads buf itself, and the CTA synchronises between the loads
+// and the writes.  Ends with a barrier.
+template <int N, int L, bool INV, bool IN_PLACE, class Ld>
+__device__ __forceinline__ void fft_first_pass(float2 *buf, Ld ld) {
+    constexpr int P = fft_radix(N, 0);
+    constexpr int NB = N / P;
+    constexpr int TOT = L * NB;
+    constexpr int PER = (TOT + kThreads - 1) / kThreads;
+    constexpr int LS = line_stride(N);
+    float2 v[PER][P];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int b = threadIdx.x + q * kThreads;
+        if (TOT % kThreads == 0 || b < TOT) {
+            const int l = b / NB, j = b % NB;
+#pragma unroll
+            for (int r = 0; r < P; ++r) v[q][r] = ld(l, j + r * NB);
+        }
+    }
+    if constexpr (IN_PLACE) __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int b = threadIdx.x + q * kThreads;
+        if (TOT % kThreads == 0 || b < TOT) {
+            const int l = b / NB, j = b % NB;
+            dft<P, INV>(v[q]);
+            float2 *dst = buf + l * LS + pad16(j * P);
+#pragma unroll
+            for (int r = 0; r < P; ++r) dst[r] = v[q][r];
+        }
+    }
+    __syncthreads();
+}
+
+// The last pass of the plan with its outputs handed to st(l, i, value),
+// sample i of line l, instead of written back to buf (the kernels store
+// straight to global memory).  Arithmetic as in stockham_pass.  LINE_FAST:
+// consecutive threads take consecutive lines (the columns of a column
+// block, interleaved in global memory), else consecutive butterflies of one
+// line.  buf is only read, so there is no barrier.
+template <int N, int L, bool INV, bool LINE_FAST, class St>
+__device__ __forceinline__ void fft_last_pass(const float2 *buf, const float2 *__restrict__ tw,
+                                              St st) {
+    constexpr int PASS = fft_passes(N) - 1;
+    constexpr int P = fft_radix(N, PASS), NS = fft_ns(N, PASS);
+    static_assert(NS * P == N && NS > 1, "the last pass of the plan");
+    constexpr int NB = N / P;
+    constexpr int TOT = L * NB;
+    constexpr int PER = (TOT + kThreads - 1) / kThreads;
+    constexpr int LS = line_stride(N);
+    const float2 *__restrict__ t = tw + fft_twoff(N, PASS);
+    float2 v[PER][P];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int b = threadIdx.x + q * kThreads;
+        if (TOT % kThreads == 0 || b < TOT) {
+            const int l = LINE_FAST ? b % L : b / NB, j = LINE_FAST ? b / L : b % NB;
+            if constexpr (NB % 16 == 0) {
+                const float2 *src = buf + l * LS + pad16(j);
+#pragma unroll
+                for (int r = 0; r < P; ++r) v[q][r] = src[r * (NB + NB / 16)];
+            } else {
+                const float2 *src = buf + l * LS;
+#pragma unroll
+                for (int r = 0; r < P; ++r) v[q][r] = src[pad16(j + r * NB)];
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int b = threadIdx.x + q * kThreads;
+        if (TOT % kThreads == 0 || b < TOT) {
+            const int l = LINE_FAST ? b % L : b / NB, j = LINE_FAST ? b / L : b % NB;
+#pragma unroll
+            for (int r = 1; r < P; ++r) {
+                const float2 w = __ldg(t + (r - 1) * NS + j);
+                v[q][r] = INV ? cmulc(v[q][r], w) : cmul(v[q][r], w);
+            }
+            dft<P, INV>(v[q]);
+#pragma unroll
+            for (int r = 0; r < P; ++r) st(l, j + r * NS, v[q][r]);
+        }
+    }
+}
+
 // Host: the twiddle tables of an n-point transform, n entries, in double
 // precision rounded once to float: pass p's block holds
 // exp(-2 pi i r k / (Ns P)) at [(r - 1) Ns + k], r = 1..P-1, k = 0..Ns-1.

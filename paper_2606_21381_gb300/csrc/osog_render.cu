@@ -84,7 +84,27 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
         raster_strip<N, ACC>(a.geo, a.w, a.sc[s], s, y0, R, smem_raw, scratch);
     }
     __syncthreads();
-    if constexpr (MODE == kStripOpdOnly) {
+    if constexpr (MODE == kStripRender) {
+        // the exit wave of the accumulated words is formed as the first FFT
+        // pass loads them, and the last pass stores G (column-blocked, only
+        // the columns some pupil passes)
+        fft_first_pass<N, L, false, true>(buf, [&](int l, int x) -> float2 {
+            return l < R ? exit_wave_fixed(*reinterpret_cast<const uint2 *>(buf + l * LS + pad16(x)))
+                         : make_float2(0.f, 0.f);
+        });
+        fft_pass_range<N, L, false, 1, fft_passes(N) - 1>(buf, a.tw);
+        const int B = SQ ? sq_rb(N) : geo.B;
+        const int lb = SQ ? clog2(sq_rb(N)) : ilog2(B);
+        const int H = SQ ? N : geo.H;
+        float2 *G = a.w.G + (size_t)s * H * N;
+        const int2 cr = a.w.colrange[s];
+        fft_last_pass<N, L, false, false>(buf, a.tw, [&](int l, int kx, float2 v) {
+            const int fx = kx < N / 2 ? kx : kx - N;
+            if (l < R && fx >= cr.x && fx <= cr.y)  // columns outside every pupil are never read
+                G[((size_t)(kx >> lb) * H + y0 + l) * B + (kx & (B - 1))] = v;
+        });
+        return;
+    } else if constexpr (MODE == kStripOpdOnly) {
         const longlong2 *acc = reinterpret_cast<const longlong2 *>(smem_raw);
         float2 *dst = a.opd_out + (size_t)y0 * N;
 #pragma unroll
@@ -98,16 +118,7 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
         }
         return;
     } else {
-        if constexpr (MODE == kStripRender) {
-#pragma unroll
-            for (int i = 0; i < ept(N); ++i) {
-                const int e = threadIdx.x + i * kThreads;
-                if (e < RN) {
-                    float2 *v = buf + (e / N) * LS + pad16(e % N);
-                    *v = exit_wave_fixed(*reinterpret_cast<const uint2 *>(v));
-                }
-            }
-        } else if constexpr (MODE == kStripFromMap) {
+        if constexpr (MODE == kStripFromMap) {
             const float tol = a.sc[s].two_over_lambda;
 #pragma unroll
             for (int i = 0; i < ept(N); ++i) {
@@ -400,39 +411,48 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
             }
             continue;  // buf0 is only read: the next modality may still use it
         }
-        if (md.op == kOpLoss) {
-            loss_columns<N>(a, s, bk, B, W, buf0, buf1);
-        } else {
-        const float2 *T = md.op == kOpTable ? md.tab + (size_t)bk * N * B : nullptr;
-        const float tnorm = md.op == kOpTable ? md.scale / md.tab[0].x : 0.f;
-#pragma unroll 4
-        for (int i = 0; i < ept(N); ++i) {
-            const int e = threadIdx.x + i * kThreads;  // line-major: consecutive y
-            const int c = e / N, y = e % N;
-            if (c < B) {
-                const int kx = bk * B + c;
-                const int fx = kx < half ? kx : kx - W;
-                const int fy = y < N / 2 ? y : y - N;
-                const int2 ch = chords[m * L + c];
-                float2 v = make_float2(0.f, 0.f);
-                if (T) {
-                    const float2 t = T[y * B + c];
-                    v = cmul(buf0[c * LS + pad16(y)], make_float2(t.x * tnorm, t.y * tnorm));
-                } else if (fy >= ch.x && fy <= ch.y) {
-                    v = cmul(buf0[c * LS + pad16(y)], transfer(md, fx, fy));
-                }
-                buf1[c * LS + pad16(y)] = v;
-            }
-        }
-        }
-        __syncthreads();
-        fft_lines<N, L, true>(buf1, a.tw);
         float2 *Qm = a.w.Q + (((size_t)s * K + m) * geo.nblocks + bk) * N * B;
-#pragma unroll
-        for (int i = 0; i < ept(N); ++i) {
-            const int e = threadIdx.x + i * kThreads;
-            if (e < NB_) Qm[e] = buf1[(e & (B - 1)) * LS + pad16(e >> lb)];
+        if (md.op == kOpPupil || md.op == kOpAllPass) {
+            // the transfer function is applied as the first inverse pass
+            // loads the spectrum (in place when buf1 is buf0)
+            auto ld = [&](int c, int y) -> float2 {
+                if (c < B) {
+                    const int2 ch = chords[m * L + c];
+                    const int fy = y < N / 2 ? y : y - N;
+                    if (fy >= ch.x && fy <= ch.y) {
+                        const int kx = bk * B + c;
+                        return cmul(buf0[c * LS + pad16(y)], transfer(md, kx < half ? kx : kx - W, fy));
+                    }
+                }
+                return make_float2(0.f, 0.f);
+            };
+            fft_first_pass<N, L, true, !MULTI>(buf1, ld);
+        } else {
+            if (md.op == kOpLoss) {
+                loss_columns<N>(a, s, bk, B, W, buf0, buf1);
+            } else {  // kOpTable
+                const float2 *T = md.tab + (size_t)bk * N * B;
+                const float tnorm = md.scale / md.tab[0].x;
+#pragma unroll 4
+                for (int i = 0; i < ept(N); ++i) {
+                    const int e = threadIdx.x + i * kThreads;  // line-major: consecutive y
+                    const int c = e / N, y = e % N;
+                    if (c < B) {
+                        const float2 t = T[y * B + c];
+                        buf1[c * LS + pad16(y)] =
+                            cmul(buf0[c * LS + pad16(y)], make_float2(t.x * tnorm, t.y * tnorm));
+                    }
+                }
+            }
+            __syncthreads();
+            fft_pass_range<N, L, true, 0, 1>(buf1, a.tw);
         }
+        fft_pass_range<N, L, true, 1, fft_passes(N) - 1>(buf1, a.tw);
+        // the last pass stores Q; consecutive threads take the block's
+        // columns, so a warp writes whole rows of the block
+        fft_last_pass<N, L, true, true>(buf1, a.tw, [&](int c, int y, float2 v) {
+            if (c < B) Qm[(size_t)y * B + c] = v;
+        });
         __syncthreads();
     }
 }
@@ -449,45 +469,30 @@ template <int N, bool SQ = false>
 __device__ __forceinline__ void inverse_item(const InverseArgs &a, int sm, int strip,
                                              unsigned char *smem_raw) {
     constexpr int L = set_elems(N) / N;
-    constexpr int LS = line_stride(N);
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
     const Geometry &geo = a.geo;
     const int K = a.K;
     const int R = SQ ? sq_rb(N) : geo.R, B = SQ ? sq_rb(N) : geo.B;
-    const int lb = SQ ? clog2(sq_rb(N)) : ilog2(B), lr = SQ ? clog2(sq_rb(N)) : ilog2(R);
+    const int lb = SQ ? clog2(sq_rb(N)) : ilog2(B);
     const int H = SQ ? N : geo.H;
     const int y0 = strip * R;
     const float2 *Qm = a.w.Q + (size_t)sm * geo.nblocks * H * B;
     const int2 cr = a.w.colrange[sm / K];
-    const int RN = R * N;  // <= set_elems(N); lines R..L-1 are never read back
-    {
-        float2 v[ept(N)];
-#pragma unroll
-        for (int i = 0; i < ept(N); ++i) {
-            const int e = threadIdx.x + i * kThreads;
-            const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
-            const int kx = bk * B + c, fx = kx < N / 2 ? kx : kx - N;
-            v[i] = e < RN && fx >= cr.x && fx <= cr.y ? Qm[((size_t)bk * H + y0 + r) * B + c]
-                                                      : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int i = 0; i < ept(N); ++i) {
-            const int e = threadIdx.x + i * kThreads;
-            const int c = e & (B - 1), r = (e >> lb) & (R - 1), bk = e >> (lb + lr);
-            if (e < RN) buf[r * LS + pad16(bk * B + c)] = v[i];
-        }
-    }
-    __syncthreads();
-    fft_lines<N, L, true>(buf, a.tw);
+    // the first pass reads the strip's rows of Q straight from global memory
+    // (columns that no pupil passes, and lines past the strip, read as zero);
+    // the last pass writes the intensity rows
+    fft_first_pass<N, L, true, false>(buf, [&](int l, int kx) -> float2 {
+        const int fx = kx < N / 2 ? kx : kx - N;
+        return l < R && fx >= cr.x && fx <= cr.y
+                   ? Qm[((size_t)(kx >> lb) * H + y0 + l) * B + (kx & (B - 1))]
+                   : make_float2(0.f, 0.f);
+    });
+    fft_pass_range<N, L, true, 1, fft_passes(N) - 1>(buf, a.tw);
     float *img = a.images + ((size_t)sm * H + y0) * N;
-#pragma unroll
-    for (int i = 0; i < ept(N); ++i) {
-        const int e = threadIdx.x + i * kThreads;
-        if (e < RN) {
-            const float2 v = buf[(e / N) * LS + pad16(e % N)];
-            img[e] = a.real_out ? v.x : fmaf(v.x, v.x, __fmul_rn(v.y, v.y));
-        }
-    }
+    const int real_out = a.real_out;
+    fft_last_pass<N, L, true, false>(buf, a.tw, [&](int l, int x, float2 v) {
+        if (l < R) img[(size_t)l * N + x] = real_out ? v.x : fmaf(v.x, v.x, __fmul_rn(v.y, v.y));
+    });
 }
 
 template <int N, bool SQ>

@@ -212,9 +212,10 @@ __device__ __forceinline__ void deposit(void *acc, float t, float dn, float mu) 
 
 // Exit wave of a pixel's phase-mode accumulators (Eq. 2 with the
 // Beer-Lambert amplitude of Eq. 4): the phase, taken modulo one cycle into
-// [-1/2, 1/2) cycles, feeds the hardware sin / cos directly.
+// [-1/2, 1/2) cycles, feeds the hardware sin / cos directly.  An empty
+// pixel (both words zero) takes the same path: sin 0, cos 0 and 2^0 are
+// exact, so it gives (1, 0) without a branch that would split the warp.
 __device__ __forceinline__ float2 exit_wave_fixed(uint2 acc) {
-    if (acc.x == 0u && acc.y == 0u) return make_float2(1.f, 0.f);
     const int p = (int)(acc.x << 9) >> 9;  // units of 2^-23 cycles
     float s, c;
     __sincosf((float)p * 7.4901405658471572e-07f, &s, &c);              // 2 pi 2^-23
@@ -222,163 +223,119 @@ __device__ __forceinline__ float2 exit_wave_fixed(uint2 acc) {
     return make_float2(a * c, a * s);
 }
 
-// Exclusive prefix sum of one value per thread over the NT threads of the
-// CTA (warp scans, then the warp totals in order); total receives the sum.
-// Begins and ends with a barrier-separated use of wsum[0 .. NT/32).
-template <int NT>
-__device__ __forceinline__ int block_excl_scan(int v, int *wsum, int &total) {
-    constexpr int NW = NT / 32;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int inc = v;
+// Inclusive prefix sum over the lanes of a warp.
+__device__ __forceinline__ int warp_incl_scan(int v) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const int t = __shfl_up_sync(kFull, inc, d);
-        if (lane >= d) inc += t;
+        const int t = __shfl_up_sync(kFull, v, d);
+        if (lane >= d) v += t;
     }
-    if (lane == 31) wsum[warp] = inc;
-    __syncthreads();
-    int before = 0;
-    total = 0;
-#pragma unroll
-    for (int k = 0; k < NW; ++k) {
-        const int c = wsum[k];
-        before += k < warp ? c : 0;
-        total += c;
-    }
-    return before + inc - v;
+    return v;
 }
 
-// Pixels of one chunk of a row item, and chunks per pass of the pixel phase.
-constexpr int kChunkPx = 8;
-constexpr int kChunkCap = 1024;
+// The lane whose range of a warp prefix holds key: the number of lanes whose
+// inclusive prefix (field (inc >> sh) & mask, non-decreasing over the lanes)
+// is at most key.  Every lane of the warp takes part; the result is at most
+// 31, and it is the owning lane whenever key is below lane 31's prefix.
+__device__ __forceinline__ int warp_owner(int inc, int key, int sh, int mask) {
+    int e = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const int t = (__shfl_sync(kFull, inc, e + s - 1) >> sh) & mask;
+        if (t <= key) e += s;
+    }
+    return e;
+}
 
-// Shared memory of raster_region beyond the accumulators: the staged band
-// entries, their row offsets, one round of row items, the items' chunk
-// offsets, one pass of chunks and the per-warp counts.
+// Pixels of one chunk of a row item.
+constexpr int kChunkPx = 4;
+
+// Shared memory of raster_region beyond the accumulators: one wave of 32
+// row items per warp and the CTA's work counter.
 template <int NT>
 __host__ __device__ constexpr size_t raster_smem() {
-    return (size_t)NT * (sizeof(int) + sizeof(Rect)) + (size_t)(NT + 4) * sizeof(int) +
-           (size_t)NT * sizeof(RowItem) + (size_t)kChunkCap * sizeof(uint32_t) +
-           2 * (NT / 32) * sizeof(int);
+    return (size_t)NT * sizeof(RowItem) + 16;
 }
 
 // OPD and ATT of the region rows [ty0, ty0 + nrows) x columns [tx0, tx1]
 // of scene s from the band list entries [lo, hi) (ids of the scene's
 // records), added into the accumulators that slot(row, x) addresses (zeroed
-// by the caller; kAccPhase: uint2, kAccOpd: two int64).  The list is
-// consumed NT entries at a time: entries whose rectangle meets the region
-// are compacted into shared memory; each staged particle gives one item per
-// region row it covers, built NT at a time and compacted ellipsoids first
-// and the other kinds after them (so that most warps run one chord
-// formula); the items' pixels are then shared out evenly over the warps in
-// chunks of up to kChunkPx.  Every thread of the CTA must call it.
+// by the caller; kAccPhase: uint2, kAccOpd: two int64).  Each warp works on
+// its own groups of 32 list entries (the first NT / 32 groups in warp
+// order, the rest handed out by a shared counter as warps finish), with no
+// CTA barrier until the end:
+//   1. the entries whose rectangle meets the region and the region rows each
+//      covers, and a warp prefix sum of those row counts;
+//   2. waves of 32 (particle, row) items, one per lane (the owning entry
+//      found by a search over the prefix), built from the particle's
+//      row-span constants into the warp's item slots;
+//   3. the wave's pixels cut into chunks of up to kChunkPx, ellipsoid items'
+//      chunks first so that most passes run one chord formula; lane l of a
+//      pass takes chunk l and evaluates its pixels as independent unrolled
+//      chains, adding each covered pixel with integer shared atomics.
+// Every thread of the CTA must call it; it ends with a CTA barrier.
 template <int NT, int ACC, typename Slot>
 __device__ void raster_region(const Work &w, const int32_t *ids, int lo, int hi, int ty0,
                               int nrows, int tx0, int tx1, float inv_lambda, Slot slot,
                               unsigned char *scratch) {
-    constexpr int NW = NT / 32;
-    int *sid = reinterpret_cast<int *>(scratch);
-    Rect *srect = reinterpret_cast<Rect *>(sid + NT);
-    int *rowpre = reinterpret_cast<int *>(srect + NT);          // [NT + 1]
-    RowItem *items = reinterpret_cast<RowItem *>(rowpre + NT + 4);
-    uint32_t *chunk = reinterpret_cast<uint32_t *>(items + NT);           // [kChunkCap]
-    int *wsum = reinterpret_cast<int *>(chunk + kChunkCap);               // [2 NW]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    RowItem *items = reinterpret_cast<RowItem *>(scratch) + warp * 32;
+    int *next = reinterpret_cast<int *>(reinterpret_cast<RowItem *>(scratch) + NT);
     const int tyl = ty0 + nrows - 1;
-    const unsigned lt = lanemask_lt();
-    for (int base = lo; base < hi; base += NT) {
-        // 1. the entries that meet the region
-        const int i = base + threadIdx.x;
-        int id = 0;
-        Rect q = {1, 0, 1, 0};
+    if (threadIdx.x == 0) *next = lo + NT;
+    __syncthreads();
+    int base = lo + warp * 32;
+    while (base < hi) {
+        int nb = 0;
+        if (lane == 0) nb = atomicAdd(next, 32);
+        // 1. the group's entries that meet the region
+        const int i = base + lane;
+        int id = 0, nr = 0, ry0 = 0, rx0 = 0, rx1 = 0;
         if (i < hi) {
             id = ids[i];
-            q = w.rect[id];
+            const Rect q = w.rect[id];
+            ry0 = max((int)q.y0, ty0);
+            rx0 = max((int)q.x0, tx0);
+            rx1 = min((int)q.x1, tx1);
+            nr = rx0 <= rx1 ? max(min((int)q.y1, tyl) - ry0 + 1, 0) : 0;
         }
-        const bool keep = i < hi && q.y0 <= tyl && q.y1 >= ty0 && q.x0 <= tx1 && q.x1 >= tx0;
-        int nl;
-        const int kslot = block_excl_scan<NT>(keep ? 1 : 0, wsum, nl);
-        if (keep) {
-            sid[kslot] = id;
-            srect[kslot] = q;
-        }
-        __syncthreads();
-        // 2. rows of the region each staged particle covers, as offsets
-        int npairs;
-        {
-            int nr = 0;
-            if ((int)threadIdx.x < nl) {
-                const Rect r = srect[threadIdx.x];
-                nr = min((int)r.y1, tyl) - max((int)r.y0, ty0) + 1;
-            }
-            const int pre = block_excl_scan<NT>(nr, wsum, npairs);
-            rowpre[threadIdx.x] = pre;
-        }
-        __syncthreads();
-        // 3. rounds of NT (particle, row) items
-        for (int pb = 0; pb < npairs; pb += NT) {
-            const int j = pb + threadIdx.x;
+        const int inc = warp_incl_scan(nr);
+        const int ex = inc - nr;
+        const int total = __shfl_sync(kFull, inc, 31);
+        // 2. waves of 32 (particle, row) items
+        for (int jb = 0; jb < total; jb += 32) {
+            const int j = jb + lane;
+            const int e = warp_owner(inc, j, 0, -1);
+            const int ide = __shfl_sync(kFull, id, e);
+            const int ye = __shfl_sync(kFull, ry0, e) + j - __shfl_sync(kFull, ex, e);
+            const int c0 = __shfl_sync(kFull, rx0, e), c1 = __shfl_sync(kFull, rx1, e);
             RowItem it;
-            bool valid = false, ell = false;
-            if (j < npairs) {
-                int p = 0, ph = nl;  // the last staged particle whose rows start at or before j
-                while (ph - p > 1) {
-                    const int mid = (p + ph) >> 1;
-                    if (rowpre[mid] <= j) p = mid; else ph = mid;
-                }
-                const Rect r = srect[p];
-                const int y = max((int)r.y0, ty0) + (j - rowpre[p]);
-                const RRec rr = w.rrec[sid[p]];
-                valid = make_row_item<ACC>(rr, max((int)r.x0, tx0), min((int)r.x1, tx1), y, y - ty0,
-                                           inv_lambda, it);
-                ell = rr.kind == 0;
-            }
-            const unsigned me = __ballot_sync(kFull, valid && ell);
-            const unsigned mo = __ballot_sync(kFull, valid && !ell);
-            if (lane == 0) {
-                wsum[warp] = __popc(me);
-                wsum[NW + warp] = __popc(mo);
-            }
-            __syncthreads();
-            int be = 0, ne = 0, bo = 0, no = 0;
-#pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                const int ce = wsum[k], co = wsum[NW + k];
-                be += k < warp ? ce : 0;
-                bo += k < warp ? co : 0;
-                ne += ce;
-                no += co;
-            }
-            if (valid) items[ell ? be + __popc(me & lt) : ne + bo + __popc(mo & lt)] = it;
-            __syncthreads();
-            // 4. pixels: every item is cut into chunks of up to kChunkPx
-            //    consecutive pixels, numbered through the items by a prefix
-            //    sum (kind order kept); each lane takes one chunk at a time
-            //    and evaluates its pixels as independent unrolled chains; a
-            //    pass hands kChunkCap chunks out evenly over the warps.
-            const int nitems = ne + no;
-            int TC;
-            const int mych = (int)threadIdx.x < nitems
-                                 ? (int)((((items[threadIdx.x].hdr >> 12) & 0xFFFu) + kChunkPx - 1) /
-                                         kChunkPx)
-                                 : 0;
-            const int cfirst = block_excl_scan<NT>(mych, wsum, TC);
-            for (int cb = 0; cb < TC; cb += kChunkCap) {
-                __syncthreads();  // the previous pass has read the chunk table
-                // chunk entry: item index (bits 0-15), first pixel of the chunk (16-31)
-                for (int c = max(cfirst, cb); c < min(cfirst + mych, cb + kChunkCap); ++c)
-                    chunk[c - cb] = (uint32_t)threadIdx.x | ((uint32_t)((c - cfirst) * kChunkPx) << 16);
-                __syncthreads();
-                const int nc = min(TC - cb, kChunkCap);
-                const int ca = (int)((long)nc * warp / NW), cz = (int)((long)nc * (warp + 1) / NW);
-                for (int c = ca + lane; c < cz; c += 32) {
-                    const uint32_t ce = chunk[c];
-                    const RowItem rit = items[ce & 0xFFFFu];  // registers: the atomics below
-                                                              // may not alias it
+            bool valid = false;
+            if (j < total)
+                valid = make_row_item<ACC>(w.rrec[ide], c0, c1, ye, ye - ty0, inv_lambda, it);
+            // 3. chunks: ellipsoid items' count in the low half-word, the
+            //    other kinds' in the high one
+            const int nch = valid ? (int)((((it.hdr >> 12) & 0xFFFu) + kChunkPx - 1) / kChunkPx) : 0;
+            const int mine = valid && ((it.hdr >> 24) & 3u) == 0 ? nch : nch << 16;
+            const int cinc = warp_incl_scan(mine);
+            const int cex = cinc - mine;
+            const int ctot = __shfl_sync(kFull, cinc, 31);
+            const int TE = ctot & 0xFFFF, TC = TE + (ctot >> 16);
+            if (valid) items[lane] = it;
+            __syncwarp();
+            for (int cb = 0; cb < TC; cb += 32) {
+                const int c = cb + lane;
+                const int sh = c < TE ? 0 : 16;
+                const int key = c < TE ? c : c - TE;
+                const int k = warp_owner(cinc, key, sh, 0xFFFF);
+                const int kex = (__shfl_sync(kFull, cex, k) >> sh) & 0xFFFF;
+                if (c < TC) {
+                    const RowItem rit = items[k];  // registers: the atomics below may not alias it
                     const uint32_t h = rit.hdr;
                     const int j0 = (int)(h & 0xFFFu), cnt = (int)((h >> 12) & 0xFFFu);
                     const int kind = (int)((h >> 24) & 3u);
-                    const int k0 = (int)(ce >> 16);
+                    const int k0 = (key - kex) * kChunkPx;
                     const int len = min(kChunkPx, cnt - k0);
                     const int x0 = j0 + k0;
                     float t[kChunkPx];
@@ -401,9 +358,11 @@ __device__ void raster_region(const Work &w, const int32_t *ids, int lo, int hi,
                         if (u < len && t[u] > 0.f) deposit<ACC>(slot(rit.row, x0 + u), t[u], rit.dn, rit.mu);
                 }
             }
-            __syncthreads();
+            __syncwarp();  // the wave's items are read before the next wave writes
         }
+        base = __shfl_sync(kFull, nb, 0);
     }
+    __syncthreads();
 }
 
 // The strip [y0, y0 + R) of scene s rasterised into the padded FFT lines of
