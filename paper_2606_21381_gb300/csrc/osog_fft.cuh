@@ -129,20 +129,59 @@ __device__ __forceinline__ constexpr int stride_off(int stride, int r) {
     return stride >= 16 ? r * (stride + stride / 16) : stride == 8 ? 8 * r + (r >> 1) : r;
 }
 
-// One Stockham pass over L lines of N points.
-template <int N, int L, int P, int NS, bool INV>
+// Synchronisation of the threads that own line l when each line of the set
+// belongs to its own group of kThreads / L threads (a named barrier per
+// line, or the warp when a line has one warp).
+template <int L>
+__device__ __forceinline__ void line_sync(int l) {
+    constexpr int TPL = kThreads / L;
+    if constexpr (TPL == 32) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + l), "r"(TPL) : "memory");
+    }
+}
+
+// True when the passes of an N-point transform can run with one thread
+// group per line: every pass has at least one butterfly per thread of the
+// group (sets of 8192 samples, N >= 1024).
+__host__ __device__ constexpr bool fft_grouped(int n) {
+    return set_elems(n) == kMaxSetElems && n >= 1024;
+}
+
+// Butterfly q of this thread in a pass of NB butterflies per line over L
+// lines: grouped, the threads [l TPL, (l + 1) TPL) take line l; otherwise
+// consecutive threads take consecutive butterflies of the whole set.
+template <int L, int NB, bool G>
+__device__ __forceinline__ void butterfly_of(int q, int &l, int &j) {
+    if constexpr (G) {
+        constexpr int TPL = kThreads / L;
+        l = threadIdx.x / TPL;
+        j = threadIdx.x % TPL + q * TPL;
+    } else {
+        const int b = threadIdx.x + q * kThreads;
+        l = b / NB;
+        j = b % NB;
+    }
+}
+
+// One Stockham pass over L lines of N points.  G: one thread group per line
+// (fft_grouped(N)); the pass then synchronises only the line's group.
+template <int N, int L, int P, int NS, bool INV, bool G = false>
 __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restrict__ tw) {
     static_assert(NS == 1 || NS == 8 || NS % 16 == 0, "unsupported Stockham stride");
     constexpr int NB = N / P;
     constexpr int TOT = L * NB;
     constexpr int PER = (TOT + kThreads - 1) / kThreads;
     constexpr int LS = line_stride(N);
+    static_assert(!G || (NB % (kThreads / L) == 0 && kThreads % L == 0), "grouped pass");
     float2 v[PER][P];
+    int l = 0;
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
-        const int b = threadIdx.x + q * kThreads;
-        if (TOT % kThreads == 0 || b < TOT) {
-            const int l = b / NB, j = b % NB;
+        int j;
+        butterfly_of<L, NB, G>(q, l, j);
+        if (G || TOT % kThreads == 0 || threadIdx.x + q * kThreads < TOT) {
             if constexpr (NB % 16 == 0) {
                 const float2 *src = buf + l * LS + pad16(j);
 #pragma unroll
@@ -154,12 +193,12 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restr
             }
         }
     }
-    __syncthreads();
+    if constexpr (G) line_sync<L>(l); else __syncthreads();
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
-        const int b = threadIdx.x + q * kThreads;
-        if (TOT % kThreads == 0 || b < TOT) {
-            const int l = b / NB, j = b % NB;
+        int j;
+        butterfly_of<L, NB, G>(q, l, j);
+        if (G || TOT % kThreads == 0 || threadIdx.x + q * kThreads < TOT) {
             const int k = j & (NS - 1);
             if constexpr (NS > 1) {
                 const float2 *t = tw + k;  // this pass's table, entry [r - 1][k]
@@ -175,7 +214,7 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restr
             for (int r = 0; r < P; ++r) dst[stride_off(NS, r)] = v[q][r];
         }
     }
-    __syncthreads();
+    if constexpr (G) line_sync<L>(l); else __syncthreads();
 }
 
 // Full FFT of the L lines (forward: exp(-2 pi i jk/N); inverse: conjugate,
@@ -190,13 +229,14 @@ __device__ __forceinline__ void fft_lines(float2 *buf, const float2 *__restrict_
     }
 }
 
-// Passes [PASS, END) of the radix plan, each an in-place Stockham pass.
-template <int N, int L, bool INV, int PASS, int END>
+// Passes [PASS, END) of the radix plan, each an in-place Stockham pass
+// (G: grouped, see stockham_pass).
+template <int N, int L, bool INV, int PASS, int END, bool G = false>
 __device__ __forceinline__ void fft_pass_range(float2 *buf, const float2 *__restrict__ tw) {
     if constexpr (PASS < END) {
-        stockham_pass<N, L, fft_radix(N, PASS), fft_ns(N, PASS), INV>(buf,
-                                                                      tw + fft_twoff(N, PASS));
-        fft_pass_range<N, L, INV, PASS + 1, END>(buf, tw);
+        stockham_pass<N, L, fft_radix(N, PASS), fft_ns(N, PASS), INV, G>(buf,
+                                                                         tw + fft_twoff(N, PASS));
+        fft_pass_range<N, L, INV, PASS + 1, END, G>(buf, tw);
     }
 }
 
@@ -205,63 +245,79 @@ __device__ __forceinline__ void fft_pass_range(float2 *buf, const float2 *__rest
 // the step that produces a line (a global load, the exit wave, a transfer
 // function) into the pass.  The butterflies and the order of every
 // operation are those of stockham_pass, so the results are bitwise the same.
-// IN_PLACE: ld reads buf itself, and the CTA synchronises between the loads
-// and the writes.  Ends with a barrier.
-template <int N, int L, bool INV, bool IN_PLACE, class Ld>
+// IN_PLACE: ld reads buf itself, and the threads synchronise between the
+// loads and the writes.  G: grouped (see stockham_pass); ld(l, i) may then
+// read only line l of buf.  Ends with a barrier (the line's, grouped).
+template <int N, int L, bool INV, bool IN_PLACE, bool G, class Ld>
 __device__ __forceinline__ void fft_first_pass(float2 *buf, Ld ld) {
     constexpr int P = fft_radix(N, 0);
     constexpr int NB = N / P;
     constexpr int TOT = L * NB;
     constexpr int PER = (TOT + kThreads - 1) / kThreads;
     constexpr int LS = line_stride(N);
+    static_assert(!G || (NB % (kThreads / L) == 0 && kThreads % L == 0), "grouped pass");
     float2 v[PER][P];
+    int l = 0;
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
-        const int b = threadIdx.x + q * kThreads;
-        if (TOT % kThreads == 0 || b < TOT) {
-            const int l = b / NB, j = b % NB;
+        int j;
+        butterfly_of<L, NB, G>(q, l, j);
+        if (G || TOT % kThreads == 0 || threadIdx.x + q * kThreads < TOT) {
 #pragma unroll
             for (int r = 0; r < P; ++r) v[q][r] = ld(l, j + r * NB);
         }
     }
-    if constexpr (IN_PLACE) __syncthreads();
+    if constexpr (IN_PLACE) {
+        if constexpr (G) line_sync<L>(l); else __syncthreads();
+    }
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
-        const int b = threadIdx.x + q * kThreads;
-        if (TOT % kThreads == 0 || b < TOT) {
-            const int l = b / NB, j = b % NB;
+        int j;
+        butterfly_of<L, NB, G>(q, l, j);
+        if (G || TOT % kThreads == 0 || threadIdx.x + q * kThreads < TOT) {
             dft<P, INV>(v[q]);
             float2 *dst = buf + l * LS + pad16(j * P);
 #pragma unroll
             for (int r = 0; r < P; ++r) dst[r] = v[q][r];
         }
     }
-    __syncthreads();
+    if constexpr (G) line_sync<L>(l); else __syncthreads();
 }
 
 // The last pass of the plan with its outputs handed to st(l, i, value),
 // sample i of line l, instead of written back to buf (the kernels store
 // straight to global memory).  Arithmetic as in stockham_pass.  LINE_FAST:
 // consecutive threads take consecutive lines (the columns of a column
-// block, interleaved in global memory), else consecutive butterflies of one
-// line.  buf is only read, so there is no barrier.
-template <int N, int L, bool INV, bool LINE_FAST, class St>
+// block, interleaved in global memory; the pass before must end with a CTA
+// barrier); G: grouped (see stockham_pass); else consecutive butterflies of
+// the whole set.  buf is only read, so there is no barrier.
+template <int N, int L, bool INV, bool LINE_FAST, bool G, class St>
 __device__ __forceinline__ void fft_last_pass(const float2 *buf, const float2 *__restrict__ tw,
                                               St st) {
     constexpr int PASS = fft_passes(N) - 1;
     constexpr int P = fft_radix(N, PASS), NS = fft_ns(N, PASS);
     static_assert(NS * P == N && NS > 1, "the last pass of the plan");
+    static_assert(!(LINE_FAST && G), "one thread mapping");
     constexpr int NB = N / P;
     constexpr int TOT = L * NB;
     constexpr int PER = (TOT + kThreads - 1) / kThreads;
     constexpr int LS = line_stride(N);
     const float2 *__restrict__ t = tw + fft_twoff(N, PASS);
     float2 v[PER][P];
+    auto which = [](int q, int &l, int &j) {
+        if constexpr (LINE_FAST) {
+            const int b = threadIdx.x + q * kThreads;
+            l = b % L;
+            j = b / L;
+        } else {
+            butterfly_of<L, NB, G>(q, l, j);
+        }
+    };
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
-        const int b = threadIdx.x + q * kThreads;
-        if (TOT % kThreads == 0 || b < TOT) {
-            const int l = LINE_FAST ? b % L : b / NB, j = LINE_FAST ? b / L : b % NB;
+        int l, j;
+        which(q, l, j);
+        if (G || TOT % kThreads == 0 || threadIdx.x + q * kThreads < TOT) {
             if constexpr (NB % 16 == 0) {
                 const float2 *src = buf + l * LS + pad16(j);
 #pragma unroll
@@ -275,9 +331,9 @@ __device__ __forceinline__ void fft_last_pass(const float2 *buf, const float2 *_
     }
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
-        const int b = threadIdx.x + q * kThreads;
-        if (TOT % kThreads == 0 || b < TOT) {
-            const int l = LINE_FAST ? b % L : b / NB, j = LINE_FAST ? b / L : b % NB;
+        int l, j;
+        which(q, l, j);
+        if (G || TOT % kThreads == 0 || threadIdx.x + q * kThreads < TOT) {
 #pragma unroll
             for (int r = 1; r < P; ++r) {
                 const float2 w = __ldg(t + (r - 1) * NS + j);

@@ -23,6 +23,10 @@ namespace osog {
 
 namespace {
 
+// The FFT passes of the sets of 8192 samples run with one thread group per
+// line (named barriers) instead of CTA-wide barriers.
+constexpr bool kGroupFft = true;
+
 // One strip (rows [strip R, strip R + R)) of scene s.
 template <int N, int MODE, bool SQ = false>
 __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, int strip,
@@ -88,17 +92,18 @@ __device__ __forceinline__ void strip_forward_item(const StripArgs &a, int s, in
         // the exit wave of the accumulated words is formed as the first FFT
         // pass loads them, and the last pass stores G (column-blocked, only
         // the columns some pupil passes)
-        fft_first_pass<N, L, false, true>(buf, [&](int l, int x) -> float2 {
+        constexpr bool GRP = kGroupFft && fft_grouped(N);
+        fft_first_pass<N, L, false, true, GRP>(buf, [&](int l, int x) -> float2 {
             return l < R ? exit_wave_fixed(*reinterpret_cast<const uint2 *>(buf + l * LS + pad16(x)))
                          : make_float2(0.f, 0.f);
         });
-        fft_pass_range<N, L, false, 1, fft_passes(N) - 1>(buf, a.tw);
+        fft_pass_range<N, L, false, 1, fft_passes(N) - 1, GRP>(buf, a.tw);
         const int B = SQ ? sq_rb(N) : geo.B;
         const int lb = SQ ? clog2(sq_rb(N)) : ilog2(B);
         const int H = SQ ? N : geo.H;
         float2 *G = a.w.G + (size_t)s * H * N;
         const int2 cr = a.w.colrange[s];
-        fft_last_pass<N, L, false, false>(buf, a.tw, [&](int l, int kx, float2 v) {
+        fft_last_pass<N, L, false, false, GRP>(buf, a.tw, [&](int l, int kx, float2 v) {
             const int fx = kx < N / 2 ? kx : kx - N;
             if (l < R && fx >= cr.x && fx <= cr.y)  // columns outside every pupil are never read
                 G[((size_t)(kx >> lb) * H + y0 + l) * B + (kx & (B - 1))] = v;
@@ -353,6 +358,7 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
     static_assert(!BULK || (SQ && N >= 1024), "bulk staging needs full column blocks");
     __shared__ uint64_t bar;  // completes the bulk copy (BULK)
     const bool bulk = BULK && !a.unit_input;
+    constexpr bool GRP = kGroupFft && fft_grouped(N);
     if (bulk) {
         if constexpr (BULK)
             if (threadIdx.x == 0)
@@ -392,7 +398,8 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
             }
             bulk_wait(&bar, a.w.status, a.wait_polls);
             first_pass_from_block<N, false>(buf0, live);
-            fft_lines<N, L, false, 1>(buf0, a.tw);
+            fft_pass_range<N, L, false, 1, fft_passes(N), GRP>(buf0, a.tw);
+            if constexpr (GRP) __syncthreads();  // every line done before any thread reads another's
         }
     } else if (!a.unit_input) {
         fft_lines<N, L, false>(buf0, a.tw);
@@ -426,7 +433,7 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
                 }
                 return make_float2(0.f, 0.f);
             };
-            fft_first_pass<N, L, true, !MULTI>(buf1, ld);
+            fft_first_pass<N, L, true, !MULTI, GRP>(buf1, ld);
         } else {
             if (md.op == kOpLoss) {
                 loss_columns<N>(a, s, bk, B, W, buf0, buf1);
@@ -447,10 +454,11 @@ __device__ __forceinline__ void column_item(const ColumnArgs &a, int s, int bk,
             __syncthreads();
             fft_pass_range<N, L, true, 0, 1>(buf1, a.tw);
         }
-        fft_pass_range<N, L, true, 1, fft_passes(N) - 1>(buf1, a.tw);
+        fft_pass_range<N, L, true, 1, fft_passes(N) - 1, GRP>(buf1, a.tw);
+        if constexpr (GRP) __syncthreads();
         // the last pass stores Q; consecutive threads take the block's
         // columns, so a warp writes whole rows of the block
-        fft_last_pass<N, L, true, true>(buf1, a.tw, [&](int c, int y, float2 v) {
+        fft_last_pass<N, L, true, true, false>(buf1, a.tw, [&](int c, int y, float2 v) {
             if (c < B) Qm[(size_t)y * B + c] = v;
         });
         __syncthreads();
@@ -481,16 +489,17 @@ __device__ __forceinline__ void inverse_item(const InverseArgs &a, int sm, int s
     // the first pass reads the strip's rows of Q straight from global memory
     // (columns that no pupil passes, and lines past the strip, read as zero);
     // the last pass writes the intensity rows
-    fft_first_pass<N, L, true, false>(buf, [&](int l, int kx) -> float2 {
+    constexpr bool GRP = kGroupFft && fft_grouped(N);
+    fft_first_pass<N, L, true, false, GRP>(buf, [&](int l, int kx) -> float2 {
         const int fx = kx < N / 2 ? kx : kx - N;
         return l < R && fx >= cr.x && fx <= cr.y
                    ? Qm[((size_t)(kx >> lb) * H + y0 + l) * B + (kx & (B - 1))]
                    : make_float2(0.f, 0.f);
     });
-    fft_pass_range<N, L, true, 1, fft_passes(N) - 1>(buf, a.tw);
+    fft_pass_range<N, L, true, 1, fft_passes(N) - 1, GRP>(buf, a.tw);
     float *img = a.images + ((size_t)sm * H + y0) * N;
     const int real_out = a.real_out;
-    fft_last_pass<N, L, true, false>(buf, a.tw, [&](int l, int x, float2 v) {
+    fft_last_pass<N, L, true, false, GRP>(buf, a.tw, [&](int l, int x, float2 v) {
         if (l < R) img[(size_t)l * N + x] = real_out ? v.x : fmaf(v.x, v.x, __fmul_rn(v.y, v.y));
     });
 }

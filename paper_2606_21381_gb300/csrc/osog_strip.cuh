@@ -422,6 +422,9 @@ __device__ __forceinline__ float2 exit_wave(float opd, float att, float two_over
 // Every product that could be contracted into a fused multiply-add is
 // written out (rounded product or fmaf), so that all kernels round alike.
 __device__ __forceinline__ float2 transfer(const ModeDev &md, int fx, int fy) {
+    // in focus and not DIC: the pupil is the constant scale (sin 0 and
+    // cos 0 are exact, so this is the value the general path gives)
+    if (md.dz == 0.f && !md.dic) return make_float2(md.scale, 0.f);
     const float kx = __fmul_rn((float)fx, md.kstep_x), ky = __fmul_rn((float)fy, md.kstep_y);
     const float qx = __fadd_rn(kx, md.qoff_x), qy = __fadd_rn(ky, md.qoff_y);
     const float q2 = fmaf(qx, qx, __fmul_rn(qy, qy));
