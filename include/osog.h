@@ -390,10 +390,10 @@ int osog_batch_submit(osog_plan_t *plan, const float *soa_all, int64_t ld,
  * Autotuner of the batched path.  For this batch shape it measures, for
  * each candidate band height (the smallest valid one and up to three
  * doublings), the exact particle-band pairs per particle the batch needs (a
- * binning dry run), then times the batch three times with three launches
+ * binning dry run), then times the batch five times with three launches
  * per group (the raster inside the strip pass, and in a tile kernel of its
  * own) and, on square canvases, with the persistent launch, and keeps the
- * fastest.  The choice is stored in the plan for (S, total particles,
+ * candidate with the fastest median.  The choice is stored in the plan for (S, total particles,
  * K) and used by later osog_batch_submit calls of that shape whose tuning
  * leaves the fields at 0; it is also written to *out when out is not NULL.
  * Arguments as for osog_batch_submit; images receive a valid render.  This

@@ -5,6 +5,7 @@
 
 #include <mutex>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "osog_fft.cuh"
@@ -1057,8 +1058,8 @@ int osog_autotune(osog_plan_t *p, const float *soa_all, int64_t ld, const int32_
         for (int mode = 0; mode < (p->H == p->W ? 3 : 2); ++mode) {
             o.persistent = mode == 2;       // one persistent launch
             o.raster_tiles = mode == 1;     // the raster in a kernel of its own
-            float t[3];
-            for (int r = 0; r < 3 && rc == OSOG_OK; ++r) {
+            float t[5];
+            for (int r = 0; r < 5 && rc == OSOG_OK; ++r) {
                 cudaEventRecord(e0, st);
                 rc = batch_enqueue(p, soa_all, ld, offsets, S, optics, images, K, o, ws, ws_bytes, st);
                 cudaEventRecord(e1, st);
@@ -1066,8 +1067,8 @@ int osog_autotune(osog_plan_t *p, const float *soa_all, int64_t ld, const int32_
                     rc = fail(OSOG_ERR_CUDA, "autotune timing");
             }
             if (rc) break;
-            const float med = t[0] + t[1] + t[2] - fminf(t[0], fminf(t[1], t[2])) -
-                              fmaxf(t[0], fmaxf(t[1], t[2]));
+            std::sort(t, t + 5);
+            const float med = t[2];
             if (med < best) {
                 best = med;
                 chosen = o;

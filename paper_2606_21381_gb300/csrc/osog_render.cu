@@ -173,7 +173,10 @@ __global__ void __launch_bounds__(kRThreads, 4) k_raster_tiles(const __grid_cons
     const int32_t *off = a.w.band_off + (size_t)s * (geo.nbands + 1);
     const int hi = min(off[band + 1], sc.pair_cap);
     const int lo = min(off[band], hi);
-    auto slot = [acc, TW, tx0](int row, int x) -> void * { return acc + row * TW + (x - tx0); };
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(acc);
+    auto slot = [base, TW, tx0](int row, int x) -> uint32_t {
+        return base + (uint32_t)(row * TW + (x - tx0)) * 8u;
+    };
     raster_region<kRThreads, kAccPhase>(a.w, a.w.pairs + sc.pair0, lo, hi, ty0, TH, tx0,
                                         tx0 + TW - 1, 0.5f * sc.two_over_lambda, slot, scratch);
     __syncthreads();

@@ -189,24 +189,29 @@ __device__ __forceinline__ float item_chord(const RowItem &it, int kind, float X
 }
 
 // Adds one particle's contribution at chord t > 0 to the pixel's accumulators
-// (phase mode: a uint2 slot, x the phase, y the absorption exponent).
+// at shared-memory address acc (phase mode: a uint2 slot, x the phase, y the
+// absorption exponent; OPD mode: two int64).  The additions are shared-space
+// reductions issued on the slot's shared address (no generic addressing, no
+// returned value).
 template <int ACC>
-__device__ __forceinline__ void deposit(void *acc, float t, float dn, float mu) {
+__device__ __forceinline__ void deposit(uint32_t acc, float t, float dn, float mu) {
     if constexpr (ACC == kAccPhase) {
-        uint32_t *a = static_cast<uint32_t *>(acc);
         const float c = t * dn;                   // cycles
         const float r = c - rintf(c);             // in [-1/2, 1/2]
         // round(r 2^23) from the mantissa of r 2^23 + 1.5 2^23
         const int q = __float_as_int(fmaf(r, 8388608.f, 12582912.f)) - 0x4B400000;
-        atomicAdd(a, (uint32_t)q);
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(acc), "r"(q) : "memory");
         if (mu != 0.f) {
             const float x = fminf(fmaxf(t * mu, -16.f), 16.f) * 1048576.f;
-            atomicAdd(reinterpret_cast<int *>(a + 1), __float2int_rn(x));
+            asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(acc + 4u), "r"(__float2int_rn(x))
+                         : "memory");
         }
     } else {
-        unsigned long long *a = static_cast<unsigned long long *>(acc);
-        atomicAdd(a, (unsigned long long)__float2ll_rn(t * dn * 4294967296.f));
-        if (mu != 0.f) atomicAdd(a + 1, (unsigned long long)__float2ll_rn(t * mu * 4294967296.f));
+        asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(acc),
+                     "l"((unsigned long long)__float2ll_rn(t * dn * 4294967296.f)) : "memory");
+        if (mu != 0.f)
+            asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(acc + 8u),
+                         "l"((unsigned long long)__float2ll_rn(t * mu * 4294967296.f)) : "memory");
     }
 }
 
@@ -265,15 +270,18 @@ __host__ __device__ constexpr size_t raster_smem() {
 // its own groups of 32 list entries (the first NT / 32 groups in warp
 // order, the rest handed out by a shared counter as warps finish), with no
 // CTA barrier until the end:
-//   1. the entries whose rectangle meets the region and the region rows each
-//      covers, and a warp prefix sum of those row counts;
+//   1. the entries whose rectangle meets the region, compacted with the
+//      ellipsoids first, the region rows each covers, and a warp prefix sum
+//      of those row counts;
 //   2. waves of 32 (particle, row) items, one per lane (the owning entry
 //      found by a search over the prefix), built from the particle's
 //      row-span constants into the warp's item slots;
 //   3. the wave's pixels cut into chunks of up to kChunkPx, ellipsoid items'
 //      chunks first so that most passes run one chord formula; lane l of a
 //      pass takes chunk l and evaluates its pixels as independent unrolled
-//      chains, adding each covered pixel with integer shared atomics.
+//      chains, adding each covered pixel with integer shared-memory
+//      reductions (a step past the chunk or outside the footprint adds zero,
+//      so the pass has no branch around them).
 // Every thread of the CTA must call it; it ends with a CTA barrier.
 template <int NT, int ACC, typename Slot>
 __device__ void raster_region(const Work &w, const int32_t *ids, int lo, int hi, int ty0,
@@ -289,16 +297,44 @@ __device__ void raster_region(const Work &w, const int32_t *ids, int lo, int hi,
     while (base < hi) {
         int nb = 0;
         if (lane == 0) nb = atomicAdd(next, 32);
-        // 1. the group's entries that meet the region
-        const int i = base + lane;
+        // 1. the group's entries that meet the region, compacted through the
+        //    warp's item slots with the ellipsoids first (so that most waves
+        //    below build items of one kind)
         int id = 0, nr = 0, ry0 = 0, rx0 = 0, rx1 = 0;
-        if (i < hi) {
-            id = ids[i];
-            const Rect q = w.rect[id];
-            ry0 = max((int)q.y0, ty0);
-            rx0 = max((int)q.x0, tx0);
-            rx1 = min((int)q.x1, tx1);
-            nr = rx0 <= rx1 ? max(min((int)q.y1, tyl) - ry0 + 1, 0) : 0;
+        {
+            const int i = base + lane;
+            bool ell = false;
+            if (i < hi) {
+                id = ids[i];
+                const Rect q = w.rect[id];
+                ry0 = max((int)q.y0, ty0);
+                rx0 = max((int)q.x0, tx0);
+                rx1 = min((int)q.x1, tx1);
+                nr = rx0 <= rx1 ? max(min((int)q.y1, tyl) - ry0 + 1, 0) : 0;
+                if (nr > 0) ell = w.rrec[id].kind == 0;
+            }
+            const unsigned lt = lanemask_lt();
+            const unsigned me = __ballot_sync(kFull, ell), mo = __ballot_sync(kFull, nr > 0 && !ell);
+            const int ne = __popc(me);
+            int4 *tmp = reinterpret_cast<int4 *>(items);
+            int *tnr = reinterpret_cast<int *>(tmp + 32);
+            if (nr > 0) {
+                const int pos = ell ? __popc(me & lt) : ne + __popc(mo & lt);
+                tmp[pos] = make_int4(id, ry0, rx0, rx1);
+                tnr[pos] = nr;
+            }
+            __syncwarp();
+            const int kept = ne + __popc(mo);
+            nr = 0;
+            if (lane < kept) {
+                const int4 e = tmp[lane];
+                id = e.x;
+                ry0 = e.y;
+                rx0 = e.z;
+                rx1 = e.w;
+                nr = tnr[lane];
+            }
+            __syncwarp();  // the slots are read before the first wave writes them
         }
         const int inc = warp_incl_scan(nr);
         const int ex = inc - nr;
@@ -331,7 +367,7 @@ __device__ void raster_region(const Work &w, const int32_t *ids, int lo, int hi,
                 const int k = warp_owner(cinc, key, sh, 0xFFFF);
                 const int kex = (__shfl_sync(kFull, cex, k) >> sh) & 0xFFFF;
                 if (c < TC) {
-                    const RowItem rit = items[k];  // registers: the atomics below may not alias it
+                    const RowItem rit = items[k];  // registers: the reductions below may not alias it
                     const uint32_t h = rit.hdr;
                     const int j0 = (int)(h & 0xFFFu), cnt = (int)((h >> 12) & 0xFFFu);
                     const int kind = (int)((h >> 24) & 3u);
@@ -353,9 +389,13 @@ __device__ void raster_region(const Work &w, const int32_t *ids, int lo, int hi,
                             t[u] = u < len ? item_chord(rit, 2, (float)(x0 + u) + 0.5f, w.plane_coef)
                                            : -1.f;
                     }
+                    // every step deposits (zero at the chunk's first pixel when the
+                    // pixel is past the chunk or outside the footprint): no branch
 #pragma unroll
-                    for (int u = 0; u < kChunkPx; ++u)
-                        if (u < len && t[u] > 0.f) deposit<ACC>(slot(rit.row, x0 + u), t[u], rit.dn, rit.mu);
+                    for (int u = 0; u < kChunkPx; ++u) {
+                        const bool on = u < len && t[u] > 0.f;
+                        deposit<ACC>(slot(rit.row, on ? x0 + u : x0), on ? t[u] : 0.f, rit.dn, rit.mu);
+                    }
                 }
             }
             __syncwarp();  // the wave's items are read before the next wave writes
@@ -375,11 +415,10 @@ __device__ void raster_strip(const Geometry &geo, const Work &w, const SceneDev 
     const int32_t *off = w.band_off + (size_t)s * (geo.nbands + 1);
     const int hi = min(off[band + 1], sc.pair_cap);
     const int lo = min(off[band], hi);
-    auto slot = [acc](int row, int x) -> void * {
-        if constexpr (ACC == kAccPhase)
-            return reinterpret_cast<uint2 *>(acc) + row * LS + pad16(x);
-        else
-            return reinterpret_cast<ulonglong2 *>(acc) + row * LS + pad16(x);
+    // shared address of the (row, x) slot: uint2 (phase) or two int64 (OPD)
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(acc);
+    auto slot = [base](int row, int x) -> uint32_t {
+        return base + (uint32_t)(row * LS + pad16(x)) * (ACC == kAccPhase ? 8u : 16u);
     };
     raster_region<kThreads, ACC>(w, w.pairs + sc.pair0, lo, hi, y0, R, 0, geo.W - 1,
                                  0.5f * sc.two_over_lambda, slot, scratch);
