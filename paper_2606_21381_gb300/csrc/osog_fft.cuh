@@ -165,6 +165,53 @@ __device__ __forceinline__ void butterfly_of(int q, int &l, int &j) {
     }
 }
 
+// Largest radix whose twiddles are formed as products (0: all read from the
+// table).  A radix-P pass needs w^{r k}, r = 1..P-1: the table entries at
+// r = 1, 2, 4 (and 8) are read and the others formed as products of two of
+// them, which takes those reads off the load path at the cost of a few
+// fused multiply-adds and a rounding error of a few units in the last place.
+constexpr int kTwiddleProducts = 16;
+
+// v[r] *= w^{r k} (conjugated for the inverse transform), r = 1..P-1, with
+// t the pass's table at entry [0][k] (entries [r - 1][k] at stride NS).
+template <int P, bool INV, int NS>
+__device__ __forceinline__ void apply_twiddles(float2 *v, const float2 *__restrict__ t) {
+    auto mul = [](float2 a, float2 w) { return INV ? cmulc(a, w) : cmul(a, w); };
+    if constexpr (P == 8 && kTwiddleProducts >= 8) {
+        const float2 w1 = __ldg(t), w2 = __ldg(t + NS), w4 = __ldg(t + 3 * NS);
+        const float2 w3 = cmul(w2, w1);
+        v[1] = mul(v[1], w1);
+        v[2] = mul(v[2], w2);
+        v[3] = mul(v[3], w3);
+        v[4] = mul(v[4], w4);
+        v[5] = mul(v[5], cmul(w4, w1));
+        v[6] = mul(v[6], cmul(w4, w2));
+        v[7] = mul(v[7], cmul(w4, w3));
+    } else if constexpr (P == 16 && kTwiddleProducts >= 16) {
+        const float2 w1 = __ldg(t), w2 = __ldg(t + NS), w4 = __ldg(t + 3 * NS),
+                     w8 = __ldg(t + 7 * NS);
+        const float2 w3 = cmul(w2, w1), w5 = cmul(w4, w1), w6 = cmul(w4, w2), w7 = cmul(w4, w3);
+        v[1] = mul(v[1], w1);
+        v[2] = mul(v[2], w2);
+        v[3] = mul(v[3], w3);
+        v[4] = mul(v[4], w4);
+        v[5] = mul(v[5], w5);
+        v[6] = mul(v[6], w6);
+        v[7] = mul(v[7], w7);
+        v[8] = mul(v[8], w8);
+        v[9] = mul(v[9], cmul(w8, w1));
+        v[10] = mul(v[10], cmul(w8, w2));
+        v[11] = mul(v[11], cmul(w8, w3));
+        v[12] = mul(v[12], cmul(w8, w4));
+        v[13] = mul(v[13], cmul(w8, w5));
+        v[14] = mul(v[14], cmul(w8, w6));
+        v[15] = mul(v[15], cmul(w8, w7));
+    } else {
+#pragma unroll
+        for (int r = 1; r < P; ++r) v[r] = mul(v[r], __ldg(t + (r - 1) * NS));
+    }
+}
+
 // One Stockham pass over L lines of N points.  G: one thread group per line
 // (fft_grouped(N)); the pass then synchronises only the line's group.
 template <int N, int L, int P, int NS, bool INV, bool G = false>
@@ -200,14 +247,7 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restr
         butterfly_of<L, NB, G>(q, l, j);
         if (G || TOT % kThreads == 0 || threadIdx.x + q * kThreads < TOT) {
             const int k = j & (NS - 1);
-            if constexpr (NS > 1) {
-                const float2 *t = tw + k;  // this pass's table, entry [r - 1][k]
-#pragma unroll
-                for (int r = 1; r < P; ++r) {
-                    const float2 w = __ldg(t + (r - 1) * NS);
-                    v[q][r] = INV ? cmulc(v[q][r], w) : cmul(v[q][r], w);
-                }
-            }
+            if constexpr (NS > 1) apply_twiddles<P, INV, NS>(v[q], tw + k);  // entries [r - 1][k]
             dft<P, INV>(v[q]);
             float2 *dst = buf + l * LS + pad16((j - k) * P + k);
 #pragma unroll
@@ -334,11 +374,7 @@ __device__ __forceinline__ void fft_last_pass(const float2 *buf, const float2 *_
         int l, j;
         which(q, l, j);
         if (G || TOT % kThreads == 0 || threadIdx.x + q * kThreads < TOT) {
-#pragma unroll
-            for (int r = 1; r < P; ++r) {
-                const float2 w = __ldg(t + (r - 1) * NS + j);
-                v[q][r] = INV ? cmulc(v[q][r], w) : cmul(v[q][r], w);
-            }
+            apply_twiddles<P, INV, NS>(v[q], t + j);
             dft<P, INV>(v[q]);
 #pragma unroll
             for (int r = 0; r < P; ++r) st(l, j + r * NS, v[q][r]);
