@@ -81,7 +81,7 @@ constexpr size_t kMaxKept = 64;  // forward states remembered per plan
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t rec, rrec, rect, cnt, band_off, pairs, G, Q, colrange, ctr, total;
+    size_t rec, rrec, rect, cnt, band_off, pairs, pair_rect, G, Q, colrange, ctr, total;
 };
 
 // Workspace regions for a launch group of up to S scenes, n records,
@@ -102,6 +102,8 @@ Layout make_layout(const Geometry &geo, int64_t n, int64_t nchunks, int S, int K
     o = align256(o + (size_t)S * (geo.nbands + 1) * sizeof(int32_t));
     l.pairs = o;
     o = align256(o + (size_t)pair_total * sizeof(int32_t));
+    l.pair_rect = o;
+    o = align256(o + (size_t)pair_total * sizeof(Rect));
     l.G = o;
     o = align256(o + (size_t)S * geo.H * geo.W * sizeof(float2));
     l.Q = o;
@@ -123,6 +125,7 @@ Work carve(void *ws, const Layout &l, int32_t *status) {
     w.cnt = reinterpret_cast<int32_t *>(b + l.cnt);
     w.band_off = reinterpret_cast<int32_t *>(b + l.band_off);
     w.pairs = reinterpret_cast<int32_t *>(b + l.pairs);
+    w.pair_rect = reinterpret_cast<Rect *>(b + l.pair_rect);
     w.G = reinterpret_cast<float2 *>(b + l.G);
     w.Q = reinterpret_cast<float2 *>(b + l.Q);
     w.colrange = reinterpret_cast<int2 *>(b + l.colrange);

@@ -324,7 +324,12 @@ k_bin_fill(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
     for (int i = threadIdx.x; i < (kChunk / 32) * kMaxBands; i += kChunk) (&wpre[0][0])[i] = 0;
     for (int b = threadIdx.x; b < geo.nbands; b += kChunk) start[b] = off[b] + pre[b];
     int b0 = 1, b1 = 0;
-    if (mine) band_range(w.rect[p], geo.BH, b0, b1);
+    Rect pr{};
+    if (mine) {
+        pr = w.rect[p];
+        band_range(pr, geo.BH, b0, b1);
+        if (b0 <= b1) pr.x1 = (int16_t)(pr.x1 | (w.rrec[p].kind << 12));
+    }
     __syncthreads();
     const bool any = b0 <= b1;
     const int lo = __reduce_min_sync(0xffffffffu, any ? b0 : kMaxBands);
@@ -350,7 +355,10 @@ k_bin_fill(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
         const unsigned m = __ballot_sync(0xffffffffu, in);
         if (in) {
             const int slot = start[b] + wpre[warp][b] + __popc(m & lt);
-            if (slot < sc.pair_cap) w.pairs[sc.pair0 + slot] = p;
+            if (slot < sc.pair_cap) {
+                w.pairs[sc.pair0 + slot] = p;
+                if (w.pair_rect) w.pair_rect[sc.pair0 + slot] = pr;
+            }
             if (w.slotmap && b - b0 < w.slotmap_ppp)
                 w.slotmap[(size_t)p * w.slotmap_ppp + (b - b0)] = slot < sc.pair_cap ? slot : -1;
         }
@@ -374,10 +382,13 @@ k_bin_single(const float *__restrict__ soa, int64_t ld, const __grid_constant__ 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < (kChunk / 32) * kMaxBands; i += kChunk) (&wpre[0][0])[i] = 0;
     int b0 = 1, b1 = 0;
+    Rect pr{};
     if (mine) {
         const Rect r = setup_particle(soa, ld, p, sc, geo, w);
         w.rect[p] = r;
         band_range(r, geo.BH, b0, b1);
+        pr = r;
+        if (b0 <= b1) pr.x1 = (int16_t)(pr.x1 | (w.rrec[p].kind << 12));
     }
     __syncthreads();
     const bool any = b0 <= b1;
@@ -433,7 +444,10 @@ k_bin_single(const float *__restrict__ soa, int64_t ld, const __grid_constant__ 
         const unsigned m = __ballot_sync(0xffffffffu, in);
         if (in) {
             const int slot = start[b] + wpre[warp][b] + __popc(m & lt);
-            if (slot < sc.pair_cap) w.pairs[sc.pair0 + slot] = p;
+            if (slot < sc.pair_cap) {
+                w.pairs[sc.pair0 + slot] = p;
+                if (w.pair_rect) w.pair_rect[sc.pair0 + slot] = pr;
+            }
             if (w.slotmap && b - b0 < w.slotmap_ppp)
                 w.slotmap[(size_t)p * w.slotmap_ppp + (b - b0)] = slot < sc.pair_cap ? slot : -1;
         }

@@ -207,6 +207,8 @@ struct Work {
     int32_t *cnt;       // [nchunks][nbands]: counts, then exclusive prefix
     int32_t *band_off;  // [S][nbands + 1]
     int32_t *pairs;     // record indices, per band, ascending
+    Rect *pair_rect = nullptr;  // per pair slot: the record's rectangle, its kind in bits
+                        // 12-13 of x1 (null: readers gather rect[] and rrec[])
     float2 *G;          // [S][W/B][H][B] row spectra
     float2 *Q;          // [S][K][W/B][H][B] filtered columns
     int2 *colrange;     // [S] signed column frequencies [lo, hi] outside which no

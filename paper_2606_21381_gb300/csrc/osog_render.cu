@@ -177,7 +177,8 @@ __global__ void __launch_bounds__(kRThreads, 4) k_raster_tiles(const __grid_cons
     auto slot = [base, TW, tx0](int row, int x) -> uint32_t {
         return base + (uint32_t)(row * TW + (x - tx0)) * 8u;
     };
-    raster_region<kRThreads, kAccPhase>(a.w, a.w.pairs + sc.pair0, lo, hi, ty0, TH, tx0,
+    raster_region<kRThreads, kAccPhase>(a.w, a.w.pairs + sc.pair0,
+                                        a.w.pair_rect ? a.w.pair_rect + sc.pair0 : nullptr, lo, hi, ty0, TH, tx0,
                                         tx0 + TW - 1, 0.5f * sc.two_over_lambda, slot, scratch);
     __syncthreads();
     // the tile's rows, two pixels per 16-byte store

@@ -265,7 +265,8 @@ __host__ __device__ constexpr size_t raster_smem() {
 
 // OPD and ATT of the region rows [ty0, ty0 + nrows) x columns [tx0, tx1]
 // of scene s from the band list entries [lo, hi) (ids of the scene's
-// records), added into the accumulators that slot(row, x) addresses (zeroed
+// records; prect, when not null, the entries' rectangles with their kinds,
+// else they are gathered by id), added into the accumulators that slot(row, x) addresses (zeroed
 // by the caller; kAccPhase: uint2, kAccOpd: two int64).  Each warp works on
 // its own groups of 32 list entries (the first NT / 32 groups in warp
 // order, the rest handed out by a shared counter as warps finish), with no
@@ -284,9 +285,9 @@ __host__ __device__ constexpr size_t raster_smem() {
 //      so the pass has no branch around them).
 // Every thread of the CTA must call it; it ends with a CTA barrier.
 template <int NT, int ACC, typename Slot>
-__device__ void raster_region(const Work &w, const int32_t *ids, int lo, int hi, int ty0,
-                              int nrows, int tx0, int tx1, float inv_lambda, Slot slot,
-                              unsigned char *scratch) {
+__device__ void raster_region(const Work &w, const int32_t *ids, const Rect *prect, int lo,
+                              int hi, int ty0, int nrows, int tx0, int tx1, float inv_lambda,
+                              Slot slot, unsigned char *scratch) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     RowItem *items = reinterpret_cast<RowItem *>(scratch) + warp * 32;
     int *next = reinterpret_cast<int *>(reinterpret_cast<RowItem *>(scratch) + NT);
@@ -306,12 +307,21 @@ __device__ void raster_region(const Work &w, const int32_t *ids, int lo, int hi,
             bool ell = false;
             if (i < hi) {
                 id = ids[i];
-                const Rect q = w.rect[id];
+                Rect q;
+                int kind = 0;
+                if (prect) {  // the slot's copy: one coalesced load, the kind packed in
+                    q = prect[i];
+                    kind = (q.x1 >> 12) & 3;
+                    q.x1 = (int16_t)(q.x1 & 0xFFF);
+                } else {
+                    q = w.rect[id];
+                }
                 ry0 = max((int)q.y0, ty0);
                 rx0 = max((int)q.x0, tx0);
                 rx1 = min((int)q.x1, tx1);
                 nr = rx0 <= rx1 ? max(min((int)q.y1, tyl) - ry0 + 1, 0) : 0;
-                if (nr > 0) ell = w.rrec[id].kind == 0;
+                if (nr > 0 && !prect) kind = w.rrec[id].kind;
+                ell = nr > 0 && kind == 0;
             }
             const unsigned lt = lanemask_lt();
             const unsigned me = __ballot_sync(kFull, ell), mo = __ballot_sync(kFull, nr > 0 && !ell);
@@ -420,8 +430,9 @@ __device__ void raster_strip(const Geometry &geo, const Work &w, const SceneDev 
     auto slot = [base](int row, int x) -> uint32_t {
         return base + (uint32_t)(row * LS + pad16(x)) * (ACC == kAccPhase ? 8u : 16u);
     };
-    raster_region<kThreads, ACC>(w, w.pairs + sc.pair0, lo, hi, y0, R, 0, geo.W - 1,
-                                 0.5f * sc.two_over_lambda, slot, scratch);
+    raster_region<kThreads, ACC>(w, w.pairs + sc.pair0, w.pair_rect ? w.pair_rect + sc.pair0 : nullptr,
+                                 lo, hi, y0, R, 0, geo.W - 1, 0.5f * sc.two_over_lambda, slot,
+                                 scratch);
 }
 
 // Elements of an n-point transform's set handled by each thread in the copy
