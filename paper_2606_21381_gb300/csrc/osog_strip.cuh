@@ -51,7 +51,7 @@ struct __align__(16) RowItem {
                     // polyhedron: cx, ey, plane offset, plane count (int bits)
     int32_t row;    // row in the rasterised region
     float dn;       // kAccPhase: dn / lambda (cycles per um); kAccOpd: dn
-    float mu;
+    float mu;       // kAccPhase: mu in units of 2^-20 per um; kAccOpd: mu
 };
 static_assert(sizeof(RowItem) == 48, "RowItem is 48 bytes");
 
@@ -141,8 +141,13 @@ __device__ __forceinline__ bool make_row_item(const RRec &r, int c0, int c1, int
     }
     it.hdr = (uint32_t)j0 | ((uint32_t)(j1 - j0 + 1) << 12) | ((uint32_t)r.kind << 24);
     it.row = row;
-    it.dn = ACC == kAccPhase ? r.dn * inv_lambda : r.dn;
-    it.mu = r.mu;
+    if constexpr (ACC == kAccPhase) {
+        it.dn = r.dn * inv_lambda;
+        it.mu = r.mu * 1048576.f;  // the exponent's unit folded in (exact: a power of two)
+    } else {
+        it.dn = r.dn;
+        it.mu = r.mu;
+    }
     return true;
 }
 
@@ -189,10 +194,11 @@ __device__ __forceinline__ float item_chord(const RowItem &it, int kind, float X
 }
 
 // Adds one particle's contribution at chord t > 0 to the pixel's accumulators
-// at shared-memory address acc (phase mode: a uint2 slot, x the phase, y the
-// absorption exponent; OPD mode: two int64).  The additions are shared-space
-// reductions issued on the slot's shared address (no generic addressing, no
-// returned value).
+// at shared-memory address acc (phase mode: a uint2 slot, x the phase in
+// 2^-23 cycles, y the absorption exponent in 2^-20; OPD mode: two int64 in
+// 2^-32 um).  dn and mu are the item's (phase mode: dn / lambda in cycles
+// per um, mu already in 2^-20 per um).  The additions are shared-space reductions issued on the slot's
+// shared address (no generic addressing, no returned value).
 template <int ACC>
 __device__ __forceinline__ void deposit(uint32_t acc, float t, float dn, float mu) {
     if constexpr (ACC == kAccPhase) {
@@ -202,7 +208,7 @@ __device__ __forceinline__ void deposit(uint32_t acc, float t, float dn, float m
         const int q = __float_as_int(fmaf(r, 8388608.f, 12582912.f)) - 0x4B400000;
         asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(acc), "r"(q) : "memory");
         if (mu != 0.f) {
-            const float x = fminf(fmaxf(t * mu, -16.f), 16.f) * 1048576.f;
+            const float x = fminf(fmaxf(t * mu, -16777216.f), 16777216.f);  // |mu t| <= 16
             asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(acc + 4u), "r"(__float2int_rn(x))
                          : "memory");
         }
