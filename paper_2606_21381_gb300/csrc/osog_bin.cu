@@ -268,6 +268,14 @@ k_bin_count(const float *__restrict__ soa, int64_t ld, const __grid_constant__ G
     }
 }
 
+// Scan of one scene's band counts (CTA s): for every band (two per warp at
+// 64 bands) the exclusive prefix over the scene's chunks, in place; then
+// the bands' starts and the scene's column hull.  Each lane keeps up to
+// kScanLoads chunk counts of a band in registers, all loaded before the
+// warp scans them, so a scene of many chunks pays one load latency per
+// kScanLoads * 32 chunks instead of one per 32.
+constexpr int kScanLoads = 8;
+
 __global__ void __launch_bounds__(1024)
 k_bin_scan(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
     __shared__ int total[kMaxBands];
@@ -276,35 +284,52 @@ k_bin_scan(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
     const SceneDev &sc = gd.sc[s];
     const int nch = (s + 1 < gd.S ? gd.sc[s + 1].chunk0 : gd.nchunks) - sc.chunk0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 992)  // lane 0 of the last warp, the one with the fewest bands
+        w.colrange[s] = column_hull(gd, s, geo);
     for (int b = warp; b < geo.nbands; b += 32) {
+        int32_t *col = w.cnt + (int64_t)sc.chunk0 * geo.nbands + b;  // chunk c at c * nbands
         int run = 0;
-        for (int c0 = 0; c0 < nch; c0 += 32) {
-            const int c = c0 + lane;
-            int32_t *cell = w.cnt + (int64_t)(sc.chunk0 + c) * geo.nbands + b;
-            const int v = c < nch ? *cell : 0;
-            int inc = v;
+        for (int c0 = 0; c0 < nch; c0 += 32 * kScanLoads) {
+            int v[kScanLoads];
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, inc, d);
-                if (lane >= d) inc += t;
+            for (int k = 0; k < kScanLoads; ++k) {
+                const int c = c0 + 32 * k + lane;
+                v[k] = c < nch ? col[(int64_t)c * geo.nbands] : 0;
             }
-            if (c < nch) *cell = run + inc - v;
-            run += __shfl_sync(0xffffffffu, inc, 31);
+#pragma unroll
+            for (int k = 0; k < kScanLoads; ++k) {
+                const int c = c0 + 32 * k + lane;
+                int inc = v[k];
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, inc, d);
+                    if (lane >= d) inc += t;
+                }
+                if (c < nch) col[(int64_t)c * geo.nbands] = run + inc - v[k];
+                run += __shfl_sync(0xffffffffu, inc, 31);
+            }
         }
         if (lane == 0) total[b] = run;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int32_t *off = w.band_off + (int64_t)s * (geo.nbands + 1);
-        int acc = 0;
-        for (int b = 0; b < geo.nbands; ++b) {
-            off[b] = acc;
-            acc += total[b];
+    if (warp == 0) {  // the bands' starts: exclusive over the bands, two per lane (nbands <= 64)
+        const int ba = 2 * lane, bb = ba + 1;
+        const int ta = ba < geo.nbands ? total[ba] : 0, tb = bb < geo.nbands ? total[bb] : 0;
+        int inc = ta + tb;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += t;
         }
-        off[geo.nbands] = acc;
-        if (acc > sc.pair_cap) latch(w.status, OSOG_ERR_BIN_OVERFLOW);
+        int32_t *off = w.band_off + (int64_t)s * (geo.nbands + 1);
+        if (ba < geo.nbands) off[ba] = inc - ta - tb;
+        if (bb < geo.nbands) off[bb] = inc - tb;
+        const int all = __shfl_sync(0xffffffffu, inc, 31);
+        if (lane == 0) {
+            off[geo.nbands] = all;
+            if (all > sc.pair_cap) latch(w.status, OSOG_ERR_BIN_OVERFLOW);
+        }
     }
-    if (threadIdx.x == 0) w.colrange[s] = column_hull(gd, s, geo);
 }
 
 __global__ void __launch_bounds__(kChunk)
