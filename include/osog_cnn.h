@@ -73,9 +73,11 @@ int osog_conv2d_backward_filter(const osog_conv_shape_t *shape, const uint16_t *
  * MMA (mma.sync).  Both compute the same products in BF16 with FP32
  * accumulation; summation order inside the tensor core differs.  With
  * tcgen05 selected, forward convolutions whose reduction R S C is below 128
- * and filter gradients with fewer than 128 output channels still run on
- * the warp-level MMA (faster there).  The switch also covers
- * osog_conv2d_backward_filter. */
+ * and filter gradients with fewer than 128 output channels and fewer than
+ * 64 filter entries R S C still run on the warp-level MMA (faster there);
+ * filter gradients with fewer than 128 output channels but at least 64
+ * filter entries take the filter entries as the tensor cores' rows.  The
+ * switch also covers osog_conv2d_backward_filter. */
 void osog_conv_use_tcgen05(int32_t enable);
 
 /* Synchronise `stream` and report a latched device error of the

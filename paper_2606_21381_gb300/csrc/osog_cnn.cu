@@ -669,7 +669,11 @@ __global__ void __launch_bounds__(UNT) k_conv_umma(const __grid_constant__ Args 
 // the pixels as the reduction, in chunks of kSplitPixels per CTA (grid.z)
 // whose partial tiles are summed in chunk order.  Both operands are copied
 // from NHWC rows as 16-byte vectors (8 channels of one pixel) into the
-// MN-major layout.
+// MN-major layout.  SWAP (fewer than 128 output channels): the roles are
+// exchanged, the filter entries are the 128 rows and the output channels
+// the BNU columns (K rounded up to 16), so that few output channels do not
+// pad the rows; the partial tiles are written in the same [k][j] layout.
+template <bool SWAP>
 __global__ void __launch_bounds__(UNT) k_wgrad_umma(const __grid_constant__ Args a, int BNU) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int bstage = BNU * UBK * 2;
@@ -702,9 +706,12 @@ __global__ void __launch_bounds__(UNT) k_wgrad_umma(const __grid_constant__ Args
     // consecutive threads read consecutive channel groups of one pixel.
     constexpr int NV = UBK * 16 / UNT;  // pixels per thread and slice
     const int grp = tid & 15, kq = tid >> 4;
-    const int m = m0 + grp * 8;
-    const int j = n0 + grp * 8;
+    // m: this thread's 8 output channels (of dY); j: its 8 filter entries
+    // (one tap of X); the row group is A's, the column group B's
+    const int m = SWAP ? n0 + grp * 8 : m0 + grp * 8;
+    const int j = SWAP ? m0 + grp * 8 : n0 + grp * 8;
     const bool jok = j < a.Ncols;
+    const bool bcol = !SWAP || grp * 8 < BNU;  // B columns past BNU are not in the stage
     int tr = 0, ts = 0, tc = 0;
     if (jok) {
         const int rs = j / g.C;
@@ -728,15 +735,15 @@ __global__ void __launch_bounds__(UNT) k_wgrad_umma(const __grid_constant__ Args
         for (int i = 0; i < NV; ++i) {
             const int k = kq + 16 * i, pix = p0 + k;
             const bool live = pix < pend;
-            const __nv_bfloat16 *sa = live && m < a.M ? a.x + (size_t)pix * g.K + m : nullptr;
-            cp16(A + canon_mn(grp * 8, k), sa, a.x);
-            const __nv_bfloat16 *sb = nullptr;
+            const __nv_bfloat16 *sy = live && m < a.M ? a.x + (size_t)pix * g.K + m : nullptr;
+            const __nv_bfloat16 *sx = nullptr;
             if (live && jok) {
                 const int h = pp[i] * g.stride + tr - g.pad, w = pq[i] * g.stride + ts - g.pad;
                 if (h >= 0 && h < g.H && w >= 0 && w < g.W)
-                    sb = a.w + (((size_t)pn[i] * g.H + h) * g.W + w) * g.C + tc;
+                    sx = a.w + (((size_t)pn[i] * g.H + h) * g.W + w) * g.C + tc;
             }
-            cp16(B + canon_mn(grp * 8, k), sb, a.w);
+            cp16(A + canon_mn(grp * 8, k), SWAP ? sx : sy, a.x);
+            if (bcol) cp16(B + canon_mn(grp * 8, k), SWAP ? sy : sx, a.w);
             // next slice: UBK pixels further
             pq[i] += UBK;
             while (pq[i] >= g.Q) {
@@ -796,7 +803,7 @@ __global__ void __launch_bounds__(UNT) k_wgrad_umma(const __grid_constant__ Args
     if (!ok && lane == 0) atomicExch(&g_cnn_status, 1);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const int quarter = warp & 3, group = warp >> 2;
-    const int row = m0 + quarter * 32 + lane;  // output channel
+    const int row = m0 + quarter * 32 + lane;  // output channel (SWAP: filter entry)
     float *part = a.part + (size_t)blockIdx.z * a.M * a.Ncols;
     for (int c0 = group * 32; c0 < BNU; c0 += 32 * (UNT / 128)) {
         uint32_t v[32];
@@ -811,7 +818,16 @@ __global__ void __launch_bounds__(UNT) k_wgrad_umma(const __grid_constant__ Args
               "=r"(v[31])
             : "r"(taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0));
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        if (row < a.M) {
+        if constexpr (SWAP) {  // lanes hold consecutive filter entries: coalesced per column
+            if (row < a.Ncols) {
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int k = n0 + c0 + jj;
+                    if (c0 + jj < BNU && k < a.M)
+                        part[(size_t)k * a.Ncols + row] = nk ? __uint_as_float(v[jj]) : 0.f;
+                }
+            }
+        } else if (row < a.M) {
 #pragma unroll
             for (int j = 0; j < 32; j += 4) {
                 const int col = n0 + c0 + j;
@@ -848,7 +864,10 @@ cudaError_t umma_prepare() {
             r = cudaFuncSetAttribute(k_conv_umma<kDgrad2>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
         if (r == cudaSuccess)
-            r = cudaFuncSetAttribute(k_wgrad_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            r = cudaFuncSetAttribute(k_wgrad_umma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kUmmaSmem);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k_wgrad_umma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      kUmmaSmem);
         return r;
     }();
@@ -867,12 +886,47 @@ cudaError_t launch_umma(const Args &a, cudaStream_t st) {
 
 // Sum of the filter-gradient partial tiles over the pixel splits, in split
 // order.
-__global__ void k_sum_splits(const float *part, int splits, int64_t count, float *out) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
+// out[i] = sum over z of part[z][i] for i < count, in a fixed order: a CTA
+// takes 32 consecutive outputs (one per lane); warp w adds the splits z = w,
+// w + kSumWarps, ... in ascending order (four loads in flight per lane), and
+// warp 0 adds the warps' sums in warp order.  Coalesced 128-byte loads and
+// count / 32 CTAs, where one thread per output walked every split alone.
+constexpr int kSumWarps = 16;
+
+__global__ void __launch_bounds__(32 * kSumWarps)
+k_sum_splits(const float *part, int splits, int64_t count, float *out) {
+    __shared__ float red[kSumWarps][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 32 + lane;
     float s = 0.f;
-    for (int z = 0; z < splits; ++z) s += part[(int64_t)z * count + i];
-    out[i] = s;
+    if (i < count) {
+        int z = warp;
+        for (; z + 3 * kSumWarps < splits; z += 4 * kSumWarps) {
+            const float a0 = part[(int64_t)z * count + i];
+            const float a1 = part[(int64_t)(z + kSumWarps) * count + i];
+            const float a2 = part[(int64_t)(z + 2 * kSumWarps) * count + i];
+            const float a3 = part[(int64_t)(z + 3 * kSumWarps) * count + i];
+            s += a0;
+            s += a1;
+            s += a2;
+            s += a3;
+        }
+        for (; z < splits; z += kSumWarps) s += part[(int64_t)z * count + i];
+    }
+    red[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && i < count) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < kSumWarps; ++w) t += red[w][lane];
+        out[i] = t;
+    }
+}
+
+// Launch of k_sum_splits over count outputs.
+static void sum_splits(const float *part, int splits, int64_t count, float *out, cudaStream_t st) {
+    if (count > 0)
+        k_sum_splits<<<(unsigned)((count + 31) / 32), 32 * kSumWarps, 0, st>>>(part, splits, count, out);
 }
 
 // Partial bias gradients for K dividing 256: CTA c sums the pixels
@@ -971,6 +1025,9 @@ int status_of(cudaError_t e) { return e == cudaSuccess ? OSOG_OK : OSOG_ERR_CUDA
 // Engine of the forward and data-gradient convolutions: the tcgen05 kernel
 // (1, default) or the warp-level MMA kernel (0).
 int g_use_tcgen05 = 1;
+// Filter gradients with fewer than 128 output channels on tcgen05 with the
+// roles exchanged (k_wgrad_umma<true>); 0 keeps them on the warp-level MMA.
+int g_wgrad_swap = 1;
 
 const __nv_bfloat16 *bf(const uint16_t *p) { return reinterpret_cast<const __nv_bfloat16 *>(p); }
 __nv_bfloat16 *bf(uint16_t *p) { return reinterpret_cast<__nv_bfloat16 *>(p); }
@@ -1082,24 +1139,32 @@ int osog_conv2d_backward_filter(const osog_conv_shape_t *shape, const uint16_t *
     a.Ncols = g.R * g.S * g.C;
     a.Kred = g.N * g.P * g.Q;
     const int splits = splits_of(g);
-    // tcgen05 for 128 or more output channels (fewer would pad the 128 rows)
+    // tcgen05: output channels as the 128 rows when there are at least 128,
+    // else, with at least 64 filter entries, the filter entries as the rows
+    // and the output channels (rounded up to 16) as the columns
     if (g_use_tcgen05 && a.M >= UM) {
         const cudaError_t e = umma_prepare();
         if (e != cudaSuccess) return status_of(e);
         dim3 grid((a.M + UM - 1) / UM, (a.Ncols + 127) / 128, splits);
-        k_wgrad_umma<<<grid, UNT, umma_smem(128), st>>>(a, 128);
+        k_wgrad_umma<false><<<grid, UNT, umma_smem(128), st>>>(a, 128);
+    } else if (g_use_tcgen05 && g_wgrad_swap && a.Ncols >= 64) {
+        const cudaError_t e = umma_prepare();
+        if (e != cudaSuccess) return status_of(e);
+        const int bnu = (a.M + 15) / 16 * 16;
+        dim3 grid((a.Ncols + UM - 1) / UM, 1, splits);
+        k_wgrad_umma<true><<<grid, UNT, umma_smem(bnu), st>>>(a, bnu);
     } else {
         dim3 grid((a.M + BM - 1) / BM, (a.Ncols + BN - 1) / BN, splits);
         k_conv_gemm<kWgrad><<<grid, NT, 0, st>>>(a);
     }
     const int64_t count = (int64_t)a.M * a.Ncols;
-    k_sum_splits<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(a.part, splits, count, dw);
+    sum_splits(a.part, splits, count, dw, st);
     const int64_t pixels = (int64_t)g.N * g.P * g.Q;
     if (256 % g.K == 0) {
         float *bpart = a.part + (size_t)splits * count;
         const int chunks = bias_chunks(g);
         k_bias_partial<<<chunks, 256, 0, st>>>(bf(dy), pixels, g.K, bpart);
-        k_sum_splits<<<(unsigned)((g.K + 255) / 256), 256, 0, st>>>(bpart, chunks, g.K, dbias);
+        sum_splits(bpart, chunks, g.K, dbias, st);
     } else {
         k_bias_grad<<<g.K, 256, 0, st>>>(bf(dy), pixels, g.K, dbias);
     }

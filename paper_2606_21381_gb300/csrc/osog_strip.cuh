@@ -274,9 +274,10 @@ __host__ __device__ constexpr size_t raster_smem() {
 // records; prect, when not null, the entries' rectangles with their kinds,
 // else they are gathered by id), added into the accumulators that slot(row, x) addresses (zeroed
 // by the caller; kAccPhase: uint2, kAccOpd: two int64).  Each warp works on
-// its own groups of 32 list entries (the first NT / 32 groups in warp
-// order, the rest handed out by a shared counter as warps finish), with no
-// CTA barrier until the end:
+// its own groups of 32 list entries (fewer when the list is short, so that
+// every warp gets a group; the first NT / 32 groups in warp order, the rest
+// handed out by a shared counter as warps finish), with no CTA barrier
+// until the end:
 //   1. the entries whose rectangle meets the region, compacted with the
 //      ellipsoids first, the region rows each covers, and a warp prefix sum
 //      of those row counts;
@@ -298,12 +299,16 @@ __device__ void raster_region(const Work &w, const int32_t *ids, const Rect *pre
     RowItem *items = reinterpret_cast<RowItem *>(scratch) + warp * 32;
     int *next = reinterpret_cast<int *>(reinterpret_cast<RowItem *>(scratch) + NT);
     const int tyl = ty0 + nrows - 1;
-    if (threadIdx.x == 0) *next = lo + NT;
+    // group size: 32 entries, or fewer for a short list so that every warp
+    // gets some (a small scene's band holds a few dozen entries)
+    constexpr int NW = NT / 32;
+    const int gsz = min(32, max(1, (hi - lo + NW - 1) / NW));
+    if (threadIdx.x == 0) *next = lo + NW * gsz;
     __syncthreads();
-    int base = lo + warp * 32;
+    int base = lo + warp * gsz;
     while (base < hi) {
         int nb = 0;
-        if (lane == 0) nb = atomicAdd(next, 32);
+        if (lane == 0) nb = atomicAdd(next, gsz);
         // 1. the group's entries that meet the region, compacted through the
         //    warp's item slots with the ellipsoids first (so that most waves
         //    below build items of one kind)
@@ -311,7 +316,7 @@ __device__ void raster_region(const Work &w, const int32_t *ids, const Rect *pre
         {
             const int i = base + lane;
             bool ell = false;
-            if (i < hi) {
+            if (lane < gsz && i < hi) {
                 id = ids[i];
                 Rect q;
                 int kind = 0;
