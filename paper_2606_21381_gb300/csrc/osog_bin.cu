@@ -268,65 +268,77 @@ k_bin_count(const float *__restrict__ soa, int64_t ld, const __grid_constant__ G
     }
 }
 
-// Scan of one scene's band counts (CTA s): for every band (two per warp at
-// 64 bands) the exclusive prefix over the scene's chunks, in place; then
-// the bands' starts and the scene's column hull.  Each lane keeps up to
-// kScanLoads chunk counts of a band in registers, all loaded before the
-// warp scans them, so a scene of many chunks pays one load latency per
-// kScanLoads * 32 chunks instead of one per 32.
-constexpr int kScanLoads = 8;
+// Scan of one scene's band counts (CTA s): for every band the exclusive
+// prefix over the scene's chunks, in place; then the bands' starts and the
+// scene's column hull.  The counts are laid out [chunk][band], so a band's
+// column is strided: the CTA moves tiles of kScanTile chunks x all bands
+// between global memory and shared memory with coalesced accesses (one
+// 128-byte line per 32 counts instead of one line per count) and scans the
+// columns in shared memory, two bands per warp, one or two chunks per lane,
+// carrying each band's running total from tile to tile.
+constexpr int kScanTile = 64;
 
 __global__ void __launch_bounds__(1024)
 k_bin_scan(const __grid_constant__ GroupDev gd, Geometry geo, Work w) {
-    __shared__ int total[kMaxBands];
+    __shared__ int tile[kScanTile][kMaxBands + 1];  // one pad word: conflict-free columns
+    __shared__ int run[kMaxBands];
     pdl_enter();
     const int s = blockIdx.x;
     const SceneDev &sc = gd.sc[s];
     const int nch = (s + 1 < gd.S ? gd.sc[s + 1].chunk0 : gd.nchunks) - sc.chunk0;
+    const int nb = geo.nbands;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 992)  // lane 0 of the last warp, the one with the fewest bands
+    if (threadIdx.x == 992)  // lane 0 of the last warp
         w.colrange[s] = column_hull(gd, s, geo);
-    for (int b = warp; b < geo.nbands; b += 32) {
-        int32_t *col = w.cnt + (int64_t)sc.chunk0 * geo.nbands + b;  // chunk c at c * nbands
-        int run = 0;
-        for (int c0 = 0; c0 < nch; c0 += 32 * kScanLoads) {
-            int v[kScanLoads];
+    if ((int)threadIdx.x < nb) run[threadIdx.x] = 0;
+    int32_t *cnt = w.cnt + (int64_t)sc.chunk0 * nb;  // [nch][nb]
+    for (int t0 = 0; t0 < nch; t0 += kScanTile) {
+        const int nt = min(kScanTile, nch - t0);
+        for (int e = threadIdx.x; e < nt * nb; e += 1024)
+            tile[e / nb][e % nb] = cnt[(int64_t)t0 * nb + e];
+        __syncthreads();
+        for (int b = warp; b < nb; b += 32) {
+            const int v0 = lane < nt ? tile[lane][b] : 0;
+            const int v1 = lane + 32 < nt ? tile[lane + 32][b] : 0;
+            int i0 = v0, i1 = v1;
 #pragma unroll
-            for (int k = 0; k < kScanLoads; ++k) {
-                const int c = c0 + 32 * k + lane;
-                v[k] = c < nch ? col[(int64_t)c * geo.nbands] : 0;
-            }
-#pragma unroll
-            for (int k = 0; k < kScanLoads; ++k) {
-                const int c = c0 + 32 * k + lane;
-                int inc = v[k];
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const int t = __shfl_up_sync(0xffffffffu, inc, d);
-                    if (lane >= d) inc += t;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, i0, d);
+                const int u = __shfl_up_sync(0xffffffffu, i1, d);
+                if (lane >= d) {
+                    i0 += t;
+                    i1 += u;
                 }
-                if (c < nch) col[(int64_t)c * geo.nbands] = run + inc - v[k];
-                run += __shfl_sync(0xffffffffu, inc, 31);
             }
+            const int tot0 = __shfl_sync(0xffffffffu, i0, 31);
+            const int tot1 = __shfl_sync(0xffffffffu, i1, 31);
+            const int base = run[b];
+            if (lane < nt) tile[lane][b] = base + i0 - v0;
+            if (lane + 32 < nt) tile[lane + 32][b] = base + tot0 + i1 - v1;
+            __syncwarp();
+            if (lane == 0) run[b] = base + tot0 + tot1;
         }
-        if (lane == 0) total[b] = run;
+        __syncthreads();
+        for (int e = threadIdx.x; e < nt * nb; e += 1024)
+            cnt[(int64_t)t0 * nb + e] = tile[e / nb][e % nb];
+        __syncthreads();  // the tile is written back before the next one is loaded
     }
-    __syncthreads();
+    __syncthreads();  // (a scene without chunks: run[] initialised)
     if (warp == 0) {  // the bands' starts: exclusive over the bands, two per lane (nbands <= 64)
         const int ba = 2 * lane, bb = ba + 1;
-        const int ta = ba < geo.nbands ? total[ba] : 0, tb = bb < geo.nbands ? total[bb] : 0;
+        const int ta = ba < nb ? run[ba] : 0, tb = bb < nb ? run[bb] : 0;
         int inc = ta + tb;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int t = __shfl_up_sync(0xffffffffu, inc, d);
             if (lane >= d) inc += t;
         }
-        int32_t *off = w.band_off + (int64_t)s * (geo.nbands + 1);
-        if (ba < geo.nbands) off[ba] = inc - ta - tb;
-        if (bb < geo.nbands) off[bb] = inc - tb;
+        int32_t *off = w.band_off + (int64_t)s * (nb + 1);
+        if (ba < nb) off[ba] = inc - ta - tb;
+        if (bb < nb) off[bb] = inc - tb;
         const int all = __shfl_sync(0xffffffffu, inc, 31);
         if (lane == 0) {
-            off[geo.nbands] = all;
+            off[nb] = all;
             if (all > sc.pair_cap) latch(w.status, OSOG_ERR_BIN_OVERFLOW);
         }
     }
